@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: ion-steps/s of the FMM + cyclotronic push on a 10,000-ion
+spheroidal Penning-trap crystal (aspect 0.3, rigid-rotor density, laser
+cooling on: two axial beams and one planar beam), order p = 10, dt = 1 ns.
+
+One benchmark step is one time step of the whole path (drift + root cube,
+octree, upward pass, M2L/L2L, L2P + P2P, kick with photon recoils + drift).
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream, with a 512 MiB write between steps to flush the
+129 MB L2 (the inputs are smaller than L2).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|tf32x3|fp64] [--p P]
+
+--impl reference times the FP64 CPU oracle (direct O(N^2) Coulomb sum and
+the literal step) on the host cores, one oracle step per benchmark step.
+Under torchrun each rank runs an independent replica (no collective on the
+data path); the value is the whole job's ion-steps over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "ion-steps/s (FMM+push), mixed vs FP64 at <=1e-6 force err; p50/p99 latency"
+UNIT = "ion-steps/s"
+WORKLOAD = "spheroid aspect 0.3, N=10000, cooling on, p=10, leaf<=32, dt=1ns"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal per-GPU rates used where no measured peak exists (GB300, 152 SMs):
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flop x max SM clock
+FP64_TFLOPS = 1.25                                # nominal dense FP64
+TF32_OVER_BF16 = 1.1 / 2.25                       # nominal dense TF32 / BF16 rate
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def launches_per_step(depth: int) -> int:
+    # drift+cube, keys, 3 scan, scatter, 3 scan, leaf gather, near_far, kick
+    k = 11
+    if depth >= 2:
+        k += 1 + (depth - 2) + (depth - 1)   # P2M, M2M levels, M2L levels
+    return k
+
+
+def run_cpu_baseline(cr, budget_s=12.0, max_steps=30):
+    import oracle
+    pos, vel, q, tr = cr["pos"], cr["vel"], cr["q"], cr["trap"]
+    beams = cr["beams"]
+    t0 = time.perf_counter()
+    steps = 0
+    p, v = pos, vel
+    while steps < max_steps and time.perf_counter() - t0 < budget_s:
+        p, v = oracle.step(p, v, q, tr, cr["dt"], 1, t0=steps * cr["dt"], step0=steps,
+                           beams=beams, gamma0=W.GAMMA0, seed=1, laser_on=True)
+        steps += 1
+    el = time.perf_counter() - t0
+    n = len(q)
+    return {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} oracle steps of the full N={n} workload (direct O(N^2) FP64 sum, "
+                      f"literal step), {el:.1f} s"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    cr = W.crystal_spheroid_10k()
+    pos, vel, q, tr, beams = cr["pos"], cr["vel"], cr["q"], cr["trap"], cr["beams"]
+    n = len(q)
+    p, v = pos, vel
+    for s in range(args.warmup):
+        p, v = oracle.step(p, v, q, tr, cr["dt"], 1, t0=s * cr["dt"], step0=s, beams=beams,
+                           gamma0=W.GAMMA0, seed=1, laser_on=True)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        k = args.warmup + s
+        p, v = oracle.step(p, v, q, tr, cr["dt"], 1, t0=k * cr["dt"], step0=k, beams=beams,
+                           gamma0=W.GAMMA0, seed=1, laser_on=True)
+    el = time.perf_counter() - t0
+    val = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of the full N={n} workload"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
+    """K single steps, each timed with CUDA events, L2 flushed in between."""
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    phases = []
+    for k in range(K):
+        flush()
+        ev[k][0].record(stream)
+        plan.step_async(st, trap, laser, dt, 1)
+        ev[k][1].record(stream)
+        if profile:
+            ev[k][1].synchronize()
+            phases.append(plan.phase_times())
+    torch.cuda.synchronize()
+    plan.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, phases
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "fp64"])
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import paper_2405_13973_gb300 as pt
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    cr = W.crystal_spheroid_10k(seed=2 + rank)
+    n = len(cr["q"])
+    trap = pt.make_trap(cr["trap"])
+    laser = pt.make_laser(cr["beams"], seed=1 + rank, gamma0=W.GAMMA0)
+    dt = cr["dt"]
+    flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    # force error of this precision at the initial state vs the FP64 GPU direct sum
+    st0 = pt.State.from_numpy(cr["pos"], cr["vel"], cr["q"])
+    pos0 = torch.stack([st0.x, st0.y, st0.z]).contiguous()
+    Ed, _ = pt.direct(pos0, st0.q, want_phi=False)
+
+    def force_err(plan):
+        E, _ = plan.forces(pos0, st0.q, want_phi=False)
+        return float(torch.sqrt(((E - Ed) ** 2).sum() / (Ed ** 2).sum()))
+
+    plan = pt.Plan(n, p=args.p, leaf_max=32, depth=-1, precision=args.precision)
+    ferr = force_err(plan)
+    st = pt.State.from_numpy(cr["pos"], cr["vel"], cr["q"])
+    plan.profile(True)
+    plan.step(st, trap, laser, dt, args.warmup)           # warm-up; chooses the depth
+    depth = plan.last_depth
+    stats = plan.stats()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms, phases = timed_steps(pt, torch, plan, st, trap, laser, dt, args.steps, flush)
+    t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(ms))
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms * 1e-3)
+
+    # phase breakdown and the roofline of the dominant kernel
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
+    P = (args.p + 1) ** 2
+    m2l_flops = 2.0 * P * P * (stats["m2l_pairs"] + stats["l2l_shifts"])
+    p2p_flops = 20.0 * stats["p2p_pairs"]
+    pk, pk_src = peaks()
+    dom = max(ph, key=ph.get)
+    roof = {"kernel": dom, "phases_ms": ph}
+    if dom == "m2l":
+        achieved = m2l_flops / (ph["m2l"] * 1e-3) / 1e12
+        if args.precision == "tf32x3":
+            peak = pk["bf16_tflops"] * TF32_OVER_BF16 / 3.0
+            roof.update(bound="tensor", peak_note=f"TF32 rate / 3 (3 products per FP32-accurate "
+                                                  f"product), from {pk_src} bf16 x nominal ratio")
+        elif args.precision == "fp32":
+            peak = FP32_ALU_TFLOPS
+            roof.update(bound="alu", peak_note="152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
+        else:
+            peak = FP64_TFLOPS
+            roof.update(bound="alu", peak_note="nominal dense FP64")
+        roof.update(achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    work=f"2 P^2 x ({stats['m2l_pairs']} M2L + {stats['l2l_shifts']} L2L) flop")
+    elif dom == "near_far":
+        achieved = p2p_flops / (ph["near_far"] * 1e-3) / 1e12
+        peak = FP32_ALU_TFLOPS if args.precision != "fp64" else FP64_TFLOPS
+        roof.update(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                    frac=achieved / peak, work=f"20 flop x {stats['p2p_pairs']} P2P pairs")
+    else:
+        # HBM-bound phase: algorithmic bytes of the state pass (x, v read+write)
+        byts = 96.0 * n
+        achieved = byts / (ph[dom] * 1e-3) / 1e9
+        roof.update(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
+                    frac=achieved / pk["hbm_gbs"], work="96 B per ion")
+    roof["traffic"] = None
+    roof["peak_source"] = pk_src
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3",
+                                                             "fp64": "f64"}[args.precision],
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": args.precision, "p": args.p,
+                      "depth": depth, "n": n, "l2": "flushed between timed steps (512 MiB write)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "force_err": ferr, "stats": stats, "roofline": roof, "clocks": clk,
+           "gpu_launches": launches_per_step(depth) * args.steps,
+           "wall_s_timed_region": t_wall}
+
+    # the plain FP64 GPU path beside it (same workload, fewer steps)
+    if rank == 0 and args.precision != "fp64" and args.fp64_steps > 0:
+        plan64 = pt.Plan(n, p=args.p, leaf_max=32, depth=-1, precision="fp64")
+        e64 = force_err(plan64)
+        st64 = pt.State.from_numpy(cr["pos"], cr["vel"], cr["q"])
+        plan64.step(st64, trap, laser, dt, 3)
+        ms64, _ = timed_steps(pt, torch, plan64, st64, trap, laser, dt, args.fp64_steps, flush,
+                              profile=False)
+        out["fp64_path"] = {"value": n * args.fp64_steps / (sum(ms64) * 1e-3),
+                            "ms_per_step": sum(ms64) / args.fp64_steps, "force_err": e64,
+                            "depth": plan64.last_depth}
+        plan64.close()
+
+    # end to end through the public API: host state in, one step, host state out
+    if not args.no_e2e:
+        host = {k: torch.empty(n, dtype=torch.float64).pin_memory()
+                for k in ("x", "y", "z", "vx", "vy", "vz")}
+        for k, a in zip(host, (cr["pos"][:, 0], cr["pos"][:, 1], cr["pos"][:, 2],
+                               cr["vel"][:, 0], cr["vel"][:, 1], cr["vel"][:, 2])):
+            host[k].copy_(torch.from_numpy(np.ascontiguousarray(a)))
+        ste = pt.State.from_numpy(cr["pos"], cr["vel"], cr["q"])
+        plan.profile(False)
+        plan.step(ste, trap, laser, dt, 1)   # recaptures the step graph without timing events
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for k in host:
+                getattr(ste, k).copy_(host[k], non_blocking=True)
+            plan.step(ste, trap, laser, dt, 1)
+            for k in host:
+                host[k].copy_(getattr(ste, k), non_blocking=True)
+            torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        out["e2e"] = {"value": world * n * args.steps / el, "unit": UNIT,
+                      "h2d_bytes_per_step": 48 * n, "d2h_bytes_per_step": 48 * n}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = run_cpu_baseline(cr)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,257 @@
+/*
+ * penning.h -- C ABI of libpenning: the FMM Coulomb field of a 3D Penning-trap
+ * ion crystal fused with the cyclotronic push, for NVIDIA GB300 (sm_103a).
+ *
+ * Method: Zaris, Johnson, Shankar, Bollinger & Parker, "Numerical Simulations
+ * of 3D Ion Crystal Dynamics in a Penning Trap using the Fast Multipole
+ * Method" (arXiv:2405.13973).
+ *
+ * Conventions shared by every call:
+ *   - SI units.  Positions in m, velocities in m/s, charges in C, fields in
+ *     V/m, potentials in V, times in s, angular frequencies in rad/s.
+ *   - Arrays of 3-vectors are structure-of-arrays: x[0..n), y[0..n), z[0..n)
+ *     stored back to back in one buffer of 3n doubles ("SoA 3n").
+ *   - Pointers documented "device" must be CUDA device (or managed) memory
+ *     of the current device; "host" pointers are ordinary host memory.  The
+ *     caller owns every buffer it passes; the library never frees them and
+ *     keeps no reference after the call returns (except a plan's captured
+ *     launch graph, which is rebuilt when the pointers change).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *     enqueue their work on it and return; results are valid once the stream
+ *     is synchronised.  Calls that must read device results on the host
+ *     (automatic depth selection, error flags, energies) synchronise the
+ *     stream themselves, as documented per call.
+ *   - Every call returns a pt_status.  No call aborts the process or throws.
+ *     A device-side error (non-finite positions) is latched in the plan and
+ *     returned by the next synchronising call on that plan.
+ *   - Plans are not thread-safe: one host thread at a time per plan.
+ */
+#ifndef PENNING_H
+#define PENNING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+    PT_OK = 0,
+    PT_ERR_ARG = -1,         /* bad argument (null pointer, size, range) */
+    PT_ERR_OOM = -2,         /* device allocation failed */
+    PT_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    PT_ERR_NONFINITE = -4,   /* a position was NaN or infinite */
+    PT_ERR_ESCAPED = -5,     /* reserved: ion outside the plan's domain */
+    PT_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+    PT_ERR_COINCIDENT = -7,  /* reserved: two ions at the same point */
+    PT_ERR_UNSUPPORTED = -8  /* this build or device lacks the feature */
+} pt_status;
+
+/* Arithmetic of the FMM (positions, velocities and the push are FP64 in
+ * every mode).
+ *   PT_FP64          : every FMM stage in FP64 on the CUDA cores.
+ *   PT_MIXED_TF32X3  : P2M/M2M/L2L/L2P/P2P in FP32; M2L on the tensor cores
+ *                      (tcgen05, TF32 hi/lo split, three products, FP32
+ *                      accumulation in tensor memory).
+ *   PT_FP32          : every FMM stage in FP32 on the CUDA cores. */
+typedef enum { PT_FP64 = 0, PT_MIXED_TF32X3 = 1, PT_FP32 = 3 } pt_precision;
+
+/* FMM stages run by fmm_forces (bit mask); default PT_PHASE_ALL. */
+enum { PT_PHASE_NEAR = 1, PT_PHASE_FAR = 2, PT_PHASE_ALL = 3 };
+
+typedef struct fmm_plan_s* fmm_plan;
+
+/* ---------------------------------------------------------------------------
+ * fmm_plan_create -- allocate a plan and its device workspace.
+ * Paper: Sec. 2.3.2 (the octree, upward and downward passes) and Eq.
+ * multipole_error (the order p of the expansions).
+ *   n_max     : largest ion count the plan will see (>= 1).
+ *   p         : expansion order, 2 <= p <= 16; (p+1)^2 real coefficients per
+ *               cell (Eq. FMM_coul truncated at n = p).
+ *   leaf_max  : target mean ion count per non-empty leaf; used when depth = 0.
+ *   depth     : octree depth D (0 <= D <= 8) or -1 for automatic: the
+ *               smallest D whose mean non-empty-leaf occupancy is <= leaf_max,
+ *               chosen from the positions at each fmm_forces call and at the
+ *               start of each pt_step call (this synchronises the stream).
+ *   precision : a pt_precision value.
+ *   out       : receives the plan (host pointer to an fmm_plan).
+ * Uses the current CUDA device.  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA,
+ * PT_ERR_UNSUPPORTED (tensor-core mode on a device that is not sm_103). */
+int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision, fmm_plan* out);
+
+/* Free a plan and its workspace (NULL is accepted).  Synchronises the device. */
+int fmm_plan_destroy(fmm_plan plan);
+
+/* Restrict the stages of fmm_forces to PT_PHASE_NEAR (direct sum over
+ * adjacent leaves, Sec. 2.3.2), PT_PHASE_FAR (multipole/local expansions) or
+ * both (default).  For testing each stage against its definition. */
+int fmm_plan_set_phases(fmm_plan plan, int phases);
+
+/* Depth used by the last fmm_forces / pt_step call on this plan (or -1). */
+int fmm_plan_last_depth(fmm_plan plan);
+
+/* ---------------------------------------------------------------------------
+ * fmm_forces -- Coulomb field (and potential) on every ion by the FMM.
+ * Paper: Eq. hamiltonian (the pair sum it approximates: the force on ion i
+ * is q_i E_i with E_i = k_e sum_{j!=i} q_j (x_i - x_j)/|x_i - x_j|^3),
+ * Sec. 2.3.1-2.3.2 (ME, LE, upward and downward passes).
+ *   n    : number of ions, 1 <= n <= n_max.
+ *   pos  : device, SoA 3n doubles (m).
+ *   q    : device, n doubles (C).
+ *   E    : device, SoA 3n doubles, written (V/m).  Coulomb part only.
+ *   phi  : device, n doubles (V) or NULL.
+ * Asynchronous unless depth is automatic.  Errors: PT_ERR_ARG, PT_ERR_CUDA,
+ * PT_ERR_NONFINITE (latched from an earlier call). */
+int fmm_forces(fmm_plan plan, int64_t n, const double* pos, const double* q, double* E,
+               double* phi, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * fmm_direct -- the same field by the O(N^2) pair sum in FP64 on the GPU.
+ * Paper: Eq. hamiltonian; the "direct" mode of Sec. 3.  Reference for error
+ * measurement at sizes the CPU cannot reach.  Arguments as fmm_forces.
+ * Asynchronous.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int fmm_direct(int64_t n, const double* pos, const double* q, double* E, double* phi,
+               void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Trap, beams, laser, state (SI).  Paper: Eqs. pot_trap, pot_wall (k_z =
+ * m omega_z^2 / q), B along +z (omega_c = q B / m), Eq. scattering_rate. */
+typedef struct {
+    double B;        /* axial magnetic field (T), along +z */
+    double omega_z;  /* axial trap frequency (rad/s) */
+    double omega_r;  /* rotating-wall frequency (rad/s) */
+    double delta;    /* rotating-wall strength (dimensionless) */
+    double mass;     /* ion mass (kg), the same for every ion */
+    double charge;   /* reference charge (C) defining k_z = m omega_z^2 / q */
+} pt_trap;
+
+typedef struct {
+    double s0;        /* peak saturation parameter S_0 */
+    double detuning;  /* Delta_l (rad/s) */
+    double kx, ky, kz;/* wave vector k_l (1/m) */
+    double waist_y;   /* w_y (m), non-uniform beams */
+    double waist_z;   /* w_z (m), non-uniform beams */
+    double offset_d;  /* beam centre y = d (m), non-uniform beams */
+    int32_t uniform;  /* 1: S = S0 everywhere; 0: S0 exp(-(y-d)^2/w_y^2 - z^2/w_z^2) */
+    int32_t pad_;
+} pt_beam;
+
+#define PT_MAX_BEAMS 8
+typedef struct {
+    int32_t n_beams;  /* 0..PT_MAX_BEAMS */
+    int32_t enabled;  /* 0: no photon kicks */
+    uint64_t seed;    /* Philox4x32-10 key */
+    double gamma0;    /* natural linewidth (rad/s), 2 pi 18 MHz for Be+ */
+    pt_beam beam[PT_MAX_BEAMS];
+} pt_laser;
+
+typedef struct {
+    int64_t n;        /* ion count */
+    double t;         /* time (s); advanced by pt_step */
+    int64_t step;     /* global step index (keys the photon random numbers) */
+    double* x;        /* device, n doubles each */
+    double* y;
+    double* z;
+    double* vx;
+    double* vy;
+    double* vz;
+    double* q;        /* device, n charges (C) */
+} pt_state;
+
+/* ---------------------------------------------------------------------------
+ * pt_step -- advance the crystal by n_steps cyclotronic steps.
+ * Paper: Eq. time_ev2, U = U0(dt/2) Ukick(t + dt/2; dt) U0(dt/2), with U0 the
+ * exact gyration of Eq. U0 (read for B along +z: the velocity turns
+ * clockwise), Ukick of Eq. velocity_kick (Coulomb by the FMM plus trap and
+ * wall fields at t + dt/2) and the photon kicks of Eq. laser_kick with
+ * Poisson counts of mean gamma_l(x, v) dt (Eq. scattering_rate) at the
+ * midpoint state.  Photon random numbers: Philox4x32-10 with key = seed and
+ * counter = (ion, beam | slot << 8, step lo, step hi); slot 0 draws the
+ * Poisson uniform, slots 1.. the sphere points (Marsaglia 1972).
+ *   state : host struct; its device arrays are updated in place and its
+ *           t and step fields advanced on return.
+ *   trap, laser : host structs (laser may be NULL = no cooling).
+ *   dt    : time step (s) > 0.   n_steps >= 0.
+ * Synchronises the stream before returning (status of the whole run).
+ * Errors: PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_NONFINITE. */
+int pt_step(fmm_plan plan, pt_state* state, const pt_trap* trap, const pt_laser* laser,
+            double dt, int64_t n_steps, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pt_step_async -- as pt_step but without synchronising: the steps are
+ * enqueued on `stream` and the call returns (state->t, state->step are
+ * advanced on return).  Needs a fixed octree depth: the plan's `depth`, or,
+ * for an automatic plan, the depth chosen by its last synchronising call
+ * (PT_ERR_ARG if there was none).  Device errors are latched and returned by
+ * pt_sync or the next synchronising call.  Consecutive asynchronous calls on
+ * one plan must use one stream.  Paper: Eq. time_ev2 as for pt_step. */
+int pt_step_async(fmm_plan plan, pt_state* state, const pt_trap* trap, const pt_laser* laser,
+                  double dt, int64_t n_steps, void* stream);
+
+/* Synchronise `stream` and return the plan's latched device error, if any. */
+int pt_sync(fmm_plan plan, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper).
+ * fmm_plan_profile: enable (1) or disable (0) CUDA-event timing of the phases
+ *   of every time step (drift + root cube, tree, upward pass, M2L + L2L,
+ *   L2P + P2P, kick + drift).  Takes effect at the next step.
+ * fmm_plan_phase_times: device milliseconds of those six phases in the last
+ *   executed step (host, 6 doubles).  The step must have completed.
+ * fmm_plan_stats: interaction counts of the last octree (host, 8 int64):
+ *   {n, depth, leaves, cells at levels >= 2, M2L translations (target,
+ *   source) with a non-empty source, P2P pair interactions (ordered, i != j),
+ *   L2L shifts, M2M shifts}.  Synchronises the stream. */
+int fmm_plan_profile(fmm_plan plan, int enable);
+int fmm_plan_phase_times(fmm_plan plan, double* ms);
+int fmm_plan_stats(fmm_plan plan, int64_t* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pt_laser_kicks -- the photon counts and recoil velocity change of one step
+ * for a given midpoint state, without applying them.  Paper: Eqs.
+ * scattering_rate and laser_kick.  Bit-reproducible definition (see pt_step).
+ *   x..vz : device, n doubles each (midpoint positions and velocities).
+ *   counts: device, n * n_beams int32 (row-major by ion) or NULL.
+ *   dv    : device, SoA 3n doubles (m/s), written.
+ * Asynchronous.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int pt_laser_kicks(const pt_laser* laser, double mass, int64_t n, const double* x,
+                   const double* y, const double* z, const double* vx, const double* vy,
+                   const double* vz, int64_t step, double dt, int32_t* counts, double* dv,
+                   void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pt_energy -- rotating-frame energy of the state at time state->t.
+ * Paper: Eq. rotation (x_r = R(omega_r t) x), Eq. pe_rot (first line, from
+ * Eqs. pot_trap and pot_wall) and Sec. 3 (energies in the rotating frame):
+ *   out[0] kinetic  sum m |v_r|^2 / 2, v_r = (v_x - w_r y, v_y + w_r x, v_z)
+ *   out[1] external sum q_i k_z (2z^2 - r^2)/4 + (q_i B w_r - m w_r^2) r^2/2
+ *                       + q_i k_z delta (x_r^2 - y_r^2)/4
+ *   out[2] Coulomb  (1/2) sum_i q_i phi_i
+ *   out[3] total.
+ *   plan   : the FMM for phi, or NULL to use the exact FP64 direct sum.
+ *   out    : host, 4 doubles (J).
+ * Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_OOM. */
+int pt_energy(fmm_plan plan, const pt_state* state, const pt_trap* trap, double* out,
+              void* stream);
+
+/* Human-readable text for a status code (static storage). */
+const char* pt_status_str(int status);
+
+/* ---------------------------------------------------------------------------
+ * fmm_tree_info -- the octree of the last fmm_forces / pt_step call, for
+ * checking the sort (Sec. 2.3.2: root cube = smallest cube around the ions,
+ * split into octants; leaf keys are Morton codes of the leaf coordinates,
+ * ix the most significant bit of each triple).
+ *   root  : host, 4 doubles written: lo_x, lo_y, lo_z, side (m).
+ *   perm  : device, n int32 written: perm[k] = original index of the ion in
+ *           sorted slot k (sorted by leaf key, ties by index) or NULL.
+ *   keys  : device, n uint32 written: leaf key of every ion (original order)
+ *           or NULL.
+ * Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PENNING_H */

@@ -1,0 +1,334 @@
+"""Python binding of libpenning: the FMM Coulomb field of a Penning-trap ion
+crystal fused with the cyclotronic push, for GB300 (sm_103a).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI of ``include/penning.h``; PyTorch supplies device
+memory and the current stream.  There is no CPU fallback: importing works
+without a GPU (the library is only loaded), but every call that computes
+needs CUDA and the compiled ``libpenning.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpenning.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "penning.h")
+
+PT_OK, PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA = 0, -1, -2, -3
+PT_ERR_NONFINITE, PT_ERR_ESCAPED, PT_ERR_TIMEOUT, PT_ERR_COINCIDENT, PT_ERR_UNSUPPORTED = (
+    -4, -5, -6, -7, -8)
+PT_FP64, PT_MIXED_TF32X3, PT_FP32 = 0, 1, 3
+PT_PHASE_NEAR, PT_PHASE_FAR, PT_PHASE_ALL = 1, 2, 3
+PT_MAX_BEAMS = 8
+PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "fp32": PT_FP32}
+
+
+class PenningError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+class pt_trap(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_double), ("omega_z", ctypes.c_double),
+                ("omega_r", ctypes.c_double), ("delta", ctypes.c_double),
+                ("mass", ctypes.c_double), ("charge", ctypes.c_double)]
+
+
+class pt_beam(ctypes.Structure):
+    _fields_ = [("s0", ctypes.c_double), ("detuning", ctypes.c_double),
+                ("kx", ctypes.c_double), ("ky", ctypes.c_double), ("kz", ctypes.c_double),
+                ("waist_y", ctypes.c_double), ("waist_z", ctypes.c_double),
+                ("offset_d", ctypes.c_double), ("uniform", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+class pt_laser(ctypes.Structure):
+    _fields_ = [("n_beams", ctypes.c_int32), ("enabled", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("gamma0", ctypes.c_double),
+                ("beam", pt_beam * PT_MAX_BEAMS)]
+
+
+class pt_state(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("t", ctypes.c_double), ("step", ctypes.c_int64)] + [
+        (k, ctypes.c_void_p) for k in ("x", "y", "z", "vx", "vy", "vz", "q")]
+
+
+_lib = None
+_lock = threading.Lock()
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def exported_functions() -> list[str]:
+    """Names of the functions declared in include/penning.h."""
+    import re
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def load(build_if_missing: bool = True):
+    """Load libpenning.so (compiling it first if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import _build
+            try:
+                _build.build()
+            except RuntimeError:
+                if not os.path.exists(LIB_PATH):
+                    raise
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libpenning.so is not built ({LIB_PATH}); run "
+                              "python -c 'import __graft_entry__ as g; g.build()'")
+        L = ctypes.CDLL(LIB_PATH)
+        L.pt_status_str.argtypes = [ctypes.c_int]
+        L.pt_status_str.restype = ctypes.c_char_p
+        L.fmm_plan_create.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(_VP)]
+        L.fmm_plan_destroy.argtypes = [_VP]
+        L.fmm_plan_set_phases.argtypes = [_VP, ctypes.c_int]
+        L.fmm_plan_last_depth.argtypes = [_VP]
+        L.fmm_forces.argtypes = [_VP, _I64, _VP, _VP, _VP, _VP, _VP]
+        L.fmm_direct.argtypes = [_I64, _VP, _VP, _VP, _VP, _VP]
+        L.pt_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                              ctypes.POINTER(pt_laser), _D, _I64, _VP]
+        L.pt_laser_kicks.argtypes = [ctypes.POINTER(pt_laser), _D, _I64, _VP, _VP, _VP, _VP, _VP,
+                                     _VP, _I64, _D, _VP, _VP, _VP]
+        L.pt_energy.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                ctypes.POINTER(_D), _VP]
+        L.fmm_tree_info.argtypes = [_VP, ctypes.POINTER(_D), _VP, _VP, _VP]
+        L.pt_step_async.argtypes = L.pt_step.argtypes
+        L.pt_sync.argtypes = [_VP, _VP]
+        L.fmm_plan_profile.argtypes = [_VP, ctypes.c_int]
+        L.fmm_plan_phase_times.argtypes = [_VP, ctypes.POINTER(_D)]
+        L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
+        _lib = L
+        return L
+
+
+def status_str(status: int) -> str:
+    return load(build_if_missing=False).pt_status_str(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != PT_OK:
+        raise PenningError(status, what)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_f64(t, shape=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+def make_trap(tr) -> pt_trap:
+    return pt_trap(tr["B"], tr["omega_z"], tr["omega_r"], tr["delta"], tr["mass"], tr["charge"])
+
+
+def make_laser(beams, seed=0, gamma0=None, enabled=True) -> pt_laser:
+    if len(beams) > PT_MAX_BEAMS:
+        raise ValueError("too many beams")
+    L = pt_laser()
+    L.n_beams = len(beams)
+    L.enabled = 1 if (enabled and len(beams)) else 0
+    L.seed = int(seed) & (2**64 - 1)
+    L.gamma0 = float(gamma0 if gamma0 is not None else 2 * 3.141592653589793 * 18e6)
+    for i, b in enumerate(beams):
+        L.beam[i] = pt_beam(b["s0"], b["detuning"], b["k"][0], b["k"][1], b["k"][2],
+                            b.get("waist_y", 1.0), b.get("waist_z", 1.0), b.get("offset_d", 0.0),
+                            1 if b.get("uniform", False) else 0, 0)
+    return L
+
+
+@dataclass
+class State:
+    """Ion state on the device (each tensor (n,) float64 CUDA) plus t and step."""
+    x: torch.Tensor
+    y: torch.Tensor
+    z: torch.Tensor
+    vx: torch.Tensor
+    vy: torch.Tensor
+    vz: torch.Tensor
+    q: torch.Tensor
+    t: float = 0.0
+    step: int = 0
+
+    @classmethod
+    def from_numpy(cls, pos, vel, q, device="cuda", t=0.0, step=0):
+        def col(a, i):
+            return torch.tensor(a[:, i], dtype=torch.float64, device=device).contiguous()
+        return cls(col(pos, 0), col(pos, 1), col(pos, 2), col(vel, 0), col(vel, 1), col(vel, 2),
+                   torch.tensor(q, dtype=torch.float64, device=device).contiguous(), t, step)
+
+    @property
+    def n(self) -> int:
+        return self.x.numel()
+
+    def pos(self):
+        return torch.stack([self.x, self.y, self.z], 1)
+
+    def vel(self):
+        return torch.stack([self.vx, self.vy, self.vz], 1)
+
+    def _c(self) -> pt_state:
+        for t in (self.x, self.y, self.z, self.vx, self.vy, self.vz, self.q):
+            _dev_f64(t, (self.n,))
+        return pt_state(self.n, float(self.t), int(self.step), *[
+            t.data_ptr() for t in (self.x, self.y, self.z, self.vx, self.vy, self.vz, self.q)])
+
+
+class Plan:
+    """An FMM plan: octree, expansion and operator workspace on the device."""
+
+    def __init__(self, n_max: int, p: int = 10, leaf_max: int = 32, depth: int = -1,
+                 precision="fp64"):
+        L = load()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ctypes.c_void_p()
+        _check(L.fmm_plan_create(int(n_max), int(p), int(leaf_max), int(depth), prec,
+                                 ctypes.byref(h)), "fmm_plan_create")
+        self._h = h
+        self.n_max, self.p, self.precision = int(n_max), int(p), prec
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load(False).fmm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_phases(self, phases: int):
+        _check(load(False).fmm_plan_set_phases(self._h, int(phases)), "fmm_plan_set_phases")
+
+    @property
+    def last_depth(self) -> int:
+        return int(load(False).fmm_plan_last_depth(self._h))
+
+    def forces(self, pos, q, E=None, phi=None, want_phi=True, stream=None):
+        """Coulomb field (3, n) V/m and potential (n,) V of every ion; pos (3, n) m."""
+        n = q.numel()
+        _dev_f64(pos, (3, n))
+        _dev_f64(q, (n,))
+        if E is None:
+            E = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+        if want_phi and phi is None:
+            phi = torch.empty(n, dtype=torch.float64, device=pos.device)
+        _check(load(False).fmm_forces(self._h, n, _ptr(pos), _ptr(q), _ptr(E),
+                                      _ptr(phi) if want_phi else None, _stream(stream)),
+               "fmm_forces")
+        return E, phi
+
+    def step(self, state: State, trap, laser: pt_laser | None, dt: float, n_steps: int,
+             stream=None):
+        """Advance state by n_steps cyclotronic steps (in place; t and step advanced)."""
+        st = state._c()
+        tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+        _check(load(False).pt_step(self._h, ctypes.byref(st), ctypes.byref(tr),
+                                   ctypes.byref(laser) if laser is not None else None,
+                                   float(dt), int(n_steps), _stream(stream)), "pt_step")
+        state.t, state.step = st.t, st.step
+        return state
+
+    def step_async(self, state: State, trap, laser: pt_laser | None, dt: float, n_steps: int,
+                   stream=None):
+        """Enqueue n_steps steps without synchronising (fixed or previously chosen depth)."""
+        st = state._c()
+        tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+        _check(load(False).pt_step_async(self._h, ctypes.byref(st), ctypes.byref(tr),
+                                         ctypes.byref(laser) if laser is not None else None,
+                                         float(dt), int(n_steps), _stream(stream)),
+               "pt_step_async")
+        state.t, state.step = st.t, st.step
+        return state
+
+    def sync(self, stream=None):
+        _check(load(False).pt_sync(self._h, _stream(stream)), "pt_sync")
+
+    def profile(self, enable: bool = True):
+        _check(load(False).fmm_plan_profile(self._h, 1 if enable else 0), "fmm_plan_profile")
+
+    PHASES = ("drift_bbox", "tree", "upward", "m2l", "near_far", "kick_drift")
+
+    def phase_times(self) -> dict:
+        out = (ctypes.c_double * 6)()
+        _check(load(False).fmm_plan_phase_times(self._h, out), "fmm_plan_phase_times")
+        return dict(zip(self.PHASES, list(out)))
+
+    def stats(self, stream=None) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        _check(load(False).fmm_plan_stats(self._h, out, _stream(stream)), "fmm_plan_stats")
+        keys = ("n", "depth", "leaves", "cells", "m2l_pairs", "p2p_pairs", "l2l_shifts",
+                "m2m_shifts")
+        return dict(zip(keys, [int(v) for v in out]))
+
+    def tree_info(self, n: int, device="cuda", stream=None):
+        root = (ctypes.c_double * 4)()
+        perm = torch.empty(n, dtype=torch.int32, device=device)
+        keys = torch.empty(n, dtype=torch.int32, device=device)
+        _check(load(False).fmm_tree_info(self._h, root, _ptr(perm), _ptr(keys), _stream(stream)),
+               "fmm_tree_info")
+        return list(root), perm, keys.view(torch.int32)
+
+
+def direct(pos, q, want_phi=True, stream=None):
+    """FP64 O(N^2) Coulomb field (3, n) and potential on the GPU."""
+    n = q.numel()
+    _dev_f64(pos, (3, n))
+    _dev_f64(q, (n,))
+    E = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+    phi = torch.empty(n, dtype=torch.float64, device=pos.device) if want_phi else None
+    _check(load().fmm_direct(n, _ptr(pos), _ptr(q), _ptr(E), _ptr(phi), _stream(stream)),
+           "fmm_direct")
+    return E, phi
+
+
+def laser_kicks(laser: pt_laser, mass: float, pos, vel, step: int, dt: float, stream=None):
+    """Photon counts (n, n_beams) int32 and recoil dv (3, n) for a midpoint state."""
+    n = pos.shape[1]
+    _dev_f64(pos, (3, n))
+    _dev_f64(vel, (3, n))
+    counts = torch.zeros((n, max(laser.n_beams, 1)), dtype=torch.int32, device=pos.device)
+    dv = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+    p = [_ptr(pos[i]) for i in range(3)] + [_ptr(vel[i]) for i in range(3)]
+    _check(load().pt_laser_kicks(ctypes.byref(laser), float(mass), n, *p, int(step), float(dt),
+                                 _ptr(counts), _ptr(dv), _stream(stream)), "pt_laser_kicks")
+    return counts[:, :laser.n_beams], dv
+
+
+def energy(state: State, trap, plan: Plan | None = None, stream=None):
+    """Rotating-frame energy parts [kinetic, external, Coulomb, total] (J)."""
+    st = state._c()
+    tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+    out = (ctypes.c_double * 4)()
+    _check(load().pt_energy(plan._h if plan is not None else None, ctypes.byref(st),
+                            ctypes.byref(tr), out, _stream(stream)), "pt_energy")
+    return list(out)

@@ -1,0 +1,609 @@
+// abi.cu -- the C entry points of libpenning (declared in include/penning.h):
+// plan management, host construction of the translation operators, the step
+// loop (captured once per configuration as a CUDA graph and replayed per
+// step) and the diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "internal.h"
+#include "operators.h"
+
+using namespace pt;
+
+namespace {
+
+constexpr int kWallChunk = 4096;  // steps per wall-phase table upload
+
+struct GraphKey {
+    int D = -1;
+    int64_t n = -1;
+    const void* ptr[7] = {nullptr};
+    PushParams pp{};
+    pt_laser laser{};
+    bool profile = false;
+    bool operator==(const GraphKey& o) const {
+        return D == o.D && n == o.n && profile == o.profile && memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
+               memcmp(&pp, &o.pp, sizeof pp) == 0 && memcmp(&laser, &o.laser, sizeof laser) == 0;
+    }
+};
+
+}  // namespace
+
+struct fmm_plan_s {
+    int device = 0;
+    int64_t n_max = 0;
+    int p = 0, P = 0, leaf_max = 32, depth = -1, precision = PT_FP64;
+    int phases = PT_PHASE_ALL;
+    int last_depth = -1;
+    int64_t last_n = 0;
+    Workspace ws;
+    std::vector<void*> allocs;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    GraphKey gkey;
+    int* h_err = nullptr;      // pinned
+    // pinned host ring for the per-chunk wall-phase tables and step counters
+    // (asynchronous steps may have several chunks in flight)
+    static constexpr int kSlots = 8;
+    double* h_wall[kSlots] = {nullptr};
+    StepCounter* h_steps[kSlots] = {nullptr};
+    cudaEvent_t slot_ev[kSlots] = {nullptr};
+    int next_slot = 0;
+    // per-phase device timing (events captured into the step graph)
+    bool profile = false;
+    static constexpr int kPhases = 6;
+    cudaEvent_t ph_ev[kPhases + 1] = {nullptr};
+};
+
+namespace {
+
+std::mutex g_tables_mu;
+std::set<int> g_tables_dev;
+
+template <typename T>
+bool dalloc(fmm_plan_s* pl, T*& p, size_t bytes) {
+    void* v = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&v, bytes) != cudaSuccess) return false;
+    pl->allocs.push_back(v);
+    p = (T*)v;
+    return true;
+}
+
+int status_from(cudaError_t e) {
+    if (e == cudaSuccess) return PT_OK;
+    if (e == cudaErrorMemoryAllocation) return PT_ERR_OOM;
+    if (e == cudaErrorNotSupported) return PT_ERR_UNSUPPORTED;
+    return PT_ERR_CUDA;
+}
+
+void free_plan(fmm_plan_s* pl) {
+    if (!pl) return;
+    cudaSetDevice(pl->device);
+    cudaDeviceSynchronize();
+    if (pl->graph) cudaGraphExecDestroy(pl->graph);
+    for (void* v : pl->allocs) cudaFree(v);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    for (int k = 0; k < fmm_plan_s::kSlots; ++k) {
+        if (pl->h_wall[k]) cudaFreeHost(pl->h_wall[k]);
+        if (pl->h_steps[k]) cudaFreeHost(pl->h_steps[k]);
+        if (pl->slot_ev[k]) cudaEventDestroy(pl->slot_ev[k]);
+    }
+    for (int k = 0; k <= fmm_plan_s::kPhases; ++k)
+        if (pl->ph_ev[k]) cudaEventDestroy(pl->ph_ev[k]);
+    if (pl->h_err) cudaFreeHost(pl->h_err);
+    delete pl;
+}
+
+int64_t pow8(int l) { return (int64_t)1 << (3 * l); }
+
+// Uploads operators in the plan's arithmetic type.
+template <typename T>
+cudaError_t upload_ops(fmm_plan_s* pl, const std::vector<double>& m2m, const std::vector<double>& l2l,
+                       const std::vector<double>& m2l) {
+    const int P = pl->P;
+    std::vector<T> tmp;
+    // M2M transposed (in-major) for the warp-per-cell kernel
+    tmp.resize((size_t)8 * P * P);
+    for (int o = 0; o < 8; ++o)
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c)
+                tmp[(size_t)o * P * P + (size_t)c * P + r] = (T)m2m[(size_t)o * P * P + (size_t)r * P + c];
+    cudaError_t e = cudaMemcpy(pl->ws.T_m2m, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    tmp.assign(l2l.begin(), l2l.end());
+    if ((e = cudaMemcpy(pl->ws.T_l2l, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    tmp.assign(m2l.begin(), m2l.end());
+    return cudaMemcpy(pl->ws.T_m2l, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+int build_operators(fmm_plan_s* pl) {
+    const int p = pl->p, P = pl->P;
+    std::vector<double> m2m((size_t)8 * P * P), l2l((size_t)8 * P * P), m2l((size_t)343 * P * P, 0.0);
+    for (int o = 0; o < 8; ++o) {
+        ops::build_m2m(p, o, &m2m[(size_t)o * P * P]);
+        ops::build_l2l(p, o, &l2l[(size_t)o * P * P]);
+    }
+    for (int ox = -3; ox <= 3; ++ox)
+        for (int oy = -3; oy <= 3; ++oy)
+            for (int oz = -3; oz <= 3; ++oz) {
+                if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                int idx = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+                ops::build_m2l(p, ox, oy, oz, &m2l[(size_t)idx * P * P]);
+            }
+    cudaError_t e = pl->ws.fp64 ? upload_ops<double>(pl, m2m, l2l, m2l)
+                                : upload_ops<float>(pl, m2m, l2l, m2l);
+    if (e != cudaSuccess) return status_from(e);
+    if (pl->precision == PT_MIXED_TF32X3) {
+        std::vector<float> packed(m2l_tc_operand_bytes(p) / sizeof(float));
+        m2l_tc_pack_operands(p, m2l.data(), l2l.data(), packed.data());
+        e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size() * sizeof(float),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return status_from(e);
+    }
+    return PT_OK;
+}
+
+int check_err(fmm_plan_s* pl, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(pl->h_err, pl->ws.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from(e);
+    if (*pl->h_err) {
+        int v = *pl->h_err;
+        cudaMemsetAsync(pl->ws.err, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
+        if (v & ERR_NONFINITE) return PT_ERR_NONFINITE;
+        if (v & ERR_TIMEOUT) return PT_ERR_TIMEOUT;
+    }
+    return PT_OK;
+}
+
+int choose_depth(fmm_plan_s* pl, int64_t n, const double* x, const double* y, const double* z,
+                 cudaStream_t s, int* D) {
+    if (pl->depth >= 0) {
+        *D = pl->depth;
+        return PT_OK;
+    }
+    int32_t counts[kMaxDepth + 1] = {0};
+    cudaError_t e = launch_level_counts(n, x, y, z, pl->ws.depth_max, pl->ws, counts, s);
+    if (e != cudaSuccess) return status_from(e);
+    int r = check_err(pl, s);
+    if (r != PT_OK) return r;
+    int d = pl->ws.depth_max;
+    for (int l = 0; l <= pl->ws.depth_max; ++l) {
+        if (counts[l] > 0 && (double)n / (double)counts[l] <= (double)pl->leaf_max) {
+            d = l;
+            break;
+        }
+    }
+    *D = d;
+    return PT_OK;
+}
+
+int forces_impl(fmm_plan_s* pl, int64_t n, const double* x, const double* y, const double* z,
+                const double* q, double* E, double* phi, cudaStream_t s, int D) {
+    cudaError_t e = launch_bbox(x, y, z, n, pl->ws, s);
+    if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, pl->ws, s);
+    if (e == cudaSuccess)
+        e = launch_fmm(n, D, pl->phases, pl->ws, pl->precision == PT_MIXED_TF32X3, E, phi, s);
+    pl->last_depth = D;
+    pl->last_n = n;
+    return status_from(e);
+}
+
+// One time step: drift + cube, tree, FMM, kick + drift.  With profiling on,
+// event records between the phases are captured too.
+cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& pp,
+                         const pt_laser& laser, int D, cudaStream_t s) {
+    Workspace& ws = pl->ws;
+    const int64_t n = st.n;
+    auto mark = [&](int k) -> cudaError_t {
+        return pl->profile ? cudaEventRecordWithFlags(pl->ph_ev[k], s, cudaEventRecordExternal)
+                           : cudaSuccess;
+    };
+    cudaError_t e = mark(0);
+    if (e == cudaSuccess) e = launch_drift_bbox(n, st.x, st.y, st.z, st.vx, st.vy, st.vz, pp, ws, s);
+    if (e == cudaSuccess) e = mark(1);
+    if (e == cudaSuccess) e = launch_tree(n, st.x, st.y, st.z, st.q, D, ws, s);
+    if (e == cudaSuccess) e = mark(2);
+    if (e == cudaSuccess)
+        e = launch_fmm_phased(n, D, PT_PHASE_ALL, ws, pl->precision == PT_MIXED_TF32X3, ws.E,
+                              nullptr, s, pl->profile ? pl->ph_ev + 3 : nullptr);
+    if (e == cudaSuccess)
+        e = launch_kick_drift(n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.q, ws.E, pp, laser, ws, s);
+    if (e == cudaSuccess) e = mark(6);
+    return e;
+}
+
+// The step loop shared by pt_step (synchronous) and pt_step_async.
+int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_laser* laser,
+              double dt, int64_t n_steps, cudaStream_t s, bool sync) {
+    Workspace& ws = plan->ws;
+    pt_laser lz;
+    memset(&lz, 0, sizeof lz);
+    if (laser) lz = *laser;
+    PushParams pp;
+    memset(&pp, 0, sizeof pp);
+    pp.h = 0.5 * dt;
+    pp.dt = dt;
+    pp.wc = trap->charge * trap->B / trap->mass;
+    pp.C = cos(pp.wc * pp.h);
+    pp.S = sin(pp.wc * pp.h);
+    pp.kz = trap->mass * trap->omega_z * trap->omega_z / trap->charge;
+    pp.delta = trap->delta;
+    pp.mass = trap->mass;
+    pp.rk = 1.054571817e-34 / trap->mass;
+    const double t0 = st->t;
+    const int64_t step0 = st->step;
+    for (int64_t s0 = 0; s0 < n_steps; s0 += ws.wall_cap) {
+        const int64_t k = (n_steps - s0) < ws.wall_cap ? (n_steps - s0) : ws.wall_cap;
+        int D;
+        if (sync || plan->depth >= 0) {
+            int r = choose_depth(plan, st->n, st->x, st->y, st->z, s, &D);
+            if (r != PT_OK) return r;
+        } else {
+            if (plan->last_depth < 0) return PT_ERR_ARG;
+            D = plan->last_depth;
+        }
+        const int slot = plan->next_slot;
+        plan->next_slot = (slot + 1) % fmm_plan_s::kSlots;
+        cudaError_t e = cudaEventSynchronize(plan->slot_ev[slot]);  // slot free again
+        if (e != cudaSuccess) return status_from(e);
+        double* hw = plan->h_wall[slot];
+        for (int64_t j = 0; j < k; ++j) {
+            double tm = (t0 + (double)(s0 + j) * dt) + 0.5 * dt;
+            hw[2 * j] = cos(2.0 * trap->omega_r * tm);
+            hw[2 * j + 1] = sin(2.0 * trap->omega_r * tm);
+        }
+        *plan->h_steps[slot] = StepCounter{0, step0 + s0, step0 + s0};
+        e = cudaMemcpyAsync(ws.wall_cs, hw, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.steps, plan->h_steps[slot], sizeof(StepCounter),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(plan->slot_ev[slot], s);
+        if (e != cudaSuccess) return status_from(e);
+        GraphKey key;
+        key.D = D;
+        key.n = st->n;
+        const void* ptrs[7] = {st->x, st->y, st->z, st->vx, st->vy, st->vz, st->q};
+        memcpy(key.ptr, ptrs, sizeof ptrs);
+        key.pp = pp;
+        key.laser = lz;
+        key.profile = plan->profile;
+        if (!plan->graph || !(key == plan->gkey)) {
+            if (plan->graph) {
+                cudaGraphExecDestroy(plan->graph);
+                plan->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return status_from(e);
+            cudaError_t e2 = enqueue_step(plan, *st, pp, lz, D, plan->cap_stream);
+            e = cudaStreamEndCapture(plan->cap_stream, &g);
+            if (e2 != cudaSuccess || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return status_from(e2 != cudaSuccess ? e2 : e);
+            }
+            e = cudaGraphInstantiate(&plan->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                plan->graph = nullptr;
+                return status_from(e);
+            }
+            plan->gkey = key;
+        }
+        for (int64_t j = 0; j < k; ++j) {
+            e = cudaGraphLaunch(plan->graph, s);
+            if (e != cudaSuccess) return status_from(e);
+        }
+        plan->last_depth = D;
+        plan->last_n = st->n;
+        if (sync) {
+            int r = check_err(plan, s);
+            if (r != PT_OK) return r;
+        }
+    }
+    st->t = t0 + (double)n_steps * dt;
+    st->step = step0 + n_steps;
+    return PT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pt_status_str(int status) {
+    switch (status) {
+        case PT_OK: return "ok";
+        case PT_ERR_ARG: return "invalid argument";
+        case PT_ERR_OOM: return "device out of memory";
+        case PT_ERR_CUDA: return "CUDA runtime error";
+        case PT_ERR_NONFINITE: return "non-finite ion position";
+        case PT_ERR_ESCAPED: return "ion escaped the domain";
+        case PT_ERR_TIMEOUT: return "bounded device wait timed out";
+        case PT_ERR_COINCIDENT: return "coincident ions";
+        case PT_ERR_UNSUPPORTED: return "unsupported on this device or build";
+        default: return "unknown status";
+    }
+}
+
+int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision, fmm_plan* out) {
+    if (!out || n_max < 1 || n_max > (int64_t)1 << 30 || p < 2 || p > kMaxOrder || leaf_max < 1 ||
+        depth < -1 || depth > kMaxDepth)
+        return PT_ERR_ARG;
+    if (precision != PT_FP64 && precision != PT_FP32 && precision != PT_MIXED_TF32X3)
+        return PT_ERR_ARG;
+    *out = nullptr;
+    fmm_plan_s* pl = new (std::nothrow) fmm_plan_s;
+    if (!pl) return PT_ERR_OOM;
+    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+        delete pl;
+        return PT_ERR_CUDA;
+    }
+    if (precision == PT_MIXED_TF32X3) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, pl->device) != cudaSuccess) {
+            delete pl;
+            return PT_ERR_CUDA;
+        }
+        if (prop.major != 10 || prop.minor != 3 || m2l_tc_operand_bytes(p) == 0) {
+            delete pl;
+            return PT_ERR_UNSUPPORTED;
+        }
+    }
+    pl->n_max = n_max;
+    pl->p = p;
+    pl->P = (p + 1) * (p + 1);
+    pl->leaf_max = leaf_max;
+    pl->depth = depth;
+    pl->precision = precision;
+    Workspace& ws = pl->ws;
+    ws.n_max = n_max;
+    ws.p = p;
+    ws.P = pl->P;
+    ws.fp64 = (precision == PT_FP64);
+    if (depth >= 0) {
+        ws.depth_max = depth;
+    } else {
+        int d = 1;
+        while (d < kMaxDepth && pow8(d - 1) < n_max) ++d;
+        ws.depth_max = d;
+    }
+    int64_t cells = 0, dense = 0;
+    for (int l = 0; l <= ws.depth_max; ++l) {
+        cells += pow8(l) < n_max ? pow8(l) : n_max;
+        dense += pow8(l);
+    }
+    ws.cells_max = cells;
+    ws.dense_max = dense;
+    ws.block_sums_cap = (dense + kScanTile - 1) / kScanTile + 16;
+    ws.bbox_blocks = 152 * 2;
+    ws.wall_cap = kWallChunk;
+    const size_t tsz = ws.fp64 ? sizeof(double) : sizeof(float);
+    const size_t PP = (size_t)pl->P * pl->P;
+    bool ok = true;
+    {
+        std::lock_guard<std::mutex> g(g_tables_mu);
+        if (!g_tables_dev.count(pl->device)) {
+            if (upload_harmonic_tables() != cudaSuccess) ok = false;
+            else g_tables_dev.insert(pl->device);
+        }
+    }
+    ok = ok && dalloc(pl, ws.key, sizeof(uint32_t) * n_max) && dalloc(pl, ws.rank, sizeof(uint32_t) * n_max) &&
+         dalloc(pl, ws.perm_tmp, sizeof(int32_t) * n_max) && dalloc(pl, ws.perm, sizeof(int32_t) * n_max) &&
+         dalloc(pl, ws.slot_of, sizeof(int32_t) * n_max) && dalloc(pl, ws.leaf_of, sizeof(int32_t) * n_max) &&
+         dalloc(pl, ws.sorted, (ws.fp64 ? sizeof(double4_32a) : sizeof(float4)) * n_max) &&
+         dalloc(pl, ws.leaf_count, sizeof(int32_t) * pow8(ws.depth_max)) &&
+         dalloc(pl, ws.leaf_start, sizeof(int32_t) * (pow8(ws.depth_max) + 1)) &&
+         dalloc(pl, ws.cid, sizeof(int32_t) * dense) && dalloc(pl, ws.code, sizeof(uint32_t) * cells) &&
+         dalloc(pl, ws.cstart, sizeof(int32_t) * cells) && dalloc(pl, ws.ccount, sizeof(int32_t) * cells) &&
+         dalloc(pl, ws.linfo, sizeof(LevelInfo)) && dalloc(pl, ws.M, tsz * pl->P * cells) &&
+         dalloc(pl, ws.L, tsz * pl->P * cells) && dalloc(pl, ws.E, sizeof(double) * 3 * n_max) &&
+         dalloc(pl, ws.block_sums, sizeof(int32_t) * ws.block_sums_cap) &&
+         dalloc(pl, ws.root, sizeof(RootCube)) &&
+         dalloc(pl, ws.bbox_partial, sizeof(double) * 8 * ws.bbox_blocks) &&
+         dalloc(pl, ws.ticket, sizeof(unsigned)) && dalloc(pl, ws.err, sizeof(int)) &&
+         dalloc(pl, ws.steps, sizeof(StepCounter)) && dalloc(pl, ws.stats, sizeof(unsigned long long) * 8) &&
+         dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap) &&
+         dalloc(pl, ws.T_m2m, tsz * 8 * PP) && dalloc(pl, ws.T_l2l, tsz * 8 * PP) &&
+         dalloc(pl, ws.T_m2l, tsz * 343 * PP);
+    if (ok && precision == PT_MIXED_TF32X3) ok = dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p));
+    if (!ok) {
+        free_plan(pl);
+        return PT_ERR_OOM;
+    }
+    if (cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ws.err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ws.steps, 0, sizeof(StepCounter)) != cudaSuccess ||
+        cudaMallocHost(&pl->h_err, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        free_plan(pl);
+        return PT_ERR_CUDA;
+    }
+    for (int k = 0; k < fmm_plan_s::kSlots; ++k) {
+        if (cudaMallocHost(&pl->h_wall[k], sizeof(double) * 2 * ws.wall_cap) != cudaSuccess ||
+            cudaMallocHost(&pl->h_steps[k], sizeof(StepCounter)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->slot_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            free_plan(pl);
+            return PT_ERR_CUDA;
+        }
+    }
+    for (int k = 0; k <= fmm_plan_s::kPhases; ++k) {
+        if (cudaEventCreate(&pl->ph_ev[k]) != cudaSuccess) {
+            free_plan(pl);
+            return PT_ERR_CUDA;
+        }
+    }
+    int r = build_operators(pl);
+    if (r != PT_OK) {
+        free_plan(pl);
+        return r;
+    }
+    *out = pl;
+    return PT_OK;
+}
+
+int fmm_plan_destroy(fmm_plan plan) {
+    free_plan(plan);
+    return PT_OK;
+}
+
+int fmm_plan_set_phases(fmm_plan plan, int phases) {
+    if (!plan || phases < 1 || phases > 3) return PT_ERR_ARG;
+    plan->phases = phases;
+    return PT_OK;
+}
+
+int fmm_plan_last_depth(fmm_plan plan) { return plan ? plan->last_depth : -1; }
+
+int fmm_forces(fmm_plan plan, int64_t n, const double* pos, const double* q, double* E,
+               double* phi, void* stream) {
+    if (!plan || !pos || !q || !E || n < 1 || n > plan->n_max) return PT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return PT_ERR_CUDA;
+    const double *x = pos, *y = pos + n, *z = pos + 2 * n;
+    int D;
+    int r = choose_depth(plan, n, x, y, z, s, &D);
+    if (r != PT_OK) return r;
+    return forces_impl(plan, n, x, y, z, q, E, phi, s, D);
+}
+
+int fmm_direct(int64_t n, const double* pos, const double* q, double* E, double* phi,
+               void* stream) {
+    if (!pos || !q || !E || n < 1) return PT_ERR_ARG;
+    return status_from(launch_direct(n, pos, q, E, phi, (cudaStream_t)stream));
+}
+
+int pt_laser_kicks(const pt_laser* laser, double mass, int64_t n, const double* x, const double* y,
+                   const double* z, const double* vx, const double* vy, const double* vz,
+                   int64_t step, double dt, int32_t* counts, double* dv, void* stream) {
+    if (!laser || !x || !y || !z || !vx || !vy || !vz || !dv || n < 1 || !(mass > 0) ||
+        laser->n_beams < 0 || laser->n_beams > PT_MAX_BEAMS)
+        return PT_ERR_ARG;
+    const double rk = 1.054571817e-34 / mass;
+    return status_from(launch_laser_kicks(*laser, rk, n, x, y, z, vx, vy, vz, step, dt, counts, dv,
+                                          (cudaStream_t)stream));
+}
+
+static int step_args_ok(fmm_plan plan, const pt_state* st, const pt_trap* trap,
+                        const pt_laser* laser, double dt, int64_t n_steps) {
+    if (!plan || !st || !trap || !(dt > 0) || n_steps < 0 || st->n < 1 || st->n > plan->n_max ||
+        !st->x || !st->y || !st->z || !st->vx || !st->vy || !st->vz || !st->q || !(trap->mass > 0) ||
+        trap->charge == 0.0 || trap->B == 0.0)
+        return PT_ERR_ARG;
+    if (laser && (laser->n_beams < 0 || laser->n_beams > PT_MAX_BEAMS)) return PT_ERR_ARG;
+    return PT_OK;
+}
+
+int pt_step(fmm_plan plan, pt_state* st, const pt_trap* trap, const pt_laser* laser, double dt,
+            int64_t n_steps, void* stream) {
+    int r = step_args_ok(plan, st, trap, laser, dt, n_steps);
+    if (r != PT_OK) return r;
+    if (n_steps == 0) return PT_OK;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return PT_ERR_CUDA;
+    return step_impl(plan, st, trap, laser, dt, n_steps, (cudaStream_t)stream, true);
+}
+
+int pt_step_async(fmm_plan plan, pt_state* st, const pt_trap* trap, const pt_laser* laser,
+                  double dt, int64_t n_steps, void* stream) {
+    int r = step_args_ok(plan, st, trap, laser, dt, n_steps);
+    if (r != PT_OK) return r;
+    if (plan->depth < 0 && plan->last_depth < 0) return PT_ERR_ARG;
+    if (n_steps == 0) return PT_OK;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return PT_ERR_CUDA;
+    return step_impl(plan, st, trap, laser, dt, n_steps, (cudaStream_t)stream, false);
+}
+
+int pt_sync(fmm_plan plan, void* stream) {
+    if (!plan) return PT_ERR_ARG;
+    return check_err(plan, (cudaStream_t)stream);
+}
+
+int fmm_plan_profile(fmm_plan plan, int enable) {
+    if (!plan) return PT_ERR_ARG;
+    plan->profile = enable != 0;
+    return PT_OK;
+}
+
+int fmm_plan_phase_times(fmm_plan plan, double* ms) {
+    if (!plan || !ms || !plan->profile) return PT_ERR_ARG;
+    for (int k = 0; k < fmm_plan_s::kPhases; ++k) {
+        float v = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&v, plan->ph_ev[k], plan->ph_ev[k + 1]);
+        if (e != cudaSuccess) return status_from(e);
+        ms[k] = v;
+    }
+    return PT_OK;
+}
+
+int fmm_plan_stats(fmm_plan plan, int64_t* out, void* stream) {
+    if (!plan || !out || plan->last_depth < 0) return PT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_tree_stats(plan->last_n, plan->last_depth, plan->ws, out, s);
+    return status_from(e);
+}
+
+int pt_energy(fmm_plan plan, const pt_state* st, const pt_trap* trap, double* out, void* stream) {
+    if (!st || !trap || !out || st->n < 1 || !st->x || !st->y || !st->z || !st->vx || !st->vy ||
+        !st->vz || !st->q || trap->charge == 0.0)
+        return PT_ERR_ARG;
+    if (plan && st->n > plan->n_max) return PT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = st->n;
+    double *pos = nullptr, *E = nullptr, *phi = nullptr, *dout = nullptr;
+    size_t bytes = sizeof(double) * (3 * n + 3 * n + n + 4 + 3 * 256);
+    if (cudaMalloc(&pos, bytes) != cudaSuccess) return PT_ERR_OOM;
+    E = pos + 3 * n;
+    phi = E + 3 * n;
+    dout = phi + n;
+    cudaError_t e = cudaMemcpyAsync(pos, st->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pos + n, st->y, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pos + 2 * n, st->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    int r = PT_OK;
+    if (e == cudaSuccess) {
+        if (plan) r = fmm_forces(plan, n, pos, st->q, E, phi, s);
+        else e = launch_direct(n, pos, st->q, E, phi, s);
+    }
+    const double kz = trap->mass * trap->omega_z * trap->omega_z / trap->charge;
+    if (e == cudaSuccess && r == PT_OK) e = launch_energy_parts(n, *st, *trap, kz, phi, dout, s);
+    double h[3] = {0, 0, 0};
+    if (e == cudaSuccess && r == PT_OK) e = cudaMemcpyAsync(h, dout, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(pos);
+    if (r != PT_OK) return r;
+    if (e != cudaSuccess) return status_from(e);
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = h[0] + h[1] + h[2];
+    return PT_OK;
+}
+
+int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream) {
+    if (!plan || !root || plan->last_depth < 0) return PT_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = plan->last_n;
+    RootCube rc;
+    cudaError_t e = cudaMemcpyAsync(&rc, plan->ws.root, sizeof rc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && perm)
+        e = cudaMemcpyAsync(perm, plan->ws.perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && keys)
+        e = cudaMemcpyAsync(keys, plan->ws.key, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from(e);
+    root[0] = rc.lo[0];
+    root[1] = rc.lo[1];
+    root[2] = rc.lo[2];
+    root[3] = rc.side;
+    return PT_OK;
+}
+
+}  // extern "C"

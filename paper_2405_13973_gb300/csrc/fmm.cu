@@ -1,0 +1,626 @@
+// fmm.cu -- the FMM stages on the CUDA cores (Sec. 2.3.2).
+//
+// Upward pass: P2M at the leaves (Eq. FMM_coul2), M2M to the parents.
+// Downward pass: at every level l >= 2 the local expansion of a cell is the
+// L2L shift of its parent's plus the M2L conversion (Eq. FMM_local) of the
+// multipole expansions of the 189 cells that are children of the parent's
+// neighbours but not neighbours themselves.  At the leaves the far field is
+// the gradient of the local expansion (L2P) and the near field the direct sum
+// over the 27 adjacent leaves (P2P).
+//
+// Cells of one level are stored octant-major, so a tile of target cells
+// shares its octant and therefore the same 189 source offsets: M2L becomes,
+// per offset o, a dense product L[:, tile] += T_o * M[:, src(tile, o)], the
+// L2L shift being one more such product with the parent's L.
+//
+// Everything is templated on the arithmetic type (double: PT_FP64, float:
+// PT_FP32 and the CUDA-core stages of PT_MIXED_TF32X3).  Coefficients are in
+// the normalised real storage of harmonics.cuh, scaled by the cell size.
+#include <cuda_runtime.h>
+
+#include "fmm_math.cuh"
+#include "harmonics.cuh"
+#include "internal.h"
+
+namespace pt {
+
+__constant__ HarmTables<double> c_tab_d;
+__constant__ HarmTables<float> c_tab_f;
+// M2L source offsets per target octant: packed (ox+3)*49 + (oy+3)*7 + (oz+3),
+// o = target - source, o_a in [b_a - 3, b_a + 2] with b the octant bits,
+// excluding the 27 neighbours.
+__constant__ int16_t c_m2l_off[8][189];
+
+template <typename T>
+__device__ __forceinline__ const HarmTables<T>& tab();
+template <>
+__device__ __forceinline__ const HarmTables<double>& tab<double>() { return c_tab_d; }
+template <>
+__device__ __forceinline__ const HarmTables<float>& tab<float>() { return c_tab_f; }
+
+void host_m2l_offsets(int16_t out[8][189]) {
+    for (int oct = 0; oct < 8; ++oct) {
+        int b[3] = {(oct >> 2) & 1, (oct >> 1) & 1, oct & 1};
+        int k = 0;
+        for (int ox = b[0] - 3; ox <= b[0] + 2; ++ox)
+            for (int oy = b[1] - 3; oy <= b[1] + 2; ++oy)
+                for (int oz = b[2] - 3; oz <= b[2] + 2; ++oz) {
+                    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                    out[oct][k++] = (int16_t)((ox + 3) * 49 + (oy + 3) * 7 + (oz + 3));
+                }
+    }
+}
+
+cudaError_t upload_harmonic_tables() {
+    static HarmTables<double> hd;
+    static HarmTables<float> hf;
+    static int16_t off[8][189];
+    static bool filled = false;
+    if (!filled) {
+        fill_harm_tables(hd);
+        fill_harm_tables(hf);
+        host_m2l_offsets(off);
+        filled = true;
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_tab_d, &hd, sizeof hd);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_f, &hf, sizeof hf);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m2l_off, off, sizeof off);
+    return e;
+}
+
+// Sorted ion records (written by the tree build): the FP64 path keeps
+// (u, q) in double; the FP32 paths keep u in 30-bit fixed point and q as
+// float bits (int4), so that near-field separations are exact integers.
+template <typename T>
+struct Ion;
+template <>
+struct Ion<double> {
+    using rec = double4_32a;
+    static __device__ __forceinline__ void get(const rec& r, double& x, double& y, double& z,
+                                               double& q) {
+        x = r.x; y = r.y; z = r.z; q = r.w;
+    }
+    // (x_t - x_s)/s for a source in the leaf at integer offset d from the target's
+    static __device__ __forceinline__ void sep(const rec& t, const rec& o, int dx, int dy, int dz,
+                                               double& rx, double& ry, double& rz) {
+        rx = (t.x - o.x) - dx;
+        ry = (t.y - o.y) - dy;
+        rz = (t.z - o.z) - dz;
+    }
+};
+template <>
+struct Ion<float> {
+    using rec = int4;
+    static __device__ __forceinline__ void get(const rec& r, float& x, float& y, float& z,
+                                               float& q) {
+        x = __int2float_rn(r.x) * 0x1p-30f;
+        y = __int2float_rn(r.y) * 0x1p-30f;
+        z = __int2float_rn(r.z) * 0x1p-30f;
+        q = __int_as_float(r.w);
+    }
+    // |t - o| < 2^30 and |d| 2^30 <= 2^30: the integer difference fits in 31 bits
+    static __device__ __forceinline__ void sep(const rec& t, const rec& o, int dx, int dy, int dz,
+                                               float& rx, float& ry, float& rz) {
+        rx = __int2float_rn((t.x - o.x) - dx * (1 << 30)) * 0x1p-30f;
+        ry = __int2float_rn((t.y - o.y) - dy * (1 << 30)) * 0x1p-30f;
+        rz = __int2float_rn((t.z - o.z) - dz * (1 << 30)) * 0x1p-30f;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// P2M: one warp per leaf, lane m accumulates column m (n = m..p).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_p2m(int D, int p, int P, const LevelInfo* linfo,
+                                             const int32_t* __restrict__ cstart,
+                                             const int32_t* __restrict__ ccount,
+                                             const typename Ion<T>::rec* __restrict__ sorted,
+                                             T* __restrict__ M) {
+    const HarmTables<T>& t = tab<T>();
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    const int m = lane;
+    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
+        const int s = cstart[g], k = ccount[g];
+        T accr[kMaxOrder + 1], acci[kMaxOrder + 1];
+#pragma unroll
+        for (int n = 0; n <= kMaxOrder; ++n) accr[n] = acci[n] = T(0);
+        if (m <= p) {
+            for (int i = 0; i < k; ++i) {
+                struct { T x, y, z, w; } u;
+                Ion<T>::get(sorted[s + i], u.x, u.y, u.z, u.w);
+                T dr = 1, di = 0;
+                for (int j = 1; j <= m; ++j) {
+                    T nr = (dr * u.x - di * u.y) * t.c[j];
+                    T ni = (dr * u.y + di * u.x) * t.c[j];
+                    dr = nr;
+                    di = ni;
+                }
+                const T r2 = u.x * u.x + u.y * u.y + u.z * u.z;
+                T y1r = 0, y1i = 0, y2r = 0, y2i = 0;
+#pragma unroll
+                for (int n = 0; n <= kMaxOrder; ++n) {
+                    if (n < m || n > p) continue;
+                    T yr, yi;
+                    if (n == m) {
+                        yr = dr;
+                        yi = di;
+                    } else if (n == m + 1) {
+                        T f = u.z * t.d[m];
+                        yr = f * y1r;
+                        yi = f * y1i;
+                    } else {
+                        T a = t.a[n][m] * u.z, b = t.b[n][m] * r2;
+                        yr = a * y1r - b * y2r;
+                        yi = a * y1i - b * y2i;
+                    }
+                    accr[n] += u.w * yr;
+                    acci[n] -= u.w * yi;
+                    y2r = y1r;
+                    y2i = y1i;
+                    y1r = yr;
+                    y1i = yi;
+                }
+            }
+            T* out = M + (int64_t)g * P;
+#pragma unroll
+            for (int n = 0; n <= kMaxOrder; ++n) {
+                if (n < m || n > p) continue;
+                int idx = re_idx(n, m);
+                out[idx] = accr[n];
+                if (m > 0) out[idx + 1] = acci[n];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M: one warp per parent; lanes over output coefficients.
+//   Tt: [8][P][P] transposed (in-major) so that lanes read consecutively.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) k_m2m(int l, int P, const LevelInfo* linfo,
+                                             const uint32_t* __restrict__ code,
+                                             const int32_t* __restrict__ cid, int64_t off_child,
+                                             const T* __restrict__ Tt, T* M) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sM = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * P;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int g0 = linfo->gbase[l], g1 = linfo->gbase[l + 1];
+    constexpr int R = ((kMaxOrder + 1) * (kMaxOrder + 1) + 31) / 32;
+    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
+        const uint32_t c = code[g];
+        T acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = T(0);
+        for (int o = 0; o < 8; ++o) {
+            const int gc = cid[off_child + ((c << 3) | o)];
+            if (gc < 0) continue;
+            __syncwarp();
+            for (int k = lane; k < P; k += 32) sM[k] = M[(int64_t)gc * P + k];
+            __syncwarp();
+            const T* To = Tt + (int64_t)o * P * P;
+            for (int k = 0; k < P; ++k) {
+                const T mk = sM[k];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    int row = lane + 32 * r;
+                    if (row < P) acc[r] += To[(int64_t)k * P + row] * mk;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int row = lane + 32 * r;
+            if (row < P) M[(int64_t)g * P + row] = acc[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2L (+ folded L2L) on the CUDA cores: block = 64 output rows x 32 targets of
+// one octant; loops over the 189 offsets (and the parent shift), each a
+// 64 x P x 32 product staged through shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kRT = 64, kNT = 32, kKC = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, const LevelInfo* linfo,
+                                                  const uint32_t* __restrict__ code,
+                                                  const int32_t* __restrict__ cid, int64_t off_l,
+                                                  int64_t off_parent, const T* __restrict__ M,
+                                                  T* L, const T* __restrict__ Tm2l,
+                                                  const T* __restrict__ Tl2l) {
+    __shared__ T As[kKC][kRT];
+    __shared__ T Bs[kKC][kNT];
+    __shared__ const T* src[kNT];
+    __shared__ int tile_oct, tile_base, tile_n;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int b = blockIdx.x, acc = 0;
+        tile_n = 0;
+        for (int o = 0; o < 8; ++o) {
+            int s0 = linfo->oct_start[l][o], s1 = linfo->oct_start[l][o + 1];
+            int nt = (s1 - s0 + kNT - 1) / kNT;
+            if (b < acc + nt) {
+                tile_oct = o;
+                tile_base = s0 + (b - acc) * kNT;
+                tile_n = min(kNT, s1 - tile_base);
+                break;
+            }
+            acc += nt;
+        }
+    }
+    __syncthreads();
+    if (tile_n <= 0) return;
+    const int oct = tile_oct, base = tile_base, ntile = tile_n;
+    const int row0 = blockIdx.y * kRT;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int lim = 1 << l;
+    T acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = T(0);
+    const int nterms = 189 + (l >= 3 ? 1 : 0);
+    for (int term = 0; term < nterms; ++term) {
+        const T* A;
+        if (term < 189) {
+            const int opi = c_m2l_off[oct][term];
+            A = Tm2l + (int64_t)opi * P * P;
+            if (tid < kNT) {
+                const T* sp = nullptr;
+                if (tid < ntile) {
+                    int ix, iy, iz;
+                    demorton3(code[base + tid], ix, iy, iz);
+                    int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3),
+                        sz = iz - (opi % 7 - 3);
+                    if (sx >= 0 && sx < lim && sy >= 0 && sy < lim && sz >= 0 && sz < lim) {
+                        int gs = cid[off_l + morton3(sx, sy, sz)];
+                        if (gs >= 0) sp = M + (int64_t)gs * P;
+                    }
+                }
+                src[tid] = sp;
+            }
+        } else {
+            A = Tl2l + (int64_t)oct * P * P;
+            if (tid < kNT) {
+                const T* sp = nullptr;
+                if (tid < ntile) {
+                    int gp = cid[off_parent + (code[base + tid] >> 3)];
+                    if (gp >= 0) sp = L + (int64_t)gp * P;
+                }
+                src[tid] = sp;
+            }
+        }
+        int any = __syncthreads_or(tid < kNT && src[tid] != nullptr);
+        if (!any) continue;
+        for (int k0 = 0; k0 < P; k0 += kKC) {
+#pragma unroll
+            for (int e = 0; e < (kRT * kKC) / 256; ++e) {
+                int idx = tid + 256 * e;
+                int r = idx / kKC, kk = idx % kKC;
+                int row = row0 + r, col = k0 + kk;
+                As[kk][r] = (row < P && col < P) ? A[(int64_t)row * P + col] : T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < (kNT * kKC) / 256; ++e) {
+                int idx = tid + 256 * e;
+                int j = idx / kKC, kk = idx % kKC;
+                const T* sp = src[j];
+                Bs[kk][j] = (sp != nullptr && k0 + kk < P) ? sp[k0 + kk] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < kKC; ++kk) {
+                T a0 = As[kk][ty * 4 + 0], a1 = As[kk][ty * 4 + 1], a2 = As[kk][ty * 4 + 2],
+                  a3 = As[kk][ty * 4 + 3];
+                T b0 = Bs[kk][tx * 2 + 0], b1 = Bs[kk][tx * 2 + 1];
+                acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+                acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+                acc[2][0] += a2 * b0; acc[2][1] += a2 * b1;
+                acc[3][0] += a3 * b0; acc[3][1] += a3 * b1;
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            int row = row0 + ty * 4 + i, j = tx * 2 + jj;
+            if (row < P && j < ntile) L[(int64_t)(base + j) * P + row] = acc[i][jj];
+        }
+}
+
+// ---------------------------------------------------------------------------
+// L2P + P2P, one thread per sorted ion; the result is written in the
+// original ion order, scaled to SI (k_e / s^2 for E, k_e / s for phi, with s
+// the leaf side).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T inv_sqrt(T r2);
+template <>
+__device__ __forceinline__ float inv_sqrt<float>(float r2) {
+    float y = rsqrtf(r2);
+    return y * (1.5f - 0.5f * r2 * y * y);  // one Newton step
+}
+template <>
+__device__ __forceinline__ double inv_sqrt<double>(double r2) {
+    return 1.0 / sqrt(r2);
+}
+
+// s + v with the rounding error carried in c (Kahan-Babuska / Neumaier).
+template <typename T>
+__device__ __forceinline__ void kb_add(T& s, T& c, T v) {
+    T t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_near_far(
+    int64_t n, int D, int p, int P, int phases, const RootCube* root, const LevelInfo* linfo,
+    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ leaf_of,
+    const int32_t* __restrict__ perm, const uint32_t* __restrict__ code,
+    const int32_t* __restrict__ cid_leaf, const int32_t* __restrict__ cstart,
+    const int32_t* __restrict__ ccount, const T* __restrict__ L, double* E, double* phi) {
+    using R = typename Ion<T>::rec;
+    const int lim = 1 << D;
+    const double sl = root->side / (double)lim;
+    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
+    for (int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; slot < n;
+         slot += (int64_t)gridDim.x * blockDim.x) {
+        const int g = leaf_of[slot];
+        const R me = sorted[slot];
+        T ex = 0, ey = 0, ez = 0, ph = 0;
+        if ((phases & PT_PHASE_FAR) && D >= 2) {
+            T fphi, gx, gy, gz, ux, uy, uz, uq;
+            Ion<T>::get(me, ux, uy, uz, uq);
+            l2p_eval<T>(p, L + (int64_t)g * P, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
+            ex = -gx;
+            ey = -gy;
+            ez = -gz;
+            ph = fphi;
+        }
+        if (phases & PT_PHASE_NEAR) {
+            // per source leaf: plain sums; across leaves: compensated sums
+            // (Kahan-Babuska), which keeps FP32 accumulation error at the
+            // level of one leaf's partial sum.
+            T cx = 0, cy = 0, cz = 0, cp = 0;
+            int ix, iy, iz;
+            demorton3(code[g], ix, iy, iz);
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+                        if (nx < 0 || ny < 0 || nz < 0 || nx >= lim || ny >= lim || nz >= lim)
+                            continue;
+                        const int gn = cid_leaf[morton3(nx, ny, nz)];
+                        if (gn < 0) continue;
+                        const int s0 = cstart[gn], s1 = s0 + ccount[gn];
+                        T px = 0, py = 0, pz = 0, pp = 0;
+                        for (int j = s0; j < s1; ++j) {
+                            if (j == slot) continue;
+                            const R o = sorted[j];
+                            T rx, ry, rz, oq, ox, oy, oz;
+                            Ion<T>::sep(me, o, dx, dy, dz, rx, ry, rz);
+                            Ion<T>::get(o, ox, oy, oz, oq);
+                            const T r2 = rx * rx + ry * ry + rz * rz;
+                            const T ir = inv_sqrt<T>(r2);
+                            const T qi = oq * ir;
+                            const T q3 = qi * ir * ir;
+                            px += q3 * rx;
+                            py += q3 * ry;
+                            pz += q3 * rz;
+                            pp += qi;
+                        }
+                        kb_add(ex, cx, px);
+                        kb_add(ey, cy, py);
+                        kb_add(ez, cz, pz);
+                        kb_add(ph, cp, pp);
+                    }
+            ex += cx;
+            ey += cy;
+            ez += cz;
+            ph += cp;
+        }
+        const int i = perm[slot];
+        E[i] = fE * (double)ex;
+        E[n + i] = fE * (double)ey;
+        E[2 * n + i] = fE * (double)ez;
+        if (phi) phi[i] = fP * (double)ph;
+    }
+}
+
+template <typename T>
+static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
+                           double* phi, cudaStream_t s, cudaEvent_t* ev) {
+    const int p = ws.p, P = ws.P;
+    DenseLayout dl = dense_layout(D);
+    T* M = (T*)ws.M;
+    T* L = (T*)ws.L;
+    const bool far = (phases & PT_PHASE_FAR) && D >= 2;
+    cudaError_t e;
+    if (far) {
+        int leaves_max = (int)(n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D)));
+        int grid = (leaves_max + 3) / 4;
+        if (grid > 152 * 16) grid = 152 * 16;
+        k_p2m<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(D, p, P, ws.linfo, ws.cstart, ws.ccount,
+                                                     (const typename Ion<T>::rec*)ws.sorted, M);
+        for (int l = D - 1; l >= 2; --l) {
+            int64_t cl = (int64_t)1 << (3 * l);
+            int cells = (int)(n < cl ? n : cl);
+            int g = (cells + 3) / 4;
+            if (g > 152 * 16) g = 152 * 16;
+            k_m2m<T><<<g, 128, 4 * P * sizeof(T), s>>>(l, P, ws.linfo, ws.code, ws.cid,
+                                                       dl.off[l + 1], (const T*)ws.T_m2m, M);
+        }
+    }
+    if (ev && (e = cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal)) != cudaSuccess)
+        return e;
+    if (far) {
+        for (int l = 2; l <= D; ++l) {
+            if (use_tc) {
+                e = launch_m2l_tc(l, D, ws, s);
+                if (e != cudaSuccess) return e;
+                continue;
+            }
+            int64_t cl = (int64_t)1 << (3 * l);
+            int cells = (int)(n < cl ? n : cl);
+            dim3 grid((cells + kNT - 1) / kNT + 8, (P + kRT - 1) / kRT);
+            k_m2l_simt<T><<<grid, 256, 0, s>>>(l, P, ws.linfo, ws.code, ws.cid, dl.off[l],
+                                               l >= 3 ? dl.off[l - 1] : 0, M, L,
+                                               (const T*)ws.T_m2l, (const T*)ws.T_l2l);
+        }
+    }
+    if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
+        return e;
+    int grid = (int)((n + 127) / 128);
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_near_far<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(
+        n, D, p, P, phases, ws.root, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
+        ws.leaf_of, ws.perm, ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount, L, E, phi);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fmm_phased(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
+                              double* phi, cudaStream_t s, cudaEvent_t* ev) {
+    if (ws.fp64) return run_fmm<double>(n, D, phases, ws, false, E, phi, s, ev);
+    return run_fmm<float>(n, D, phases, ws, use_tc, E, phi, s, ev);
+}
+
+cudaError_t launch_fmm(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
+                       double* phi, cudaStream_t s) {
+    return launch_fmm_phased(n, D, phases, ws, use_tc, E, phi, s, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Interaction counts of the current tree (for algorithmic work accounting).
+// ---------------------------------------------------------------------------
+__global__ void k_tree_stats(int D, const LevelInfo* linfo, const uint32_t* __restrict__ code,
+                             const int32_t* __restrict__ cid, DenseLayout dl,
+                             const int32_t* __restrict__ ccount, unsigned long long* st) {
+    const int lmin = dl.lmin;
+    const int g0 = linfo->gbase[lmin], g1 = linfo->gbase[D + 1];
+    unsigned long long m2l = 0, p2p = 0, shifts = 0;
+    for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < g1; g += gridDim.x * blockDim.x) {
+        int l = lmin;
+        while (l < D && g >= linfo->gbase[l + 1]) ++l;
+        int ix, iy, iz;
+        demorton3(code[g], ix, iy, iz);
+        const int lim = 1 << l;
+        if (l >= 2) {
+            const int oct = code[g] & 7;
+            for (int t = 0; t < 189; ++t) {
+                int opi = c_m2l_off[oct][t];
+                int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3), sz = iz - (opi % 7 - 3);
+                if (sx < 0 || sy < 0 || sz < 0 || sx >= lim || sy >= lim || sz >= lim) continue;
+                if (cid[dl.off[l] + morton3(sx, sy, sz)] >= 0) ++m2l;
+            }
+        }
+        if (l >= 3) ++shifts;
+        if (l == D) {
+            long long cnt = ccount[g], nb = 0;
+            for (int dx = -1; dx <= 1; ++dx)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+                        if (nx < 0 || ny < 0 || nz < 0 || nx >= lim || ny >= lim || nz >= lim) continue;
+                        int gn = cid[dl.off[D] + morton3(nx, ny, nz)];
+                        if (gn >= 0) nb += ccount[gn];
+                    }
+            p2p += (unsigned long long)(cnt * nb - cnt);
+        }
+    }
+    atomicAdd(&st[0], m2l);
+    atomicAdd(&st[1], p2p);
+    atomicAdd(&st[2], shifts);
+}
+
+cudaError_t launch_tree_stats(int64_t n, int D, Workspace& ws, int64_t* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ws.stats, 0, sizeof(unsigned long long) * 8, s);
+    if (e != cudaSuccess) return e;
+    DenseLayout dl = dense_layout(D);
+    k_tree_stats<<<152, 256, 0, s>>>(D, ws.linfo, ws.code, ws.cid, dl, ws.ccount, ws.stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long h[3];
+    LevelInfo li;
+    if ((e = cudaMemcpyAsync(h, ws.stats, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&li, ws.linfo, sizeof li, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    out[0] = n;
+    out[1] = D;
+    out[2] = li.gbase[D + 1] - li.gbase[D];
+    out[3] = D >= 2 ? li.gbase[D + 1] - li.gbase[2] : 0;
+    out[4] = (int64_t)h[0];
+    out[5] = (int64_t)h[1];
+    out[6] = (int64_t)h[2];
+    out[7] = (int64_t)h[2];
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Direct O(N^2) field in FP64 (Eq. hamiltonian), shared-memory source tiles,
+// Neumaier-compensated accumulation.
+// ---------------------------------------------------------------------------
+struct Neu {
+    double s = 0, c = 0;
+    __device__ __forceinline__ void add(double v) {
+        double t = s + v;
+        if (fabs(s) >= fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double val() const { return s + c; }
+};
+
+__global__ void __launch_bounds__(256) k_direct(int64_t n, const double* __restrict__ pos,
+                                                const double* __restrict__ q, double* E,
+                                                double* phi) {
+    __shared__ double4_32a tile[256];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double xi = 0, yi = 0, zi = 0;
+    if (i < n) { xi = pos[i]; yi = pos[n + i]; zi = pos[2 * n + i]; }
+    Neu ax, ay, az, ap;
+    for (int64_t t0 = 0; t0 < n; t0 += 256) {
+        int64_t j = t0 + threadIdx.x;
+        tile[threadIdx.x] = j < n ? make_double4_32a(pos[j], pos[n + j], pos[2 * n + j], q[j])
+                                  : make_double4_32a(0, 0, 0, 0);
+        __syncthreads();
+        int cnt = (int)(n - t0 < 256 ? n - t0 : 256);
+        for (int k = 0; k < cnt; ++k) {
+            if (t0 + k == i) continue;
+            double4_32a o = tile[k];
+            double dx = xi - o.x, dy = yi - o.y, dz = zi - o.z;
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double ir = 1.0 / r;
+            double w = o.w * ir / r2;
+            ax.add(w * dx);
+            ay.add(w * dy);
+            az.add(w * dz);
+            ap.add(o.w * ir);
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+        E[i] = kCoulomb * ax.val();
+        E[n + i] = kCoulomb * ay.val();
+        E[2 * n + i] = kCoulomb * az.val();
+        if (phi) phi[i] = kCoulomb * ap.val();
+    }
+}
+
+cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double* E, double* phi,
+                          cudaStream_t s) {
+    int grid = (int)((n + 255) / 256);
+    k_direct<<<grid > 0 ? grid : 1, 256, 0, s>>>(n, pos, q, E, phi);
+    return cudaGetLastError();
+}
+
+}  // namespace pt

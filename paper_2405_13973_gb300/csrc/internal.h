@@ -1,0 +1,146 @@
+// internal.h -- declarations shared by the CUDA translation units of
+// libpenning (host launchers and the plan workspace).  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/penning.h"
+
+namespace pt {
+
+constexpr int kMaxDepth = 8;      // uniform octree depth limit (8^8 leaf cells)
+constexpr int kMaxOrder = 16;     // expansion order limit
+constexpr int kScanTile = 2048;   // elements per block in the device scans
+// 1/(4 pi eps0) with the CODATA 2018 eps0, evaluated as (1 / ((4 pi) eps0))
+constexpr double kCoulomb = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
+
+// Root cube of the octree (Sec. 2.3.2): lower corner and side length.
+struct RootCube {
+    double lo[3];
+    double side;
+};
+
+// Per-level bookkeeping written on the device by the compaction pass.
+//   gbase[l]        first global compact id of level l (gbase[D+1] = total)
+//   oct_start[l][o] first global id of the cells of level l whose Morton code
+//                   ends in octant o (cells are grouped octant-major)
+struct LevelInfo {
+    int32_t gbase[kMaxDepth + 2];
+    int32_t oct_start[kMaxDepth + 1][9];
+};
+
+// Step counter shared by the kernels of one time step (advanced on the
+// device so that a captured step graph can be replayed).
+struct StepCounter {
+    int64_t cur;    // index of the step being computed
+    int64_t next;   // index the next step will take
+    int64_t base;   // first step of the current chunk (indexes the wall table)
+};
+
+// Device workspace owned by a plan.
+struct Workspace {
+    int64_t n_max = 0;
+    int depth_max = 0;
+    int p = 0, P = 0;
+    bool fp64 = true;
+    int64_t cells_max = 0;      // capacity of the compact cell arrays
+    int64_t dense_max = 0;      // capacity of the concatenated dense maps
+
+    uint32_t* key = nullptr;       // [n] leaf key of every ion (original order)
+    uint32_t* rank = nullptr;      // [n] arrival rank inside its leaf
+    int32_t* perm_tmp = nullptr;   // [n] slot -> ion, unordered inside a leaf
+    int32_t* perm = nullptr;       // [n] slot -> ion, ordered by ion index
+    int32_t* slot_of = nullptr;    // [n] ion -> slot
+    int32_t* leaf_of = nullptr;    // [n] slot -> global compact id of its leaf
+    void* sorted = nullptr;        // [n] float4 / double4 (u_x, u_y, u_z, q)
+    int32_t* leaf_count = nullptr; // [8^Dmax] ions per leaf code
+    int32_t* leaf_start = nullptr; // [8^Dmax + 1] exclusive scan of leaf_count
+    int32_t* cid = nullptr;        // [dense_max] dense (level, code) -> global id or -1
+    uint32_t* code = nullptr;      // [cells_max] global id -> Morton code
+    int32_t* cstart = nullptr;     // [cells_max] first slot of a leaf
+    int32_t* ccount = nullptr;     // [cells_max] ions in a leaf
+    LevelInfo* linfo = nullptr;    // level bookkeeping (device)
+    void* M = nullptr;             // [cells_max][P] multipole coefficients
+    void* L = nullptr;             // [cells_max][P] local coefficients
+    double* E = nullptr;           // [3n] Coulomb field of the last evaluation (SoA, SI)
+    int32_t* block_sums = nullptr; // scan scratch
+    int64_t block_sums_cap = 0;
+    RootCube* root = nullptr;
+    double* bbox_partial = nullptr;  // [bbox blocks][6]
+    int bbox_blocks = 0;
+    unsigned* ticket = nullptr;      // last-block-done counter
+    int* err = nullptr;              // device error flags (bit mask)
+    StepCounter* steps = nullptr;
+    unsigned long long* stats = nullptr;  // [8] interaction counters
+    double* wall_cs = nullptr;       // [wall_cap][2] cos, sin of 2 w_r t_mid per step
+    int64_t wall_cap = 0;
+    // operators (device), P x P each, row-major out x in
+    void* T_m2m = nullptr;   // [8][P][P]
+    void* T_l2l = nullptr;   // [8][P][P]
+    void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
+    float* T_m2l_tc = nullptr;  // tensor-core operand tiles (mixed mode)
+};
+
+enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+
+// Offsets of the concatenated dense maps: levels lmin..D.
+struct DenseLayout {
+    int lmin = 0, D = 0;
+    int64_t off[kMaxDepth + 2] = {0};
+    int64_t total = 0;
+};
+DenseLayout dense_layout(int D);
+
+// ---- tree (tree.cu) ----------------------------------------------------------
+cudaError_t launch_bbox(const double* x, const double* y, const double* z, int64_t n,
+                        Workspace& ws, cudaStream_t s);
+cudaError_t launch_tree(int64_t n, const double* x, const double* y, const double* z,
+                        const double* q, int D, Workspace& ws, cudaStream_t s);
+cudaError_t launch_level_counts(int64_t n, const double* x, const double* y, const double* z,
+                                int D, Workspace& ws, int32_t* host_counts, cudaStream_t s);
+
+// ---- FMM stages (fmm.cu) -----------------------------------------------------
+cudaError_t upload_harmonic_tables();
+cudaError_t launch_fmm(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
+                       double* phi, cudaStream_t s);
+// As launch_fmm; if ev is not null, records ev[0] after the upward pass,
+// ev[1] after M2L/L2L and ev[2] after L2P/P2P.
+cudaError_t launch_fmm_phased(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
+                              double* phi, cudaStream_t s, cudaEvent_t* ev);
+// Interaction counts of the last tree (synchronises s).  out[8] = {n, D,
+// leaves, cells at levels >= 2, M2L pairs, P2P pairs (ordered, i != j),
+// L2L shifts, M2M shifts}.
+cudaError_t launch_tree_stats(int64_t n, int D, Workspace& ws, int64_t* out, cudaStream_t s);
+cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double* E, double* phi,
+                          cudaStream_t s);
+
+// ---- tensor-core M2L (m2l_tc.cu) ---------------------------------------------
+cudaError_t launch_m2l_tc(int level, int D, Workspace& ws, cudaStream_t s);
+size_t m2l_tc_operand_bytes(int p);
+void m2l_tc_pack_operands(int p, const double* T_m2l_host, const double* T_l2l_host, float* out);
+
+// ---- push (push.cu) ----------------------------------------------------------
+struct PushParams {
+    double h;          // dt/2
+    double dt;
+    double C, S, wc;   // cos(wc h), sin(wc h), q B / m
+    double kz;         // m w_z^2 / q
+    double delta;
+    double mass;
+    double t0;         // time of the chunk's first step
+    int64_t step0;     // its global index
+    double rk;         // hbar / m
+};
+cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                              double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s);
+cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                              double* vz, const double* q, const double* E, const PushParams& pp,
+                              const pt_laser& laser, Workspace& ws, cudaStream_t s);
+cudaError_t launch_laser_kicks(const pt_laser& laser, double rk, int64_t n, const double* x,
+                               const double* y, const double* z, const double* vx,
+                               const double* vy, const double* vz, int64_t step, double dt,
+                               int32_t* counts, double* dv, cudaStream_t s);
+cudaError_t launch_energy_parts(int64_t n, const pt_state& st, const pt_trap& trap, double kz,
+                                const double* phi, double* d_out, cudaStream_t s);
+
+}  // namespace pt

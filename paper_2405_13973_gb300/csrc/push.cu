@@ -1,0 +1,339 @@
+// push.cu -- the cyclotronic push (Eq. time_ev2) and the laser-cooling kicks
+// (Eqs. scattering_rate, laser_kick), FP64.
+//
+// This translation unit is compiled with -fmad=false: every expression below
+// is the literal sequence of IEEE double operations written, so that the
+// photon counts and recoil kicks are bit-reproducible definitions (the same
+// counter-based random numbers give the same kicks on any conforming
+// implementation of the same sequence).
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+// (seed lo, seed hi), counter = (ion, beam | slot << 8, step lo, step hi).
+// exp: Cody-Waite reduction with ln2 split into a 40-bit head and a tail,
+// degree-13 Taylor polynomial by Horner, scaling by 2^k through the exponent
+// bits (two steps below the normal range).
+#include <cuda_runtime.h>
+
+#include "bbox.cuh"
+#include "internal.h"
+
+namespace pt {
+
+constexpr int kMaxPhotons = 64;
+constexpr int kMaxTries = 64;
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
+    uint64_t k = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return (double)k * 0x1.0p-53;
+}
+
+__device__ __forceinline__ void stream_block(uint64_t seed, int64_t step, int64_t ion, int beam,
+                                             uint32_t slot, uint32_t out[4]) {
+    uint64_t st = (uint64_t)step;
+    philox4x32_10((uint32_t)ion, (uint32_t)beam | (slot << 8), (uint32_t)st, (uint32_t)(st >> 32),
+                  (uint32_t)seed, (uint32_t)(seed >> 32), out);
+}
+
+__device__ double pt_exp(double x) {
+    const double LN2_HI = 0x1.62e42fefa2000p-1;
+    const double LN2_LO = 0x1.9ef35793c7673p-41;
+    const double INV_LN2 = 0x1.71547652b82fep+0;
+    if (x != x) return x;
+    if (x > 709.8) return INFINITY;
+    if (x < -745.2) return 0.0;
+    double kf = floor(x * INV_LN2 + 0.5);
+    double r = (x - kf * LN2_HI) - kf * LN2_LO;
+    double c[14];
+    double fact = 1.0;
+#pragma unroll
+    for (int j = 0; j <= 13; ++j) {
+        if (j > 0) fact = fact * (double)j;
+        c[j] = 1.0 / fact;
+    }
+    double p = c[13];
+#pragma unroll
+    for (int j = 12; j >= 0; --j) p = p * r + c[j];
+    int k = (int)kf;
+    if (k >= -1022) return p * __longlong_as_double((long long)(k + 1023) << 52);
+    return (p * __longlong_as_double((long long)(k + 600 + 1023) << 52)) *
+           __longlong_as_double((long long)(-600 + 1023) << 52);
+}
+
+__device__ __forceinline__ double saturation(const pt_beam& b, double y, double z) {
+    if (b.uniform) return b.s0;
+    double dy = y - b.offset_d;
+    double a = (dy * dy) / (b.waist_y * b.waist_y) + (z * z) / (b.waist_z * b.waist_z);
+    return b.s0 * pt_exp(-a);
+}
+
+__device__ __forceinline__ double scatter_rate(const pt_beam& b, double gamma0, double y, double z,
+                                               double vx, double vy, double vz) {
+    double S = saturation(b, y, z);
+    double g = 0.5 * gamma0;
+    double g2 = g * g;
+    double kv = (b.kx * vx + b.ky * vy) + b.kz * vz;
+    double det = b.detuning - kv;
+    double den = g2 * (1.0 + 2.0 * S) + det * det;
+    return ((S * gamma0) * g2) / den;
+}
+
+__device__ __forceinline__ int poisson(double lambda, double u) {
+    double p = pt_exp(-lambda);
+    double F = p;
+    int k = 0;
+    while (u >= F && k < kMaxPhotons) {
+        k = k + 1;
+        p = p * lambda / (double)k;
+        F = F + p;
+    }
+    return k;
+}
+
+// Photon counts and recoil of ion i at its midpoint state (Eq. laser_kick).
+__device__ void laser_ion(const pt_laser& L, double rk, int64_t i, int64_t step, double dt,
+                          double y, double z, double vx, double vy, double vz, int32_t* counts_row,
+                          double& ax, double& ay, double& az) {
+    ax = 0.0;
+    ay = 0.0;
+    az = 0.0;
+    for (int l = 0; l < L.n_beams; ++l) {
+        const pt_beam& b = L.beam[l];
+        double rate = scatter_rate(b, L.gamma0, y, z, vx, vy, vz);
+        double lam = rate * dt;
+        uint32_t blk[4];
+        stream_block(L.seed, step, i, l, 0u, blk);
+        int cnt = poisson(lam, u01(blk[0], blk[1]));
+        if (counts_row) counts_row[l] = cnt;
+        if (cnt == 0) continue;
+        double kmag = sqrt((b.kx * b.kx + b.ky * b.ky) + b.kz * b.kz);
+        double fc = (double)cnt * rk;
+        ax = ax + fc * b.kx;
+        ay = ay + fc * b.ky;
+        az = az + fc * b.kz;
+        double em = rk * kmag;
+        uint32_t slot = 1;
+        for (int j = 0; j < cnt; ++j) {
+            double v1 = 0.0, v2 = 0.0, s = 0.0;
+            for (int tr = 0; tr < kMaxTries; ++tr) {
+                stream_block(L.seed, step, i, l, slot, blk);
+                slot = slot + 1;
+                v1 = 2.0 * u01(blk[0], blk[1]) - 1.0;
+                v2 = 2.0 * u01(blk[2], blk[3]) - 1.0;
+                s = v1 * v1 + v2 * v2;
+                if (s < 1.0) break;
+            }
+            double w = 2.0 * sqrt(1.0 - s);
+            ax = ax + em * (v1 * w);
+            ay = ay + em * (v2 * w);
+            az = az + em * (1.0 - 2.0 * s);
+        }
+    }
+}
+
+// Exact gyration U0(h) (Eq. U0, B along +z: clockwise velocity rotation).
+__device__ __forceinline__ void gyrate(const PushParams& pp, double& x, double& y, double& z,
+                                       double& vx, double& vy, double vz) {
+    double ux = vx, uy = vy;
+    x = x + (ux * pp.S + uy * (1.0 - pp.C)) / pp.wc;
+    y = y + (uy * pp.S - ux * (1.0 - pp.C)) / pp.wc;
+    z = z + vz * pp.h;
+    vx = ux * pp.C + uy * pp.S;
+    vy = -ux * pp.S + uy * pp.C;
+}
+
+// First half-drift of a step, fused with the bounding cube of the midpoint
+// positions; the finalising thread also advances the step counter.
+__global__ void __launch_bounds__(256) k_drift_bbox(int64_t n, double* x, double* y, double* z,
+                                                    double* vx, double* vy, const double* vz,
+                                                    PushParams pp, double* partial,
+                                                    unsigned* ticket, RootCube* root, int* err,
+                                                    StepCounter* steps) {
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i];
+        gyrate(pp, px, py, pz, ux, uy, vz[i]);
+        x[i] = px;
+        y[i] = py;
+        z[i] = pz;
+        vx[i] = ux;
+        vy[i] = uy;
+        double p[3] = {px, py, pz};
+        for (int a = 0; a < 3; ++a) {
+            bad |= !isfinite(p[a]);
+            mn[a] = fmin(mn[a], p[a]);
+            mx[a] = fmax(mx[a], p[a]);
+        }
+    }
+    if (bbox_block_and_finalise(mn, mx, bad, partial, ticket, root, err)) {
+        steps->cur = steps->next;
+        steps->next = steps->next + 1;
+    }
+}
+
+// Kick (Eq. velocity_kick with the laser kicks of Eq. laser_kick) and the
+// second half-drift.
+__global__ void __launch_bounds__(128) k_kick_drift(int64_t n, double* x, double* y, double* z,
+                                                    double* vx, double* vy, double* vz,
+                                                    const double* __restrict__ q,
+                                                    const double* __restrict__ E, PushParams pp,
+                                                    pt_laser laser, const StepCounter* steps,
+                                                    const double* __restrict__ wall_cs) {
+    const int64_t step = steps->cur;
+    const int64_t widx = step - steps->base;
+    const double c = wall_cs[2 * widx], s = wall_cs[2 * widx + 1];
+    const double kw = 0.5 * pp.kz * pp.delta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i], uz = vz[i];
+        double etx = 0.5 * pp.kz * px, ety = 0.5 * pp.kz * py, etz = -pp.kz * pz;
+        double ewx = -kw * (px * c - py * s);
+        double ewy = -kw * (-py * c - px * s);
+        double Fx = etx + ewx, Fy = ety + ewy, Fz = etz;
+        double dx = 0.0, dy = 0.0, dz = 0.0;
+        if (laser.enabled && laser.n_beams > 0)
+            laser_ion(laser, pp.rk, i, step, pp.dt, py, pz, ux, uy, uz, nullptr, dx, dy, dz);
+        double qm = q[i] / pp.mass;
+        ux = ux + qm * (E[i] + Fx) * pp.dt + dx;
+        uy = uy + qm * (E[n + i] + Fy) * pp.dt + dy;
+        uz = uz + qm * (E[2 * n + i] + Fz) * pp.dt + dz;
+        gyrate(pp, px, py, pz, ux, uy, uz);
+        x[i] = px;
+        y[i] = py;
+        z[i] = pz;
+        vx[i] = ux;
+        vy[i] = uy;
+        vz[i] = uz;
+    }
+}
+
+__global__ void k_laser_kicks(pt_laser laser, double rk, int64_t n, const double* x,
+                              const double* y, const double* z, const double* vx,
+                              const double* vy, const double* vz, int64_t step, double dt,
+                              int32_t* counts, double* dv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double ax, ay, az;
+        laser_ion(laser, rk, i, step, dt, y[i], z[i], vx[i], vy[i], vz[i],
+                  counts ? counts + i * laser.n_beams : nullptr, ax, ay, az);
+        dv[i] = ax;
+        dv[n + i] = ay;
+        dv[2 * n + i] = az;
+    }
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > 152 * 16) g = 152 * 16;
+    return g > 0 ? (int)g : 1;
+}
+
+cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                              double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s) {
+    k_drift_bbox<<<ws.bbox_blocks, 256, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_partial,
+                                                ws.ticket, ws.root, ws.err, ws.steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                              double* vz, const double* q, const double* E, const PushParams& pp,
+                              const pt_laser& laser, Workspace& ws, cudaStream_t s) {
+    k_kick_drift<<<grid_for(n, 128), 128, 0, s>>>(n, x, y, z, vx, vy, vz, q, E, pp, laser,
+                                                   ws.steps, ws.wall_cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_laser_kicks(const pt_laser& laser, double rk, int64_t n, const double* x,
+                               const double* y, const double* z, const double* vx,
+                               const double* vy, const double* vz, int64_t step, double dt,
+                               int32_t* counts, double* dv, cudaStream_t s) {
+    k_laser_kicks<<<grid_for(n, 128), 128, 0, s>>>(laser, rk, n, x, y, z, vx, vy, vz, step, dt,
+                                                    counts, dv);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rotating-frame energy parts (Eq. rotation, Eq. pe_rot first line), a
+// deterministic two-stage reduction with compensated sums.
+// ---------------------------------------------------------------------------
+struct Neu2 {
+    double s = 0, c = 0;
+    __device__ void add(double v) {
+        double t = s + v;
+        if (fabs(s) >= fabs(v)) c += (s - t) + v;
+        else c += (v - t) + s;
+        s = t;
+    }
+};
+
+constexpr int kEnergyBlocks = 256;
+
+__global__ void __launch_bounds__(256) k_energy_partial(int64_t n, pt_state st, pt_trap trap,
+                                                        double kz, double c, double s,
+                                                        const double* phi, double* partial) {
+    __shared__ double sh[3][256];
+    Neu2 a[3];
+    const double m = trap.mass, wr = trap.omega_r, B = trap.B;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double x = st.x[i], y = st.y[i], z = st.z[i];
+        double wx = st.vx[i] - wr * y, wy = st.vy[i] + wr * x, vz = st.vz[i];
+        a[0].add(0.5 * m * (wx * wx + wy * wy + vz * vz));
+        double xr = c * x - s * y, yr = s * x + c * y;
+        double r2 = x * x + y * y;
+        double qi = st.q[i];
+        a[1].add(0.25 * qi * kz * (2.0 * z * z - r2));
+        a[1].add(0.5 * (qi * B * wr - m * wr * wr) * r2);
+        a[1].add(0.25 * qi * kz * trap.delta * (xr * xr - yr * yr));
+        if (phi) a[2].add(0.5 * qi * phi[i]);
+    }
+    for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] = a[k].s + a[k].c;
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        Neu2 t;
+        for (int j = 0; j < (int)blockDim.x; ++j) t.add(sh[threadIdx.x][j]);
+        partial[blockIdx.x * 3 + threadIdx.x] = t.s + t.c;
+    }
+}
+
+__global__ void k_energy_final(const double* partial, int nb, double* out) {
+    if (threadIdx.x < 3) {
+        Neu2 t;
+        for (int b = 0; b < nb; ++b) t.add(partial[b * 3 + threadIdx.x]);
+        out[threadIdx.x] = t.s + t.c;
+    }
+}
+
+cudaError_t launch_energy_parts(int64_t n, const pt_state& st, const pt_trap& trap, double kz,
+                                const double* phi, double* d_out, cudaStream_t s) {
+    double c = cos(trap.omega_r * st.t), sn = sin(trap.omega_r * st.t);
+    double* partial = d_out + 4;  // caller provides 4 + 3 * kEnergyBlocks doubles
+    k_energy_partial<<<kEnergyBlocks, 256, 0, s>>>(n, st, trap, kz, c, sn, phi, partial);
+    k_energy_final<<<1, 32, 0, s>>>(partial, kEnergyBlocks, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace pt

@@ -129,6 +129,20 @@ def rotating_maxwellian(pos, omega_r, temperature, seed, m=MASS):
     return v
 
 
+def lattice_sphere(n, density, jitter, seed):
+    """The n sites of a simple-cubic lattice (spacing density^(-1/3)) nearest
+    the origin, each displaced by Gaussian jitter of `jitter` x spacing: a
+    start without close pairs."""
+    a = density ** (-1.0 / 3.0)
+    m = int(math.ceil((3.0 * n / (4.0 * math.pi)) ** (1.0 / 3.0))) + 2
+    g = np.arange(-m, m + 1, dtype=np.float64)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = np.linalg.norm(pts, axis=1) + 1e-9 * (pts @ np.array([1.0, 1e-3, 1e-6]))
+    pts = pts[np.argsort(r, kind="stable")[:n]]
+    rng = np.random.default_rng(seed)
+    return (pts + rng.normal(size=pts.shape) * jitter) * a
+
+
 def charges(n, q=E_CHARGE):
     return np.full(n, q, dtype=np.float64)
 
@@ -141,6 +155,17 @@ def crystal_sphere_1k(seed=1):
     vel = rotating_maxwellian(pos, tr["omega_r"], 10e-3, seed + 1000)
     return {"name": "sphere_N1000", "pos": pos, "vel": vel, "q": charges(1000), "trap": tr,
             "beams": [], "laser": False, "p": 8, "leaf": 32, "dt": DT, "n_steps": 1000}
+
+
+def crystal_lattice_1k(seed=5, n=1000, temperature=10e-3):
+    """N = 1,000 on a jittered cubic lattice at the beta = 1 rigid-rotor density,
+    rigid rotation plus a 10 mK Maxwellian: no close pairs."""
+    tr = trap(beta=1.0)
+    n0 = rigid_rotor_density(tr["omega_r"])
+    pos = lattice_sphere(n, n0, 0.05, seed)
+    vel = rotating_maxwellian(pos, tr["omega_r"], temperature, seed + 1000)
+    return {"name": f"lattice_N{n}", "pos": pos, "vel": vel, "q": charges(n), "trap": tr,
+            "beams": [], "laser": False, "p": 10, "leaf": 32, "dt": DT, "n_steps": 1000}
 
 
 def crystal_spheroid_10k(seed=2, n=10000, aspect=0.3):
