@@ -235,6 +235,24 @@ int pt_laser_kicks(const pt_laser* laser, double mass, int64_t n, const double* 
 int pt_energy(fmm_plan plan, const pt_state* state, const pt_trap* trap, double* out,
               void* stream);
 
+/* ---------------------------------------------------------------------------
+ * pt_energy_noalloc -- pt_energy with the exact FP64 direct sum (as with a
+ * NULL plan), for callers that cannot allocate device memory: code running
+ * inside a CUDA stream capture (where cudaMalloc is not allowed), real-time
+ * loops that cannot afford cudaMalloc's implicit device synchronisation, and
+ * programs whose device memory is reserved up front by their own allocator.
+ * The paper has no counterpart; this is a library-service variant.
+ *   state, trap, out, stream : as pt_energy.
+ * Allocates nothing: its scratch is a fixed array inside the library
+ * (3.5 MiB, held by every GPU that loads the library until exit), which
+ * limits state->n to 65536 (larger: PT_ERR_ARG, nothing queued).  The first
+ * call on a device looks the array up and should come before any stream
+ * capture.  All calls on a device share the array: calls that overlap on
+ * the GPU (other streams or threads) race and must be serialised.  Each
+ * call overwrites all the scratch it reads, so no clearing is needed.
+ * Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int pt_energy_noalloc(const pt_state* state, const pt_trap* trap, double* out, void* stream);
+
 /* Human-readable text for a status code (static storage). */
 const char* pt_status_str(int status);
 

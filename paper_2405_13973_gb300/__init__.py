@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_profile.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_phase_times.argtypes = [_VP, ctypes.POINTER(_D)]
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
+        L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                        ctypes.POINTER(_D), _VP]
         _lib = L
         return L
 
