@@ -148,6 +148,13 @@ int build_operators(fmm_plan_s* pl) {
         e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size() * sizeof(float),
                        cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return status_from(e);
+        std::vector<float> lt((size_t)8 * P * P);
+        for (int o = 0; o < 8; ++o)
+            for (int r = 0; r < P; ++r)
+                for (int c = 0; c < P; ++c)
+                    lt[(size_t)o * P * P + (size_t)c * P + r] = (float)l2l[(size_t)o * P * P + (size_t)r * P + c];
+        e = cudaMemcpy(pl->ws.T_l2l_t, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return status_from(e);
     }
     return PT_OK;
 }
@@ -370,6 +377,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     ws.p = p;
     ws.P = pl->P;
     ws.fp64 = (precision == PT_FP64);
+    ws.ld = ws.fp64 ? pl->P : ((pl->P + 31) / 32) * 32;
     if (depth >= 0) {
         ws.depth_max = depth;
     } else {
@@ -393,7 +401,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     {
         std::lock_guard<std::mutex> g(g_tables_mu);
         if (!g_tables_dev.count(pl->device)) {
-            if (upload_harmonic_tables() != cudaSuccess) ok = false;
+            if (upload_harmonic_tables() != cudaSuccess || m2l_tc_init() != cudaSuccess) ok = false;
             else g_tables_dev.insert(pl->device);
         }
     }
@@ -405,8 +413,8 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
          dalloc(pl, ws.leaf_start, sizeof(int32_t) * (pow8(ws.depth_max) + 1)) &&
          dalloc(pl, ws.cid, sizeof(int32_t) * dense) && dalloc(pl, ws.code, sizeof(uint32_t) * cells) &&
          dalloc(pl, ws.cstart, sizeof(int32_t) * cells) && dalloc(pl, ws.ccount, sizeof(int32_t) * cells) &&
-         dalloc(pl, ws.linfo, sizeof(LevelInfo)) && dalloc(pl, ws.M, tsz * pl->P * cells) &&
-         dalloc(pl, ws.L, tsz * pl->P * cells) && dalloc(pl, ws.E, sizeof(double) * 3 * n_max) &&
+         dalloc(pl, ws.linfo, sizeof(LevelInfo)) && dalloc(pl, ws.M, tsz * ws.ld * cells) &&
+         dalloc(pl, ws.L, tsz * ws.ld * cells) && dalloc(pl, ws.E, sizeof(double) * 3 * n_max) &&
          dalloc(pl, ws.block_sums, sizeof(int32_t) * ws.block_sums_cap) &&
          dalloc(pl, ws.root, sizeof(RootCube)) &&
          dalloc(pl, ws.bbox_partial, sizeof(double) * 8 * ws.bbox_blocks) &&
@@ -415,12 +423,20 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
          dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap) &&
          dalloc(pl, ws.T_m2m, tsz * 8 * PP) && dalloc(pl, ws.T_l2l, tsz * 8 * PP) &&
          dalloc(pl, ws.T_m2l, tsz * 343 * PP);
-    if (ok && precision == PT_MIXED_TF32X3) ok = dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p));
+    if (ok && precision == PT_MIXED_TF32X3) {
+        ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
+        ok = dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p)) &&
+             dalloc(pl, ws.T_l2l_t, sizeof(float) * 8 * PP) &&
+             dalloc(pl, ws.tc_part, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) *
+                                        cells * ws.ld);
+    }
     if (!ok) {
         free_plan(pl);
         return PT_ERR_OOM;
     }
-    if (cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
+        cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
+        cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ws.err, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ws.steps, 0, sizeof(StepCounter)) != cudaSuccess ||
         cudaMallocHost(&pl->h_err, sizeof(int)) != cudaSuccess ||

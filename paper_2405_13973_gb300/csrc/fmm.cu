@@ -111,7 +111,7 @@ struct Ion<float> {
 // P2M: one warp per leaf, lane m accumulates column m (n = m..p).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_p2m(int D, int p, int P, const LevelInfo* linfo,
+__global__ void __launch_bounds__(128) k_p2m(int D, int p, int ld, const LevelInfo* linfo,
                                              const int32_t* __restrict__ cstart,
                                              const int32_t* __restrict__ ccount,
                                              const typename Ion<T>::rec* __restrict__ sorted,
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(128) k_p2m(int D, int p, int P, const LevelInf
                     y1i = yi;
                 }
             }
-            T* out = M + (int64_t)g * P;
+            T* out = M + (int64_t)g * ld;
 #pragma unroll
             for (int n = 0; n <= kMaxOrder; ++n) {
                 if (n < m || n > p) continue;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(128) k_p2m(int D, int p, int P, const LevelInf
 //   Tt: [8][P][P] transposed (in-major) so that lanes read consecutively.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_m2m(int l, int P, const LevelInfo* linfo,
+__global__ void __launch_bounds__(128) k_m2m(int l, int P, int ld, const LevelInfo* linfo,
                                              const uint32_t* __restrict__ code,
                                              const int32_t* __restrict__ cid, int64_t off_child,
                                              const T* __restrict__ Tt, T* M) {
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128) k_m2m(int l, int P, const LevelInfo* linf
             const int gc = cid[off_child + ((c << 3) | o)];
             if (gc < 0) continue;
             __syncwarp();
-            for (int k = lane; k < P; k += 32) sM[k] = M[(int64_t)gc * P + k];
+            for (int k = lane; k < P; k += 32) sM[k] = M[(int64_t)gc * ld + k];
             __syncwarp();
             const T* To = Tt + (int64_t)o * P * P;
             for (int k = 0; k < P; ++k) {
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(128) k_m2m(int l, int P, const LevelInfo* linf
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             int row = lane + 32 * r;
-            if (row < P) M[(int64_t)g * P + row] = acc[r];
+            if (row < P) M[(int64_t)g * ld + row] = acc[r];
         }
     }
 }
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(128) k_m2m(int l, int P, const LevelInfo* linf
 constexpr int kRT = 64, kNT = 32, kKC = 16;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, const LevelInfo* linfo,
+__global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, int ld, const LevelInfo* linfo,
                                                   const uint32_t* __restrict__ code,
                                                   const int32_t* __restrict__ cid, int64_t off_l,
                                                   int64_t off_parent, const T* __restrict__ M,
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, const LevelInfo*
                         sz = iz - (opi % 7 - 3);
                     if (sx >= 0 && sx < lim && sy >= 0 && sy < lim && sz >= 0 && sz < lim) {
                         int gs = cid[off_l + morton3(sx, sy, sz)];
-                        if (gs >= 0) sp = M + (int64_t)gs * P;
+                        if (gs >= 0) sp = M + (int64_t)gs * ld;
                     }
                 }
                 src[tid] = sp;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, const LevelInfo*
                 const T* sp = nullptr;
                 if (tid < ntile) {
                     int gp = cid[off_parent + (code[base + tid] >> 3)];
-                    if (gp >= 0) sp = L + (int64_t)gp * P;
+                    if (gp >= 0) sp = L + (int64_t)gp * ld;
                 }
                 src[tid] = sp;
             }
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, const LevelInfo*
 #pragma unroll
         for (int jj = 0; jj < 2; ++jj) {
             int row = row0 + ty * 4 + i, j = tx * 2 + jj;
-            if (row < P && j < ntile) L[(int64_t)(base + j) * P + row] = acc[i][jj];
+            if (row < P && j < ntile) L[(int64_t)(base + j) * ld + row] = acc[i][jj];
         }
 }
 
@@ -361,7 +361,7 @@ __device__ __forceinline__ void kb_add(T& s, T& c, T v) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_far(
-    int64_t n, int D, int p, int P, int phases, const RootCube* root, const LevelInfo* linfo,
+    int64_t n, int D, int p, int ld, int phases, const RootCube* root, const LevelInfo* linfo,
     const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ leaf_of,
     const int32_t* __restrict__ perm, const uint32_t* __restrict__ code,
     const int32_t* __restrict__ cid_leaf, const int32_t* __restrict__ cstart,
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(128) k_near_far(
         if ((phases & PT_PHASE_FAR) && D >= 2) {
             T fphi, gx, gy, gz, ux, uy, uz, uq;
             Ion<T>::get(me, ux, uy, uz, uq);
-            l2p_eval<T>(p, L + (int64_t)g * P, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
+            l2p_eval<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
             ex = -gx;
             ey = -gy;
             ez = -gz;
@@ -447,30 +447,36 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         int leaves_max = (int)(n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D)));
         int grid = (leaves_max + 3) / 4;
         if (grid > 152 * 16) grid = 152 * 16;
-        k_p2m<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(D, p, P, ws.linfo, ws.cstart, ws.ccount,
+        k_p2m<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount,
                                                      (const typename Ion<T>::rec*)ws.sorted, M);
         for (int l = D - 1; l >= 2; --l) {
             int64_t cl = (int64_t)1 << (3 * l);
             int cells = (int)(n < cl ? n : cl);
             int g = (cells + 3) / 4;
             if (g > 152 * 16) g = 152 * 16;
-            k_m2m<T><<<g, 128, 4 * P * sizeof(T), s>>>(l, P, ws.linfo, ws.code, ws.cid,
+            k_m2m<T><<<g, 128, 4 * P * sizeof(T), s>>>(l, P, ws.ld, ws.linfo, ws.code, ws.cid,
                                                        dl.off[l + 1], (const T*)ws.T_m2m, M);
         }
     }
     if (ev && (e = cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
-    if (far) {
+    if (far && use_tc) {
+        // one launch for every level's M2L; splits fill the SMs on small trees
+        int64_t tiles = 0;
         for (int l = 2; l <= D; ++l) {
-            if (use_tc) {
-                e = launch_m2l_tc(l, D, ws, s);
-                if (e != cudaSuccess) return e;
-                continue;
-            }
+            int64_t cl = (int64_t)1 << (3 * l);
+            tiles += ((n < cl ? n : cl) + 127) / 128 + 8;
+        }
+        int splits = (int)((2 * 152 + tiles - 1) / tiles);
+        if (splits < 1) splits = 1;
+        if (splits > ws.tc_splits_max) splits = ws.tc_splits_max;
+        if ((e = launch_m2l_tc_all(n, D, ws, splits, s)) != cudaSuccess) return e;
+    } else if (far) {
+        for (int l = 2; l <= D; ++l) {
             int64_t cl = (int64_t)1 << (3 * l);
             int cells = (int)(n < cl ? n : cl);
             dim3 grid((cells + kNT - 1) / kNT + 8, (P + kRT - 1) / kRT);
-            k_m2l_simt<T><<<grid, 256, 0, s>>>(l, P, ws.linfo, ws.code, ws.cid, dl.off[l],
+            k_m2l_simt<T><<<grid, 256, 0, s>>>(l, P, ws.ld, ws.linfo, ws.code, ws.cid, dl.off[l],
                                                l >= 3 ? dl.off[l - 1] : 0, M, L,
                                                (const T*)ws.T_m2l, (const T*)ws.T_l2l);
         }
@@ -480,7 +486,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     int grid = (int)((n + 127) / 128);
     if (grid > 152 * 16) grid = 152 * 16;
     k_near_far<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(
-        n, D, p, P, phases, ws.root, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
+        n, D, p, ws.ld, phases, ws.root, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
         ws.leaf_of, ws.perm, ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount, L, E, phi);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)

@@ -42,6 +42,7 @@ struct Workspace {
     int64_t n_max = 0;
     int depth_max = 0;
     int p = 0, P = 0;
+    int ld = 0;                 // row stride of M and L (P for FP64, P rounded up to 32 for FP32)
     bool fp64 = true;
     int64_t cells_max = 0;      // capacity of the compact cell arrays
     int64_t dense_max = 0;      // capacity of the concatenated dense maps
@@ -60,8 +61,8 @@ struct Workspace {
     int32_t* cstart = nullptr;     // [cells_max] first slot of a leaf
     int32_t* ccount = nullptr;     // [cells_max] ions in a leaf
     LevelInfo* linfo = nullptr;    // level bookkeeping (device)
-    void* M = nullptr;             // [cells_max][P] multipole coefficients
-    void* L = nullptr;             // [cells_max][P] local coefficients
+    void* M = nullptr;             // [cells_max][ld] multipole coefficients (padding zero)
+    void* L = nullptr;             // [cells_max][ld] local coefficients
     double* E = nullptr;           // [3n] Coulomb field of the last evaluation (SoA, SI)
     int32_t* block_sums = nullptr; // scan scratch
     int64_t block_sums_cap = 0;
@@ -79,6 +80,9 @@ struct Workspace {
     void* T_l2l = nullptr;   // [8][P][P]
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
     float* T_m2l_tc = nullptr;  // tensor-core operand tiles (mixed mode)
+    float* T_l2l_t = nullptr;   // [8][P][P] L2L transposed, FP32 (mixed mode)
+    float* tc_part = nullptr;   // [tc_splits_max - 1][cells_max][ld] M2L split partials
+    int tc_splits_max = 1;
 };
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
@@ -116,8 +120,14 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
 
 // ---- tensor-core M2L (m2l_tc.cu) ---------------------------------------------
 cudaError_t launch_m2l_tc(int level, int D, Workspace& ws, cudaStream_t s);
-size_t m2l_tc_operand_bytes(int p);
+// M2L of every level on the tensor cores, then per level the split partials
+// and the L2L shift of the parent (so L is complete on return).
+cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s);
+cudaError_t m2l_tc_init();
+size_t m2l_tc_operand_bytes(int p);   // 0 if the order is not supported
+size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
 void m2l_tc_pack_operands(int p, const double* T_m2l_host, const double* T_l2l_host, float* out);
+void host_m2l_offsets(int16_t out[8][189]);
 
 // ---- push (push.cu) ----------------------------------------------------------
 struct PushParams {

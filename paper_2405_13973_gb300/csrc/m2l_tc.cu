@@ -1,13 +1,539 @@
-// m2l_tc.cu -- M2L on the tensor cores (placeholder until the tcgen05 kernel
-// lands: reports the mode as unsupported).
+// m2l_tc.cu -- M2L (Eq. FMM_local) on the 5th-generation tensor cores.
+//
+// Problem: for every target cell t of level l >= 2 and each of the 189
+// source offsets o of its octant, L_t += T_o M_{t-o} (Sec. 2.3.2: the
+// children of the parent's neighbours that are not neighbours of t).  Cells
+// of one (level, octant) share the 189 operators, so a tile of 128 such
+// targets is, per offset, one dense product
+//     D[128 x N] += A[128 x K] * B[K x N],
+//     A row r = M of the source of target r (gathered; zero if empty),
+//     B = T_o^T (K = input coefficients, N = output coefficients).
+//
+// Precision (3xTF32): every FP32 operand x is split into hi = rna_tf32(x) and
+// lo = rna_tf32(x - hi); D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in
+// FP32 in tensor memory, which reproduces FP32 products to about 2^-21.
+//
+// Data movement: the operators are split and laid out on the host in the
+// 128-byte-swizzled K-major shared-memory image of each 32-wide K chunk, so
+// one cp.async.bulk per (offset, chunk) brings B_hi and B_lo.  A rows are
+// gathered by all threads, split and stored into the same swizzled layout.
+// Two stages: the loads of chunk i+1 overlap the MMAs of chunk i.  One
+// thread issues tcgen05.mma (M = 128, N = P rounded up to 16, K = 8 per
+// instruction) and commits to an mbarrier per stage.
+//
+// Parallelism: one launch covers every level; the 189 offsets of a tile are
+// split S ways across CTAs.  Split 0 writes L; splits 1.. write partial
+// buffers that k_l2l_reduce adds, level by level, together with the L2L shift
+// of the parent's local expansion.
+//
+// Every wait on an mbarrier is bounded: on expiry the CTA records
+// ERR_TIMEOUT, stops issuing, waits (bounded) for its own work in flight,
+// frees its tensor memory and returns.
 #include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
 
+#include <cmath>
+
+#include "harmonics.cuh"
 #include "internal.h"
 
 namespace pt {
 
-size_t m2l_tc_operand_bytes(int) { return 0; }
-void m2l_tc_pack_operands(int, const double*, const double*, float*) {}
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;
+constexpr int kMaxSplits = 8;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+struct TcGeom {
+    int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0;
+    int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0;
+};
+
+TcGeom tc_geom(int p) {
+    TcGeom g;
+    g.P = (p + 1) * (p + 1);
+    g.Kpad = ((g.P + 31) / 32) * 32;
+    g.Npad = ((g.P + 15) / 16) * 16;
+    g.kchunks = g.Kpad / 32;
+    g.tmem_cols = g.Npad <= 128 ? 128 : 256;
+    g.a_bytes = kTcRows * 128;      // one of A_hi / A_lo for a 32-wide chunk
+    g.b_bytes = g.Npad * 128;       // one of B_hi / B_lo
+    g.stage_bytes = 2 * g.a_bytes + 2 * g.b_bytes;
+    g.smem_bytes = 2 * g.stage_bytes + 1024;
+    return g;
+}
+
+bool tc_supported(int p) { return tc_geom(p).Npad <= 256; }
+
+// byte offset of element (row, k) of a 32-wide chunk in the 128B-swizzled
+// K-major layout: 8-row atoms of 1024 B, 16-byte units XOR-ed with row % 8.
+inline size_t swz_off(int row, int k) {
+    return (size_t)(row >> 3) * 1024 + (size_t)(row & 7) * 128 +
+           (size_t)(((k >> 2) ^ (row & 7)) << 4) + (size_t)(k & 3) * 4;
+}
+
+inline float rna_tf32_host(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    if ((b & 0x7F800000u) != 0x7F800000u) b = (b + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &b, 4);
+    return r;
+}
+
+__constant__ int16_t c_tc_off[8][189];
+
+// ---- PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait (2 s of %globaltimer); false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t rna_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 B apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;             // version
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+// instruction descriptor: D f32, A and B tf32, both K-major, N and M
+__host__ __device__ constexpr uint32_t idesc_tf32(int N, int M) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+    int D, P, ld, kchunks, Npad, tmem_cols, splits;
+    uint32_t idesc;
+    const LevelInfo* linfo;
+    const uint32_t* code;
+    const int32_t* cid;
+    int64_t off[kMaxDepth + 2];
+    const float* M;
+    float* L;
+    float* part;           // [splits-1][cells][ld]
+    int64_t part_stride;   // cells_max * ld
+    const float* ops;      // [343][kchunks][2][Npad][32] swizzled
+    int* err;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t full_bar[2], done_bar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int srow[kTcRows];
+    __shared__ int t_level, t_oct, t_base, t_rows, t_split, abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    const int a_bytes = kTcRows * 128, b_bytes = a.Npad * 128;
+    const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+
+    if (tid == 0) {
+        // which (level, octant, tile, split) is this CTA?
+        const int split = blockIdx.x % a.splits;
+        int t = blockIdx.x / a.splits, acc = 0;
+        t_rows = 0;
+        for (int l = 2; l <= a.D && t_rows == 0; ++l)
+            for (int o = 0; o < 8; ++o) {
+                int s0 = a.linfo->oct_start[l][o], s1 = a.linfo->oct_start[l][o + 1];
+                int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
+                if (t < acc + nt) {
+                    t_level = l;
+                    t_oct = o;
+                    t_base = s0 + (t - acc) * kTcRows;
+                    t_rows = min(kTcRows, s1 - t_base);
+                    break;
+                }
+                acc += nt;
+            }
+        t_split = split;
+        abort_sh = 0;
+    }
+    __syncthreads();
+    if (t_rows <= 0) return;
+    const int l = t_level, oct = t_oct, tbase = t_base, rows = t_rows, split = t_split;
+
+    if (tid == 0) {
+        mbar_init(&full_bar[0], 1);
+        mbar_init(&full_bar[1], 1);
+        mbar_init(&done_bar[0], 1);
+        mbar_init(&done_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_base_sh)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    // target coordinates of this thread's row (rows 0..127 by threads 0..127)
+    int tix = 0, tiy = 0, tiz = 0;
+    if (tid < kTcRows && tid < rows) demorton3(a.code[tbase + tid], tix, tiy, tiz);
+    const int lim = 1 << l;
+    const int t0 = (189 * split) / a.splits, t1 = (189 * (split + 1)) / a.splits;
+    int it = 0;  // chunks issued
+    int copy_pending = -1;  // (thread 0) stage whose bulk copy has not been waited for
+    uint32_t copy_parity = 0;
+    bool ok = true;
+
+    for (int term = t0; term < t1 && ok; ++term) {
+        const int opi = c_tc_off[oct][term];
+        if (tid < kTcRows) {
+            int g = -1;
+            if (tid < rows) {
+                int sx = tix - (opi / 49 - 3), sy = tiy - ((opi / 7) % 7 - 3),
+                    sz = tiz - (opi % 7 - 3);
+                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                    g = a.cid[a.off[l] + morton3(sx, sy, sz)];
+            }
+            srow[tid] = g;
+        }
+        const int any = __syncthreads_or(tid < kTcRows && srow[tid] >= 0);
+        if (!any) continue;
+        for (int kc = 0; kc < a.kchunks; ++kc) {
+            const int st = it & 1, use = it >> 1;
+            unsigned char* sA_hi = base + st * stage_bytes;
+            unsigned char* sA_lo = sA_hi + a_bytes;
+            unsigned char* sB = sA_lo + a_bytes;  // B_hi then B_lo
+            if (tid == 0) {
+                if (it >= 2 && !mbar_wait(&done_bar[st], (use - 1) & 1)) abort_sh = 1;
+                if (!abort_sh) {
+                    mbar_arrive_expect_tx(&full_bar[st], 2 * b_bytes);
+                    const float* src = a.ops + ((size_t)opi * a.kchunks + kc) * 2 * a.Npad * 32;
+                    bulk_g2s(sB, src, 2 * b_bytes, &full_bar[st]);
+                    copy_pending = st;
+                    copy_parity = use & 1;
+                }
+            }
+            __syncthreads();  // stage free (its previous MMAs done) for everyone
+            if (abort_sh) {
+                ok = false;
+                break;
+            }
+            // gather + split the A chunk
+            for (int idx = tid; idx < kTcRows * 8; idx += kTcThreads) {
+                const int r = idx >> 3, c = idx & 7;
+                const int g = srow[r];
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g >= 0) v = *reinterpret_cast<const float4*>(a.M + (int64_t)g * a.ld + kc * 32 + c * 4);
+                uint4 hi, lo;
+                hi.x = rna_tf32(v.x); lo.x = rna_tf32(v.x - __uint_as_float(hi.x));
+                hi.y = rna_tf32(v.y); lo.y = rna_tf32(v.y - __uint_as_float(hi.y));
+                hi.z = rna_tf32(v.z); lo.z = rna_tf32(v.z - __uint_as_float(hi.z));
+                hi.w = rna_tf32(v.w); lo.w = rna_tf32(v.w - __uint_as_float(hi.w));
+                const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((c ^ (r & 7))) << 4);
+                *reinterpret_cast<uint4*>(sA_hi + off) = hi;
+                *reinterpret_cast<uint4*>(sA_lo + off) = lo;
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                if (!mbar_wait(&full_bar[st], use & 1)) {
+                    abort_sh = 1;
+                } else {
+                    copy_pending = -1;
+                    tc_fence_after();
+                    const uint32_t ah = smem_addr(sA_hi), al = smem_addr(sA_lo);
+                    const uint32_t bh = smem_addr(sB), bl = bh + b_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                        mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
+                        mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, 1u);
+                        mma_tf32(tmem, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                    }
+                    mma_commit(&done_bar[st]);
+                }
+            }
+            ++it;
+        }
+    }
+    __syncthreads();
+    if (abort_sh) ok = false;
+    // wait for the last committed MMAs (bounded), then read the accumulator
+    if (tid == 0 && it > 0) {
+        const int st = (it - 1) & 1, use = (it - 1) >> 1;
+        if (!mbar_wait(&done_bar[st], use & 1)) abort_sh = 2;
+        if (it > 1) {  // the other stage's last commit as well
+            const int st2 = (it - 2) & 1, use2 = (it - 2) >> 1;
+            if (!mbar_wait(&done_bar[st2], use2 & 1)) abort_sh = 2;
+        }
+    }
+    // on abort: one more bounded wait for a bulk copy still in flight
+    if (tid == 0 && abort_sh && copy_pending >= 0) mbar_wait(&full_bar[copy_pending], copy_parity);
+    __syncthreads();
+    tc_fence_after();
+    if (abort_sh) {
+        if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+        ok = false;
+    }
+    float* out = split == 0 ? a.L : a.part + (int64_t)(split - 1) * a.part_stride;
+    if (ok) {
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = quad * 32 + lane;
+        const int g = tbase + row;
+        for (int cb = half; cb * 16 < a.Npad; cb += 2) {
+            uint32_t r[16];
+            if (it > 0) {
+                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), r);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r[j] = 0u;
+            }
+            if (row < rows) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = cb * 16 + j;
+                    if (col < a.P) out[(int64_t)g * a.ld + col] = __uint_as_float(r[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(a.tmem_cols)
+                     : "memory");
+}
+
+// L(l) += sum of the split partials + L2L shift of the parent's L (l >= 3).
+// One warp per cell, lanes over output coefficients; Tt = L2L transposed.
+__global__ void __launch_bounds__(128) k_l2l_reduce(int l, int P, int ld, int nparts,
+                                                    const LevelInfo* linfo,
+                                                    const uint32_t* __restrict__ code,
+                                                    const int32_t* __restrict__ cid,
+                                                    int64_t off_parent, const float* __restrict__ part,
+                                                    int64_t part_stride,
+                                                    const float* __restrict__ Tt, float* L) {
+    extern __shared__ float sL[];
+    float* sp = sL + (threadIdx.x >> 5) * P;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int g0 = linfo->gbase[l], g1 = linfo->gbase[l + 1];
+    constexpr int R = ((kMaxOrder + 1) * (kMaxOrder + 1) + 31) / 32;
+    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            float v = 0.f;
+            if (row < P) {
+                v = L[(int64_t)g * ld + row];
+                for (int s = 0; s < nparts; ++s) v += part[s * part_stride + (int64_t)g * ld + row];
+            }
+            acc[r] = v;
+        }
+        if (l >= 3) {
+            const uint32_t c = code[g];
+            const int gp = cid[off_parent + (c >> 3)];
+            __syncwarp();
+            for (int k = lane; k < P; k += 32) sp[k] = L[(int64_t)gp * ld + k];
+            __syncwarp();
+            const float* To = Tt + (int64_t)(c & 7) * P * P;
+            for (int k = 0; k < P; ++k) {
+                const float lk = sp[k];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int row = lane + 32 * r;
+                    if (row < P) acc[r] += To[(int64_t)k * P + row] * lk;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = lane + 32 * r;
+            if (row < P) L[(int64_t)g * ld + row] = acc[r];
+        }
+    }
+}
+
+}  // namespace
+
+void host_m2l_offsets(int16_t out[8][189]);
+
+size_t m2l_tc_operand_bytes(int p) {
+    if (!tc_supported(p)) return 0;
+    TcGeom g = tc_geom(p);
+    return (size_t)343 * g.kchunks * 2 * g.Npad * 32 * sizeof(float);
+}
+
+size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
+    const double budget = 512.0 * 1024 * 1024;
+    double per = (double)cells_max * ld * sizeof(float);
+    int s = 1 + (int)(budget / per);
+    if (s > kMaxSplits) s = kMaxSplits;
+    (void)p;
+    return (size_t)s;
+}
+
+void m2l_tc_pack_operands(int p, const double* T_m2l, const double* /*T_l2l*/, float* out) {
+    TcGeom g = tc_geom(p);
+    const int P = g.P;
+    const size_t tile = (size_t)g.Npad * 32;  // floats per hi (or lo) tile
+    for (int opi = 0; opi < 343; ++opi)
+        for (int kc = 0; kc < g.kchunks; ++kc) {
+            float* hi = out + ((size_t)opi * g.kchunks + kc) * 2 * tile;
+            float* lo = hi + tile;
+            for (int n = 0; n < g.Npad; ++n)
+                for (int k = 0; k < 32; ++k) {
+                    const int kk = kc * 32 + k;
+                    float v = (n < P && kk < P) ? (float)T_m2l[(size_t)opi * P * P + (size_t)n * P + kk]
+                                                : 0.0f;
+                    float h = rna_tf32_host(v);
+                    float r = rna_tf32_host(v - h);
+                    const size_t o = swz_off(n, k) / 4;
+                    hi[o] = h;
+                    lo[o] = r;
+                }
+        }
+}
+
+cudaError_t m2l_tc_init() {
+    static int16_t off[8][189];
+    host_m2l_offsets(off);
+    cudaError_t e = cudaMemcpyToSymbol(c_tc_off, off, sizeof off);
+    if (e != cudaSuccess) return e;
+    // largest supported order: N = 256 columns
+    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc_geom(15).smem_bytes);
+}
+
+cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    TcGeom g = tc_geom(ws.p);
+    TcArgs a;
+    memset(&a, 0, sizeof a);
+    a.D = D;
+    a.P = g.P;
+    a.ld = ws.ld;
+    a.kchunks = g.kchunks;
+    a.Npad = g.Npad;
+    a.tmem_cols = g.tmem_cols;
+    a.splits = splits;
+    a.idesc = idesc_tf32(g.Npad, kTcRows);
+    a.linfo = ws.linfo;
+    a.code = ws.code;
+    a.cid = ws.cid;
+    DenseLayout dl = dense_layout(D);
+    for (int l = 0; l < kMaxDepth + 2; ++l) a.off[l] = dl.off[l];
+    a.M = (const float*)ws.M;
+    a.L = (float*)ws.L;
+    a.part = ws.tc_part;
+    a.part_stride = ws.cells_max * ws.ld;
+    a.ops = ws.T_m2l_tc;
+    a.err = ws.err;
+    int64_t tiles = 0;
+    for (int l = 2; l <= D; ++l) {
+        int64_t cl = (int64_t)1 << (3 * l);
+        int64_t cells = n < cl ? n : cl;
+        tiles += (cells + kTcRows - 1) / kTcRows + 8;
+    }
+    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, g.smem_bytes, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int l = 2; l <= D; ++l) {
+        int64_t cl = (int64_t)1 << (3 * l);
+        int cells = (int)(n < cl ? n : cl);
+        int grid = (cells + 3) / 4;
+        if (grid > 152 * 16) grid = 152 * 16;
+        k_l2l_reduce<<<grid, 128, 4 * g.P * sizeof(float), s>>>(
+            l, g.P, ws.ld, splits - 1, ws.linfo, ws.code, ws.cid, l >= 3 ? dl.off[l - 1] : 0,
+            ws.tc_part, ws.cells_max * ws.ld, ws.T_l2l_t, (float*)ws.L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_m2l_tc(int, int, Workspace&, cudaStream_t) { return cudaErrorNotSupported; }
 
 }  // namespace pt
