@@ -108,11 +108,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def launches_per_step(depth: int) -> int:
+def launches_per_step(depth: int, precision: str) -> int:
     # drift+cube, keys, 3 scan, scatter, 3 scan, leaf gather, near_far, kick
     k = 11
     if depth >= 2:
-        k += 1 + (depth - 2) + (depth - 1)   # P2M, M2M levels, M2L levels
+        k += 1 + (depth - 2)                 # P2M, M2M per level
+        if precision == "tf32x3":
+            k += 1 + (depth - 1)             # one M2L launch, L2L per level
+        else:
+            k += depth - 1                   # M2L (+ folded L2L) per level
     return k
 
 
@@ -306,7 +310,7 @@ def main():
                       "depth": depth, "n": n, "l2": "flushed between timed steps (512 MiB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "force_err": ferr, "stats": stats, "roofline": roof, "clocks": clk,
-           "gpu_launches": launches_per_step(depth) * args.steps,
+           "gpu_launches": launches_per_step(depth, args.precision) * args.steps,
            "wall_s_timed_region": t_wall}
 
     # the plain FP64 GPU path beside it (same workload, fewer steps)

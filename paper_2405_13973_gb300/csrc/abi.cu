@@ -144,16 +144,9 @@ int build_operators(fmm_plan_s* pl) {
     if (e != cudaSuccess) return status_from(e);
     if (pl->precision == PT_MIXED_TF32X3) {
         std::vector<float> packed(m2l_tc_operand_bytes(p) / sizeof(float));
-        m2l_tc_pack_operands(p, m2l.data(), l2l.data(), packed.data());
+        m2l_tc_pack_operands(p, m2l.data(), m2m.data(), l2l.data(), packed.data());
         e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size() * sizeof(float),
                        cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return status_from(e);
-        std::vector<float> lt((size_t)8 * P * P);
-        for (int o = 0; o < 8; ++o)
-            for (int r = 0; r < P; ++r)
-                for (int c = 0; c < P; ++c)
-                    lt[(size_t)o * P * P + (size_t)c * P + r] = (float)l2l[(size_t)o * P * P + (size_t)r * P + c];
-        e = cudaMemcpy(pl->ws.T_l2l_t, lt.data(), lt.size() * sizeof(float), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return status_from(e);
     }
     return PT_OK;
@@ -426,7 +419,6 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     if (ok && precision == PT_MIXED_TF32X3) {
         ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
         ok = dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p)) &&
-             dalloc(pl, ws.T_l2l_t, sizeof(float) * 8 * PP) &&
              dalloc(pl, ws.tc_part, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) *
                                         cells * ws.ld);
     }

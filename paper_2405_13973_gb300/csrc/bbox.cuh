@@ -51,16 +51,33 @@ __device__ __forceinline__ bool bbox_block_and_finalise(double mn[3], double mx[
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return false;
+    if (!last) return false;
     __threadfence();
+    // the last block combines every block's partial, all threads in parallel
     double u[3], v[3];
     int b = 0;
     for (int a = 0; a < 3; ++a) { u[a] = INFINITY; v[a] = -INFINITY; }
-    for (unsigned k = 0; k < gridDim.x; ++k) {
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
         const volatile double* pp = partial + k * 8;
         for (int a = 0; a < 3; ++a) { u[a] = fmin(u[a], pp[a]); v[a] = fmax(v[a], pp[3 + a]); }
         b |= (pp[6] != 0.0);
     }
+    for (int a = 0; a < 3; ++a) {
+        double a0 = warp_min(u[a]), a1 = warp_max(v[a]);
+        if (lane == 0) { smn[a][wid] = a0; smx[a][wid] = a1; }
+    }
+    int wb2 = __any_sync(0xffffffffu, b);
+    __syncthreads();
+    if (lane == 0) sbad[wid] = wb2;
+    __syncthreads();
+    if (threadIdx.x != 0) return false;
+    for (int a = 0; a < 3; ++a) {
+        u[a] = smn[a][0];
+        v[a] = smx[a][0];
+        for (int w = 1; w < nw; ++w) { u[a] = fmin(u[a], smn[a][w]); v[a] = fmax(v[a], smx[a][w]); }
+    }
+    b = 0;
+    for (int w = 0; w < nw; ++w) b |= sbad[w];
     double side = 0.0;
     for (int a = 0; a < 3; ++a) {
         double e = __dsub_rn(v[a], u[a]);

@@ -450,6 +450,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         k_p2m<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount,
                                                      (const typename Ion<T>::rec*)ws.sorted, M);
         for (int l = D - 1; l >= 2; --l) {
+            if (use_tc) {
+                if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
+                continue;
+            }
             int64_t cl = (int64_t)1 << (3 * l);
             int cells = (int)(n < cl ? n : cl);
             int g = (cells + 3) / 4;

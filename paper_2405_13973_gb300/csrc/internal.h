@@ -80,7 +80,6 @@ struct Workspace {
     void* T_l2l = nullptr;   // [8][P][P]
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
     float* T_m2l_tc = nullptr;  // tensor-core operand tiles (mixed mode)
-    float* T_l2l_t = nullptr;   // [8][P][P] L2L transposed, FP32 (mixed mode)
     float* tc_part = nullptr;   // [tc_splits_max - 1][cells_max][ld] M2L split partials
     int tc_splits_max = 1;
 };
@@ -126,7 +125,10 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
-void m2l_tc_pack_operands(int p, const double* T_m2l_host, const double* T_l2l_host, float* out);
+void m2l_tc_pack_operands(int p, const double* T_m2l, const double* T_m2m, const double* T_l2l,
+                          float* out);
+// M2M of one level (targets = parents at level l) on the tensor cores.
+cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s);
 void host_m2l_offsets(int16_t out[8][189]);
 
 // ---- push (push.cu) ----------------------------------------------------------

@@ -21,10 +21,15 @@
 // thread issues tcgen05.mma (M = 128, N = P rounded up to 16, K = 8 per
 // instruction) and commits to an mbarrier per stage.
 //
-// Parallelism: one launch covers every level; the 189 offsets of a tile are
-// split S ways across CTAs.  Split 0 writes L; splits 1.. write partial
-// buffers that k_l2l_reduce adds, level by level, together with the L2L shift
-// of the parent's local expansion.
+// The same gathered product serves the two other dense translations:
+//   M2M (upward pass): a tile of parents, 8 terms (child octants), A = the
+//     children's M, B = the octant's M2M operator;
+//   L2L (downward pass): a tile of children of one octant, 1 term, A = the
+//     parent's L, B = the octant's L2L operator, and the epilogue adds the
+//     child's own M2L result (and the split partials).
+// Parallelism: one M2L launch covers every level; the 189 offsets of a tile
+// are split S ways across CTAs.  Split 0 writes L; splits 1.. write partial
+// buffers that the L2L launches add, level by level.
 //
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // ERR_TIMEOUT, stops issuing, waits (bounded) for its own work in flight,
@@ -183,7 +188,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2 };
+constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator indices
+
 struct TcArgs {
+    int mode, level;      // level: the target level of M2M / L2L launches
     int D, P, ld, kchunks, Npad, tmem_cols, splits;
     uint32_t idesc;
     const LevelInfo* linfo;
@@ -192,6 +201,7 @@ struct TcArgs {
     int64_t off[kMaxDepth + 2];
     const float* M;
     float* L;
+    float* Mout;           // M2M output (= M, other level)
     float* part;           // [splits-1][cells][ld]
     int64_t part_stride;   // cells_max * ld
     const float* ops;      // [343][kchunks][2][Npad][32] swizzled
@@ -212,12 +222,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
 
     if (tid == 0) {
         // which (level, octant, tile, split) is this CTA?
-        const int split = blockIdx.x % a.splits;
-        int t = blockIdx.x / a.splits, acc = 0;
+        const int gsplit = a.mode == MODE_M2L ? a.splits : 1;  // CTAs per tile
+        const int split = blockIdx.x % gsplit;
+        int t = blockIdx.x / gsplit, acc = 0;
         t_rows = 0;
-        for (int l = 2; l <= a.D && t_rows == 0; ++l)
-            for (int o = 0; o < 8; ++o) {
-                int s0 = a.linfo->oct_start[l][o], s1 = a.linfo->oct_start[l][o + 1];
+        const int lfirst = a.mode == MODE_M2L ? 2 : a.level;
+        const int llast = a.mode == MODE_M2L ? a.D : a.level;
+        const int ngroups = a.mode == MODE_M2M ? 1 : 8;
+        for (int l = lfirst; l <= llast && t_rows == 0; ++l)
+            for (int o = 0; o < ngroups; ++o) {
+                int s0, s1;
+                if (a.mode == MODE_M2M) {
+                    s0 = a.linfo->gbase[l];
+                    s1 = a.linfo->gbase[l + 1];
+                } else {
+                    s0 = a.linfo->oct_start[l][o];
+                    s1 = a.linfo->oct_start[l][o + 1];
+                }
                 int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
                 if (t < acc + nt) {
                     t_level = l;
@@ -254,25 +275,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    // target coordinates of this thread's row (rows 0..127 by threads 0..127)
+    // target coordinates and code of this thread's row (rows 0..127 by threads 0..127)
     int tix = 0, tiy = 0, tiz = 0;
-    if (tid < kTcRows && tid < rows) demorton3(a.code[tbase + tid], tix, tiy, tiz);
+    uint32_t tcode = 0;
+    if (tid < kTcRows && tid < rows) {
+        tcode = a.code[tbase + tid];
+        demorton3(tcode, tix, tiy, tiz);
+    }
     const int lim = 1 << l;
-    const int t0 = (189 * split) / a.splits, t1 = (189 * (split + 1)) / a.splits;
+    int t0 = 0, t1 = 0;
+    if (a.mode == MODE_M2L) {
+        t0 = (189 * split) / a.splits;
+        t1 = (189 * (split + 1)) / a.splits;
+    } else if (a.mode == MODE_M2M) {
+        t1 = 8;
+    } else {
+        t1 = l >= 3 ? 1 : 0;
+    }
+    const float* src_base = a.mode == MODE_L2L ? a.L : a.M;
     int it = 0;  // chunks issued
     int copy_pending = -1;  // (thread 0) stage whose bulk copy has not been waited for
     uint32_t copy_parity = 0;
     bool ok = true;
 
     for (int term = t0; term < t1 && ok; ++term) {
-        const int opi = c_tc_off[oct][term];
+        int opi;
+        if (a.mode == MODE_M2L) opi = c_tc_off[oct][term];
+        else if (a.mode == MODE_M2M) opi = kOpM2M + term;
+        else opi = kOpL2L + oct;
         if (tid < kTcRows) {
             int g = -1;
             if (tid < rows) {
-                int sx = tix - (opi / 49 - 3), sy = tiy - ((opi / 7) % 7 - 3),
-                    sz = tiz - (opi % 7 - 3);
-                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
-                    g = a.cid[a.off[l] + morton3(sx, sy, sz)];
+                if (a.mode == MODE_M2L) {
+                    int sx = tix - (opi / 49 - 3), sy = tiy - ((opi / 7) % 7 - 3),
+                        sz = tiz - (opi % 7 - 3);
+                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                        g = a.cid[a.off[l] + morton3(sx, sy, sz)];
+                } else if (a.mode == MODE_M2M) {
+                    g = a.cid[a.off[l + 1] + ((tcode << 3) | (uint32_t)term)];
+                } else {
+                    g = a.cid[a.off[l - 1] + (tcode >> 3)];
+                }
             }
             srow[tid] = g;
         }
@@ -303,7 +346,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 const int r = idx >> 3, c = idx & 7;
                 const int g = srow[r];
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g >= 0) v = *reinterpret_cast<const float4*>(a.M + (int64_t)g * a.ld + kc * 32 + c * 4);
+                if (g >= 0) v = *reinterpret_cast<const float4*>(src_base + (int64_t)g * a.ld + kc * 32 + c * 4);
                 uint4 hi, lo;
                 hi.x = rna_tf32(v.x); lo.x = rna_tf32(v.x - __uint_as_float(hi.x));
                 hi.y = rna_tf32(v.y); lo.y = rna_tf32(v.y - __uint_as_float(hi.y));
@@ -355,7 +398,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
         ok = false;
     }
-    float* out = split == 0 ? a.L : a.part + (int64_t)(split - 1) * a.part_stride;
+    float* out;
+    if (a.mode == MODE_M2M) out = a.Mout;
+    else if (a.mode == MODE_L2L || split == 0) out = a.L;
+    else out = a.part + (int64_t)(split - 1) * a.part_stride;
     if (ok) {
         const int quad = warp & 3, half = warp >> 2;
         const int row = quad * 32 + lane;
@@ -372,7 +418,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = cb * 16 + j;
-                    if (col < a.P) out[(int64_t)g * a.ld + col] = __uint_as_float(r[j]);
+                    if (col >= a.P) continue;
+                    const int64_t o = (int64_t)g * a.ld + col;
+                    float v = __uint_as_float(r[j]);
+                    if (a.mode == MODE_L2L) {
+                        v += a.L[o];  // this cell's own M2L result (split 0)
+                        for (int sp = 0; sp + 1 < a.splits; ++sp) v += a.part[sp * a.part_stride + o];
+                    }
+                    out[o] = v;
                 }
             }
         }
@@ -386,57 +439,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                      : "memory");
 }
 
-// L(l) += sum of the split partials + L2L shift of the parent's L (l >= 3).
-// One warp per cell, lanes over output coefficients; Tt = L2L transposed.
-__global__ void __launch_bounds__(128) k_l2l_reduce(int l, int P, int ld, int nparts,
-                                                    const LevelInfo* linfo,
-                                                    const uint32_t* __restrict__ code,
-                                                    const int32_t* __restrict__ cid,
-                                                    int64_t off_parent, const float* __restrict__ part,
-                                                    int64_t part_stride,
-                                                    const float* __restrict__ Tt, float* L) {
-    extern __shared__ float sL[];
-    float* sp = sL + (threadIdx.x >> 5) * P;
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    const int g0 = linfo->gbase[l], g1 = linfo->gbase[l + 1];
-    constexpr int R = ((kMaxOrder + 1) * (kMaxOrder + 1) + 31) / 32;
-    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
-        float acc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int row = lane + 32 * r;
-            float v = 0.f;
-            if (row < P) {
-                v = L[(int64_t)g * ld + row];
-                for (int s = 0; s < nparts; ++s) v += part[s * part_stride + (int64_t)g * ld + row];
-            }
-            acc[r] = v;
-        }
-        if (l >= 3) {
-            const uint32_t c = code[g];
-            const int gp = cid[off_parent + (c >> 3)];
-            __syncwarp();
-            for (int k = lane; k < P; k += 32) sp[k] = L[(int64_t)gp * ld + k];
-            __syncwarp();
-            const float* To = Tt + (int64_t)(c & 7) * P * P;
-            for (int k = 0; k < P; ++k) {
-                const float lk = sp[k];
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int row = lane + 32 * r;
-                    if (row < P) acc[r] += To[(int64_t)k * P + row] * lk;
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int row = lane + 32 * r;
-            if (row < P) L[(int64_t)g * ld + row] = acc[r];
-        }
-    }
-}
-
 }  // namespace
 
 void host_m2l_offsets(int16_t out[8][189]);
@@ -444,7 +446,7 @@ void host_m2l_offsets(int16_t out[8][189]);
 size_t m2l_tc_operand_bytes(int p) {
     if (!tc_supported(p)) return 0;
     TcGeom g = tc_geom(p);
-    return (size_t)343 * g.kchunks * 2 * g.Npad * 32 * sizeof(float);
+    return (size_t)kNumOps * g.kchunks * 2 * g.Npad * 32 * sizeof(float);
 }
 
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
@@ -456,26 +458,34 @@ size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
     return (size_t)s;
 }
 
-void m2l_tc_pack_operands(int p, const double* T_m2l, const double* /*T_l2l*/, float* out) {
+// Operators 0..342: M2L by offset index; 343..350: M2M by child octant;
+// 351..358: L2L by child octant.  Each P x P (out x in) operator T becomes B
+// with B[k][n] = T[n][k], split into TF32 hi/lo and swizzled per 32-wide K
+// chunk: [op][chunk][hi | lo][Npad rows of 128 B].
+void m2l_tc_pack_operands(int p, const double* T_m2l, const double* T_m2m, const double* T_l2l,
+                          float* out) {
     TcGeom g = tc_geom(p);
     const int P = g.P;
     const size_t tile = (size_t)g.Npad * 32;  // floats per hi (or lo) tile
-    for (int opi = 0; opi < 343; ++opi)
+    for (int opi = 0; opi < kNumOps; ++opi) {
+        const double* T = opi < kOpM2M ? T_m2l + (size_t)opi * P * P
+                          : opi < kOpL2L ? T_m2m + (size_t)(opi - kOpM2M) * P * P
+                                         : T_l2l + (size_t)(opi - kOpL2L) * P * P;
         for (int kc = 0; kc < g.kchunks; ++kc) {
             float* hi = out + ((size_t)opi * g.kchunks + kc) * 2 * tile;
             float* lo = hi + tile;
             for (int n = 0; n < g.Npad; ++n)
                 for (int k = 0; k < 32; ++k) {
                     const int kk = kc * 32 + k;
-                    float v = (n < P && kk < P) ? (float)T_m2l[(size_t)opi * P * P + (size_t)n * P + kk]
-                                                : 0.0f;
-                    float h = rna_tf32_host(v);
-                    float r = rna_tf32_host(v - h);
+                    double t = (n < P && kk < P) ? T[(size_t)n * P + kk] : 0.0;
+                    float h = rna_tf32_host((float)t);
+                    float r = rna_tf32_host((float)(t - (double)h));
                     const size_t o = swz_off(n, k) / 4;
                     hi[o] = h;
                     lo[o] = r;
                 }
         }
+    }
 }
 
 cudaError_t m2l_tc_init() {
@@ -488,8 +498,8 @@ cudaError_t m2l_tc_init() {
                                 tc_geom(15).smem_bytes);
 }
 
-cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s) {
-    if (D < 2) return cudaSuccess;
+static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
+    (void)n;
     TcGeom g = tc_geom(ws.p);
     TcArgs a;
     memset(&a, 0, sizeof a);
@@ -508,27 +518,45 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
     for (int l = 0; l < kMaxDepth + 2; ++l) a.off[l] = dl.off[l];
     a.M = (const float*)ws.M;
     a.L = (float*)ws.L;
+    a.Mout = (float*)ws.M;
     a.part = ws.tc_part;
     a.part_stride = ws.cells_max * ws.ld;
     a.ops = ws.T_m2l_tc;
     a.err = ws.err;
+    return a;
+}
+
+static int64_t level_cells(int64_t n, int l) {
+    int64_t cl = (int64_t)1 << (3 * l);
+    return n < cl ? n : cl;
+}
+
+cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s) {
+    TcArgs a = base_args(n, D, ws, 1);
+    a.mode = MODE_M2M;
+    a.level = l;
+    const int64_t tiles = (level_cells(n, l) + kTcRows - 1) / kTcRows;
+    k_m2l_tc<<<(unsigned)tiles, kTcThreads, tc_geom(ws.p).smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    const int smem = tc_geom(ws.p).smem_bytes;
+    TcArgs a = base_args(n, D, ws, splits);
+    a.mode = MODE_M2L;
     int64_t tiles = 0;
-    for (int l = 2; l <= D; ++l) {
-        int64_t cl = (int64_t)1 << (3 * l);
-        int64_t cells = n < cl ? n : cl;
-        tiles += (cells + kTcRows - 1) / kTcRows + 8;
-    }
-    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, g.smem_bytes, s>>>(a);
+    for (int l = 2; l <= D; ++l) tiles += (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
+    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // L2L shifts level by level, each adding the cell's M2L partials
     for (int l = 2; l <= D; ++l) {
-        int64_t cl = (int64_t)1 << (3 * l);
-        int cells = (int)(n < cl ? n : cl);
-        int grid = (cells + 3) / 4;
-        if (grid > 152 * 16) grid = 152 * 16;
-        k_l2l_reduce<<<grid, 128, 4 * g.P * sizeof(float), s>>>(
-            l, g.P, ws.ld, splits - 1, ws.linfo, ws.code, ws.cid, l >= 3 ? dl.off[l - 1] : 0,
-            ws.tc_part, ws.cells_max * ws.ld, ws.T_l2l_t, (float*)ws.L);
+        TcArgs b = base_args(n, D, ws, splits);
+        b.mode = MODE_L2L;
+        b.level = l;
+        const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
+        k_m2l_tc<<<(unsigned)t2, kTcThreads, smem, s>>>(b);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
