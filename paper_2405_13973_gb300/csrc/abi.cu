@@ -426,7 +426,8 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         free_plan(pl);
         return PT_ERR_OOM;
     }
-    if (cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
+    if ((ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) * cells * ws.ld) != cudaSuccess) ||
+        cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ws.err, 0, sizeof(int)) != cudaSuccess ||

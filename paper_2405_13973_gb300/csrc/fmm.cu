@@ -51,22 +51,6 @@ void host_m2l_offsets(int16_t out[8][189]) {
     }
 }
 
-cudaError_t upload_harmonic_tables() {
-    static HarmTables<double> hd;
-    static HarmTables<float> hf;
-    static int16_t off[8][189];
-    static bool filled = false;
-    if (!filled) {
-        fill_harm_tables(hd);
-        fill_harm_tables(hf);
-        host_m2l_offsets(off);
-        filled = true;
-    }
-    cudaError_t e = cudaMemcpyToSymbol(c_tab_d, &hd, sizeof hd);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_f, &hf, sizeof hf);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m2l_off, off, sizeof off);
-    return e;
-}
 
 // Sorted ion records (written by the tree build): the FP64 path keeps
 // (u, q) in double; the FP32 paths keep u in 30-bit fixed point and q as
@@ -87,6 +71,17 @@ struct Ion<double> {
         ry = (t.y - o.y) - dy;
         rz = (t.z - o.z) - dz;
     }
+    // a source expressed in the target leaf's frame (u + d)
+    static __device__ __forceinline__ rec shifted(const rec& o, int dx, int dy, int dz) {
+        return make_double4_32a(o.x + dx, o.y + dy, o.z + dz, o.w);
+    }
+    static __device__ __forceinline__ void sep_shifted(const rec& t, const rec& o, double& rx,
+                                                       double& ry, double& rz, double& q) {
+        rx = t.x - o.x;
+        ry = t.y - o.y;
+        rz = t.z - o.z;
+        q = o.w;
+    }
 };
 template <>
 struct Ion<float> {
@@ -105,72 +100,71 @@ struct Ion<float> {
         ry = __int2float_rn((t.y - o.y) - dy * (1 << 30)) * 0x1p-30f;
         rz = __int2float_rn((t.z - o.z) - dz * (1 << 30)) * 0x1p-30f;
     }
+    // a source in the target leaf's frame: u + d 2^30 stays within
+    // [-2^29 - 2^30, 2^29 - 1 + 2^30], so u_t - (u_s + d 2^30) fits in int32
+    static __device__ __forceinline__ rec shifted(const rec& o, int dx, int dy, int dz) {
+        return make_int4(o.x + dx * (1 << 30), o.y + dy * (1 << 30), o.z + dz * (1 << 30), o.w);
+    }
+    static __device__ __forceinline__ void sep_shifted(const rec& t, const rec& o, float& rx,
+                                                       float& ry, float& rz, float& q) {
+        rx = __int2float_rn(t.x - o.x) * 0x1p-30f;
+        ry = __int2float_rn(t.y - o.y) * 0x1p-30f;
+        rz = __int2float_rn(t.z - o.z) * 0x1p-30f;
+        q = __int_as_float(o.w);
+    }
 };
 
+constexpr int kP2mThreads = 128;
+constexpr int kP2mIons = 32;
+
 // ---------------------------------------------------------------------------
-// P2M: one warp per leaf, lane m accumulates column m (n = m..p).
+// P2M: one block per leaf.  Each thread evaluates conj(Y^_n^m(u)) q of one ion
+// (all n, m, by the column recurrences) into shared memory, then each thread
+// owns coefficients and sums them over the leaf's ions in slot order
+// (deterministic).  Leaves with more ions than kP2mIons are done in passes.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_p2m(int D, int p, int ld, const LevelInfo* linfo,
-                                             const int32_t* __restrict__ cstart,
-                                             const int32_t* __restrict__ ccount,
-                                             const typename Ion<T>::rec* __restrict__ sorted,
-                                             T* __restrict__ M) {
+__global__ void __launch_bounds__(kP2mThreads) k_p2m(int D, int p, int ld, const LevelInfo* linfo,
+                                                     const int32_t* __restrict__ cstart,
+                                                     const int32_t* __restrict__ ccount,
+                                                     const typename Ion<T>::rec* __restrict__ sorted,
+                                                     T* __restrict__ M) {
+    extern __shared__ unsigned char p2m_smem[];
+    const int P = (p + 1) * (p + 1);
+    T* terms = reinterpret_cast<T*>(p2m_smem);  // [kP2mIons][P]
     const HarmTables<T>& t = tab<T>();
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
-    const int m = lane;
-    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
+    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int s = cstart[g], k = ccount[g];
-        T accr[kMaxOrder + 1], acci[kMaxOrder + 1];
+        T acc[(kMaxOrder + 1) * (kMaxOrder + 1) / kP2mThreads + 1];
+        constexpr int NA = (kMaxOrder + 1) * (kMaxOrder + 1) / kP2mThreads + 1;
 #pragma unroll
-        for (int n = 0; n <= kMaxOrder; ++n) accr[n] = acci[n] = T(0);
-        if (m <= p) {
-            for (int i = 0; i < k; ++i) {
-                struct { T x, y, z, w; } u;
-                Ion<T>::get(sorted[s + i], u.x, u.y, u.z, u.w);
-                T dr = 1, di = 0;
-                for (int j = 1; j <= m; ++j) {
-                    T nr = (dr * u.x - di * u.y) * t.c[j];
-                    T ni = (dr * u.y + di * u.x) * t.c[j];
-                    dr = nr;
-                    di = ni;
-                }
-                const T r2 = u.x * u.x + u.y * u.y + u.z * u.z;
-                T y1r = 0, y1i = 0, y2r = 0, y2i = 0;
-#pragma unroll
-                for (int n = 0; n <= kMaxOrder; ++n) {
-                    if (n < m || n > p) continue;
-                    T yr, yi;
-                    if (n == m) {
-                        yr = dr;
-                        yi = di;
-                    } else if (n == m + 1) {
-                        T f = u.z * t.d[m];
-                        yr = f * y1r;
-                        yi = f * y1i;
-                    } else {
-                        T a = t.a[n][m] * u.z, b = t.b[n][m] * r2;
-                        yr = a * y1r - b * y2r;
-                        yi = a * y1i - b * y2i;
-                    }
-                    accr[n] += u.w * yr;
-                    acci[n] -= u.w * yi;
-                    y2r = y1r;
-                    y2i = y1i;
-                    y1r = yr;
-                    y1i = yi;
-                }
+        for (int r = 0; r < NA; ++r) acc[r] = T(0);
+        for (int i0 = 0; i0 < k; i0 += kP2mIons) {
+            const int ni = min(kP2mIons, k - i0);
+            __syncthreads();
+            if (threadIdx.x < ni) {
+                T x, y, z, q;
+                Ion<T>::get(sorted[s + i0 + threadIdx.x], x, y, z, q);
+                T* row = terms + threadIdx.x * P;
+                for_each_ups<T>(p, x, y, z, t, [&](int n, int m, T re, T im) {
+                    const int idx = re_idx(n, m);
+                    row[idx] = q * re;
+                    if (m > 0) row[idx + 1] = -q * im;
+                });
             }
-            T* out = M + (int64_t)g * ld;
+            __syncthreads();
 #pragma unroll
-            for (int n = 0; n <= kMaxOrder; ++n) {
-                if (n < m || n > p) continue;
-                int idx = re_idx(n, m);
-                out[idx] = accr[n];
-                if (m > 0) out[idx + 1] = acci[n];
+            for (int r = 0; r < NA; ++r) {
+                const int c = threadIdx.x + r * kP2mThreads;
+                if (c < P)
+                    for (int i = 0; i < ni; ++i) acc[r] += terms[i * P + c];
             }
+        }
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+            const int c = threadIdx.x + r * kP2mThreads;
+            if (c < P) M[(int64_t)g * ld + c] = acc[r];
         }
     }
 }
@@ -359,78 +353,142 @@ __device__ __forceinline__ void kb_add(T& s, T& c, T v) {
     s = t;
 }
 
+// L2P + P2P, one block per target leaf: the sources of the 27 adjacent
+// leaves are staged in shared memory in the target leaf's frame; thread
+// (target i, chunk c) sums every nchunk-th source; the chunk partials are
+// combined in a fixed order with compensated sums (deterministic), the far
+// field (L2P) is added, and the field is written in the original ion order,
+// scaled to SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
+constexpr int kNfThreads = 128;
+constexpr int kNfSrc = 1024;   // staged sources per pass
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_near_far(
+__global__ void __launch_bounds__(kNfThreads) k_near_far(
     int64_t n, int D, int p, int ld, int phases, const RootCube* root, const LevelInfo* linfo,
-    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ leaf_of,
-    const int32_t* __restrict__ perm, const uint32_t* __restrict__ code,
-    const int32_t* __restrict__ cid_leaf, const int32_t* __restrict__ cstart,
-    const int32_t* __restrict__ ccount, const T* __restrict__ L, double* E, double* phi) {
+    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
+    const uint32_t* __restrict__ code, const int32_t* __restrict__ cid_leaf,
+    const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
+    const T* __restrict__ L, double* E, double* phi) {
     using R = typename Ion<T>::rec;
+    __shared__ R src[kNfSrc];
+    __shared__ int nb_start[27], nb_count[27], nb_pre[28];
+    __shared__ T part[kNfThreads][4];
+    const int tid = threadIdx.x;
     const int lim = 1 << D;
     const double sl = root->side / (double)lim;
     const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
-    for (int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; slot < n;
-         slot += (int64_t)gridDim.x * blockDim.x) {
-        const int g = leaf_of[slot];
-        const R me = sorted[slot];
-        T ex = 0, ey = 0, ez = 0, ph = 0;
-        if ((phases & PT_PHASE_FAR) && D >= 2) {
-            T fphi, gx, gy, gz, ux, uy, uz, uq;
-            Ion<T>::get(me, ux, uy, uz, uq);
-            l2p_eval<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
-            ex = -gx;
-            ey = -gy;
-            ez = -gz;
-            ph = fphi;
+    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    const bool near = (phases & PT_PHASE_NEAR) != 0;
+    const bool far = (phases & PT_PHASE_FAR) && D >= 2;
+    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+        const int ts = cstart[g], nt = ccount[g];
+        int ix, iy, iz;
+        demorton3(code[g], ix, iy, iz);
+        if (tid < 27) {
+            const int dx = tid / 9 - 1, dy = (tid / 3) % 3 - 1, dz = tid % 3 - 1;
+            const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
+            int st = 0, ct = 0;
+            if (near && nx >= 0 && ny >= 0 && nz >= 0 && nx < lim && ny < lim && nz < lim) {
+                const int gn = cid_leaf[morton3(nx, ny, nz)];
+                if (gn >= 0) {
+                    st = cstart[gn];
+                    ct = ccount[gn];
+                }
+            }
+            nb_start[tid] = st;
+            nb_count[tid] = ct;
         }
-        if (phases & PT_PHASE_NEAR) {
-            // per source leaf: plain sums; across leaves: compensated sums
-            // (Kahan-Babuska), which keeps FP32 accumulation error at the
-            // level of one leaf's partial sum.
-            T cx = 0, cy = 0, cz = 0, cp = 0;
-            int ix, iy, iz;
-            demorton3(code[g], ix, iy, iz);
-            for (int dx = -1; dx <= 1; ++dx)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dz = -1; dz <= 1; ++dz) {
-                        int nx = ix + dx, ny = iy + dy, nz = iz + dz;
-                        if (nx < 0 || ny < 0 || nz < 0 || nx >= lim || ny >= lim || nz >= lim)
-                            continue;
-                        const int gn = cid_leaf[morton3(nx, ny, nz)];
-                        if (gn < 0) continue;
-                        const int s0 = cstart[gn], s1 = s0 + ccount[gn];
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < 27; ++k) {
+                nb_pre[k] = acc;
+                acc += nb_count[k];
+            }
+            nb_pre[27] = acc;
+        }
+        __syncthreads();
+        const int ns = nb_pre[27];
+        for (int t0 = 0; t0 < nt; t0 += kNfThreads) {   // targets in blocks of 128
+            const int ntb = min(kNfThreads, nt - t0);
+            const int nch = kNfThreads / ntb;            // source chunks per target
+            const int ti = tid % ntb, ch = tid / ntb;
+            const bool active = ch < nch;
+            const R me = sorted[ts + t0 + ti];
+            T ex = 0, ey = 0, ez = 0, ph = 0, cex = 0, cey = 0, cez = 0, cph = 0;
+            for (int s0 = 0; s0 < ns; s0 += kNfSrc) {    // sources in passes of kNfSrc
+                const int nsb = min(kNfSrc, ns - s0);
+                __syncthreads();
+                for (int j = tid; j < nsb; j += kNfThreads) {
+                    const int v = s0 + j;
+                    int k = 0;
+                    while (v >= nb_pre[k + 1]) ++k;
+                    const int dx = k / 9 - 1, dy = (k / 3) % 3 - 1, dz = k % 3 - 1;
+                    const int slot = nb_start[k] + (v - nb_pre[k]);
+                    src[j] = Ion<T>::shifted(sorted[slot], dx, dy, dz);
+                }
+                __syncthreads();
+                if (active) {
+                    // the target's own entry: leaf offset d = 0 is neighbour 13
+                    const int self = nb_pre[13] + (t0 + ti) - s0;
+                    // plain sums over blocks of 64 sources, compensated across blocks
+                    for (int jb = ch; jb < nsb; jb += 64 * nch) {
+                        const int je = min(nsb, jb + 64 * nch);
                         T px = 0, py = 0, pz = 0, pp = 0;
-                        for (int j = s0; j < s1; ++j) {
-                            if (j == slot) continue;
-                            const R o = sorted[j];
-                            T rx, ry, rz, oq, ox, oy, oz;
-                            Ion<T>::sep(me, o, dx, dy, dz, rx, ry, rz);
-                            Ion<T>::get(o, ox, oy, oz, oq);
+                        for (int j = jb; j < je; j += nch) {
+                            if (j == self) continue;
+                            T rx, ry, rz, q;
+                            Ion<T>::sep_shifted(me, src[j], rx, ry, rz, q);
                             const T r2 = rx * rx + ry * ry + rz * rz;
                             const T ir = inv_sqrt<T>(r2);
-                            const T qi = oq * ir;
+                            const T qi = q * ir;
                             const T q3 = qi * ir * ir;
                             px += q3 * rx;
                             py += q3 * ry;
                             pz += q3 * rz;
                             pp += qi;
                         }
-                        kb_add(ex, cx, px);
-                        kb_add(ey, cy, py);
-                        kb_add(ez, cz, pz);
-                        kb_add(ph, cp, pp);
+                        kb_add(ex, cex, px);
+                        kb_add(ey, cey, py);
+                        kb_add(ez, cez, pz);
+                        kb_add(ph, cph, pp);
                     }
-            ex += cx;
-            ey += cy;
-            ez += cz;
-            ph += cp;
+                }
+            }
+            part[tid][0] = ex + cex;
+            part[tid][1] = ey + cey;
+            part[tid][2] = ez + cez;
+            part[tid][3] = ph + cph;
+            __syncthreads();
+            if (tid < ntb) {
+                // fixed-order compensated combination of the chunk partials
+                T sx = 0, sy = 0, sz = 0, sp = 0, cx = 0, cy = 0, cz = 0, cp = 0;
+                for (int c = 0; c < nch; ++c) {
+                    const int th = c * ntb + tid;
+                    kb_add(sx, cx, part[th][0]);
+                    kb_add(sy, cy, part[th][1]);
+                    kb_add(sz, cz, part[th][2]);
+                    kb_add(sp, cp, part[th][3]);
+                }
+                T fx = sx + cx, fy = sy + cy, fz = sz + cz, fp = sp + cp;
+                if (far) {
+                    T fphi, gx, gy, gz, ux, uy, uz, uq;
+                    Ion<T>::get(me, ux, uy, uz, uq);
+                    l2p_eval<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
+                    fx -= gx;
+                    fy -= gy;
+                    fz -= gz;
+                    fp += fphi;
+                }
+                const int i = perm[ts + t0 + tid];
+                E[i] = fE * (double)fx;
+                E[n + i] = fE * (double)fy;
+                E[2 * n + i] = fE * (double)fz;
+                if (phi) phi[i] = fP * (double)fp;
+            }
+            __syncthreads();
         }
-        const int i = perm[slot];
-        E[i] = fE * (double)ex;
-        E[n + i] = fE * (double)ey;
-        E[2 * n + i] = fE * (double)ez;
-        if (phi) phi[i] = fP * (double)ph;
+        __syncthreads();
     }
 }
 
@@ -445,10 +503,9 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     cudaError_t e;
     if (far) {
         int leaves_max = (int)(n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D)));
-        int grid = (leaves_max + 3) / 4;
-        if (grid > 152 * 16) grid = 152 * 16;
-        k_p2m<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount,
-                                                     (const typename Ion<T>::rec*)ws.sorted, M);
+        int grid = leaves_max < 152 * 16 ? leaves_max : 152 * 16;
+        k_p2m<T><<<grid > 0 ? grid : 1, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
+            D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M);
         for (int l = D - 1; l >= 2; --l) {
             if (use_tc) {
                 if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
@@ -487,11 +544,11 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     }
     if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
-    int grid = (int)((n + 127) / 128);
-    if (grid > 152 * 16) grid = 152 * 16;
-    k_near_far<T><<<grid > 0 ? grid : 1, 128, 0, s>>>(
+    int64_t leaves = n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D));
+    int grid = (int)(leaves < 152 * 16 ? leaves : 152 * 16);
+    k_near_far<T><<<grid > 0 ? grid : 1, kNfThreads, 0, s>>>(
         n, D, p, ws.ld, phases, ws.root, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
-        ws.leaf_of, ws.perm, ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount, L, E, phi);
+        ws.perm, ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount, L, E, phi);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
@@ -631,6 +688,30 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
     int grid = (int)((n + 255) / 256);
     k_direct<<<grid > 0 ? grid : 1, 256, 0, s>>>(n, pos, q, E, phi);
     return cudaGetLastError();
+}
+
+cudaError_t upload_harmonic_tables() {
+    static HarmTables<double> hd;
+    static HarmTables<float> hf;
+    static int16_t off[8][189];
+    static bool filled = false;
+    if (!filled) {
+        fill_harm_tables(hd);
+        fill_harm_tables(hf);
+        host_m2l_offsets(off);
+        filled = true;
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_tab_d, &hd, sizeof hd);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_f, &hf, sizeof hf);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m2l_off, off, sizeof off);
+    const int pmax = (kMaxOrder + 1) * (kMaxOrder + 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2m<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kP2mIons * pmax * (int)sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kP2mIons * pmax * (int)sizeof(float));
+    return e;
 }
 
 }  // namespace pt

@@ -47,14 +47,15 @@ namespace pt {
 
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 320;
+constexpr int kMaxStages = 3;
 constexpr int kTcRows = 128;
 constexpr int kMaxSplits = 8;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct TcGeom {
     int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0;
-    int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0;
+    int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0, stages = 2;
 };
 
 TcGeom tc_geom(int p) {
@@ -67,7 +68,8 @@ TcGeom tc_geom(int p) {
     g.a_bytes = kTcRows * 128;      // one of A_hi / A_lo for a 32-wide chunk
     g.b_bytes = g.Npad * 128;       // one of B_hi / B_lo
     g.stage_bytes = 2 * g.a_bytes + 2 * g.b_bytes;
-    g.smem_bytes = 2 * g.stage_bytes + 1024;
+    g.stages = (kMaxStages * g.stage_bytes + 1024 <= 227 * 1024) ? kMaxStages : 2;
+    g.smem_bytes = g.stages * g.stage_bytes + 1024;
     return g;
 }
 
@@ -102,6 +104,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -193,7 +198,7 @@ constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator ind
 
 struct TcArgs {
     int mode, level;      // level: the target level of M2M / L2L launches
-    int D, P, ld, kchunks, Npad, tmem_cols, splits;
+    int D, P, ld, kchunks, Npad, tmem_cols, splits, stages;
     uint32_t idesc;
     const LevelInfo* linfo;
     const uint32_t* code;
@@ -208,21 +213,29 @@ struct TcArgs {
     int* err;
 };
 
+// Warp roles: warp 0 = operator producer (bulk copies), warp 1 = MMA issuer,
+// warps 2..9 = A producers (gather + split) and, at the end, the epilogue.
+constexpr int kProdWarps = 8;
+constexpr int kWarpA0 = 2;
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     extern __shared__ unsigned char smem_dyn[];
-    __shared__ __align__(8) uint64_t full_bar[2], done_bar[2];
+    __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
+        empty_bar[kMaxStages], acc_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int srow[kTcRows];
-    __shared__ int t_level, t_oct, t_base, t_rows, t_split, abort_sh;
+    __shared__ uint32_t tmask[6];
+    __shared__ uint8_t tlist[192];
+    __shared__ int t_level, t_oct, t_base, t_rows, t_split, tl_begin, tl_end, abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int a_bytes = kTcRows * 128, b_bytes = a.Npad * 128;
     const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    const int NS = a.stages;
 
     if (tid == 0) {
-        // which (level, octant, tile, split) is this CTA?
-        const int gsplit = a.mode == MODE_M2L ? a.splits : 1;  // CTAs per tile
+        // which (level, group, tile, split) is this CTA?
+        const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;  // CTAs per tile
         const int split = blockIdx.x % gsplit;
         int t = blockIdx.x / gsplit, acc = 0;
         t_rows = 0;
@@ -251,16 +264,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             }
         t_split = split;
         abort_sh = 0;
+        for (int w = 0; w < 6; ++w) tmask[w] = 0u;
     }
     __syncthreads();
     if (t_rows <= 0) return;
     const int l = t_level, oct = t_oct, tbase = t_base, rows = t_rows, split = t_split;
+    const int lim = 1 << l;
 
+    // ---- term list: the offsets (M2L) with at least one source in this tile
+    if (a.mode == MODE_M2L) {
+        if (tid >= kWarpA0 * 32) {
+            const int ta = tid - kWarpA0 * 32;  // 0..255
+            const int row = ta & 127, half = ta >> 7;
+            if (row < rows) {
+                int ix, iy, iz;
+                demorton3(a.code[tbase + row], ix, iy, iz);
+                for (int term = half; term < 189; term += 2) {
+                    const int opi = c_tc_off[oct][term];
+                    int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3), sz = iz - (opi % 7 - 3);
+                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim &&
+                        a.cid[a.off[l] + morton3(sx, sy, sz)] >= 0)
+                        atomicOr(&tmask[term >> 5], 1u << (term & 31));
+                }
+            }
+        }
+    }
     if (tid == 0) {
-        mbar_init(&full_bar[0], 1);
-        mbar_init(&full_bar[1], 1);
-        mbar_init(&done_bar[0], 1);
-        mbar_init(&done_bar[1], 1);
+        mbar_init(&acc_bar, 1);
+        mbar_init(&drain_bar, 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&fullA_bar[s], kProdWarps * 32);
+            mbar_init(&fullB_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -273,162 +309,212 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_base_sh;
-
-    // target coordinates and code of this thread's row (rows 0..127 by threads 0..127)
-    int tix = 0, tiy = 0, tiz = 0;
-    uint32_t tcode = 0;
-    if (tid < kTcRows && tid < rows) {
-        tcode = a.code[tbase + tid];
-        demorton3(tcode, tix, tiy, tiz);
-    }
-    const int lim = 1 << l;
-    int t0 = 0, t1 = 0;
-    if (a.mode == MODE_M2L) {
-        t0 = (189 * split) / a.splits;
-        t1 = (189 * (split + 1)) / a.splits;
-    } else if (a.mode == MODE_M2M) {
-        t1 = 8;
-    } else {
-        t1 = l >= 3 ? 1 : 0;
-    }
-    const float* src_base = a.mode == MODE_L2L ? a.L : a.M;
-    int it = 0;  // chunks issued
-    int copy_pending = -1;  // (thread 0) stage whose bulk copy has not been waited for
-    uint32_t copy_parity = 0;
-    bool ok = true;
-
-    for (int term = t0; term < t1 && ok; ++term) {
-        int opi;
-        if (a.mode == MODE_M2L) opi = c_tc_off[oct][term];
-        else if (a.mode == MODE_M2M) opi = kOpM2M + term;
-        else opi = kOpL2L + oct;
-        if (tid < kTcRows) {
-            int g = -1;
-            if (tid < rows) {
-                if (a.mode == MODE_M2L) {
-                    int sx = tix - (opi / 49 - 3), sy = tiy - ((opi / 7) % 7 - 3),
-                        sz = tiz - (opi % 7 - 3);
-                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
-                        g = a.cid[a.off[l] + morton3(sx, sy, sz)];
-                } else if (a.mode == MODE_M2M) {
-                    g = a.cid[a.off[l + 1] + ((tcode << 3) | (uint32_t)term)];
-                } else {
-                    g = a.cid[a.off[l - 1] + (tcode >> 3)];
-                }
-            }
-            srow[tid] = g;
+    if (tid == 0) {
+        int cnt = 0;
+        if (a.mode == MODE_M2L) {
+            for (int term = 0; term < 189; ++term)
+                if (tmask[term >> 5] & (1u << (term & 31))) tlist[cnt++] = (uint8_t)term;
+        } else if (a.mode == MODE_M2M) {
+            for (int term = 0; term < 8; ++term) tlist[cnt++] = (uint8_t)term;
+        } else if (l >= 3) {
+            tlist[cnt++] = 0;
         }
-        const int any = __syncthreads_or(tid < kTcRows && srow[tid] >= 0);
-        if (!any) continue;
-        for (int kc = 0; kc < a.kchunks; ++kc) {
-            const int st = it & 1, use = it >> 1;
+        const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;
+        tl_begin = (cnt * split) / gsplit;
+        tl_end = (cnt * (split + 1)) / gsplit;
+    }
+    __syncthreads();
+    const uint32_t tmem = tmem_base_sh;
+    const int n_it = (tl_end - tl_begin) * a.kchunks;
+
+    auto op_of = [&](int term) -> int {
+        if (a.mode == MODE_M2L) return c_tc_off[oct][term];
+        if (a.mode == MODE_M2M) return kOpM2M + term;
+        return kOpL2L + oct;
+    };
+
+    int last_copy_st = -1;
+    uint32_t last_copy_par = 0;
+    if (warp == 0) {
+        // ---- operator producer
+        if (lane == 0) {
+            for (int it = 0; it < n_it; ++it) {
+                const int st = it % NS, use = it / NS;
+                if (!mbar_wait(&empty_bar[st], (use & 1) ^ 1)) { abort_sh = 1; break; }
+                if (abort_sh) break;
+                const int term = tlist[tl_begin + it / a.kchunks], kc = it % a.kchunks;
+                unsigned char* sB = base + st * stage_bytes + 2 * a_bytes;
+                mbar_arrive_expect_tx(&fullB_bar[st], 2 * b_bytes);
+                const float* src = a.ops + ((size_t)op_of(term) * a.kchunks + kc) * 2 * a.Npad * 32;
+                bulk_g2s(sB, src, 2 * b_bytes, &fullB_bar[st]);
+                last_copy_st = st;
+                last_copy_par = use & 1;
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            for (int it = 0; it < n_it; ++it) {
+                const int st = it % NS, use = it / NS;
+                if (!mbar_wait(&fullB_bar[st], use & 1) || !mbar_wait(&fullA_bar[st], use & 1)) {
+                    abort_sh = 1;
+                    break;
+                }
+                if (abort_sh) break;
+                tc_fence_after();
+                unsigned char* sA_hi = base + st * stage_bytes;
+                const uint32_t ah = smem_addr(sA_hi), al = ah + a_bytes;
+                const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                    mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
+                    mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, 1u);
+                    mma_tf32(tmem, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                }
+                mma_commit(&empty_bar[st]);  // frees the stage once these MMAs finish
+            }
+            if (n_it > 0) mma_commit(&acc_bar);  // accumulator complete
+        }
+    } else {
+        // ---- A producers: each thread owns rows r0 + 32 j (j < 4) and 16-byte unit c
+        const int ta = tid - kWarpA0 * 32;
+        const int r0 = ta >> 3, c = ta & 7;
+        int tix[4], tiy[4], tiz[4];
+        uint32_t tcode[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + 32 * j;
+            tcode[j] = 0;
+            tix[j] = tiy[j] = tiz[j] = 0;
+            if (r < rows) {
+                tcode[j] = a.code[tbase + r];
+                demorton3(tcode[j], tix[j], tiy[j], tiz[j]);
+            }
+        }
+        const float* src_base = a.mode == MODE_L2L ? a.L : a.M;
+        // source cells of this thread's rows for a term
+        auto sources = [&](int ti, int (&gout)[4]) {
+            const int term = tlist[tl_begin + ti];
+            const int opi = op_of(term);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int gs = -1;
+                if (r0 + 32 * j < rows) {
+                    if (a.mode == MODE_M2L) {
+                        int sx = tix[j] - (opi / 49 - 3), sy = tiy[j] - ((opi / 7) % 7 - 3),
+                            sz = tiz[j] - (opi % 7 - 3);
+                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                            gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
+                    } else if (a.mode == MODE_M2M) {
+                        gs = a.cid[a.off[l + 1] + ((tcode[j] << 3) | (uint32_t)term)];
+                    } else {
+                        gs = a.cid[a.off[l - 1] + (tcode[j] >> 3)];
+                    }
+                }
+                gout[j] = gs;
+            }
+        };
+        auto gather = [&](int kc, const int (&gs)[4], float4 (&v)[4]) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gs[j] >= 0)
+                    v[j] = *reinterpret_cast<const float4*>(src_base + (int64_t)gs[j] * a.ld + kc * 32 + c * 4);
+            }
+        };
+        // software pipeline: the loads of iteration it + 1 are in flight while
+        // iteration it waits for its stage and is split and stored
+        int g[4] = {-1, -1, -1, -1};
+        float4 v[4];
+        if (n_it > 0) {
+            sources(0, g);
+            gather(0, g, v);
+        }
+        for (int it = 0; it < n_it; ++it) {
+            const int st = it % NS, use = it / NS;
+            int gn[4] = {g[0], g[1], g[2], g[3]};
+            float4 vn[4];
+            const int it1 = it + 1;
+            if (it1 < n_it) {
+                const int ti1 = it1 / a.kchunks, kc1 = it1 % a.kchunks;
+                if (kc1 == 0) sources(ti1, gn);
+                gather(kc1, gn, vn);
+            }
+            if (!mbar_wait(&empty_bar[st], (use & 1) ^ 1)) { abort_sh = 1; break; }
+            if (abort_sh) break;
             unsigned char* sA_hi = base + st * stage_bytes;
             unsigned char* sA_lo = sA_hi + a_bytes;
-            unsigned char* sB = sA_lo + a_bytes;  // B_hi then B_lo
-            if (tid == 0) {
-                if (it >= 2 && !mbar_wait(&done_bar[st], (use - 1) & 1)) abort_sh = 1;
-                if (!abort_sh) {
-                    mbar_arrive_expect_tx(&full_bar[st], 2 * b_bytes);
-                    const float* src = a.ops + ((size_t)opi * a.kchunks + kc) * 2 * a.Npad * 32;
-                    bulk_g2s(sB, src, 2 * b_bytes, &full_bar[st]);
-                    copy_pending = st;
-                    copy_parity = use & 1;
-                }
-            }
-            __syncthreads();  // stage free (its previous MMAs done) for everyone
-            if (abort_sh) {
-                ok = false;
-                break;
-            }
-            // gather + split the A chunk
-            for (int idx = tid; idx < kTcRows * 8; idx += kTcThreads) {
-                const int r = idx >> 3, c = idx & 7;
-                const int g = srow[r];
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g >= 0) v = *reinterpret_cast<const float4*>(src_base + (int64_t)g * a.ld + kc * 32 + c * 4);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = r0 + 32 * j;
                 uint4 hi, lo;
-                hi.x = rna_tf32(v.x); lo.x = rna_tf32(v.x - __uint_as_float(hi.x));
-                hi.y = rna_tf32(v.y); lo.y = rna_tf32(v.y - __uint_as_float(hi.y));
-                hi.z = rna_tf32(v.z); lo.z = rna_tf32(v.z - __uint_as_float(hi.z));
-                hi.w = rna_tf32(v.w); lo.w = rna_tf32(v.w - __uint_as_float(hi.w));
-                const int off = (r >> 3) * 1024 + (r & 7) * 128 + (((c ^ (r & 7))) << 4);
+                hi.x = rna_tf32(v[j].x); lo.x = rna_tf32(v[j].x - __uint_as_float(hi.x));
+                hi.y = rna_tf32(v[j].y); lo.y = rna_tf32(v[j].y - __uint_as_float(hi.y));
+                hi.z = rna_tf32(v[j].z); lo.z = rna_tf32(v[j].z - __uint_as_float(hi.z));
+                hi.w = rna_tf32(v[j].w); lo.w = rna_tf32(v[j].w - __uint_as_float(hi.w));
+                const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
                 *reinterpret_cast<uint4*>(sA_hi + off) = hi;
                 *reinterpret_cast<uint4*>(sA_lo + off) = lo;
             }
             fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                if (!mbar_wait(&full_bar[st], use & 1)) {
-                    abort_sh = 1;
+            mbar_arrive(&fullA_bar[st]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                g[j] = gn[j];
+                v[j] = vn[j];
+            }
+        }
+    }
+
+    // ---- epilogue (warps 2..9): wait for the accumulator, then write out
+    bool ok = true;
+    if (warp >= kWarpA0) {
+        if (n_it > 0 && !abort_sh) {
+            if (lane == 0 && !mbar_wait(&acc_bar, 0)) abort_sh = 1;
+            __syncwarp();
+        }
+        tc_fence_after();
+        if (abort_sh) ok = false;
+        float* out;
+        if (split > 0) out = a.part + (int64_t)(split - 1) * a.part_stride;
+        else if (a.mode == MODE_M2M) out = a.Mout;
+        else out = a.L;
+        if (ok) {
+            const int quad = warp & 3, half = (warp - kWarpA0) >> 2;
+            const int row = quad * 32 + lane;
+            const int g = tbase + row;
+            for (int cb = half; cb * 16 < a.Npad; cb += 2) {
+                uint32_t r[16];
+                if (n_it > 0) {
+                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), r);
                 } else {
-                    copy_pending = -1;
-                    tc_fence_after();
-                    const uint32_t ah = smem_addr(sA_hi), al = smem_addr(sA_lo);
-                    const uint32_t bh = smem_addr(sB), bl = bh + b_bytes;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                        mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
-                        mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, 1u);
-                        mma_tf32(tmem, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                    for (int j = 0; j < 16; ++j) r[j] = 0u;
+                }
+                if (row < rows) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = cb * 16 + j;
+                        if (col >= a.P) continue;
+                        const int64_t o = (int64_t)g * a.ld + col;
+                        float v = __uint_as_float(r[j]);
+                        if (a.mode == MODE_L2L) v += a.L[o];  // the cell's own M2L result
+                        out[o] = v;
                     }
-                    mma_commit(&done_bar[st]);
                 }
             }
-            ++it;
         }
     }
     __syncthreads();
-    if (abort_sh) ok = false;
-    // wait for the last committed MMAs (bounded), then read the accumulator
-    if (tid == 0 && it > 0) {
-        const int st = (it - 1) & 1, use = (it - 1) >> 1;
-        if (!mbar_wait(&done_bar[st], use & 1)) abort_sh = 2;
-        if (it > 1) {  // the other stage's last commit as well
-            const int st2 = (it - 2) & 1, use2 = (it - 2) >> 1;
-            if (!mbar_wait(&done_bar[st2], use2 & 1)) abort_sh = 2;
-        }
-    }
-    // on abort: one more bounded wait for a bulk copy still in flight
-    if (tid == 0 && abort_sh && copy_pending >= 0) mbar_wait(&full_bar[copy_pending], copy_parity);
-    __syncthreads();
-    tc_fence_after();
     if (abort_sh) {
-        if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
-        ok = false;
-    }
-    float* out;
-    if (a.mode == MODE_M2M) out = a.Mout;
-    else if (a.mode == MODE_L2L || split == 0) out = a.L;
-    else out = a.part + (int64_t)(split - 1) * a.part_stride;
-    if (ok) {
-        const int quad = warp & 3, half = warp >> 2;
-        const int row = quad * 32 + lane;
-        const int g = tbase + row;
-        for (int cb = half; cb * 16 < a.Npad; cb += 2) {
-            uint32_t r[16];
-            if (it > 0) {
-                tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), r);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) r[j] = 0u;
-            }
-            if (row < rows) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = cb * 16 + j;
-                    if (col >= a.P) continue;
-                    const int64_t o = (int64_t)g * a.ld + col;
-                    float v = __uint_as_float(r[j]);
-                    if (a.mode == MODE_L2L) {
-                        v += a.L[o];  // this cell's own M2L result (split 0)
-                        for (int sp = 0; sp + 1 < a.splits; ++sp) v += a.part[sp * a.part_stride + o];
-                    }
-                    out[o] = v;
-                }
-            }
+        // drain (bounded): the issuer's MMAs in flight and the last bulk copy
+        if (tid == 32) {
+            mma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0);
         }
+        if (tid == 0 && last_copy_st >= 0) mbar_wait(&fullB_bar[last_copy_st], last_copy_par);
+        if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
     }
     tc_fence_before();
     __syncthreads();
@@ -437,6 +523,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(a.tmem_cols)
                      : "memory");
+}
+
+// L += the split partials of M2L, for every cell of levels 2..D (fixed order,
+// whole padded rows: the partials' padding stays zero from allocation).
+__global__ void k_tc_reduce(int lfirst, int llast, int ld, int nparts, const LevelInfo* linfo,
+                            const float4* __restrict__ part, int64_t part_stride4, float4* L) {
+    const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[llast + 1];
+    const int64_t w = ld / 4;
+    for (int64_t e = g0 * w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g1 * w;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = L[e];
+        for (int s = 0; s < nparts; ++s) {
+            const float4 q = part[s * part_stride4 + e];
+            v.x += q.x;
+            v.y += q.y;
+            v.z += q.z;
+            v.w += q.w;
+        }
+        L[e] = v;
+    }
 }
 
 }  // namespace
@@ -493,9 +599,10 @@ cudaError_t m2l_tc_init() {
     host_m2l_offsets(off);
     cudaError_t e = cudaMemcpyToSymbol(c_tc_off, off, sizeof off);
     if (e != cudaSuccess) return e;
-    // largest supported order: N = 256 columns
-    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                tc_geom(15).smem_bytes);
+    int most = 0;
+    for (int q = 2; q <= kMaxOrder; ++q)
+        if (tc_supported(q) && tc_geom(q).smem_bytes > most) most = tc_geom(q).smem_bytes;
+    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
@@ -510,6 +617,7 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.Npad = g.Npad;
     a.tmem_cols = g.tmem_cols;
     a.splits = splits;
+    a.stages = g.stages;
     a.idesc = idesc_tf32(g.Npad, kTcRows);
     a.linfo = ws.linfo;
     a.code = ws.code;
@@ -532,11 +640,20 @@ static int64_t level_cells(int64_t n, int l) {
 }
 
 cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s) {
-    TcArgs a = base_args(n, D, ws, 1);
+    const int64_t tiles = (level_cells(n, l) + kTcRows - 1) / kTcRows;
+    // split the 8 child terms across CTAs when the level has few tiles
+    int splits = (int)((152 + tiles - 1) / tiles);
+    if (splits > 8) splits = 8;
+    if (splits > ws.tc_splits_max) splits = ws.tc_splits_max;
+    if (splits < 1) splits = 1;
+    TcArgs a = base_args(n, D, ws, splits);
     a.mode = MODE_M2M;
     a.level = l;
-    const int64_t tiles = (level_cells(n, l) + kTcRows - 1) / kTcRows;
-    k_m2l_tc<<<(unsigned)tiles, kTcThreads, tc_geom(ws.p).smem_bytes, s>>>(a);
+    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, tc_geom(ws.p).smem_bytes, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || splits == 1) return e;
+    k_tc_reduce<<<152 * 2, 256, 0, s>>>(l, l, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
+                                        ws.cells_max * ws.ld / 4, (float4*)ws.M);
     return cudaGetLastError();
 }
 
@@ -550,6 +667,11 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
     k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (splits > 1) {
+        k_tc_reduce<<<152 * 4, 256, 0, s>>>(2, D, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
+                                           ws.cells_max * ws.ld / 4, (float4*)ws.L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // L2L shifts level by level, each adding the cell's M2L partials
     for (int l = 2; l <= D; ++l) {
         TcArgs b = base_args(n, D, ws, splits);
