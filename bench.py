@@ -114,7 +114,9 @@ def launches_per_step(depth: int, precision: str) -> int:
     if depth >= 2:
         k += 1 + (depth - 2)                 # P2M, M2M per level
         if precision == "tf32x3":
-            k += 1 + (depth - 1)             # one M2L launch, L2L per level
+            # M2M splits reduce per level, plan + items + M2L + tile reduce,
+            # L2L per level >= 3
+            k += (depth - 2) + 4 + (depth - 2)
         else:
             k += depth - 1                   # M2L (+ folded L2L) per level
     return k
@@ -194,7 +196,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp64"])
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")

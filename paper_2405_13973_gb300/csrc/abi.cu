@@ -418,7 +418,11 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
          dalloc(pl, ws.T_m2l, tsz * 343 * PP);
     if (ok && precision == PT_MIXED_TF32X3) {
         ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
-        ok = dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p)) &&
+        int64_t tcap = 0;
+        for (int l = 2; l <= ws.depth_max; ++l) tcap += ((pow8(l) < n_max ? pow8(l) : n_max) + 127) / 128 + 8;
+        ws.tc_tiles_cap = tcap > 0 ? tcap : 1;
+        ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap));
+        ok = ok && dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p)) &&
              dalloc(pl, ws.tc_part, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) *
                                         cells * ws.ld);
     }
@@ -426,7 +430,8 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         free_plan(pl);
         return PT_ERR_OOM;
     }
-    if ((ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) * cells * ws.ld) != cudaSuccess) ||
+    if ((ws.tc_work && cudaMemset(ws.tc_work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap)) != cudaSuccess) ||
+        (ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) * cells * ws.ld) != cudaSuccess) ||
         cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||

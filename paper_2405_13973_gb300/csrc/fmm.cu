@@ -231,12 +231,15 @@ __global__ void __launch_bounds__(256) k_m2l_simt(int l, int P, int ld, const Le
     __shared__ T Bs[kKC][kNT];
     __shared__ const T* src[kNT];
     __shared__ int tile_oct, tile_base, tile_n;
+    __shared__ int s_oct[9];
     const int tid = threadIdx.x;
+    if (tid < 9) s_oct[tid] = linfo->oct_start[l][tid];
+    __syncthreads();
     if (tid == 0) {
         int b = blockIdx.x, acc = 0;
         tile_n = 0;
         for (int o = 0; o < 8; ++o) {
-            int s0 = linfo->oct_start[l][o], s1 = linfo->oct_start[l][o + 1];
+            int s0 = s_oct[o], s1 = s_oct[o + 1];
             int nt = (s1 - s0 + kNT - 1) / kNT;
             if (b < acc + nt) {
                 tile_oct = o;
@@ -421,8 +424,10 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
                 __syncthreads();
                 for (int j = tid; j < nsb; j += kNfThreads) {
                     const int v = s0 + j;
-                    int k = 0;
-                    while (v >= nb_pre[k + 1]) ++k;
+                    int k = 0;  // largest k with nb_pre[k] <= v (binary search over 28 bounds)
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (k + step <= 26 && nb_pre[k + step] <= v) k += step;
                     const int dx = k / 9 - 1, dy = (k / 3) % 3 - 1, dz = k % 3 - 1;
                     const int slot = nb_start[k] + (v - nb_pre[k]);
                     src[j] = Ion<T>::shifted(sorted[slot], dx, dy, dz);

@@ -82,6 +82,8 @@ struct Workspace {
     float* T_m2l_tc = nullptr;  // tensor-core operand tiles (mixed mode)
     float* tc_part = nullptr;   // [tc_splits_max - 1][cells_max][ld] M2L split partials
     int tc_splits_max = 1;
+    void* tc_work = nullptr;    // M2L work list (tiles, items)
+    int64_t tc_tiles_cap = 0;
 };
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
@@ -125,6 +127,7 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
+size_t m2l_tc_work_bytes(int64_t tiles_cap);
 void m2l_tc_pack_operands(int p, const double* T_m2l, const double* T_m2m, const double* T_l2l,
                           float* out);
 // M2M of one level (targets = parents at level l) on the tensor cores.

@@ -50,7 +50,7 @@ namespace {
 constexpr int kTcThreads = 320;
 constexpr int kMaxStages = 3;
 constexpr int kTcRows = 128;
-constexpr int kMaxSplits = 8;
+constexpr int kMaxSplits = 12;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct TcGeom {
@@ -125,9 +125,11 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 // bounded wait (2 s of %globaltimer); false on expiry
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
         if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
     }
 }
@@ -209,9 +211,35 @@ struct TcArgs {
     float* Mout;           // M2M output (= M, other level)
     float* part;           // [splits-1][cells][ld]
     int64_t part_stride;   // cells_max * ld
-    const float* ops;      // [343][kchunks][2][Npad][32] swizzled
+    const float* ops;      // [359][kchunks][2][Npad][32] swizzled
     int* err;
+    // M2L work list (written by k_tc_plan)
+    const struct TcTile* tiles;
+    const struct TcItem* items;
+    const struct TcPlanHdr* hdr;
 };
+
+// One M2L tile (128 targets of one level and octant) and its non-empty
+// offsets; one work item = a contiguous run of them (one CTA).
+struct TcTile {
+    int level, oct, base, rows, cnt, nsplit, pad0, pad1;
+    uint8_t terms[192];
+};
+struct TcItem {
+    int tile, begin, end, rank;
+};
+struct TcPlanHdr {
+    unsigned ticket;
+    int n_tiles, n_items, pad;
+};
+
+// LevelInfo copied to shared memory by all threads at once (the tile
+// enumeration otherwise walks it with a chain of dependent global loads).
+__device__ __forceinline__ void stage_linfo(const LevelInfo* g, LevelInfo* s) {
+    const int* src = reinterpret_cast<const int*>(g);
+    int* dst = reinterpret_cast<int*>(s);
+    for (int i = threadIdx.x; i < (int)(sizeof(LevelInfo) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+}
 
 // Warp roles: warp 0 = operator producer (bulk copies), warp 1 = MMA issuer,
 // warps 2..9 = A producers (gather + split) and, at the end, the epilogue.
@@ -223,38 +251,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
         empty_bar[kMaxStages], acc_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ uint32_t tmask[6];
     __shared__ uint8_t tlist[192];
-    __shared__ int t_level, t_oct, t_base, t_rows, t_split, tl_begin, tl_end, abort_sh;
+    __shared__ int t_level, t_oct, t_base, t_rows, t_split, tl_begin, tl_end, abort_sh, tile_idx;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int a_bytes = kTcRows * 128, b_bytes = a.Npad * 128;
     const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
     const int NS = a.stages;
+    __shared__ LevelInfo li;
+    if (a.mode != MODE_M2L) stage_linfo(a.linfo, &li);
+    __syncthreads();
 
     if (tid == 0) {
-        // which (level, group, tile, split) is this CTA?
-        const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;  // CTAs per tile
-        const int split = blockIdx.x % gsplit;
-        int t = blockIdx.x / gsplit, acc = 0;
         t_rows = 0;
-        const int lfirst = a.mode == MODE_M2L ? 2 : a.level;
-        const int llast = a.mode == MODE_M2L ? a.D : a.level;
-        const int ngroups = a.mode == MODE_M2M ? 1 : 8;
-        for (int l = lfirst; l <= llast && t_rows == 0; ++l)
+        abort_sh = 0;
+        if (a.mode == MODE_M2L) {
+            // this CTA's work item: a run of one tile's non-empty offsets
+            if ((int)blockIdx.x < a.hdr->n_items) {
+                const TcItem it = a.items[blockIdx.x];
+                const TcTile& tl = a.tiles[it.tile];
+                t_level = tl.level;
+                t_oct = tl.oct;
+                t_base = tl.base;
+                t_rows = tl.rows;
+                t_split = it.rank;
+                tl_begin = it.begin;
+                tl_end = it.end;
+                tile_idx = it.tile;
+            }
+        } else {
+            // which (group, tile, split) of the launch's level is this CTA?
+            const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;  // CTAs per tile
+            const int split = blockIdx.x % gsplit;
+            int t = blockIdx.x / gsplit, acc = 0;
+            const int l0 = a.level;
+            const int ngroups = a.mode == MODE_M2M ? 1 : 8;
             for (int o = 0; o < ngroups; ++o) {
                 int s0, s1;
                 if (a.mode == MODE_M2M) {
-                    s0 = a.linfo->gbase[l];
-                    s1 = a.linfo->gbase[l + 1];
+                    s0 = li.gbase[l0];
+                    s1 = li.gbase[l0 + 1];
                 } else {
-                    s0 = a.linfo->oct_start[l][o];
-                    s1 = a.linfo->oct_start[l][o + 1];
+                    s0 = li.oct_start[l0][o];
+                    s1 = li.oct_start[l0][o + 1];
                 }
                 int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
                 if (t < acc + nt) {
-                    t_level = l;
+                    t_level = l0;
                     t_oct = o;
                     t_base = s0 + (t - acc) * kTcRows;
                     t_rows = min(kTcRows, s1 - t_base);
@@ -262,32 +306,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 }
                 acc += nt;
             }
-        t_split = split;
-        abort_sh = 0;
-        for (int w = 0; w < 6; ++w) tmask[w] = 0u;
+            t_split = split;
+        }
     }
     __syncthreads();
     if (t_rows <= 0) return;
     const int l = t_level, oct = t_oct, tbase = t_base, rows = t_rows, split = t_split;
     const int lim = 1 << l;
-
-    // ---- term list: the offsets (M2L) with at least one source in this tile
     if (a.mode == MODE_M2L) {
-        if (tid >= kWarpA0 * 32) {
-            const int ta = tid - kWarpA0 * 32;  // 0..255
-            const int row = ta & 127, half = ta >> 7;
-            if (row < rows) {
-                int ix, iy, iz;
-                demorton3(a.code[tbase + row], ix, iy, iz);
-                for (int term = half; term < 189; term += 2) {
-                    const int opi = c_tc_off[oct][term];
-                    int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3), sz = iz - (opi % 7 - 3);
-                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim &&
-                        a.cid[a.off[l] + morton3(sx, sy, sz)] >= 0)
-                        atomicOr(&tmask[term >> 5], 1u << (term & 31));
-                }
-            }
-        }
+        for (int k = tid; k < tl_end - tl_begin; k += kTcThreads)
+            tlist[k] = a.tiles[tile_idx].terms[tl_begin + k];
     }
     if (tid == 0) {
         mbar_init(&acc_bar, 1);
@@ -310,18 +338,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     __syncthreads();
     tc_fence_after();
     if (tid == 0) {
-        int cnt = 0;
         if (a.mode == MODE_M2L) {
-            for (int term = 0; term < 189; ++term)
-                if (tmask[term >> 5] & (1u << (term & 31))) tlist[cnt++] = (uint8_t)term;
-        } else if (a.mode == MODE_M2M) {
-            for (int term = 0; term < 8; ++term) tlist[cnt++] = (uint8_t)term;
-        } else if (l >= 3) {
-            tlist[cnt++] = 0;
+            tl_end -= tl_begin;   // tlist holds this item's terms from index 0
+            tl_begin = 0;
+        } else {
+            int cnt = 0;
+            if (a.mode == MODE_M2M) {
+                for (int term = 0; term < 8; ++term) tlist[cnt++] = (uint8_t)term;
+            } else if (l >= 3) {
+                tlist[cnt++] = 0;
+            }
+            const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;
+            tl_begin = (cnt * split) / gsplit;
+            tl_end = (cnt * (split + 1)) / gsplit;
         }
-        const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;
-        tl_begin = (cnt * split) / gsplit;
-        tl_end = (cnt * (split + 1)) / gsplit;
     }
     __syncthreads();
     const uint32_t tmem = tmem_base_sh;
@@ -441,7 +471,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 if (kc1 == 0) sources(ti1, gn);
                 gather(kc1, gn, vn);
             }
-            if (!mbar_wait(&empty_bar[st], (use & 1) ^ 1)) { abort_sh = 1; break; }
+            // one lane polls the stage barrier for the whole warp
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait(&empty_bar[st], (use & 1) ^ 1) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) { abort_sh = 1; break; }
             if (abort_sh) break;
             unsigned char* sA_hi = base + st * stage_bytes;
             unsigned char* sA_lo = sA_hi + a_bytes;
@@ -493,14 +527,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                     for (int j = 0; j < 16; ++j) r[j] = 0u;
                 }
                 if (row < rows) {
+                    // L2L adds the cell's own M2L result: load the 16 values
+                    // first (out aliases L, so interleaved load/store pairs
+                    // would serialise on the memory round trip)
+                    float own[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int col = cb * 16 + j;
-                        if (col >= a.P) continue;
-                        const int64_t o = (int64_t)g * a.ld + col;
-                        float v = __uint_as_float(r[j]);
-                        if (a.mode == MODE_L2L) v += a.L[o];  // the cell's own M2L result
-                        out[o] = v;
+                        own[j] = (a.mode == MODE_L2L && col < a.P) ? a.L[(int64_t)g * a.ld + col] : 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = cb * 16 + j;
+                        if (col < a.P) out[(int64_t)g * a.ld + col] = __uint_as_float(r[j]) + own[j];
                     }
                 }
             }
@@ -523,6 +562,222 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(a.tmem_cols)
                      : "memory");
+}
+
+// Work list of the M2L launch, first part: one block per tile collects the
+// offsets with at least one source among the tile's targets (4 threads per
+// target row) and stores them in term order.
+constexpr int kPlanThreads = 512;
+constexpr int kOccWords = (1 << 15) / 32;  // occupancy bits of one level up to depth 5
+constexpr int kWaveItems = 148;
+
+__global__ void __launch_bounds__(kPlanThreads) k_tc_plan(TcArgs a, TcTile* tiles) {
+    __shared__ uint32_t mask[6];
+    __shared__ int t_level, t_oct, t_base, t_rows;
+    __shared__ LevelInfo li;
+    const int tid = threadIdx.x;
+    stage_linfo(a.linfo, &li);
+    __syncthreads();
+    if (tid == 0) {
+        t_rows = 0;
+        int t = blockIdx.x, acc = 0;
+        for (int l = 2; l <= a.D && t_rows == 0; ++l)
+            for (int o = 0; o < 8; ++o) {
+                int s0 = li.oct_start[l][o], s1 = li.oct_start[l][o + 1];
+                int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
+                if (t < acc + nt) {
+                    t_level = l;
+                    t_oct = o;
+                    t_base = s0 + (t - acc) * kTcRows;
+                    t_rows = min(kTcRows, s1 - t_base);
+                    break;
+                }
+                acc += nt;
+            }
+    }
+    if (tid < 6) mask[tid] = 0u;
+    __syncthreads();
+    const int rows = t_rows, l = t_level, oct = t_oct;
+    // occupancy bitmap of the level in shared memory when it fits (8^l <= 32768)
+    __shared__ uint32_t occ[kOccWords];
+    const bool use_occ = rows > 0 && l <= 5;
+    if (use_occ) {
+        const int ncell = 1 << (3 * l);
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int c0 = warp * 32; c0 < ncell; c0 += kPlanThreads) {
+            const bool on = a.cid[a.off[l] + c0 + lane] >= 0;
+            const uint32_t b = __ballot_sync(0xffffffffu, on);
+            if (lane == 0) occ[c0 >> 5] = b;
+        }
+    }
+    __syncthreads();
+    if (rows > 0) {
+        const int row = tid & (kTcRows - 1), part = tid >> 7;  // 4 parts of the 189 terms
+        if (row < rows) {
+            int ix, iy, iz;
+            demorton3(a.code[t_base + row], ix, iy, iz);
+            const int lim = 1 << l;
+            uint32_t m[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll 8
+            for (int term = part; term < 189; term += 4) {
+                const int opi = c_tc_off[oct][term];
+                int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3), sz = iz - (opi % 7 - 3);
+                bool inb = sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim;
+                bool on = false;
+                if (inb) {
+                    const uint32_t c = morton3(sx, sy, sz);
+                    on = use_occ ? ((occ[c >> 5] >> (c & 31)) & 1u) != 0u
+                                 : a.cid[a.off[l] + c] >= 0;
+                }
+                if (on) m[term >> 5] |= 1u << (term & 31);
+            }
+#pragma unroll
+            for (int w = 0; w < 6; ++w)
+                if (m[w]) atomicOr(&mask[w], m[w]);
+        }
+        __syncthreads();
+        TcTile& tl = tiles[blockIdx.x];
+        if (tid < 189) {  // compact the set terms in term order
+            const int w = tid >> 5;
+            const uint32_t bit = 1u << (tid & 31);
+            if (mask[w] & bit) {
+                int pos = __popc(mask[w] & (bit - 1u));
+                for (int v = 0; v < w; ++v) pos += __popc(mask[v]);
+                tl.terms[pos] = (uint8_t)tid;
+            }
+        }
+        if (tid == 0) {
+            int cnt = 0;
+            for (int w = 0; w < 6; ++w) cnt += __popc(mask[w]);
+            tl.level = l;
+            tl.oct = oct;
+            tl.base = t_base;
+            tl.rows = rows;
+            tl.cnt = cnt;
+        }
+    }
+}
+
+// Cuts every tile's list into runs (one work item each): the run length is
+// chosen so that all runs fill about one wave of CTAs; each tile gets at
+// least one and at most max_splits runs.  One block; tiles in chunks.
+constexpr int kItemThreads = 1024;
+
+__global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInfo* linfo,
+                                                           int ntile_cap, int max_splits,
+                                                           TcPlanHdr* hdr, TcTile* tiles,
+                                                           TcItem* items) {
+    __shared__ int warp_sum[32];
+    __shared__ int s_total, s_ntile, s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        int ntile = 0;  // tiles are numbered densely from 0 in (level, octant) order
+        for (int l2 = 2; l2 <= D; ++l2)
+            for (int o = 0; o < 8; ++o) {
+                int s0 = linfo->oct_start[l2][o], s1 = linfo->oct_start[l2][o + 1];
+                ntile += (s1 - s0 + kTcRows - 1) / kTcRows;
+            }
+        s_ntile = ntile < ntile_cap ? ntile : ntile_cap;
+        s_carry = 0;
+    }
+    __syncthreads();
+    const int ntile = s_ntile;
+    // total non-empty offsets over all tiles
+    int part = 0;
+    for (int b = tid; b < ntile; b += kItemThreads) part += tiles[b].cnt;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) warp_sum[wid] = part;
+    __syncthreads();
+    if (tid == 0) {
+        int t = 0;
+        for (int w = 0; w < kItemThreads / 32; ++w) t += warp_sum[w];
+        s_total = t;
+    }
+    __syncthreads();
+    int tpi = (s_total + kWaveItems - 1) / kWaveItems;  // runs of about one wave in total
+    if (tpi < 4) tpi = 4;
+    // tiles in chunks of kItemThreads: exclusive scan of the run counts
+    for (int c0 = 0; c0 < ntile; c0 += kItemThreads) {
+        const int b = c0 + tid;
+        int cnt = 0, ns = 0;
+        if (b < ntile) {
+            cnt = tiles[b].cnt;
+            ns = (cnt + tpi - 1) / tpi;
+            if (ns < 1) ns = 1;
+            if (ns > max_splits) ns = max_splits;
+        }
+        int x = ns;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        __syncthreads();
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = warp_sum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const int off = s_carry + (wid > 0 ? warp_sum[wid - 1] : 0) + x - ns;
+        if (b < ntile) {
+            tiles[b].nsplit = ns;
+            for (int k = 0; k < ns; ++k) {
+                TcItem it;
+                it.tile = b;
+                it.begin = (cnt * k) / ns;
+                it.end = (cnt * (k + 1)) / ns;
+                it.rank = k;
+                items[off + k] = it;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += warp_sum[kItemThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        hdr->n_tiles = ntile;
+        hdr->n_items = s_carry;
+    }
+}
+
+// L += the split partials of the M2L items, per tile in rank order; 8 blocks
+// per tile, each a slice of its rows.
+constexpr int kRedSlices = 8;
+
+__global__ void __launch_bounds__(256) k_tc_reduce_tiles(int ld, const TcPlanHdr* hdr,
+                                                         const TcTile* tiles,
+                                                         const float4* __restrict__ part,
+                                                         int64_t part_stride4, float4* L) {
+    const int n_tiles = hdr->n_tiles;
+    const int w = ld / 4;
+    for (int bb = blockIdx.x; bb < n_tiles * kRedSlices; bb += gridDim.x) {
+        const int b = bb / kRedSlices, slice = bb % kRedSlices;
+        const int ns = tiles[b].nsplit, base = tiles[b].base, rows = tiles[b].rows;
+        if (ns <= 1) continue;
+        const int r0 = (rows * slice) / kRedSlices, r1 = (rows * (slice + 1)) / kRedSlices;
+        for (int e = threadIdx.x; e < (r1 - r0) * w; e += blockDim.x) {
+            const int64_t idx = (int64_t)(base + r0 + e / w) * w + (e % w);
+            float4 q[kMaxSplits - 1];
+#pragma unroll
+            for (int k = 0; k < kMaxSplits - 1; ++k)
+                if (k + 1 < ns) q[k] = part[k * part_stride4 + idx];
+            float4 v = L[idx];
+#pragma unroll
+            for (int k = 0; k < kMaxSplits - 1; ++k)
+                if (k + 1 < ns) {
+                    v.x += q[k].x;
+                    v.y += q[k].y;
+                    v.z += q[k].z;
+                    v.w += q[k].w;
+                }
+            L[idx] = v;
+        }
+    }
 }
 
 // L += the split partials of M2L, for every cell of levels 2..D (fixed order,
@@ -657,24 +912,40 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s) {
+cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p).smem_bytes;
-    TcArgs a = base_args(n, D, ws, splits);
-    a.mode = MODE_M2L;
     int64_t tiles = 0;
     for (int l = 2; l <= D; ++l) tiles += (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
-    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, smem, s>>>(a);
+    if (tiles > ws.tc_tiles_cap) return cudaErrorInvalidValue;
+    const int max_splits = ws.tc_splits_max < kMaxSplits ? ws.tc_splits_max : kMaxSplits;
+    TcPlanHdr* hdr = (TcPlanHdr*)ws.tc_work;
+    TcTile* tl = (TcTile*)(hdr + 1);
+    TcItem* items = (TcItem*)(tl + ws.tc_tiles_cap);
+    TcArgs a = base_args(n, D, ws, 1);
+    a.mode = MODE_M2L;
+    a.tiles = tl;
+    a.items = items;
+    a.hdr = hdr;
+    k_tc_plan<<<(unsigned)tiles, kPlanThreads, 0, s>>>(a, tl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (splits > 1) {
-        k_tc_reduce<<<152 * 4, 256, 0, s>>>(2, D, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
-                                           ws.cells_max * ws.ld / 4, (float4*)ws.L);
+    k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, max_splits, hdr, tl, items);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the plan makes at most kWaveItems + (number of tiles) items
+    int64_t grid = kWaveItems + tiles;
+    if (grid > tiles * max_splits) grid = tiles * max_splits;
+    k_m2l_tc<<<(unsigned)grid, kTcThreads, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (max_splits > 1) {
+        int64_t rg = tiles * kRedSlices;
+        k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 8 ? rg : 152 * 8), 256, 0, s>>>(
+            ws.ld, hdr, tl, (const float4*)ws.tc_part, ws.cells_max * ws.ld / 4, (float4*)ws.L);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // L2L shifts level by level, each adding the cell's M2L partials
-    for (int l = 2; l <= D; ++l) {
-        TcArgs b = base_args(n, D, ws, splits);
+    // L2L shifts level by level (level 2 has no parent expansion)
+    for (int l = 3; l <= D; ++l) {
+        TcArgs b = base_args(n, D, ws, 1);
         b.mode = MODE_L2L;
         b.level = l;
         const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
@@ -682,6 +953,11 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+size_t m2l_tc_work_bytes(int64_t tiles_cap) {
+    return sizeof(TcPlanHdr) + (size_t)tiles_cap * sizeof(TcTile) +
+           (size_t)tiles_cap * kMaxSplits * sizeof(TcItem);
 }
 
 cudaError_t launch_m2l_tc(int, int, Workspace&, cudaStream_t) { return cudaErrorNotSupported; }

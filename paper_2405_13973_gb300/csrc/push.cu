@@ -253,8 +253,10 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s) {
-    k_drift_bbox<<<ws.bbox_blocks, 256, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_partial,
-                                                ws.ticket, ws.root, ws.err, ws.steps);
+    int64_t g = (n + 255) / 256;
+    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
+    k_drift_bbox<<<g > 0 ? (int)g : 1, 256, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_partial,
+                                                      ws.ticket, ws.root, ws.err, ws.steps);
     return cudaGetLastError();
 }
 

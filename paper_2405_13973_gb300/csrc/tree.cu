@@ -55,7 +55,9 @@ __global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ 
 
 cudaError_t launch_bbox(const double* x, const double* y, const double* z, int64_t n,
                         Workspace& ws, cudaStream_t s) {
-    k_bbox<<<ws.bbox_blocks, 256, 0, s>>>(x, y, z, n, ws.bbox_partial, ws.ticket, ws.root, ws.err);
+    int64_t g = (n + 255) / 256;
+    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
+    k_bbox<<<g > 0 ? (int)g : 1, 256, 0, s>>>(x, y, z, n, ws.bbox_partial, ws.ticket, ws.root, ws.err);
     return cudaGetLastError();
 }
 
