@@ -10,7 +10,7 @@ on the launching stream, with a 512 MiB write between steps to flush the
 129 MB L2 (the inputs are smaller than L2).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|tf32x3|fp64] [--p P]
+                  [--precision fp32|tf32x3|bf16x3|fp64] [--p P]
 
 --impl reference times the FP64 CPU oracle (direct O(N^2) Coulomb sum and
 the literal step) on the host cores, one oracle step per benchmark step.
@@ -113,7 +113,7 @@ def launches_per_step(depth: int, precision: str) -> int:
     k = 11
     if depth >= 2:
         k += 1 + (depth - 2)                 # P2M, M2M per level
-        if precision == "tf32x3":
+        if precision in ("tf32x3", "bf16x3"):
             # M2M splits reduce per level, plan + items + M2L + tile reduce,
             # L2L per level >= 3
             k += (depth - 2) + 4 + (depth - 2)
@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "bf16x3", "fp64"])
     ap.add_argument("--p", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
@@ -281,6 +281,10 @@ def main():
             peak = pk["bf16_tflops"] * TF32_OVER_BF16 / 3.0
             roof.update(bound="tensor", peak_note=f"TF32 rate / 3 (3 products per FP32-accurate "
                                                   f"product), from {pk_src} bf16 x nominal ratio")
+        elif args.precision == "bf16x3":
+            peak = pk["bf16_tflops"] / 6.0
+            roof.update(bound="tensor", peak_note=f"{pk_src} bf16 rate / 6 (6 products per "
+                                                  f"FP32-accurate product)")
         elif args.precision == "fp32":
             peak = FP32_ALU_TFLOPS
             roof.update(bound="alu", peak_note="152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
@@ -305,7 +309,7 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3",
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3",
                                                              "fp64": "f64"}[args.precision],
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": args.precision, "p": args.p,

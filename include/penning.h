@@ -51,11 +51,21 @@ typedef enum {
 /* Arithmetic of the FMM (positions, velocities and the push are FP64 in
  * every mode).
  *   PT_FP64          : every FMM stage in FP64 on the CUDA cores.
- *   PT_MIXED_TF32X3  : P2M/M2M/L2L/L2P/P2P in FP32; M2L on the tensor cores
- *                      (tcgen05, TF32 hi/lo split, three products, FP32
- *                      accumulation in tensor memory).
+ *   PT_MIXED_TF32X3  : P2M/L2P/P2P in FP32 on the CUDA cores; M2M, M2L and
+ *                      L2L on the tensor cores (tcgen05, operands split into
+ *                      TF32 hi + lo, three products, FP32 accumulation in
+ *                      tensor memory: products good to about 2^-21).
+ *   PT_MIXED_BF16X3  : as PT_MIXED_TF32X3 with operands split into three
+ *                      BF16 pieces and six products (products good to about
+ *                      2^-24, the accuracy of FP32 multiplies) in the same
+ *                      tensor time.
  *   PT_FP32          : every FMM stage in FP32 on the CUDA cores. */
-typedef enum { PT_FP64 = 0, PT_MIXED_TF32X3 = 1, PT_FP32 = 3 } pt_precision;
+typedef enum {
+    PT_FP64 = 0,
+    PT_MIXED_TF32X3 = 1,
+    PT_MIXED_BF16X3 = 2,
+    PT_FP32 = 3
+} pt_precision;
 
 /* FMM stages run by fmm_forces (bit mask); default PT_PHASE_ALL. */
 enum { PT_PHASE_NEAR = 1, PT_PHASE_FAR = 2, PT_PHASE_ALL = 3 };

@@ -23,10 +23,11 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "penning.h")
 PT_OK, PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA = 0, -1, -2, -3
 PT_ERR_NONFINITE, PT_ERR_ESCAPED, PT_ERR_TIMEOUT, PT_ERR_COINCIDENT, PT_ERR_UNSUPPORTED = (
     -4, -5, -6, -7, -8)
-PT_FP64, PT_MIXED_TF32X3, PT_FP32 = 0, 1, 3
+PT_FP64, PT_MIXED_TF32X3, PT_MIXED_BF16X3, PT_FP32 = 0, 1, 2, 3
 PT_PHASE_NEAR, PT_PHASE_FAR, PT_PHASE_ALL = 1, 2, 3
 PT_MAX_BEAMS = 8
-PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "fp32": PT_FP32}
+PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "bf16x3": PT_MIXED_BF16X3,
+              "fp32": PT_FP32}
 
 
 class PenningError(RuntimeError):

@@ -76,6 +76,11 @@ bool dalloc(fmm_plan_s* pl, T*& p, size_t bytes) {
     return true;
 }
 
+// the two tensor-core modes share every kernel but the operand format
+bool is_tc(int precision) {
+    return precision == PT_MIXED_TF32X3 || precision == PT_MIXED_BF16X3;
+}
+
 int status_from(cudaError_t e) {
     if (e == cudaSuccess) return PT_OK;
     if (e == cudaErrorMemoryAllocation) return PT_ERR_OOM;
@@ -142,11 +147,11 @@ int build_operators(fmm_plan_s* pl) {
     cudaError_t e = pl->ws.fp64 ? upload_ops<double>(pl, m2m, l2l, m2l)
                                 : upload_ops<float>(pl, m2m, l2l, m2l);
     if (e != cudaSuccess) return status_from(e);
-    if (pl->precision == PT_MIXED_TF32X3) {
-        std::vector<float> packed(m2l_tc_operand_bytes(p) / sizeof(float));
-        m2l_tc_pack_operands(p, m2l.data(), m2m.data(), l2l.data(), packed.data());
-        e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size() * sizeof(float),
-                       cudaMemcpyHostToDevice);
+    if (is_tc(pl->precision)) {
+        const bool bf16 = pl->precision == PT_MIXED_BF16X3;
+        std::vector<unsigned char> packed(m2l_tc_operand_bytes(p, bf16));
+        m2l_tc_pack_operands(p, bf16, m2l.data(), m2m.data(), l2l.data(), packed.data());
+        e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return status_from(e);
     }
     return PT_OK;
@@ -193,7 +198,7 @@ int forces_impl(fmm_plan_s* pl, int64_t n, const double* x, const double* y, con
     cudaError_t e = launch_bbox(x, y, z, n, pl->ws, s);
     if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, pl->ws, s);
     if (e == cudaSuccess)
-        e = launch_fmm(n, D, pl->phases, pl->ws, pl->precision == PT_MIXED_TF32X3, E, phi, s);
+        e = launch_fmm(n, D, pl->phases, pl->ws, is_tc(pl->precision), E, phi, s);
     pl->last_depth = D;
     pl->last_n = n;
     return status_from(e);
@@ -215,7 +220,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
     if (e == cudaSuccess) e = launch_tree(n, st.x, st.y, st.z, st.q, D, ws, s);
     if (e == cudaSuccess) e = mark(2);
     if (e == cudaSuccess)
-        e = launch_fmm_phased(n, D, PT_PHASE_ALL, ws, pl->precision == PT_MIXED_TF32X3, ws.E,
+        e = launch_fmm_phased(n, D, PT_PHASE_ALL, ws, is_tc(pl->precision), ws.E,
                               nullptr, s, pl->profile ? pl->ph_ev + 3 : nullptr);
     if (e == cudaSuccess)
         e = launch_kick_drift(n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.q, ws.E, pp, laser, ws, s);
@@ -339,8 +344,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     if (!out || n_max < 1 || n_max > (int64_t)1 << 30 || p < 2 || p > kMaxOrder || leaf_max < 1 ||
         depth < -1 || depth > kMaxDepth)
         return PT_ERR_ARG;
-    if (precision != PT_FP64 && precision != PT_FP32 && precision != PT_MIXED_TF32X3)
-        return PT_ERR_ARG;
+    if (precision != PT_FP64 && precision != PT_FP32 && !is_tc(precision)) return PT_ERR_ARG;
     *out = nullptr;
     fmm_plan_s* pl = new (std::nothrow) fmm_plan_s;
     if (!pl) return PT_ERR_OOM;
@@ -348,13 +352,14 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         delete pl;
         return PT_ERR_CUDA;
     }
-    if (precision == PT_MIXED_TF32X3) {
+    if (is_tc(precision)) {
         cudaDeviceProp prop;
         if (cudaGetDeviceProperties(&prop, pl->device) != cudaSuccess) {
             delete pl;
             return PT_ERR_CUDA;
         }
-        if (prop.major != 10 || prop.minor != 3 || m2l_tc_operand_bytes(p) == 0) {
+        if (prop.major != 10 || prop.minor != 3 ||
+            m2l_tc_operand_bytes(p, precision == PT_MIXED_BF16X3) == 0) {
             delete pl;
             return PT_ERR_UNSUPPORTED;
         }
@@ -370,6 +375,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     ws.p = p;
     ws.P = pl->P;
     ws.fp64 = (precision == PT_FP64);
+    ws.tc_bf16 = (precision == PT_MIXED_BF16X3) ? 1 : 0;
     ws.ld = ws.fp64 ? pl->P : ((pl->P + 31) / 32) * 32;
     if (depth >= 0) {
         ws.depth_max = depth;
@@ -416,13 +422,13 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
          dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap) &&
          dalloc(pl, ws.T_m2m, tsz * 8 * PP) && dalloc(pl, ws.T_l2l, tsz * 8 * PP) &&
          dalloc(pl, ws.T_m2l, tsz * 343 * PP);
-    if (ok && precision == PT_MIXED_TF32X3) {
+    if (ok && is_tc(precision)) {
         ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
         int64_t tcap = 0;
         for (int l = 2; l <= ws.depth_max; ++l) tcap += ((pow8(l) < n_max ? pow8(l) : n_max) + 127) / 128 + 8;
         ws.tc_tiles_cap = tcap > 0 ? tcap : 1;
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap));
-        ok = ok && dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p)) &&
+        ok = ok && dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p, ws.tc_bf16 != 0)) &&
              dalloc(pl, ws.tc_part, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) *
                                         cells * ws.ld);
     }

@@ -79,7 +79,8 @@ struct Workspace {
     void* T_m2m = nullptr;   // [8][P][P]
     void* T_l2l = nullptr;   // [8][P][P]
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
-    float* T_m2l_tc = nullptr;  // tensor-core operand tiles (mixed mode)
+    void* T_m2l_tc = nullptr;   // tensor-core operand tiles (mixed modes)
+    int tc_bf16 = 0;            // tensor-core operand format: 0 TF32 hi/lo, 1 BF16 hi/mid/lo
     float* tc_part = nullptr;   // [tc_splits_max - 1][cells_max][ld] M2L split partials
     int tc_splits_max = 1;
     void* tc_work = nullptr;    // M2L work list (tiles, items)
@@ -125,11 +126,11 @@ cudaError_t launch_m2l_tc(int level, int D, Workspace& ws, cudaStream_t s);
 // and the L2L shift of the parent (so L is complete on return).
 cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s);
 cudaError_t m2l_tc_init();
-size_t m2l_tc_operand_bytes(int p);   // 0 if the order is not supported
+size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
 size_t m2l_tc_work_bytes(int64_t tiles_cap);
-void m2l_tc_pack_operands(int p, const double* T_m2l, const double* T_m2m, const double* T_l2l,
-                          float* out);
+void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T_m2m,
+                          const double* T_l2l, void* out);
 // M2M of one level (targets = parents at level l) on the tensor cores.
 cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s);
 void host_m2l_offsets(int16_t out[8][189]);

@@ -9,17 +9,26 @@
 //     A row r = M of the source of target r (gathered; zero if empty),
 //     B = T_o^T (K = input coefficients, N = output coefficients).
 //
-// Precision (3xTF32): every FP32 operand x is split into hi = rna_tf32(x) and
-// lo = rna_tf32(x - hi); D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi in
-// FP32 in tensor memory, which reproduces FP32 products to about 2^-21.
+// Precision: tensor-core inputs are split into pieces whose products, summed
+// in FP32 in tensor memory, rebuild the FP32 (or FP64) operands.
+//   3xTF32: x = hi + lo, hi = rna_tf32(x), lo = rna_tf32(x - hi) (22 of
+//     FP32's 24 bits); D += A_hi B_hi + A_hi B_lo + A_lo B_hi.  Each product
+//     is good to about 2^-21.
+//   BF16x3: x = hi + mid + lo with three round-to-nearest bf16 pieces (8 bits
+//     each: an FP32 value exactly, an FP64 operator to 2^-24); D += the six
+//     products whose piece orders sum to at most 2 (hh, hm, mh, hl, lh, mm).
+//     The dropped terms are below 2^-25 of the product, so each product is
+//     as good as an FP32 multiply; the BF16 rate is twice the TF32 rate, so
+//     six BF16 products take the tensor time of three TF32 ones.
 //
 // Data movement: the operators are split and laid out on the host in the
-// 128-byte-swizzled K-major shared-memory image of each 32-wide K chunk, so
-// one cp.async.bulk per (offset, chunk) brings B_hi and B_lo.  A rows are
-// gathered by all threads, split and stored into the same swizzled layout.
-// Two stages: the loads of chunk i+1 overlap the MMAs of chunk i.  One
-// thread issues tcgen05.mma (M = 128, N = P rounded up to 16, K = 8 per
-// instruction) and commits to an mbarrier per stage.
+// swizzled K-major shared-memory image of each 32-wide K chunk (128-byte
+// rows and swizzle for TF32, 64-byte rows and swizzle for BF16), so one
+// cp.async.bulk per (offset, chunk) brings every piece of B.  A rows are
+// gathered by all threads, split and stored into the same layout.  Up to
+// four stages: the loads of later chunks overlap the MMAs of chunk i.  One
+// thread issues tcgen05.mma (M = 128, N = P rounded up to 16, 32 bytes of K
+// per instruction) and commits to an mbarrier per stage.
 //
 // The same gathered product serves the two other dense translations:
 //   M2M (upward pass): a tile of parents, 8 terms (child octants), A = the
@@ -34,6 +43,7 @@
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // ERR_TIMEOUT, stops issuing, waits (bounded) for its own work in flight,
 // frees its tensor memory and returns.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -48,38 +58,68 @@ namespace pt {
 namespace {
 
 constexpr int kTcThreads = 320;
-constexpr int kMaxStages = 3;
+constexpr int kMaxStages = 4;
 constexpr int kTcRows = 128;
 constexpr int kMaxSplits = 12;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct TcGeom {
-    int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0;
+    int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0, acc_cols = 0, pieces = 2,
+        row_bytes = 128;
     int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0, stages = 2;
 };
 
-TcGeom tc_geom(int p) {
+TcGeom tc_geom(int p, bool bf16) {
     TcGeom g;
     g.P = (p + 1) * (p + 1);
     g.Kpad = ((g.P + 31) / 32) * 32;
     g.Npad = ((g.P + 15) / 16) * 16;
     g.kchunks = g.Kpad / 32;
-    g.tmem_cols = g.Npad <= 128 ? 128 : 256;
-    g.a_bytes = kTcRows * 128;      // one of A_hi / A_lo for a 32-wide chunk
-    g.b_bytes = g.Npad * 128;       // one of B_hi / B_lo
-    g.stage_bytes = 2 * g.a_bytes + 2 * g.b_bytes;
-    g.stages = (kMaxStages * g.stage_bytes + 1024 <= 227 * 1024) ? kMaxStages : 2;
+    // two accumulators (leading products | the rest), each a power of two >= 32 columns
+    g.acc_cols = 32;
+    while (g.acc_cols < g.Npad) g.acc_cols *= 2;
+    g.tmem_cols = 2 * g.acc_cols;
+    g.pieces = bf16 ? 3 : 2;
+    g.row_bytes = bf16 ? 64 : 128;       // 32 K values of one row
+    g.a_bytes = kTcRows * g.row_bytes;   // one piece of A for a 32-wide chunk
+    g.b_bytes = g.Npad * g.row_bytes;    // one piece of B
+    g.stage_bytes = g.pieces * (g.a_bytes + g.b_bytes);
+    g.stages = (227 * 1024 - 1024) / g.stage_bytes;
+    if (g.stages > kMaxStages) g.stages = kMaxStages;
     g.smem_bytes = g.stages * g.stage_bytes + 1024;
     return g;
 }
 
-bool tc_supported(int p) { return tc_geom(p).Npad <= 256; }
+bool tc_supported(int p, bool bf16) {
+    const TcGeom g = tc_geom(p, bf16);
+    return g.Npad <= 256 && g.stages >= 2;
+}
 
-// byte offset of element (row, k) of a 32-wide chunk in the 128B-swizzled
-// K-major layout: 8-row atoms of 1024 B, 16-byte units XOR-ed with row % 8.
+// byte offset of element (row, k) of a 32-wide chunk in the swizzled K-major
+// layouts.  TF32: 128-byte rows, 8-row atoms of 1024 B, 16-byte units XOR-ed
+// with row % 8.  BF16: 64-byte rows, 8-row atoms of 512 B, 16-byte units
+// XOR-ed with (row % 8) / 2 (address bits 4-5 with bits 7-8).
 inline size_t swz_off(int row, int k) {
     return (size_t)(row >> 3) * 1024 + (size_t)(row & 7) * 128 +
            (size_t)(((k >> 2) ^ (row & 7)) << 4) + (size_t)(k & 3) * 4;
+}
+inline size_t swz64_off(int row, int k) {
+    return (size_t)(row >> 3) * 512 + (size_t)(row & 7) * 64 +
+           (size_t)(((k >> 3) ^ ((row & 7) >> 1)) << 4) + (size_t)(k & 7) * 2;
+}
+
+// round-to-nearest-even FP32 -> BF16 (finite inputs)
+inline uint16_t bf16_bits_host(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return (uint16_t)(b >> 16);
+}
+inline double bf16_value_host(uint16_t h) {
+    const uint32_t b = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &b, 4);
+    return (double)f;
 }
 
 inline float rna_tf32_host(float x) {
@@ -154,20 +194,35 @@ __device__ __forceinline__ uint32_t rna_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 B apart (stride byte offset), descriptor version 1
+// shared-memory matrix descriptor, K-major, descriptor version 1:
+//   128-byte swizzle (layout 2), 8-row atoms 1024 B apart, or
+//   64-byte swizzle (layout 4), 8-row atoms 512 B apart (stride byte offset).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)1 << 16;             // leading byte offset (unused with these swizzles)
     d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
     d |= (uint64_t)1 << 46;             // version
     d |= (uint64_t)2 << 61;             // 128-byte swizzle
     return d;
 }
-// instruction descriptor: D f32, A and B tf32, both K-major, N and M
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;             // 64-byte swizzle
+    return d;
+}
+// instruction descriptors: D f32, A and B K-major, N and M; A/B tf32 (kind::tf32)
+// or bf16 (kind::f16)
 __host__ __device__ constexpr uint32_t idesc_tf32(int N, int M) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int N, int M) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
@@ -177,6 +232,25 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t b
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
         "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
         : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// x = hi + mid + lo, each round-to-nearest bf16 of the remainder so far
+__device__ __forceinline__ void split_bf16x3(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
+    const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(bh);
+    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(bm);
+    const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
+    h = __bfloat16_as_ushort(bh);
+    m = __bfloat16_as_ushort(bm);
+    l = __bfloat16_as_ushort(bl);
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
@@ -200,7 +274,8 @@ constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator ind
 
 struct TcArgs {
     int mode, level;      // level: the target level of M2M / L2L launches
-    int D, P, ld, kchunks, Npad, tmem_cols, splits, stages;
+    int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages;
+    int bf16, pieces, a_bytes, b_bytes;  // operand format and per-piece tile bytes
     uint32_t idesc;
     const LevelInfo* linfo;
     const uint32_t* code;
@@ -211,7 +286,7 @@ struct TcArgs {
     float* Mout;           // M2M output (= M, other level)
     float* part;           // [splits-1][cells][ld]
     int64_t part_stride;   // cells_max * ld
-    const float* ops;      // [359][kchunks][2][Npad][32] swizzled
+    const unsigned char* ops;  // [359][kchunks][pieces][Npad rows] swizzled
     int* err;
     // M2L work list (written by k_tc_plan)
     const struct TcTile* tiles;
@@ -256,8 +331,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-    const int a_bytes = kTcRows * 128, b_bytes = a.Npad * 128;
-    const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    const int a_bytes = a.a_bytes, b_bytes = a.b_bytes, pieces = a.pieces;
+    const int stage_bytes = pieces * (a_bytes + b_bytes);
     const int NS = a.stages;
     __shared__ LevelInfo li;
     if (a.mode != MODE_M2L) stage_linfo(a.linfo, &li);
@@ -373,10 +448,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 if (!mbar_wait(&empty_bar[st], (use & 1) ^ 1)) { abort_sh = 1; break; }
                 if (abort_sh) break;
                 const int term = tlist[tl_begin + it / a.kchunks], kc = it % a.kchunks;
-                unsigned char* sB = base + st * stage_bytes + 2 * a_bytes;
-                mbar_arrive_expect_tx(&fullB_bar[st], 2 * b_bytes);
-                const float* src = a.ops + ((size_t)op_of(term) * a.kchunks + kc) * 2 * a.Npad * 32;
-                bulk_g2s(sB, src, 2 * b_bytes, &fullB_bar[st]);
+                unsigned char* sB = base + st * stage_bytes + pieces * a_bytes;
+                mbar_arrive_expect_tx(&fullB_bar[st], pieces * b_bytes);
+                const unsigned char* src =
+                    a.ops + ((size_t)op_of(term) * a.kchunks + kc) * pieces * b_bytes;
+                bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
                 last_copy_st = st;
                 last_copy_par = use & 1;
             }
@@ -392,15 +468,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 }
                 if (abort_sh) break;
                 tc_fence_after();
-                unsigned char* sA_hi = base + st * stage_bytes;
-                const uint32_t ah = smem_addr(sA_hi), al = ah + a_bytes;
-                const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+                const uint32_t ah = smem_addr(base + st * stage_bytes);
+                // accumulator 0 takes only the leading products hi x hi, the
+                // rest (2^-8 / 2^-11 of them and smaller) go to accumulator 1:
+                // the large running sum sees one tensor-core accumulation per
+                // K-step instead of six (three)
+                const uint32_t d0 = tmem, d1 = tmem + (uint32_t)a.acc_cols;
+                if (a.bf16) {
+                    // pieces hi, mid, lo of A then of B; 2 K-steps of 16 values
+                    const uint32_t am = ah + a_bytes, al = am + a_bytes;
+                    const uint32_t bh = ah + 3 * a_bytes, bm = bh + b_bytes, bl = bm + b_bytes;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                    mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
-                    mma_tf32(tmem, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, 1u);
-                    mma_tf32(tmem, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                        const uint32_t o = 32 * kk;
+                        mma_bf16(d1, sdesc64(am + o), sdesc64(bm + o), a.idesc, acc);
+                        mma_bf16(d1, sdesc64(ah + o), sdesc64(bl + o), a.idesc, 1u);
+                        mma_bf16(d1, sdesc64(al + o), sdesc64(bh + o), a.idesc, 1u);
+                        mma_bf16(d1, sdesc64(ah + o), sdesc64(bm + o), a.idesc, 1u);
+                        mma_bf16(d1, sdesc64(am + o), sdesc64(bh + o), a.idesc, 1u);
+                        mma_bf16(d0, sdesc64(ah + o), sdesc64(bh + o), a.idesc, acc);
+                    }
+                } else {
+                    const uint32_t al = ah + a_bytes;
+                    const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                        mma_tf32(d1, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, acc);
+                        mma_tf32(d1, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                        mma_tf32(d0, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
+                    }
                 }
                 mma_commit(&empty_bar[st]);  // frees the stage once these MMAs finish
             }
@@ -478,18 +576,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             if (!okw) { abort_sh = 1; break; }
             if (abort_sh) break;
             unsigned char* sA_hi = base + st * stage_bytes;
-            unsigned char* sA_lo = sA_hi + a_bytes;
+            if (a.bf16) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int r = r0 + 32 * j;
-                uint4 hi, lo;
-                hi.x = rna_tf32(v[j].x); lo.x = rna_tf32(v[j].x - __uint_as_float(hi.x));
-                hi.y = rna_tf32(v[j].y); lo.y = rna_tf32(v[j].y - __uint_as_float(hi.y));
-                hi.z = rna_tf32(v[j].z); lo.z = rna_tf32(v[j].z - __uint_as_float(hi.z));
-                hi.w = rna_tf32(v[j].w); lo.w = rna_tf32(v[j].w - __uint_as_float(hi.w));
-                const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
-                *reinterpret_cast<uint4*>(sA_hi + off) = hi;
-                *reinterpret_cast<uint4*>(sA_lo + off) = lo;
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + 32 * j;
+                    uint32_t h0, h1, h2, h3, m0, m1, m2, m3, l0, l1, l2, l3;
+                    split_bf16x3(v[j].x, h0, m0, l0);
+                    split_bf16x3(v[j].y, h1, m1, l1);
+                    split_bf16x3(v[j].z, h2, m2, l2);
+                    split_bf16x3(v[j].w, h3, m3, l3);
+                    // 4 values = half a 16-byte unit of the 64-byte row
+                    const int off = (r >> 3) * 512 + (r & 7) * 64 +
+                                    (((c >> 1) ^ ((r & 7) >> 1)) << 4) + (c & 1) * 8;
+                    *reinterpret_cast<uint2*>(sA_hi + off) = make_uint2(h0 | (h1 << 16), h2 | (h3 << 16));
+                    *reinterpret_cast<uint2*>(sA_hi + a_bytes + off) =
+                        make_uint2(m0 | (m1 << 16), m2 | (m3 << 16));
+                    *reinterpret_cast<uint2*>(sA_hi + 2 * a_bytes + off) =
+                        make_uint2(l0 | (l1 << 16), l2 | (l3 << 16));
+                }
+            } else {
+                unsigned char* sA_lo = sA_hi + a_bytes;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = r0 + 32 * j;
+                    uint4 hi, lo;
+                    hi.x = rna_tf32(v[j].x); lo.x = rna_tf32(v[j].x - __uint_as_float(hi.x));
+                    hi.y = rna_tf32(v[j].y); lo.y = rna_tf32(v[j].y - __uint_as_float(hi.y));
+                    hi.z = rna_tf32(v[j].z); lo.z = rna_tf32(v[j].z - __uint_as_float(hi.z));
+                    hi.w = rna_tf32(v[j].w); lo.w = rna_tf32(v[j].w - __uint_as_float(hi.w));
+                    const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+                    *reinterpret_cast<uint4*>(sA_hi + off) = hi;
+                    *reinterpret_cast<uint4*>(sA_lo + off) = lo;
+                }
             }
             fence_proxy_async();
             mbar_arrive(&fullA_bar[st]);
@@ -521,7 +639,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             for (int cb = half; cb * 16 < a.Npad; cb += 2) {
                 uint32_t r[16];
                 if (n_it > 0) {
-                    tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16), r);
+                    const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16);
+                    uint32_t r1[16];
+                    tmem_ld16(t0, r);
+                    tmem_ld16(t0 + (uint32_t)a.acc_cols, r1);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r1[j]));
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) r[j] = 0u;
@@ -804,10 +928,10 @@ __global__ void k_tc_reduce(int lfirst, int llast, int ld, int nparts, const Lev
 
 void host_m2l_offsets(int16_t out[8][189]);
 
-size_t m2l_tc_operand_bytes(int p) {
-    if (!tc_supported(p)) return 0;
-    TcGeom g = tc_geom(p);
-    return (size_t)kNumOps * g.kchunks * 2 * g.Npad * 32 * sizeof(float);
+size_t m2l_tc_operand_bytes(int p, bool bf16) {
+    if (!tc_supported(p, bf16)) return 0;
+    TcGeom g = tc_geom(p, bf16);
+    return (size_t)kNumOps * g.kchunks * g.pieces * g.b_bytes;
 }
 
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
@@ -821,29 +945,40 @@ size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
 
 // Operators 0..342: M2L by offset index; 343..350: M2M by child octant;
 // 351..358: L2L by child octant.  Each P x P (out x in) operator T becomes B
-// with B[k][n] = T[n][k], split into TF32 hi/lo and swizzled per 32-wide K
-// chunk: [op][chunk][hi | lo][Npad rows of 128 B].
-void m2l_tc_pack_operands(int p, const double* T_m2l, const double* T_m2m, const double* T_l2l,
-                          float* out) {
-    TcGeom g = tc_geom(p);
+// with B[k][n] = T[n][k], split into pieces (TF32 hi/lo or BF16 hi/mid/lo)
+// and swizzled per 32-wide K chunk: [op][chunk][piece][Npad rows].
+void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T_m2m,
+                          const double* T_l2l, void* out) {
+    const TcGeom g = tc_geom(p, bf16);
     const int P = g.P;
-    const size_t tile = (size_t)g.Npad * 32;  // floats per hi (or lo) tile
+    unsigned char* bytes = static_cast<unsigned char*>(out);
     for (int opi = 0; opi < kNumOps; ++opi) {
         const double* T = opi < kOpM2M ? T_m2l + (size_t)opi * P * P
                           : opi < kOpL2L ? T_m2m + (size_t)(opi - kOpM2M) * P * P
                                          : T_l2l + (size_t)(opi - kOpL2L) * P * P;
         for (int kc = 0; kc < g.kchunks; ++kc) {
-            float* hi = out + ((size_t)opi * g.kchunks + kc) * 2 * tile;
-            float* lo = hi + tile;
+            unsigned char* chunk = bytes + ((size_t)opi * g.kchunks + kc) * g.pieces * g.b_bytes;
             for (int n = 0; n < g.Npad; ++n)
                 for (int k = 0; k < 32; ++k) {
                     const int kk = kc * 32 + k;
-                    double t = (n < P && kk < P) ? T[(size_t)n * P + kk] : 0.0;
-                    float h = rna_tf32_host((float)t);
-                    float r = rna_tf32_host((float)(t - (double)h));
-                    const size_t o = swz_off(n, k) / 4;
-                    hi[o] = h;
-                    lo[o] = r;
+                    const double t = (n < P && kk < P) ? T[(size_t)n * P + kk] : 0.0;
+                    if (bf16) {
+                        const uint16_t h = bf16_bits_host((float)t);
+                        const double r1 = t - bf16_value_host(h);
+                        const uint16_t m = bf16_bits_host((float)r1);
+                        const double r2 = r1 - bf16_value_host(m);
+                        const uint16_t l = bf16_bits_host((float)r2);
+                        const size_t o = swz64_off(n, k);
+                        memcpy(chunk + o, &h, 2);
+                        memcpy(chunk + g.b_bytes + o, &m, 2);
+                        memcpy(chunk + 2 * g.b_bytes + o, &l, 2);
+                    } else {
+                        const float h = rna_tf32_host((float)t);
+                        const float r = rna_tf32_host((float)(t - (double)h));
+                        const size_t o = swz_off(n, k);
+                        memcpy(chunk + o, &h, 4);
+                        memcpy(chunk + g.b_bytes + o, &r, 4);
+                    }
                 }
         }
     }
@@ -856,13 +991,15 @@ cudaError_t m2l_tc_init() {
     if (e != cudaSuccess) return e;
     int most = 0;
     for (int q = 2; q <= kMaxOrder; ++q)
-        if (tc_supported(q) && tc_geom(q).smem_bytes > most) most = tc_geom(q).smem_bytes;
+        for (int b = 0; b < 2; ++b)
+            if (tc_supported(q, b) && tc_geom(q, b).smem_bytes > most) most = tc_geom(q, b).smem_bytes;
     return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
 }
 
 static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     (void)n;
-    TcGeom g = tc_geom(ws.p);
+    const bool bf16 = ws.tc_bf16 != 0;
+    TcGeom g = tc_geom(ws.p, bf16);
     TcArgs a;
     memset(&a, 0, sizeof a);
     a.D = D;
@@ -871,9 +1008,14 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.kchunks = g.kchunks;
     a.Npad = g.Npad;
     a.tmem_cols = g.tmem_cols;
+    a.acc_cols = g.acc_cols;
     a.splits = splits;
     a.stages = g.stages;
-    a.idesc = idesc_tf32(g.Npad, kTcRows);
+    a.bf16 = bf16 ? 1 : 0;
+    a.pieces = g.pieces;
+    a.a_bytes = g.a_bytes;
+    a.b_bytes = g.b_bytes;
+    a.idesc = bf16 ? idesc_bf16(g.Npad, kTcRows) : idesc_tf32(g.Npad, kTcRows);
     a.linfo = ws.linfo;
     a.code = ws.code;
     a.cid = ws.cid;
@@ -884,7 +1026,7 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.Mout = (float*)ws.M;
     a.part = ws.tc_part;
     a.part_stride = ws.cells_max * ws.ld;
-    a.ops = ws.T_m2l_tc;
+    a.ops = static_cast<const unsigned char*>(ws.T_m2l_tc);
     a.err = ws.err;
     return a;
 }
@@ -904,7 +1046,7 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
     TcArgs a = base_args(n, D, ws, splits);
     a.mode = MODE_M2M;
     a.level = l;
-    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, tc_geom(ws.p).smem_bytes, s>>>(a);
+    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || splits == 1) return e;
     k_tc_reduce<<<152 * 2, 256, 0, s>>>(l, l, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
@@ -914,7 +1056,7 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
 
 cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
-    const int smem = tc_geom(ws.p).smem_bytes;
+    const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
     int64_t tiles = 0;
     for (int l = 2; l <= D; ++l) tiles += (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
     if (tiles > ws.tc_tiles_cap) return cudaErrorInvalidValue;

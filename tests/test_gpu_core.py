@@ -94,7 +94,7 @@ def test_fmm_fp64_converges_geometrically_in_p(sphere4k):
     assert errs[3][1] < 1e-7, errs
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_fmm_auto_depth_error(sphere4k, precision):
     pos, q, Eo, phio = sphere4k
     plan = pt.Plan(len(q), p=10, leaf_max=32, depth=-1, precision=precision)
@@ -106,28 +106,30 @@ def test_fmm_auto_depth_error(sphere4k, precision):
         kp, _, _ = oracle.leaf_keys(pos, d - 1)
         assert len(q) / len(np.unique(kp)) > 32
     eF = rel(E.cpu().numpy().T, Eo)
-    assert eF < {"fp64": 1e-5, "fp32": 2e-5, "tf32x3": 2e-5}[precision], (d, eF)
+    assert eF < {"fp64": 1e-5, "fp32": 2e-5, "tf32x3": 2e-5, "bf16x3": 2e-5}[precision], (d, eF)
     plan.close()
 
 
+@pytest.mark.parametrize("tc", ["tf32x3", "bf16x3"])
 @pytest.mark.parametrize("depth", [2, 3, 4])
-def test_tensor_core_m2l_matches_cuda_core_m2l(sphere4k, depth):
-    # Far field (P2M, M2M, M2L, L2L, L2P) with M2L on the tensor cores (3xTF32)
-    # vs the same stages with M2L in FP32 on the CUDA cores: they differ only
-    # by the split-TF32 product rounding (about 2^-22 per product).
+def test_tensor_core_m2l_matches_cuda_core_m2l(sphere4k, depth, tc):
+    # Far field (P2M, M2M, M2L, L2L, L2P) with M2M/M2L/L2L on the tensor cores
+    # vs the same stages in FP32 on the CUDA cores: they differ only by the
+    # split-product rounding (about 2^-21 per 3xTF32 product, 2^-24 per
+    # BF16x3 product, the same as an FP32 multiply) and the FP32 sums.
     pos, q, Eo, _ = sphere4k
     out = {}
-    for prec in ("fp32", "tf32x3"):
+    for prec in ("fp32", tc):
         plan = pt.Plan(len(q), p=10, depth=depth, precision=prec)
         plan.set_phases(pt.PT_PHASE_FAR)
         E, _ = plan.forces(dev_pos(pos), dev_vec(q))
         out[prec] = E.cpu().numpy().T
         plan.close()
-    assert rel(out["tf32x3"], out["fp32"]) < 1e-5
+    assert rel(out[tc], out["fp32"]) < {"tf32x3": 1e-5, "bf16x3": 5e-6}[tc]
 
 
 def test_field_of_one_and_two_ions():
-    for precision in ("fp64", "fp32", "tf32x3"):
+    for precision in ("fp64", "fp32", "tf32x3", "bf16x3"):
         plan = pt.Plan(2, p=6, precision=precision)
         E, phi = plan.forces(dev_pos(np.array([[1e-5, -2e-5, 3e-5]])), dev_vec([W.E_CHARGE]))
         assert torch.all(E == 0) and torch.all(phi == 0)
@@ -182,7 +184,7 @@ def test_lone_ion_trajectory_bit_exact(laser_on):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_one_step_is_the_drift_plus_the_fmm_field_kick(precision):
     # After one step the GPU and oracle states differ only through the field:
     # v_gpu - v_oracle = R(w_c dt/2) (q/m) dt (E_fmm(x_mid) - E_direct(x_mid)),
