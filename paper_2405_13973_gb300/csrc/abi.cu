@@ -427,17 +427,20 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         int64_t tcap = 0;
         for (int l = 2; l <= ws.depth_max; ++l) tcap += ((pow8(l) < n_max ? pow8(l) : n_max) + 127) / 128 + 8;
         ws.tc_tiles_cap = tcap > 0 ? tcap : 1;
-        ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap));
+        ws.tc_slab_cap = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap);
+        ws.tc_part_floats = m2l_tc_part_floats(cells, ws.ld, ws.tc_splits_max, ws.tc_tiles_cap,
+                                               ws.tc_slab_cap);
+        ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
         ok = ok && dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p, ws.tc_bf16 != 0)) &&
-             dalloc(pl, ws.tc_part, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) *
-                                        cells * ws.ld);
+             dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
     }
     if (!ok) {
         free_plan(pl);
         return PT_ERR_OOM;
     }
-    if ((ws.tc_work && cudaMemset(ws.tc_work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap)) != cudaSuccess) ||
-        (ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * (size_t)(ws.tc_splits_max > 1 ? ws.tc_splits_max - 1 : 1) * cells * ws.ld) != cudaSuccess) ||
+    if ((ws.tc_work &&
+         cudaMemset(ws.tc_work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap)) != cudaSuccess) ||
+        (ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * ws.tc_part_floats) != cudaSuccess) ||
         cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||

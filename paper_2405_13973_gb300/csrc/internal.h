@@ -81,8 +81,10 @@ struct Workspace {
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
     void* T_m2l_tc = nullptr;   // tensor-core operand tiles (mixed modes)
     int tc_bf16 = 0;            // tensor-core operand format: 0 TF32 hi/lo, 1 BF16 hi/mid/lo
-    float* tc_part = nullptr;   // [tc_splits_max - 1][cells_max][ld] M2L split partials
-    int tc_splits_max = 1;
+    float* tc_part = nullptr;   // M2M split partials, then M2L item slabs (tc_part_floats)
+    size_t tc_part_floats = 0;
+    int tc_splits_max = 1;      // M2M CTAs per tile
+    int64_t tc_slab_cap = 1;    // M2L items of rank > 0 (partial slabs)
     void* tc_work = nullptr;    // M2L work list (tiles, items)
     int64_t tc_tiles_cap = 0;
 };
@@ -128,7 +130,11 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaS
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
-size_t m2l_tc_work_bytes(int64_t tiles_cap);
+size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap);
+// partial slabs of the M2L work items (at most a 256 MB pool)
+int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap);
+size_t m2l_tc_part_floats(int64_t cells_max, int ld, int m2m_splits, int64_t tiles_cap,
+                          int64_t slab_cap);
 void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T_m2m,
                           const double* T_l2l, void* out);
 // M2M of one level (targets = parents at level l) on the tensor cores.

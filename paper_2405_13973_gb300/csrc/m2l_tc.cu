@@ -57,17 +57,21 @@ namespace pt {
 
 namespace {
 
-constexpr int kTcThreads = 320;
+constexpr int kTcThreads = 448;
 constexpr int kMaxStages = 4;
 constexpr int kTcRows = 128;
-constexpr int kMaxSplits = 12;
+constexpr int kMaxSplits = 8;    // M2M: CTAs per tile (one per child octant at most)
+constexpr int kChainCap = 4;     // M2L: at most this many offsets per work item
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 struct TcGeom {
     int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0, acc_cols = 0, pieces = 2,
         row_bytes = 128;
-    int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0, stages = 2;
+    int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0, stages = 2, raw = 2;
 };
+
+// raw FP32 A chunks in flight per producer thread (cp.async ring): 16 KB a slot
+constexpr int kRawSlotBytes = 128 * 32 * 4;
 
 TcGeom tc_geom(int p, bool bf16) {
     TcGeom g;
@@ -84,9 +88,15 @@ TcGeom tc_geom(int p, bool bf16) {
     g.a_bytes = kTcRows * g.row_bytes;   // one piece of A for a 32-wide chunk
     g.b_bytes = g.Npad * g.row_bytes;    // one piece of B
     g.stage_bytes = g.pieces * (g.a_bytes + g.b_bytes);
-    g.stages = (227 * 1024 - 1024) / g.stage_bytes;
+    // three raw A slots when three operand stages still fit, else two
+    g.raw = 3;
+    g.stages = (227 * 1024 - 1024 - g.raw * kRawSlotBytes) / g.stage_bytes;
+    if (g.stages < 3) {
+        g.raw = 2;
+        g.stages = (227 * 1024 - 1024 - g.raw * kRawSlotBytes) / g.stage_bytes;
+    }
     if (g.stages > kMaxStages) g.stages = kMaxStages;
-    g.smem_bytes = g.stages * g.stage_bytes + 1024;
+    g.smem_bytes = g.stages * g.stage_bytes + g.raw * kRawSlotBytes + 1024;
     return g;
 }
 
@@ -179,6 +189,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             "r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+// 16-byte global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// wait until at most n (1 or 2) of this thread's newest copy groups are pending
+__device__ __forceinline__ void cp_async_wait(int n) {
+    if (n >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -274,7 +298,7 @@ constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator ind
 
 struct TcArgs {
     int mode, level;      // level: the target level of M2M / L2L launches
-    int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages;
+    int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages, raw;
     int bf16, pieces, a_bytes, b_bytes;  // operand format and per-piece tile bytes
     uint32_t idesc;
     const LevelInfo* linfo;
@@ -284,7 +308,7 @@ struct TcArgs {
     const float* M;
     float* L;
     float* Mout;           // M2M output (= M, other level)
-    float* part;           // [splits-1][cells][ld]
+    float* part;           // M2M: [splits-1][cells][ld]; M2L: [item][128][ld] slabs
     int64_t part_stride;   // cells_max * ld
     const unsigned char* ops;  // [359][kchunks][pieces][Npad rows] swizzled
     int* err;
@@ -295,9 +319,10 @@ struct TcArgs {
 };
 
 // One M2L tile (128 targets of one level and octant) and its non-empty
-// offsets; one work item = a contiguous run of them (one CTA).
+// offsets; one work item = a contiguous run of them.  The tile's items are
+// item0 .. item0 + nsplit - 1 of the work list.
 struct TcTile {
-    int level, oct, base, rows, cnt, nsplit, pad0, pad1;
+    int level, oct, base, rows, cnt, nsplit, item0, pad1;
     uint8_t terms[192];
 };
 struct TcItem {
@@ -317,83 +342,127 @@ __device__ __forceinline__ void stage_linfo(const LevelInfo* g, LevelInfo* s) {
 }
 
 // Warp roles: warp 0 = operator producer (bulk copies), warp 1 = MMA issuer,
-// warps 2..9 = A producers (gather + split) and, at the end, the epilogue.
+// warps 2..9 = A producers (gather + split), warps 10..13 = epilogue (one
+// TMEM lane quarter each).  The epilogue has warps of its own so that the
+// producers run on into the next work item while the accumulators drain.
 constexpr int kProdWarps = 8;
 constexpr int kWarpA0 = 2;
+constexpr int kWarpEpi0 = kWarpA0 + kProdWarps;
+constexpr int kEpiThreads = 128;
 
+// One unit of work for a CTA: a run [begin, end) of the term list of one tile
+// of 128 target cells.  rank > 0 runs of M2L (and split > 0 of M2M) write
+// partial sums that a reduction adds afterwards.
+struct TcWork {
+    int level, oct, base, rows, begin, end, rank, tile, slot;
+};
+
+// Work item idx of this launch: M2L reads the device work list; M2M and L2L
+// derive (tile, split) from the block index (one item per CTA).
+template <int MODE>
+__device__ __forceinline__ bool tc_work(const TcArgs& a, const LevelInfo& li, int idx, TcWork& w) {
+    w.rows = 0;
+    if (MODE == MODE_M2L) {
+        const TcItem it = a.items[idx];
+        const TcTile& tl = a.tiles[it.tile];
+        w.level = tl.level;
+        w.oct = tl.oct;
+        w.base = tl.base;
+        w.rows = tl.rows;
+        w.begin = it.begin;
+        w.end = it.end;
+        w.rank = it.rank;
+        w.tile = it.tile;
+        w.slot = idx;
+        return w.rows > 0;
+    }
+    const int gsplit = MODE == MODE_L2L ? 1 : a.splits;  // CTAs per tile
+    const int split = idx % gsplit;
+    const int l0 = a.level;
+    int t = idx / gsplit, acc = 0;
+    const int ngroups = MODE == MODE_M2M ? 1 : 8;
+    for (int o = 0; o < ngroups; ++o) {
+        int s0, s1;
+        if (MODE == MODE_M2M) {
+            s0 = li.gbase[l0];
+            s1 = li.gbase[l0 + 1];
+        } else {
+            s0 = li.oct_start[l0][o];
+            s1 = li.oct_start[l0][o + 1];
+        }
+        const int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
+        if (t < acc + nt) {
+            w.level = l0;
+            w.oct = o;
+            w.base = s0 + (t - acc) * kTcRows;
+            w.rows = min(kTcRows, s1 - w.base);
+            break;
+        }
+        acc += nt;
+    }
+    const int cnt = MODE == MODE_M2M ? 8 : (l0 >= 3 ? 1 : 0);
+    w.begin = (cnt * split) / gsplit;
+    w.end = (cnt * (split + 1)) / gsplit;
+    w.rank = split;
+    w.tile = -1;
+    w.slot = -1;
+    return w.rows > 0;
+}
+
+// packed operator index of term j of a work item
+template <int MODE>
+__device__ __forceinline__ int tc_op(const TcArgs& a, const TcWork& w, int j) {
+    if (MODE == MODE_M2L) return c_tc_off[w.oct][a.tiles[w.tile].terms[j]];
+    if (MODE == MODE_M2M) return kOpM2M + j;
+    return kOpL2L + w.oct;
+}
+
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// One instantiation per mode and operand format (MODE == MODE, BF16 == BF16):
+// each kernel carries only its own paths.
+template <int MODE, int BF16>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     extern __shared__ unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
-        empty_bar[kMaxStages], acc_bar, drain_bar;
+        empty_bar[kMaxStages], accf_bar, acce_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ uint8_t tlist[192];
-    __shared__ int t_level, t_oct, t_base, t_rows, t_split, tl_begin, tl_end, abort_sh, tile_idx;
+    __shared__ int abort_sh;
+    __shared__ LevelInfo li;
+    volatile int* abort_v = &abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int a_bytes = a.a_bytes, b_bytes = a.b_bytes, pieces = a.pieces;
     const int stage_bytes = pieces * (a_bytes + b_bytes);
     const int NS = a.stages;
-    __shared__ LevelInfo li;
-    if (a.mode != MODE_M2L) stage_linfo(a.linfo, &li);
-    __syncthreads();
-
+    // work items of this CTA: idx = first, first + stride, ... < count
+    int count, first, stride;
+    if (MODE == MODE_M2L) {
+        count = a.hdr->n_items;
+        first = blockIdx.x;
+        stride = gridDim.x;
+    } else {
+        count = blockIdx.x + 1;
+        first = blockIdx.x;
+        stride = 1;
+        stage_linfo(a.linfo, &li);
+    }
+    if (first >= count) return;  // uniform across the block
     if (tid == 0) {
-        t_rows = 0;
         abort_sh = 0;
-        if (a.mode == MODE_M2L) {
-            // this CTA's work item: a run of one tile's non-empty offsets
-            if ((int)blockIdx.x < a.hdr->n_items) {
-                const TcItem it = a.items[blockIdx.x];
-                const TcTile& tl = a.tiles[it.tile];
-                t_level = tl.level;
-                t_oct = tl.oct;
-                t_base = tl.base;
-                t_rows = tl.rows;
-                t_split = it.rank;
-                tl_begin = it.begin;
-                tl_end = it.end;
-                tile_idx = it.tile;
-            }
-        } else {
-            // which (group, tile, split) of the launch's level is this CTA?
-            const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;  // CTAs per tile
-            const int split = blockIdx.x % gsplit;
-            int t = blockIdx.x / gsplit, acc = 0;
-            const int l0 = a.level;
-            const int ngroups = a.mode == MODE_M2M ? 1 : 8;
-            for (int o = 0; o < ngroups; ++o) {
-                int s0, s1;
-                if (a.mode == MODE_M2M) {
-                    s0 = li.gbase[l0];
-                    s1 = li.gbase[l0 + 1];
-                } else {
-                    s0 = li.oct_start[l0][o];
-                    s1 = li.oct_start[l0][o + 1];
-                }
-                int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
-                if (t < acc + nt) {
-                    t_level = l0;
-                    t_oct = o;
-                    t_base = s0 + (t - acc) * kTcRows;
-                    t_rows = min(kTcRows, s1 - t_base);
-                    break;
-                }
-                acc += nt;
-            }
-            t_split = split;
-        }
-    }
-    __syncthreads();
-    if (t_rows <= 0) return;
-    const int l = t_level, oct = t_oct, tbase = t_base, rows = t_rows, split = t_split;
-    const int lim = 1 << l;
-    if (a.mode == MODE_M2L) {
-        for (int k = tid; k < tl_end - tl_begin; k += kTcThreads)
-            tlist[k] = a.tiles[tile_idx].terms[tl_begin + k];
-    }
-    if (tid == 0) {
-        mbar_init(&acc_bar, 1);
+        mbar_init(&accf_bar, 1);
+        mbar_init(&acce_bar, kEpiThreads);
         mbar_init(&drain_bar, 1);
         for (int s = 0; s < NS; ++s) {
             mbar_init(&fullA_bar[s], kProdWarps * 32);
@@ -412,272 +481,321 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
-        if (a.mode == MODE_M2L) {
-            tl_end -= tl_begin;   // tlist holds this item's terms from index 0
-            tl_begin = 0;
-        } else {
-            int cnt = 0;
-            if (a.mode == MODE_M2M) {
-                for (int term = 0; term < 8; ++term) tlist[cnt++] = (uint8_t)term;
-            } else if (l >= 3) {
-                tlist[cnt++] = 0;
-            }
-            const int gsplit = a.mode == MODE_L2L ? 1 : a.splits;
-            tl_begin = (cnt * split) / gsplit;
-            tl_end = (cnt * (split + 1)) / gsplit;
-        }
-    }
-    __syncthreads();
     const uint32_t tmem = tmem_base_sh;
-    const int n_it = (tl_end - tl_begin) * a.kchunks;
 
-    auto op_of = [&](int term) -> int {
-        if (a.mode == MODE_M2L) return c_tc_off[oct][term];
-        if (a.mode == MODE_M2M) return kOpM2M + term;
-        return kOpL2L + oct;
-    };
+    int issued_par[kMaxStages];  // operator producer: parity of the last copy per stage
+#pragma unroll
+    for (int s = 0; s < kMaxStages; ++s) issued_par[s] = -1;
 
-    int last_copy_st = -1;
-    uint32_t last_copy_par = 0;
     if (warp == 0) {
         // ---- operator producer
         if (lane == 0) {
-            for (int it = 0; it < n_it; ++it) {
-                const int st = it % NS, use = it / NS;
-                if (!mbar_wait(&empty_bar[st], (use & 1) ^ 1)) { abort_sh = 1; break; }
-                if (abort_sh) break;
-                const int term = tlist[tl_begin + it / a.kchunks], kc = it % a.kchunks;
-                unsigned char* sB = base + st * stage_bytes + pieces * a_bytes;
-                mbar_arrive_expect_tx(&fullB_bar[st], pieces * b_bytes);
-                const unsigned char* src =
-                    a.ops + ((size_t)op_of(term) * a.kchunks + kc) * pieces * b_bytes;
-                bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
-                last_copy_st = st;
-                last_copy_par = use & 1;
+            int g = 0;
+            for (int idx = first; idx < count && !*abort_v; idx += stride) {
+                TcWork w;
+                if (!tc_work<MODE>(a, li, idx, w)) continue;
+                const int n_it = (w.end - w.begin) * a.kchunks;
+                for (int it = 0; it < n_it; ++it, ++g) {
+                    const int st = g % NS, use = g / NS;
+                    if (!mbar_wait_or_abort(&empty_bar[st], (use & 1) ^ 1, abort_v)) {
+                        *abort_v = 1;
+                        break;
+                    }
+                    const int j = w.begin + it / a.kchunks, kc = it % a.kchunks;
+                    unsigned char* sB = base + st * stage_bytes + pieces * a_bytes;
+                    mbar_arrive_expect_tx(&fullB_bar[st], pieces * b_bytes);
+                    const unsigned char* src =
+                        a.ops + ((size_t)tc_op<MODE>(a, w, j) * a.kchunks + kc) * pieces * b_bytes;
+                    bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
+                    issued_par[st] = use & 1;
+                }
             }
         }
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            for (int it = 0; it < n_it; ++it) {
-                const int st = it % NS, use = it / NS;
-                if (!mbar_wait(&fullB_bar[st], use & 1) || !mbar_wait(&fullA_bar[st], use & 1)) {
-                    abort_sh = 1;
+            int g = 0, jacc = 0;
+            for (int idx = first; idx < count && !*abort_v; idx += stride) {
+                TcWork w;
+                if (!tc_work<MODE>(a, li, idx, w)) continue;
+                const int n_it = (w.end - w.begin) * a.kchunks;
+                if (n_it == 0) continue;
+                // the epilogue of the previous item has read the accumulators
+                if (jacc > 0 && !mbar_wait_or_abort(&acce_bar, (jacc - 1) & 1, abort_v)) {
+                    *abort_v = 1;
                     break;
                 }
-                if (abort_sh) break;
                 tc_fence_after();
-                const uint32_t ah = smem_addr(base + st * stage_bytes);
                 // accumulator 0 takes only the leading products hi x hi, the
-                // rest (2^-8 / 2^-11 of them and smaller) go to accumulator 1:
-                // the large running sum sees one tensor-core accumulation per
-                // K-step instead of six (three)
+                // rest (2^-8 / 2^-11 of them and smaller) go to accumulator 1
                 const uint32_t d0 = tmem, d1 = tmem + (uint32_t)a.acc_cols;
-                if (a.bf16) {
-                    // pieces hi, mid, lo of A then of B; 2 K-steps of 16 values
-                    const uint32_t am = ah + a_bytes, al = am + a_bytes;
-                    const uint32_t bh = ah + 3 * a_bytes, bm = bh + b_bytes, bl = bm + b_bytes;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                        const uint32_t o = 32 * kk;
-                        mma_bf16(d1, sdesc64(am + o), sdesc64(bm + o), a.idesc, acc);
-                        mma_bf16(d1, sdesc64(ah + o), sdesc64(bl + o), a.idesc, 1u);
-                        mma_bf16(d1, sdesc64(al + o), sdesc64(bh + o), a.idesc, 1u);
-                        mma_bf16(d1, sdesc64(ah + o), sdesc64(bm + o), a.idesc, 1u);
-                        mma_bf16(d1, sdesc64(am + o), sdesc64(bh + o), a.idesc, 1u);
-                        mma_bf16(d0, sdesc64(ah + o), sdesc64(bh + o), a.idesc, acc);
+                for (int it = 0; it < n_it; ++it, ++g) {
+                    const int st = g % NS, use = g / NS;
+                    if (!mbar_wait_or_abort(&fullB_bar[st], use & 1, abort_v) ||
+                        !mbar_wait_or_abort(&fullA_bar[st], use & 1, abort_v)) {
+                        *abort_v = 1;
+                        break;
                     }
-                } else {
-                    const uint32_t al = ah + a_bytes;
-                    const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+                    tc_fence_after();
+                    const uint32_t ah = smem_addr(base + st * stage_bytes);
+                    if (BF16) {
+                        // pieces hi, mid, lo of A then of B; 2 K-steps of 16 values
+                        const uint32_t am = ah + a_bytes, al = am + a_bytes;
+                        const uint32_t bh = ah + 3 * a_bytes, bm = bh + b_bytes, bl = bm + b_bytes;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                        mma_tf32(d1, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, acc);
-                        mma_tf32(d1, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
-                        mma_tf32(d0, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                            const uint32_t o = 32 * kk;
+                            mma_bf16(d1, sdesc64(am + o), sdesc64(bm + o), a.idesc, acc);
+                            mma_bf16(d1, sdesc64(ah + o), sdesc64(bl + o), a.idesc, 1u);
+                            mma_bf16(d1, sdesc64(al + o), sdesc64(bh + o), a.idesc, 1u);
+                            mma_bf16(d1, sdesc64(ah + o), sdesc64(bm + o), a.idesc, 1u);
+                            mma_bf16(d1, sdesc64(am + o), sdesc64(bh + o), a.idesc, 1u);
+                            mma_bf16(d0, sdesc64(ah + o), sdesc64(bh + o), a.idesc, acc);
+                        }
+                    } else {
+                        const uint32_t al = ah + a_bytes;
+                        const uint32_t bh = ah + 2 * a_bytes, bl = bh + b_bytes;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+                            mma_tf32(d1, sdesc(ah + 32 * kk), sdesc(bl + 32 * kk), a.idesc, acc);
+                            mma_tf32(d1, sdesc(al + 32 * kk), sdesc(bh + 32 * kk), a.idesc, 1u);
+                            mma_tf32(d0, sdesc(ah + 32 * kk), sdesc(bh + 32 * kk), a.idesc, acc);
+                        }
                     }
+                    mma_commit(&empty_bar[st]);  // frees the stage once these MMAs finish
                 }
-                mma_commit(&empty_bar[st]);  // frees the stage once these MMAs finish
+                if (*abort_v) break;
+                mma_commit(&accf_bar);  // this item's accumulators are complete
+                ++jacc;
             }
-            if (n_it > 0) mma_commit(&acc_bar);  // accumulator complete
         }
-    } else {
-        // ---- A producers: each thread owns rows r0 + 32 j (j < 4) and 16-byte unit c
+    } else if (warp < kWarpEpi0) {
+        // ---- A producers: each thread owns rows r0 + 32 j (j < 4) and 16-byte unit c.
+        // Its raw FP32 values travel by cp.async into its own slots of a ring
+        // of a.raw chunks, a.raw - 1 iterations ahead of their split.
         const int ta = tid - kWarpA0 * 32;
         const int r0 = ta >> 3, c = ta & 7;
-        int tix[4], tiy[4], tiz[4];
-        uint32_t tcode[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = r0 + 32 * j;
-            tcode[j] = 0;
-            tix[j] = tiy[j] = tiz[j] = 0;
-            if (r < rows) {
-                tcode[j] = a.code[tbase + r];
-                demorton3(tcode[j], tix[j], tiy[j], tiz[j]);
-            }
-        }
-        const float* src_base = a.mode == MODE_L2L ? a.L : a.M;
-        // source cells of this thread's rows for a term
-        auto sources = [&](int ti, int (&gout)[4]) {
-            const int term = tlist[tl_begin + ti];
-            const int opi = op_of(term);
+        const float* src_base = MODE == MODE_L2L ? a.L : a.M;
+        unsigned char* raw = base + NS * stage_bytes;  // [slot][j][256 threads][16 B]
+        const int R = a.raw;
+        int g = 0;
+        for (int idx = first; idx < count && !*abort_v; idx += stride) {
+            TcWork w;
+            if (!tc_work<MODE>(a, li, idx, w)) continue;
+            const int n_it = (w.end - w.begin) * a.kchunks;
+            const int l = w.level, lim = 1 << l;
+            int tix[4], tiy[4], tiz[4];
+            uint32_t tcode[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int gs = -1;
-                if (r0 + 32 * j < rows) {
-                    if (a.mode == MODE_M2L) {
-                        int sx = tix[j] - (opi / 49 - 3), sy = tiy[j] - ((opi / 7) % 7 - 3),
-                            sz = tiz[j] - (opi % 7 - 3);
-                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
-                            gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
-                    } else if (a.mode == MODE_M2M) {
-                        gs = a.cid[a.off[l + 1] + ((tcode[j] << 3) | (uint32_t)term)];
-                    } else {
-                        gs = a.cid[a.off[l - 1] + (tcode[j] >> 3)];
+                const int r = r0 + 32 * j;
+                tcode[j] = 0;
+                tix[j] = tiy[j] = tiz[j] = 0;
+                if (r < w.rows) {
+                    tcode[j] = a.code[w.base + r];
+                    demorton3(tcode[j], tix[j], tiy[j], tiz[j]);
+                }
+            }
+            // source cells of this thread's rows for term t
+            int pg[4] = {-1, -1, -1, -1};
+            auto sources = [&](int t) {
+                int opi = 0, term = t;
+                if (MODE == MODE_M2L) opi = c_tc_off[w.oct][a.tiles[w.tile].terms[t]];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int gs = -1;
+                    if (r0 + 32 * j < w.rows) {
+                        if (MODE == MODE_M2L) {
+                            int sx = tix[j] - (opi / 49 - 3), sy = tiy[j] - ((opi / 7) % 7 - 3),
+                                sz = tiz[j] - (opi % 7 - 3);
+                            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                                gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
+                        } else if (MODE == MODE_M2M) {
+                            gs = a.cid[a.off[l + 1] + ((tcode[j] << 3) | (uint32_t)term)];
+                        } else {
+                            gs = a.cid[a.off[l - 1] + (tcode[j] >> 3)];
+                        }
+                    }
+                    pg[j] = gs;
+                }
+            };
+            // copies of iteration j into ring slot (g + j) % R; one group per iteration
+            // (empty past the end, so that the count of pending groups is fixed)
+            auto prefetch = [&](int j) {
+                if (j < n_it) {
+                    const int kc = j % a.kchunks;
+                    if (kc == 0) sources(w.begin + j / a.kchunks);
+                    unsigned char* slot = raw + ((g + j) % R) * kRawSlotBytes + ta * 16;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int gs = pg[q];
+                        const float* src = gs >= 0 ? src_base + (int64_t)gs * a.ld + kc * 32 + c * 4
+                                                   : src_base;
+                        cp_async16(slot + q * 4096, src, gs >= 0 ? 16u : 0u);
                     }
                 }
-                gout[j] = gs;
-            }
-        };
-        auto gather = [&](int kc, const int (&gs)[4], float4 (&v)[4]) {
+                cp_async_commit();
+            };
+            for (int j = 0; j < R - 1; ++j) prefetch(j);
+            for (int it = 0; it < n_it; ++it) {
+                prefetch(it + R - 1);
+                const int gg = g + it;
+                const int st = gg % NS, use = gg / NS;
+                cp_async_wait(R - 1);  // this thread's copies of iteration it have landed
+                const unsigned char* mine = raw + (gg % R) * kRawSlotBytes + ta * 16;
+                float4 v[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gs[j] >= 0)
-                    v[j] = *reinterpret_cast<const float4*>(src_base + (int64_t)gs[j] * a.ld + kc * 32 + c * 4);
+                for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const float4*>(mine + q * 4096);
+                // one lane polls the stage barrier for the whole warp
+                int okw = 1;
+                if (lane == 0) okw = mbar_wait_or_abort(&empty_bar[st], (use & 1) ^ 1, abort_v) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    *abort_v = 1;
+                    break;
+                }
+                unsigned char* sA_hi = base + st * stage_bytes;
+                if (BF16) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = r0 + 32 * j;
+                        uint32_t h0, h1, h2, h3, m0, m1, m2, m3, l0, l1, l2, l3;
+                        split_bf16x3(v[j].x, h0, m0, l0);
+                        split_bf16x3(v[j].y, h1, m1, l1);
+                        split_bf16x3(v[j].z, h2, m2, l2);
+                        split_bf16x3(v[j].w, h3, m3, l3);
+                        // 4 values = half a 16-byte unit of the 64-byte row
+                        const int off = (r >> 3) * 512 + (r & 7) * 64 +
+                                        (((c >> 1) ^ ((r & 7) >> 1)) << 4) + (c & 1) * 8;
+                        *reinterpret_cast<uint2*>(sA_hi + off) =
+                            make_uint2(h0 | (h1 << 16), h2 | (h3 << 16));
+                        *reinterpret_cast<uint2*>(sA_hi + a_bytes + off) =
+                            make_uint2(m0 | (m1 << 16), m2 | (m3 << 16));
+                        *reinterpret_cast<uint2*>(sA_hi + 2 * a_bytes + off) =
+                            make_uint2(l0 | (l1 << 16), l2 | (l3 << 16));
+                    }
+                } else {
+                    unsigned char* sA_lo = sA_hi + a_bytes;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = r0 + 32 * j;
+                        uint4 hi, lo;
+                        hi.x = rna_tf32(v[j].x); lo.x = rna_tf32(v[j].x - __uint_as_float(hi.x));
+                        hi.y = rna_tf32(v[j].y); lo.y = rna_tf32(v[j].y - __uint_as_float(hi.y));
+                        hi.z = rna_tf32(v[j].z); lo.z = rna_tf32(v[j].z - __uint_as_float(hi.z));
+                        hi.w = rna_tf32(v[j].w); lo.w = rna_tf32(v[j].w - __uint_as_float(hi.w));
+                        const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
+                        *reinterpret_cast<uint4*>(sA_hi + off) = hi;
+                        *reinterpret_cast<uint4*>(sA_lo + off) = lo;
+                    }
+                }
+                fence_proxy_async();
+                mbar_arrive(&fullA_bar[st]);
             }
-        };
-        // software pipeline: the loads of iteration it + 1 are in flight while
-        // iteration it waits for its stage and is split and stored
-        int g[4] = {-1, -1, -1, -1};
-        float4 v[4];
-        if (n_it > 0) {
-            sources(0, g);
-            gather(0, g, v);
+            g += n_it;
         }
-        for (int it = 0; it < n_it; ++it) {
-            const int st = it % NS, use = it / NS;
-            int gn[4] = {g[0], g[1], g[2], g[3]};
-            float4 vn[4];
-            const int it1 = it + 1;
-            if (it1 < n_it) {
-                const int ti1 = it1 / a.kchunks, kc1 = it1 % a.kchunks;
-                if (kc1 == 0) sources(ti1, gn);
-                gather(kc1, gn, vn);
-            }
-            // one lane polls the stage barrier for the whole warp
-            int okw = 1;
-            if (lane == 0) okw = mbar_wait(&empty_bar[st], (use & 1) ^ 1) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw) { abort_sh = 1; break; }
-            if (abort_sh) break;
-            unsigned char* sA_hi = base + st * stage_bytes;
-            if (a.bf16) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int r = r0 + 32 * j;
-                    uint32_t h0, h1, h2, h3, m0, m1, m2, m3, l0, l1, l2, l3;
-                    split_bf16x3(v[j].x, h0, m0, l0);
-                    split_bf16x3(v[j].y, h1, m1, l1);
-                    split_bf16x3(v[j].z, h2, m2, l2);
-                    split_bf16x3(v[j].w, h3, m3, l3);
-                    // 4 values = half a 16-byte unit of the 64-byte row
-                    const int off = (r >> 3) * 512 + (r & 7) * 64 +
-                                    (((c >> 1) ^ ((r & 7) >> 1)) << 4) + (c & 1) * 8;
-                    *reinterpret_cast<uint2*>(sA_hi + off) = make_uint2(h0 | (h1 << 16), h2 | (h3 << 16));
-                    *reinterpret_cast<uint2*>(sA_hi + a_bytes + off) =
-                        make_uint2(m0 | (m1 << 16), m2 | (m3 << 16));
-                    *reinterpret_cast<uint2*>(sA_hi + 2 * a_bytes + off) =
-                        make_uint2(l0 | (l1 << 16), l2 | (l3 << 16));
-                }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the tile
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        int jacc = 0;
+        for (int idx = first; idx < count && !*abort_v; idx += stride) {
+            TcWork w;
+            if (!tc_work<MODE>(a, li, idx, w)) continue;
+            const int n_it = (w.end - w.begin) * a.kchunks;
+            float* out;
+            int64_t orow;
+            if (MODE == MODE_M2L && w.rank > 0) {
+                out = a.part + (int64_t)w.slot * kTcRows * a.ld;  // this item's partial slab
+                orow = row;
+            } else if (MODE == MODE_M2M && w.rank > 0) {
+                out = a.part + (int64_t)(w.rank - 1) * a.part_stride;
+                orow = w.base + row;
             } else {
-                unsigned char* sA_lo = sA_hi + a_bytes;
+                out = MODE == MODE_M2M ? a.Mout : a.L;
+                orow = w.base + row;
+            }
+            if (n_it > 0) {
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait_or_abort(&accf_bar, jacc & 1, abort_v) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    *abort_v = 1;
+                    break;
+                }
+                tc_fence_after();
+            }
+            // columns in groups of 4 x 16; the L2L epilogue's loads of the
+            // cell's own M2L result are all issued before the group's stores.
+            // Columns P .. Npad-1 hold exact zeros (zero operator rows), so
+            // whole 16-byte units are written.
+            float* orow_p = out + orow * a.ld;
+            const float* own_p = a.L + orow * a.ld;
+            const bool live = row < w.rows;
+            for (int cb0 = 0; cb0 * 16 < a.Npad; cb0 += 4) {
+                float4 own[16];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int r = r0 + 32 * j;
-                    uint4 hi, lo;
-                    hi.x = rna_tf32(v[j].x); lo.x = rna_tf32(v[j].x - __uint_as_float(hi.x));
-                    hi.y = rna_tf32(v[j].y); lo.y = rna_tf32(v[j].y - __uint_as_float(hi.y));
-                    hi.z = rna_tf32(v[j].z); lo.z = rna_tf32(v[j].z - __uint_as_float(hi.z));
-                    hi.w = rna_tf32(v[j].w); lo.w = rna_tf32(v[j].w - __uint_as_float(hi.w));
-                    const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4);
-                    *reinterpret_cast<uint4*>(sA_hi + off) = hi;
-                    *reinterpret_cast<uint4*>(sA_lo + off) = lo;
+                for (int q = 0; q < 16; ++q) {
+                    own[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (MODE == MODE_L2L && live && (cb0 * 16 + q * 4) < a.Npad)
+                        own[q] = *reinterpret_cast<const float4*>(own_p + cb0 * 16 + q * 4);
+                }
+#pragma unroll
+                for (int cq = 0; cq < 4; ++cq) {
+                    const int cb = cb0 + cq;
+                    if (cb * 16 >= a.Npad) break;
+                    uint32_t r[16];
+                    if (n_it > 0) {
+                        const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16);
+                        uint32_t r1[16];
+                        tmem_ld16(t0, r);
+                        tmem_ld16(t0 + (uint32_t)a.acc_cols, r1);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r1[j]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) r[j] = 0u;
+                    }
+                    if (live) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 o = own[cq * 4 + q];
+                            float4 v;
+                            v.x = __uint_as_float(r[4 * q + 0]) + o.x;
+                            v.y = __uint_as_float(r[4 * q + 1]) + o.y;
+                            v.z = __uint_as_float(r[4 * q + 2]) + o.z;
+                            v.w = __uint_as_float(r[4 * q + 3]) + o.w;
+                            *reinterpret_cast<float4*>(orow_p + cb * 16 + 4 * q) = v;
+                        }
+                    }
                 }
             }
-            fence_proxy_async();
-            mbar_arrive(&fullA_bar[st]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                g[j] = gn[j];
-                v[j] = vn[j];
+            if (n_it > 0) {
+                // accumulators read: the issuer may start the next item
+                tc_fence_before();
+                mbar_arrive(&acce_bar);
+                ++jacc;
             }
         }
     }
 
-    // ---- epilogue (warps 2..9): wait for the accumulator, then write out
-    bool ok = true;
-    if (warp >= kWarpA0) {
-        if (n_it > 0 && !abort_sh) {
-            if (lane == 0 && !mbar_wait(&acc_bar, 0)) abort_sh = 1;
-            __syncwarp();
-        }
-        tc_fence_after();
-        if (abort_sh) ok = false;
-        float* out;
-        if (split > 0) out = a.part + (int64_t)(split - 1) * a.part_stride;
-        else if (a.mode == MODE_M2M) out = a.Mout;
-        else out = a.L;
-        if (ok) {
-            const int quad = warp & 3, half = (warp - kWarpA0) >> 2;
-            const int row = quad * 32 + lane;
-            const int g = tbase + row;
-            for (int cb = half; cb * 16 < a.Npad; cb += 2) {
-                uint32_t r[16];
-                if (n_it > 0) {
-                    const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16);
-                    uint32_t r1[16];
-                    tmem_ld16(t0, r);
-                    tmem_ld16(t0 + (uint32_t)a.acc_cols, r1);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        r[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(r1[j]));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) r[j] = 0u;
-                }
-                if (row < rows) {
-                    // L2L adds the cell's own M2L result: load the 16 values
-                    // first (out aliases L, so interleaved load/store pairs
-                    // would serialise on the memory round trip)
-                    float own[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = cb * 16 + j;
-                        own[j] = (a.mode == MODE_L2L && col < a.P) ? a.L[(int64_t)g * a.ld + col] : 0.f;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = cb * 16 + j;
-                        if (col < a.P) out[(int64_t)g * a.ld + col] = __uint_as_float(r[j]) + own[j];
-                    }
-                }
-            }
-        }
-    }
     __syncthreads();
-    if (abort_sh) {
-        // drain (bounded): the issuer's MMAs in flight and the last bulk copy
+    if (*abort_v) {
+        // drain (bounded): the issuer's MMAs in flight and every bulk copy
+        // still owed to a stage
         if (tid == 32) {
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0);
         }
-        if (tid == 0 && last_copy_st >= 0) mbar_wait(&fullB_bar[last_copy_st], last_copy_par);
-        if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+        if (tid == 0) {
+            for (int s = 0; s < NS; ++s)
+                if (issued_par[s] >= 0) mbar_wait(&fullB_bar[s], (uint32_t)issued_par[s]);
+            atomicOr(a.err, ERR_TIMEOUT);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -737,11 +855,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_tc_plan(TcArgs a, TcTile* tile
     __syncthreads();
     if (rows > 0) {
         const int row = tid & (kTcRows - 1), part = tid >> 7;  // 4 parts of the 189 terms
+        uint32_t m[6] = {0u, 0u, 0u, 0u, 0u, 0u};
         if (row < rows) {
             int ix, iy, iz;
             demorton3(a.code[t_base + row], ix, iy, iz);
             const int lim = 1 << l;
-            uint32_t m[6] = {0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll 8
             for (int term = part; term < 189; term += 4) {
                 const int opi = c_tc_off[oct][term];
@@ -755,9 +873,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_tc_plan(TcArgs a, TcTile* tile
                 }
                 if (on) m[term >> 5] |= 1u << (term & 31);
             }
+        }
+        // OR over the warp first: one shared atomic per warp and word
 #pragma unroll
-            for (int w = 0; w < 6; ++w)
-                if (m[w]) atomicOr(&mask[w], m[w]);
+        for (int w = 0; w < 6; ++w) {
+            const uint32_t v = __reduce_or_sync(0xffffffffu, m[w]);
+            if ((tid & 31) == 0 && v) atomicOr(&mask[w], v);
         }
         __syncthreads();
         TcTile& tl = tiles[blockIdx.x];
@@ -782,13 +903,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_tc_plan(TcArgs a, TcTile* tile
     }
 }
 
-// Cuts every tile's list into runs (one work item each): the run length is
-// chosen so that all runs fill about one wave of CTAs; each tile gets at
-// least one and at most max_splits runs.  One block; tiles in chunks.
+// Cuts every tile's list into runs (one work item each), in tile order.
+// Run length: short enough that there are about a wave of runs, and never
+// more than kChainCap offsets, because the tensor-core accumulator rounds
+// every accumulation toward zero and its error grows with the number of
+// products summed into it (runs are summed afterwards in FP32 round to
+// nearest); long enough that the runs with rank > 0 fit slab_cap partial
+// slabs.  One block; tiles in chunks.
 constexpr int kItemThreads = 1024;
 
 __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInfo* linfo,
-                                                           int ntile_cap, int max_splits,
+                                                           int ntile_cap, int slab_cap,
                                                            TcPlanHdr* hdr, TcTile* tiles,
                                                            TcItem* items) {
     __shared__ int warp_sum[32];
@@ -818,8 +943,12 @@ __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInf
         s_total = t;
     }
     __syncthreads();
-    int tpi = (s_total + kWaveItems - 1) / kWaveItems;  // runs of about one wave in total
-    if (tpi < 4) tpi = 4;
+    const int total = s_total;
+    int tpi = (total + kWaveItems - 1) / kWaveItems;
+    if (tpi > kChainCap) tpi = kChainCap;
+    const int tpi_mem = (total + slab_cap - 1) / slab_cap;
+    if (tpi < tpi_mem) tpi = tpi_mem;
+    if (tpi < 1) tpi = 1;
     // tiles in chunks of kItemThreads: exclusive scan of the run counts
     for (int c0 = 0; c0 < ntile; c0 += kItemThreads) {
         const int b = c0 + tid;
@@ -828,7 +957,6 @@ __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInf
             cnt = tiles[b].cnt;
             ns = (cnt + tpi - 1) / tpi;
             if (ns < 1) ns = 1;
-            if (ns > max_splits) ns = max_splits;
         }
         int x = ns;
         for (int o = 1; o < 32; o <<= 1) {
@@ -850,6 +978,7 @@ __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInf
         const int off = s_carry + (wid > 0 ? warp_sum[wid - 1] : 0) + x - ns;
         if (b < ntile) {
             tiles[b].nsplit = ns;
+            tiles[b].item0 = off;
             for (int k = 0; k < ns; ++k) {
                 TcItem it;
                 it.tile = b;
@@ -869,36 +998,41 @@ __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInf
     }
 }
 
-// L += the split partials of the M2L items, per tile in rank order; 8 blocks
-// per tile, each a slice of its rows.
-constexpr int kRedSlices = 8;
+// L += the partial slabs of the M2L items of rank > 0, per tile in rank
+// order; 32 blocks per tile, each a slice of its rows, eight slabs in flight.
+constexpr int kRedSlices = 32;
 
 __global__ void __launch_bounds__(256) k_tc_reduce_tiles(int ld, const TcPlanHdr* hdr,
                                                          const TcTile* tiles,
-                                                         const float4* __restrict__ part,
-                                                         int64_t part_stride4, float4* L) {
+                                                         const float4* __restrict__ slabs,
+                                                         float4* L) {
     const int n_tiles = hdr->n_tiles;
     const int w = ld / 4;
+    const int64_t slab4 = (int64_t)kTcRows * w;
     for (int bb = blockIdx.x; bb < n_tiles * kRedSlices; bb += gridDim.x) {
         const int b = bb / kRedSlices, slice = bb % kRedSlices;
         const int ns = tiles[b].nsplit, base = tiles[b].base, rows = tiles[b].rows;
         if (ns <= 1) continue;
+        const float4* first = slabs + (int64_t)(tiles[b].item0 + 1) * slab4;
         const int r0 = (rows * slice) / kRedSlices, r1 = (rows * (slice + 1)) / kRedSlices;
         for (int e = threadIdx.x; e < (r1 - r0) * w; e += blockDim.x) {
-            const int64_t idx = (int64_t)(base + r0 + e / w) * w + (e % w);
-            float4 q[kMaxSplits - 1];
-#pragma unroll
-            for (int k = 0; k < kMaxSplits - 1; ++k)
-                if (k + 1 < ns) q[k] = part[k * part_stride4 + idx];
+            const int64_t local = (int64_t)(r0 + e / w) * w + (e % w);
+            const int64_t idx = (int64_t)base * w + local;
             float4 v = L[idx];
+            int k = 0;
+            for (; k + 8 <= ns - 1; k += 8) {
+                float4 q[8];
 #pragma unroll
-            for (int k = 0; k < kMaxSplits - 1; ++k)
-                if (k + 1 < ns) {
-                    v.x += q[k].x;
-                    v.y += q[k].y;
-                    v.z += q[k].z;
-                    v.w += q[k].w;
+                for (int u = 0; u < 8; ++u) q[u] = first[(k + u) * slab4 + local];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    v.x += q[u].x; v.y += q[u].y; v.z += q[u].z; v.w += q[u].w;
                 }
+            }
+            for (; k < ns - 1; ++k) {
+                const float4 q = first[k * slab4 + local];
+                v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+            }
             L[idx] = v;
         }
     }
@@ -943,6 +1077,20 @@ size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
     return (size_t)s;
 }
 
+int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap) {
+    const double budget = 256.0 * 1024 * 1024;
+    int64_t s = (int64_t)(budget / ((double)kTcRows * ld * sizeof(float)));
+    if (s > tiles_cap * 189) s = tiles_cap * 189;
+    return s > 1 ? s : 1;
+}
+
+size_t m2l_tc_part_floats(int64_t cells_max, int ld, int m2m_splits, int64_t tiles_cap,
+                          int64_t slab_cap) {
+    const size_t m2m = (size_t)(m2m_splits > 1 ? m2m_splits - 1 : 1) * cells_max * ld;
+    const size_t m2l = (size_t)(tiles_cap + slab_cap) * kTcRows * ld;
+    return m2m > m2l ? m2m : m2l;
+}
+
 // Operators 0..342: M2L by offset index; 343..350: M2M by child octant;
 // 351..358: L2L by child octant.  Each P x P (out x in) operator T becomes B
 // with B[k][n] = T[n][k], split into pieces (TF32 hi/lo or BF16 hi/mid/lo)
@@ -984,6 +1132,18 @@ void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T
     }
 }
 
+template <int MODE>
+static cudaError_t tc_launch_mode(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
+    if (a.bf16) k_m2l_tc<MODE, 1><<<grid, kTcThreads, smem, s>>>(a);
+    else k_m2l_tc<MODE, 0><<<grid, kTcThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
+    if (a.mode == MODE_M2L) return tc_launch_mode<MODE_M2L>(a, grid, smem, s);
+    if (a.mode == MODE_M2M) return tc_launch_mode<MODE_M2M>(a, grid, smem, s);
+    return tc_launch_mode<MODE_L2L>(a, grid, smem, s);
+}
+
 cudaError_t m2l_tc_init() {
     static int16_t off[8][189];
     host_m2l_offsets(off);
@@ -993,7 +1153,18 @@ cudaError_t m2l_tc_init() {
     for (int q = 2; q <= kMaxOrder; ++q)
         for (int b = 0; b < 2; ++b)
             if (tc_supported(q, b) && tc_geom(q, b).smem_bytes > most) most = tc_geom(q, b).smem_bytes;
-    return cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t r = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(f, at, most);
+    };
+    set((const void*)k_m2l_tc<MODE_M2L, 0>);
+    set((const void*)k_m2l_tc<MODE_M2L, 1>);
+    set((const void*)k_m2l_tc<MODE_M2M, 0>);
+    set((const void*)k_m2l_tc<MODE_M2M, 1>);
+    set((const void*)k_m2l_tc<MODE_L2L, 0>);
+    set((const void*)k_m2l_tc<MODE_L2L, 1>);
+    return r;
 }
 
 static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
@@ -1011,6 +1182,7 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.acc_cols = g.acc_cols;
     a.splits = splits;
     a.stages = g.stages;
+    a.raw = g.raw;
     a.bf16 = bf16 ? 1 : 0;
     a.pieces = g.pieces;
     a.a_bytes = g.a_bytes;
@@ -1046,8 +1218,7 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
     TcArgs a = base_args(n, D, ws, splits);
     a.mode = MODE_M2M;
     a.level = l;
-    k_m2l_tc<<<(unsigned)(tiles * splits), kTcThreads, tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = tc_launch(a, (unsigned)(tiles * splits), tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes, s);
     if (e != cudaSuccess || splits == 1) return e;
     k_tc_reduce<<<152 * 2, 256, 0, s>>>(l, l, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
                                         ws.cells_max * ws.ld / 4, (float4*)ws.M);
@@ -1060,7 +1231,6 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
     int64_t tiles = 0;
     for (int l = 2; l <= D; ++l) tiles += (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
     if (tiles > ws.tc_tiles_cap) return cudaErrorInvalidValue;
-    const int max_splits = ws.tc_splits_max < kMaxSplits ? ws.tc_splits_max : kMaxSplits;
     TcPlanHdr* hdr = (TcPlanHdr*)ws.tc_work;
     TcTile* tl = (TcTile*)(hdr + 1);
     TcItem* items = (TcItem*)(tl + ws.tc_tiles_cap);
@@ -1072,34 +1242,32 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
     k_tc_plan<<<(unsigned)tiles, kPlanThreads, 0, s>>>(a, tl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, max_splits, hdr, tl, items);
+    k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, (int)ws.tc_slab_cap, hdr, tl,
+                                          items);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the plan makes at most kWaveItems + (number of tiles) items
-    int64_t grid = kWaveItems + tiles;
-    if (grid > tiles * max_splits) grid = tiles * max_splits;
-    k_m2l_tc<<<(unsigned)grid, kTcThreads, smem, s>>>(a);
+    // persistent: one CTA per SM walks the work list
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = tc_launch(a, (unsigned)(sms > 0 ? sms : 152), smem, s)) != cudaSuccess) return e;
+    const int64_t rg = tiles * kRedSlices;
+    k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 16 ? rg : 152 * 16), 256, 0, s>>>(
+        ws.ld, hdr, tl, (const float4*)ws.tc_part, (float4*)ws.L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (max_splits > 1) {
-        int64_t rg = tiles * kRedSlices;
-        k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 8 ? rg : 152 * 8), 256, 0, s>>>(
-            ws.ld, hdr, tl, (const float4*)ws.tc_part, ws.cells_max * ws.ld / 4, (float4*)ws.L);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
     // L2L shifts level by level (level 2 has no parent expansion)
     for (int l = 3; l <= D; ++l) {
         TcArgs b = base_args(n, D, ws, 1);
         b.mode = MODE_L2L;
         b.level = l;
         const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
-        k_m2l_tc<<<(unsigned)t2, kTcThreads, smem, s>>>(b);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = tc_launch(b, (unsigned)t2, smem, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-size_t m2l_tc_work_bytes(int64_t tiles_cap) {
+size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap) {
     return sizeof(TcPlanHdr) + (size_t)tiles_cap * sizeof(TcTile) +
-           (size_t)tiles_cap * kMaxSplits * sizeof(TcItem);
+           (size_t)(tiles_cap + slab_cap) * sizeof(TcItem);
 }
 
 cudaError_t launch_m2l_tc(int, int, Workspace&, cudaStream_t) { return cudaErrorNotSupported; }
