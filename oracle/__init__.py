@@ -51,6 +51,8 @@ def lib():
             L.orc_num_threads.restype = ctypes.c_int
             L.orc_coulomb_direct.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D, _D]
             L.orc_coulomb_near.argtypes = [_I64, _D, _D, _D, _D, ctypes.c_int, _D, _D, _D, _D]
+            L.orc_coulomb_targets.argtypes = [_I64, _D, _D, _D, _D, _I64,
+                                              ctypes.POINTER(ctypes.c_int64), _D, _D, _D, _D]
             L.orc_root_cube.argtypes = [_I64, _D, _D, _D, _D, _D]
             L.orc_leaf_keys.argtypes = [_I64, _D, _D, _D, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_uint64), _D, _D]
@@ -118,6 +120,21 @@ def coulomb_direct(pos, q, want_phi=True):
     phi = np.empty(n) if want_phi else None
     lib().orc_coulomb_direct(n, _p(x), _p(y), _p(z), _p(q), _p(E[0]), _p(E[1]), _p(E[2]),
                              _p(phi) if want_phi else None)
+    return np.stack(E, 1), phi
+
+
+def coulomb_targets(pos, q, idx, want_phi=True):
+    """E (m,3) and phi (m,) at the ions idx from all other ions (SI)."""
+    pos = _f64(pos)
+    x, y, z = (_f64(pos[:, a]) for a in range(3))
+    q = _f64(q)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = len(idx)
+    E = [np.empty(m) for _ in range(3)]
+    phi = np.empty(m) if want_phi else None
+    lib().orc_coulomb_targets(len(q), _p(x), _p(y), _p(z), _p(q), m,
+                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              _p(E[0]), _p(E[1]), _p(E[2]), _p(phi) if want_phi else None)
     return np.stack(E, 1), phi
 
 

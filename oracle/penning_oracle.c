@@ -214,6 +214,38 @@ void orc_coulomb_direct(int64_t n, const double* x, const double* y, const doubl
     orc_coulomb_impl(n, x, y, z, q, Ex, Ey, Ez, phi, NULL, 1.0, -1);
 }
 
+/* The same sum (Eq. hamiltonian's pair term) at m chosen targets only:
+ * target k is ion idx[k]; every other ion j != idx[k] is a source.  Same
+ * pair expression and compensated accumulation in ascending j, so at a full
+ * sample it reproduces orc_coulomb_direct bit for bit.  Serves the large-N
+ * checks, where the all-pairs sum is out of reach on the host. */
+void orc_coulomb_targets(int64_t n, const double* x, const double* y, const double* z,
+                         const double* q, int64_t m, const int64_t* idx, double* Ex, double* Ey,
+                         double* Ez, double* phi) {
+    const double ke = orc_ke();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < m; ++k) {
+        const int64_t i = idx[k];
+        orc_acc ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ap = {0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double r = sqrt(r2);
+            double inv_r = 1.0 / r;
+            double w = q[j] * inv_r / r2; /* q_j / r^3 */
+            acc_add(&ax, w * dx);
+            acc_add(&ay, w * dy);
+            acc_add(&az, w * dz);
+            acc_add(&ap, q[j] * inv_r);
+        }
+        Ex[k] = ke * acc_val(&ax);
+        Ey[k] = ke * acc_val(&ay);
+        Ez[k] = ke * acc_val(&az);
+        if (phi) phi[k] = ke * acc_val(&ap);
+    }
+}
+
 /* ======================================================================
  * Octree root cube and leaf keys (Sec. 2.3.2: "the smallest cube containing
  * all N ions is found" and is divided recursively into octants).

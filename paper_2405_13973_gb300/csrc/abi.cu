@@ -427,7 +427,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         int64_t tcap = 0;
         for (int l = 2; l <= ws.depth_max; ++l) tcap += ((pow8(l) < n_max ? pow8(l) : n_max) + 127) / 128 + 8;
         ws.tc_tiles_cap = tcap > 0 ? tcap : 1;
-        ws.tc_slab_cap = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap);
+        ws.tc_slab_cap = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, n_max);
         ws.tc_part_floats = m2l_tc_part_floats(cells, ws.ld, ws.tc_splits_max, ws.tc_tiles_cap,
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));

@@ -160,3 +160,23 @@ def test_near_field_membership():
     assert pn[0] == pytest.approx(KE * Q / 0.2, rel=1e-15)
     assert pn[1] == pytest.approx(KE * Q / 0.2, rel=1e-15)
     assert pn[2] == 0.0 and En[2, 0] == 0.0
+
+
+def test_sampled_targets_reproduce_the_full_sum():
+    # The sampled-target sum is the same definition restricted to chosen
+    # targets: at every sampled ion it equals the all-pairs sum exactly
+    # (same pair expression, same ascending source order), and it sees the
+    # ion's own charge nowhere.
+    rng = np.random.default_rng(17)
+    n = 300
+    pos = rng.normal(size=(n, 3)) * 1e-5
+    q = W.E_CHARGE * (1.0 + rng.random(n))
+    E, phi = oracle.coulomb_direct(pos, q)
+    idx = np.array([0, 7, 299, 150, 7])
+    Es, ps = oracle.coulomb_targets(pos, q, idx)
+    assert np.array_equal(Es, E[idx]) and np.array_equal(ps, phi[idx])
+    # removing the target ion's charge changes nothing at that target
+    q2 = q.copy()
+    q2[150] = 0.0
+    Es2, ps2 = oracle.coulomb_targets(pos, q2, np.array([150]))
+    assert np.array_equal(Es2[0], E[150]) and ps2[0] == phi[150]
