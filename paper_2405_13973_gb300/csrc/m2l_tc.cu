@@ -141,7 +141,6 @@ inline float rna_tf32_host(float x) {
     return r;
 }
 
-__constant__ int16_t c_tc_off[8][189];
 
 // ---- PTX wrappers -----------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -318,13 +317,60 @@ struct TcArgs {
     const struct TcPlanHdr* hdr;
 };
 
-// One M2L tile (128 targets of one level and octant) and its non-empty
-// offsets; one work item = a contiguous run of them.  The tile's items are
-// item0 .. item0 + nsplit - 1 of the work list.
+// One M2L tile (up to 128 targets of one level) and its non-empty offsets,
+// as operator indices (ox+3)*49 + (oy+3)*7 + (oz+3) in increasing order; one
+// work item = a contiguous run of them.  oct is the targets' common child
+// octant, or -1 for a mixed tile (a sparse level's cells of every octant).
+// The tile's items are item0 .. item0 + nsplit - 1 of the work list.
+constexpr int kMaxTerms = 320;  // >= 316 offsets of [-3,3]^3 outside [-1,1]^3
 struct TcTile {
     int level, oct, base, rows, cnt, nsplit, item0, pad1;
-    uint8_t terms[192];
+    uint16_t terms[kMaxTerms];
 };
+
+// Tiles of level l: one group per child octant (the 189 offsets of an octant
+// share their operators) when the level is dense; when it holds fewer than
+// kMixedCells cells, tiles of consecutive cells of every octant, so that
+// sparse upper levels do not run mostly empty 128-row products.
+constexpr int kMixedCells = 512;
+__host__ __device__ __forceinline__ bool tc_level_mixed(const LevelInfo& li, int l) {
+    return li.gbase[l + 1] - li.gbase[l] < kMixedCells;
+}
+// number of tiles of level l
+__host__ __device__ inline int tc_level_tiles(const LevelInfo& li, int l) {
+    if (tc_level_mixed(li, l)) return (li.gbase[l + 1] - li.gbase[l] + kTcRows - 1) / kTcRows;
+    int nt = 0;
+    for (int o = 0; o < 8; ++o) nt += (li.oct_start[l][o + 1] - li.oct_start[l][o] + kTcRows - 1) / kTcRows;
+    return nt;
+}
+// tile t of the M2L launch (levels 2..D in order); false past the last tile
+__host__ __device__ inline bool tc_tile(const LevelInfo& li, int D, int t, int& level, int& oct,
+                                        int& base, int& rows) {
+    int acc = 0;
+    for (int l = 2; l <= D; ++l) {
+        const bool mixed = tc_level_mixed(li, l);
+        for (int o = 0; o < (mixed ? 1 : 8); ++o) {
+            const int s0 = mixed ? li.gbase[l] : li.oct_start[l][o];
+            const int s1 = mixed ? li.gbase[l + 1] : li.oct_start[l][o + 1];
+            const int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
+            if (t < acc + nt) {
+                level = l;
+                oct = mixed ? -1 : o;
+                base = s0 + (t - acc) * kTcRows;
+                rows = min(kTcRows, s1 - base);
+                return true;
+            }
+            acc += nt;
+        }
+    }
+    return false;
+}
+// does a target of child octant (bx, by, bz) take offset o?  (its source is a
+// child of a neighbour of the target's parent: o_a in [b_a - 3, b_a + 2])
+__host__ __device__ __forceinline__ bool tc_admits(int ox, int oy, int oz, int bx, int by, int bz) {
+    return ox >= bx - 3 && ox <= bx + 2 && oy >= by - 3 && oy <= by + 2 && oz >= bz - 3 &&
+           oz <= bz + 2;
+}
 struct TcItem {
     int tile, begin, end, rank;
 };
@@ -412,7 +458,7 @@ __device__ __forceinline__ bool tc_work(const TcArgs& a, const LevelInfo& li, in
 // packed operator index of term j of a work item
 template <int MODE>
 __device__ __forceinline__ int tc_op(const TcArgs& a, const TcWork& w, int j) {
-    if (MODE == MODE_M2L) return c_tc_off[w.oct][a.tiles[w.tile].terms[j]];
+    if (MODE == MODE_M2L) return a.tiles[w.tile].terms[j];
     if (MODE == MODE_M2M) return kOpM2M + j;
     return kOpL2L + w.oct;
 }
@@ -602,15 +648,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             int pg[4] = {-1, -1, -1, -1};
             auto sources = [&](int t) {
                 int opi = 0, term = t;
-                if (MODE == MODE_M2L) opi = c_tc_off[w.oct][a.tiles[w.tile].terms[t]];
+                if (MODE == MODE_M2L) opi = a.tiles[w.tile].terms[t];
+                const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     int gs = -1;
                     if (r0 + 32 * j < w.rows) {
                         if (MODE == MODE_M2L) {
-                            int sx = tix[j] - (opi / 49 - 3), sy = tiy[j] - ((opi / 7) % 7 - 3),
-                                sz = tiz[j] - (opi % 7 - 3);
-                            if (sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                            // a mixed tile's rows differ in octant: each takes its own offsets
+                            const int sx = tix[j] - ox, sy = tiy[j] - oy, sz = tiz[j] - oz;
+                            if (tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
+                                sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
                                 gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
                         } else if (MODE == MODE_M2M) {
                             gs = a.cid[a.off[l + 1] + ((tcode[j] << 3) | (uint32_t)term)];
@@ -806,100 +854,111 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                      : "memory");
 }
 
-// Work list of the M2L launch, first part: one block per tile collects the
-// offsets with at least one source among the tile's targets (4 threads per
-// target row) and stores them in term order.
+// Work list of the M2L launch, first part: one block per tile finds the
+// offsets with at least one source among the tile's targets and stores them
+// in increasing order.  Up to level kBitmapLevel the level's occupancy is a
+// bitmap of x-rows (one 64-bit word per (y, z) row) in shared memory, so an
+// (offset, target row) test is one shift and one AND; deeper levels test
+// each (offset, target) through the cell-id table.
 constexpr int kPlanThreads = 512;
-constexpr int kOccWords = (1 << 15) / 32;  // occupancy bits of one level up to depth 5
 constexpr int kWaveItems = 148;
+constexpr int kBitmapLevel = 6;
+
+__host__ __device__ inline int tc_plan_smem_bytes(int D) {
+    const int l = D < kBitmapLevel ? D : kBitmapLevel;
+    return 2 * (1 << (2 * l)) * (int)sizeof(unsigned long long);
+}
 
 __global__ void __launch_bounds__(kPlanThreads) k_tc_plan(TcArgs a, TcTile* tiles) {
-    __shared__ uint32_t mask[6];
-    __shared__ int t_level, t_oct, t_base, t_rows;
+    extern __shared__ unsigned long long bm[];  // occupancy rows | target rows
+    __shared__ uint8_t flag[343];
+    __shared__ int rowlist[kTcRows];
+    __shared__ int wcnt[kPlanThreads / 32];
+    __shared__ int t_level, t_oct, t_base, t_rows, nrows;
     __shared__ LevelInfo li;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     stage_linfo(a.linfo, &li);
     __syncthreads();
     if (tid == 0) {
-        t_rows = 0;
-        int t = blockIdx.x, acc = 0;
-        for (int l = 2; l <= a.D && t_rows == 0; ++l)
-            for (int o = 0; o < 8; ++o) {
-                int s0 = li.oct_start[l][o], s1 = li.oct_start[l][o + 1];
-                int nt = (s1 - s0 + kTcRows - 1) / kTcRows;
-                if (t < acc + nt) {
-                    t_level = l;
-                    t_oct = o;
-                    t_base = s0 + (t - acc) * kTcRows;
-                    t_rows = min(kTcRows, s1 - t_base);
-                    break;
-                }
-                acc += nt;
-            }
+        if (!tc_tile(li, a.D, blockIdx.x, t_level, t_oct, t_base, t_rows)) t_rows = 0;
+        nrows = 0;
     }
-    if (tid < 6) mask[tid] = 0u;
+    for (int i = tid; i < 343; i += kPlanThreads) flag[i] = 0;
     __syncthreads();
-    const int rows = t_rows, l = t_level, oct = t_oct;
-    // occupancy bitmap of the level in shared memory when it fits (8^l <= 32768)
-    __shared__ uint32_t occ[kOccWords];
-    const bool use_occ = rows > 0 && l <= 5;
-    if (use_occ) {
-        const int ncell = 1 << (3 * l);
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int c0 = warp * 32; c0 < ncell; c0 += kPlanThreads) {
-            const bool on = a.cid[a.off[l] + c0 + lane] >= 0;
-            const uint32_t b = __ballot_sync(0xffffffffu, on);
-            if (lane == 0) occ[c0 >> 5] = b;
+    const int rows = t_rows, l = t_level, base = t_base;
+    if (rows <= 0) return;  // uniform
+    const int side = 1 << l;
+    if (l <= kBitmapLevel) {
+        const int nr = side * side;
+        unsigned long long* occ = bm;
+        unsigned long long* tg = bm + nr;
+        for (int i = tid; i < 2 * nr; i += kPlanThreads) bm[i] = 0ull;
+        __syncthreads();
+        for (int c = li.gbase[l] + tid; c < li.gbase[l + 1]; c += kPlanThreads) {
+            int x, y, z;
+            demorton3(a.code[c], x, y, z);
+            atomicOr(&occ[z * side + y], 1ull << x);
         }
-    }
-    __syncthreads();
-    if (rows > 0) {
-        const int row = tid & (kTcRows - 1), part = tid >> 7;  // 4 parts of the 189 terms
-        uint32_t m[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-        if (row < rows) {
-            int ix, iy, iz;
-            demorton3(a.code[t_base + row], ix, iy, iz);
-            const int lim = 1 << l;
-#pragma unroll 8
-            for (int term = part; term < 189; term += 4) {
-                const int opi = c_tc_off[oct][term];
-                int sx = ix - (opi / 49 - 3), sy = iy - ((opi / 7) % 7 - 3), sz = iz - (opi % 7 - 3);
-                bool inb = sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim;
-                bool on = false;
-                if (inb) {
-                    const uint32_t c = morton3(sx, sy, sz);
-                    on = use_occ ? ((occ[c >> 5] >> (c & 31)) & 1u) != 0u
-                                 : a.cid[a.off[l] + c] >= 0;
-                }
-                if (on) m[term >> 5] |= 1u << (term & 31);
-            }
-        }
-        // OR over the warp first: one shared atomic per warp and word
-#pragma unroll
-        for (int w = 0; w < 6; ++w) {
-            const uint32_t v = __reduce_or_sync(0xffffffffu, m[w]);
-            if ((tid & 31) == 0 && v) atomicOr(&mask[w], v);
+        for (int r = tid; r < rows; r += kPlanThreads) {
+            int x, y, z;
+            demorton3(a.code[base + r], x, y, z);
+            if (atomicOr(&tg[z * side + y], 1ull << x) == 0ull) rowlist[atomicAdd(&nrows, 1)] = z * side + y;
         }
         __syncthreads();
-        TcTile& tl = tiles[blockIdx.x];
-        if (tid < 189) {  // compact the set terms in term order
-            const int w = tid >> 5;
-            const uint32_t bit = 1u << (tid & 31);
-            if (mask[w] & bit) {
-                int pos = __popc(mask[w] & (bit - 1u));
-                for (int v = 0; v < w; ++v) pos += __popc(mask[v]);
-                tl.terms[pos] = (uint8_t)tid;
-            }
+        const int K = nrows;
+        for (int i = tid; i < 343 * K; i += kPlanThreads) {
+            const int op = i / K;
+            if (flag[op]) continue;
+            const int ox = op / 49 - 3, oy = (op / 7) % 7 - 3, oz = op % 7 - 3;
+            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+            const int row = rowlist[i % K];
+            const int ty = row % side, tz = row / side;
+            if (oy < (ty & 1) - 3 || oy > (ty & 1) + 2 || oz < (tz & 1) - 3 || oz > (tz & 1) + 2)
+                continue;
+            const int sy = ty - oy, sz = tz - oz;
+            if (sy < 0 || sz < 0 || sy >= side || sz >= side) continue;
+            const unsigned long long src = occ[sz * side + sy];
+            const unsigned long long sh = ox >= 0 ? (src << ox) : (src >> -ox);
+            unsigned long long tb = tg[row];
+            // x parity: offset +3 needs an odd target x, -3 an even one
+            if (ox == 3) tb &= 0xAAAAAAAAAAAAAAAAull;
+            else if (ox == -3) tb &= 0x5555555555555555ull;
+            if (sh & tb) flag[op] = 1;
         }
-        if (tid == 0) {
-            int cnt = 0;
-            for (int w = 0; w < 6; ++w) cnt += __popc(mask[w]);
-            tl.level = l;
-            tl.oct = oct;
-            tl.base = t_base;
-            tl.rows = rows;
-            tl.cnt = cnt;
+    } else {
+        for (int i = tid; i < 343 * rows; i += kPlanThreads) {
+            const int op = i / rows;
+            if (flag[op]) continue;
+            const int ox = op / 49 - 3, oy = (op / 7) % 7 - 3, oz = op % 7 - 3;
+            if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+            int x, y, z;
+            demorton3(a.code[base + i % rows], x, y, z);
+            if (!tc_admits(ox, oy, oz, x & 1, y & 1, z & 1)) continue;
+            const int sx = x - ox, sy = y - oy, sz = z - oz;
+            if (sx < 0 || sy < 0 || sz < 0 || sx >= side || sy >= side || sz >= side) continue;
+            if (a.cid[a.off[l] + morton3(sx, sy, sz)] >= 0) flag[op] = 1;
         }
+    }
+    __syncthreads();
+    // flagged offsets in increasing order
+    const bool f = tid < 343 && flag[tid];
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    TcTile& tl = tiles[blockIdx.x];
+    if (f) {
+        int pos = __popc(bal & ((1u << lane) - 1u));
+        for (int v = 0; v < wid; ++v) pos += wcnt[v];
+        tl.terms[pos] = (uint16_t)tid;
+    }
+    if (tid == 0) {
+        int cnt = 0;
+        for (int v = 0; v < kPlanThreads / 32; ++v) cnt += wcnt[v];
+        tl.level = l;
+        tl.oct = t_oct;
+        tl.base = base;
+        tl.rows = rows;
+        tl.cnt = cnt;
     }
 }
 
@@ -920,12 +979,8 @@ __global__ void __launch_bounds__(kItemThreads) k_tc_items(int D, const LevelInf
     __shared__ int s_total, s_ntile, s_carry;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
-        int ntile = 0;  // tiles are numbered densely from 0 in (level, octant) order
-        for (int l2 = 2; l2 <= D; ++l2)
-            for (int o = 0; o < 8; ++o) {
-                int s0 = linfo->oct_start[l2][o], s1 = linfo->oct_start[l2][o + 1];
-                ntile += (s1 - s0 + kTcRows - 1) / kTcRows;
-            }
+        int ntile = 0;  // tiles are numbered densely from 0 (the plan's order)
+        for (int l = 2; l <= D; ++l) ntile += tc_level_tiles(*linfo, l);
         s_ntile = ntile < ntile_cap ? ntile : ntile_cap;
         s_carry = 0;
     }
@@ -1149,9 +1204,8 @@ static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStrea
 }
 
 cudaError_t m2l_tc_init() {
-    static int16_t off[8][189];
-    host_m2l_offsets(off);
-    cudaError_t e = cudaMemcpyToSymbol(c_tc_off, off, sizeof off);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc_plan_smem_bytes(kBitmapLevel));
     if (e != cudaSuccess) return e;
     int most = 0;
     for (int q = 2; q <= kMaxOrder; ++q)
@@ -1243,7 +1297,7 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
     a.tiles = tl;
     a.items = items;
     a.hdr = hdr;
-    k_tc_plan<<<(unsigned)tiles, kPlanThreads, 0, s>>>(a, tl);
+    k_tc_plan<<<(unsigned)tiles, kPlanThreads, tc_plan_smem_bytes(D), s>>>(a, tl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, (int)ws.tc_slab_cap, hdr, tl,
