@@ -398,10 +398,15 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     const size_t PP = (size_t)pl->P * pl->P;
     bool ok = true;
     {
+        // per-device tables and kernel attributes: a failure here is a CUDA
+        // error, not a lack of memory
         std::lock_guard<std::mutex> g(g_tables_mu);
         if (!g_tables_dev.count(pl->device)) {
-            if (upload_harmonic_tables() != cudaSuccess || m2l_tc_init() != cudaSuccess) ok = false;
-            else g_tables_dev.insert(pl->device);
+            if (upload_harmonic_tables() != cudaSuccess || m2l_tc_init() != cudaSuccess) {
+                free_plan(pl);
+                return PT_ERR_CUDA;
+            }
+            g_tables_dev.insert(pl->device);
         }
     }
     ok = ok && dalloc(pl, ws.key, sizeof(uint32_t) * n_max) && dalloc(pl, ws.rank, sizeof(uint32_t) * n_max) &&
