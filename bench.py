@@ -137,7 +137,7 @@ class ClockSampler:
 
 def launches_per_step(depth: int, precision: str) -> int:
     # drift+cube, keys, 3 scan, scatter, 3 scan, leaf gather, near_far, kick
-    k = 11
+    k = 12
     if depth >= 2:
         k += 1 + (depth - 2)                 # P2M, M2M per level
         if precision in ("tf32x3", "bf16x3"):
