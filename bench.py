@@ -149,6 +149,24 @@ def launches_per_step(depth: int, precision: str) -> int:
     return k
 
 
+def replica_seeds(rank):
+    """(crystal seed, photon-stream seed) of an independent replica: every
+    rank simulates its own crystal and draws its own photons."""
+    return 2 + rank, 1 + rank
+
+
+def job_rate(local_ms, world, n, steps, dist=None, device="cpu"):
+    """Slowest rank's timed milliseconds and the whole job's ion-steps/s
+    (every rank advanced its own n ions by `steps` steps)."""
+    t = float(local_ms)
+    if dist is not None:
+        import torch
+        tt = torch.tensor([t], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, world * n * steps / (t * 1e-3)
+
+
 def run_cpu_baseline(cr, budget_s=12.0, max_steps=30):
     import oracle
     pos, vel, q, tr = cr["pos"], cr["vel"], cr["q"], cr["trap"]
@@ -248,10 +266,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    cr = W.crystal_spheroid_10k(seed=2 + rank)
+    crystal_seed, photon_seed = replica_seeds(rank)
+    cr = W.crystal_spheroid_10k(seed=crystal_seed)
     n = len(cr["q"])
     trap = pt.make_trap(cr["trap"])
-    laser = pt.make_laser(cr["beams"], seed=1 + rank, gamma0=W.GAMMA0)
+    laser = pt.make_laser(cr["beams"], seed=photon_seed, gamma0=W.GAMMA0)
     dt = cr["dt"]
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -287,13 +306,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(sum(ms))
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms, value = job_rate(sum(ms), world, n, args.steps, dist, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms * 1e-3)
 
     # phase breakdown and the roofline of the dominant kernel
     ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
