@@ -215,6 +215,64 @@ def reference_arm(args, rank):
     return 0
 
 
+def ensemble_arm(args, rank):
+    """Batched ensemble: every crystal its own plan (depth from the autotuner
+    for its ion-count band), all advanced by one graph launch per step."""
+    import torch
+    import paper_2405_13973_gb300 as pt
+    from paper_2405_13973_gb300 import autotune
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    crs = W.ensemble_crystals(args.ensemble, seed=17 * rank)
+
+    def crystal(n):
+        c = W.ensemble_member(n, 0.3, seed=3, cooling=False)
+        return c["pos"], c["vel"], c["q"], c["trap"], c["dt"]
+
+    t_tune = time.perf_counter()
+    depths = [autotune.tune_depth(len(c["q"]), args.p, args.precision, crystal) for c in crs]
+    t_tune = time.perf_counter() - t_tune
+    plans = [pt.Plan(len(c["q"]), p=args.p, leaf_max=32, depth=d, precision=args.precision)
+             for c, d in zip(crs, depths)]
+    states = [pt.State.from_numpy(c["pos"], c["vel"], c["q"]) for c in crs]
+    traps = [pt.make_trap(c["trap"]) for c in crs]
+    lasers = [pt.make_laser(c["beams"], seed=1 + k, gamma0=W.GAMMA0) for k, c in enumerate(crs)]
+    dts = [c["dt"] for c in crs]
+    ens = pt.Ensemble(plans)
+    ens.step(states, traps, lasers, dts, args.warmup)
+    ens.sync()
+    ions = sum(len(c["q"]) for c in crs)
+    flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(args.steps):
+        flush_buf.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ens.step(states, traps, lasers, dts, 1)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ens.sync()
+    total = float(sum(ms))
+    line = {"metric": "ion-steps/s (batched ensemble of independent crystals)",
+            "value": ions * args.steps / (total * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"{args.ensemble} crystals, N log-uniform [100, 20000], "
+                                   f"aspect U[0.1, 1], cooling on, p={args.p}, dt=1ns",
+                       "ions": ions, "depths": sorted(set(depths)),
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "autotune_s": t_tune, "graph_launches_per_step": 1}
+    ens.close()
+    for pl in plans:
+        pl.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
     """K single steps, each timed with CUDA events, L2 flushed in between."""
     stream = torch.cuda.current_stream()
@@ -247,6 +305,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="batched-ensemble measurement with this many crystals instead of the "
+                         "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -256,6 +317,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank)
+    if args.ensemble > 0:
+        return ensemble_arm(args, rank)
 
     import torch
     import paper_2405_13973_gb300 as pt

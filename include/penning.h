@@ -279,6 +279,46 @@ const char* pt_status_str(int status);
  * Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
 int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent crystals (e.g. trajectories of the stochastic
+ * laser cooling of Sec. 2.2, or crystals of different ion counts and rotation
+ * frequencies) advanced together.  Each member is the step of Eq. time_ev2
+ * on its own crystal with its own plan; the members do not interact.
+ *
+ * pt_ensemble_create -- groups n_members distinct plans of one device.
+ *   plans : host array of n_members plans, one per crystal.  The caller keeps
+ *           them and must not destroy or use them elsewhere while the
+ *           ensemble is stepping them.
+ *   out   : receives the ensemble.
+ * Errors: PT_ERR_ARG (NULL, duplicate plans, mixed devices), PT_ERR_OOM,
+ * PT_ERR_CUDA. */
+typedef struct pt_ensemble_s* pt_ensemble;
+int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out);
+
+/* pt_ensemble_step -- advances every member b by n_steps steps.
+ *   states : host array of n_members pt_state (device pointers inside);
+ *            member b's t and step advance as with pt_step.
+ *   traps  : host array of n_members traps.
+ *   lasers : host array of n_members lasers, or NULL for no cooling.
+ *   dt     : host array of n_members time steps (s).
+ *   stream : CUDA stream (cudaStream_t) or NULL.
+ * Every step of the whole ensemble is one launch of one CUDA graph holding
+ * each member's step as a parallel branch (captured once, again when a
+ * member's depth, buffers or parameters change).  A member's result equals
+ * the same plan stepped alone by pt_step, bit for bit.  Asynchronous like
+ * pt_step_async: automatic-depth plans keep the depth chosen at their first
+ * step; device errors are latched and returned by pt_ensemble_sync.
+ * Errors: PT_ERR_ARG (any member's arguments as in pt_step), PT_ERR_CUDA. */
+int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
+                     const pt_laser* lasers, const double* dt, int64_t n_steps, void* stream);
+
+/* pt_ensemble_sync -- waits for the stream and returns the first member's
+ * latched device error (PT_ERR_NONFINITE, PT_ERR_TIMEOUT, ...) or PT_OK. */
+int pt_ensemble_sync(pt_ensemble ens, void* stream);
+
+/* pt_ensemble_destroy -- frees the ensemble (not its plans). */
+int pt_ensemble_destroy(pt_ensemble ens);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,11 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
+        L.pt_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
+        L.pt_ensemble_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                       ctypes.POINTER(pt_laser), ctypes.POINTER(_D), _I64, _VP]
+        L.pt_ensemble_sync.argtypes = [_VP, _VP]
+        L.pt_ensemble_destroy.argtypes = [_VP]
         _lib = L
         return L
 
@@ -335,3 +340,46 @@ def energy(state: State, trap, plan: Plan | None = None, stream=None):
     _check(load().pt_energy(plan._h if plan is not None else None, ctypes.byref(st),
                             ctypes.byref(tr), out, _stream(stream)), "pt_energy")
     return list(out)
+
+
+class Ensemble:
+    """Independent crystals advanced together: every step of all members is
+    one launch of one CUDA graph (members as parallel branches).  The plans
+    stay the caller's; a member's result equals its plan stepped alone."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (_VP * len(self.plans))(*[pl._h.value for pl in self.plans])
+        h = ctypes.c_void_p()
+        _check(load(False).pt_ensemble_create(len(self.plans), arr, ctypes.byref(h)),
+               "pt_ensemble_create")
+        self._h = h
+
+    def step(self, states, traps, lasers, dts, n_steps: int, stream=None):
+        """Enqueue n_steps steps of every member (asynchronous; see sync)."""
+        m = len(self.plans)
+        if not (len(states) == len(traps) == len(dts) == m) or (lasers is not None and len(lasers) != m):
+            raise ValueError("one state, trap, dt (and laser) per member")
+        st = (pt_state * m)(*[s._c() for s in states])
+        tr = (pt_trap * m)(*[t if isinstance(t, pt_trap) else make_trap(t) for t in traps])
+        lz = (pt_laser * m)(*lasers) if lasers is not None else None
+        dt = (ctypes.c_double * m)(*[float(d) for d in dts])
+        _check(load(False).pt_ensemble_step(self._h, st, tr, lz, dt, int(n_steps),
+                                            _stream(stream)), "pt_ensemble_step")
+        for s, c in zip(states, st):
+            s.t, s.step = c.t, c.step
+        return states
+
+    def sync(self, stream=None):
+        _check(load(False).pt_ensemble_sync(self._h, _stream(stream)), "pt_ensemble_sync")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load(False).pt_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

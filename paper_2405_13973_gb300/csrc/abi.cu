@@ -6,7 +6,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <set>
 #include <vector>
@@ -59,6 +61,7 @@ struct fmm_plan_s {
     bool profile = false;
     static constexpr int kPhases = 6;
     cudaEvent_t ph_ev[kPhases + 1] = {nullptr};
+    bool ops_held = false;     // holds a reference on the shared operator set
 };
 
 namespace {
@@ -88,12 +91,40 @@ int status_from(cudaError_t e) {
     return PT_ERR_CUDA;
 }
 
+// Translation operators are read-only and depend only on (device, p,
+// precision): plans of the same kind share one copy (an ensemble of hundreds
+// of crystals would otherwise hold hundreds of identical 100 MB sets).
+struct OpSet {
+    int refs = 0;
+    void* T_m2m = nullptr;
+    void* T_l2l = nullptr;
+    void* T_m2l = nullptr;
+    void* T_m2l_tc = nullptr;
+};
+std::mutex g_ops_mu;
+std::map<std::tuple<int, int, int>, OpSet> g_ops;
+
+void release_ops(fmm_plan_s* pl) {
+    if (!pl->ops_held) return;
+    std::lock_guard<std::mutex> g(g_ops_mu);
+    auto it = g_ops.find(std::make_tuple(pl->device, pl->p, pl->precision));
+    if (it != g_ops.end() && --it->second.refs == 0) {
+        cudaFree(it->second.T_m2m);
+        cudaFree(it->second.T_l2l);
+        cudaFree(it->second.T_m2l);
+        if (it->second.T_m2l_tc) cudaFree(it->second.T_m2l_tc);
+        g_ops.erase(it);
+    }
+    pl->ops_held = false;
+}
+
 void free_plan(fmm_plan_s* pl) {
     if (!pl) return;
     cudaSetDevice(pl->device);
     cudaDeviceSynchronize();
     if (pl->graph) cudaGraphExecDestroy(pl->graph);
     for (void* v : pl->allocs) cudaFree(v);
+    release_ops(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     for (int k = 0; k < fmm_plan_s::kSlots; ++k) {
         if (pl->h_wall[k]) cudaFreeHost(pl->h_wall[k]);
@@ -154,6 +185,49 @@ int build_operators(fmm_plan_s* pl) {
         e = cudaMemcpy(pl->ws.T_m2l_tc, packed.data(), packed.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return status_from(e);
     }
+    return PT_OK;
+}
+
+// Points the plan at the shared operator set of its (device, p, precision),
+// building and uploading it on first use.
+int acquire_ops(fmm_plan_s* pl, size_t op_bytes) {
+    std::lock_guard<std::mutex> g(g_ops_mu);
+    const auto key = std::make_tuple(pl->device, pl->p, pl->precision);
+    auto it = g_ops.find(key);
+    Workspace& ws = pl->ws;
+    if (it == g_ops.end()) {
+        OpSet o;
+        const size_t tc = is_tc(pl->precision) ? m2l_tc_operand_bytes(pl->p, ws.tc_bf16 != 0) : 0;
+        if (cudaMalloc(&o.T_m2m, 8 * op_bytes) != cudaSuccess ||
+            cudaMalloc(&o.T_l2l, 8 * op_bytes) != cudaSuccess ||
+            cudaMalloc(&o.T_m2l, 343 * op_bytes) != cudaSuccess ||
+            (tc && cudaMalloc(&o.T_m2l_tc, tc) != cudaSuccess)) {
+            cudaFree(o.T_m2m);
+            cudaFree(o.T_l2l);
+            cudaFree(o.T_m2l);
+            return PT_ERR_OOM;
+        }
+        ws.T_m2m = o.T_m2m;
+        ws.T_l2l = o.T_l2l;
+        ws.T_m2l = o.T_m2l;
+        ws.T_m2l_tc = o.T_m2l_tc;
+        int r = build_operators(pl);
+        if (r != PT_OK) {
+            cudaFree(o.T_m2m);
+            cudaFree(o.T_l2l);
+            cudaFree(o.T_m2l);
+            if (o.T_m2l_tc) cudaFree(o.T_m2l_tc);
+            ws.T_m2m = ws.T_l2l = ws.T_m2l = ws.T_m2l_tc = nullptr;
+            return r;
+        }
+        it = g_ops.emplace(key, o).first;
+    }
+    it->second.refs++;
+    ws.T_m2m = it->second.T_m2m;
+    ws.T_l2l = it->second.T_l2l;
+    ws.T_m2l = it->second.T_m2l;
+    ws.T_m2l_tc = it->second.T_m2l_tc;
+    pl->ops_held = true;
     return PT_OK;
 }
 
@@ -228,13 +302,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
     return e;
 }
 
-// The step loop shared by pt_step (synchronous) and pt_step_async.
-int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_laser* laser,
-              double dt, int64_t n_steps, cudaStream_t s, bool sync) {
-    Workspace& ws = plan->ws;
-    pt_laser lz;
-    memset(&lz, 0, sizeof lz);
-    if (laser) lz = *laser;
+PushParams make_push(const pt_trap* trap, double dt) {
     PushParams pp;
     memset(&pp, 0, sizeof pp);
     pp.h = 0.5 * dt;
@@ -246,43 +314,70 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
     pp.delta = trap->delta;
     pp.mass = trap->mass;
     pp.rk = 1.054571817e-34 / trap->mass;
+    return pp;
+}
+
+// Before a chunk of k steps starting at step step0 + s0: the octree depth
+// and, through the next pinned slot, the chunk's wall phases
+// cos/sin(2 w_r t_mid) and the device step counter (queued on s).
+int prepare_chunk(fmm_plan_s* plan, const pt_state* st, const pt_trap* trap, double dt, double t0,
+                  int64_t step0, int64_t s0, int64_t k, bool sync, cudaStream_t s, int* D) {
+    Workspace& ws = plan->ws;
+    if (sync || plan->depth >= 0) {
+        int r = choose_depth(plan, st->n, st->x, st->y, st->z, s, D);
+        if (r != PT_OK) return r;
+    } else {
+        if (plan->last_depth < 0) return PT_ERR_ARG;
+        *D = plan->last_depth;
+    }
+    const int slot = plan->next_slot;
+    plan->next_slot = (slot + 1) % fmm_plan_s::kSlots;
+    cudaError_t e = cudaEventSynchronize(plan->slot_ev[slot]);  // slot free again
+    if (e != cudaSuccess) return status_from(e);
+    double* hw = plan->h_wall[slot];
+    for (int64_t j = 0; j < k; ++j) {
+        double tm = (t0 + (double)(s0 + j) * dt) + 0.5 * dt;
+        hw[2 * j] = cos(2.0 * trap->omega_r * tm);
+        hw[2 * j + 1] = sin(2.0 * trap->omega_r * tm);
+    }
+    *plan->h_steps[slot] = StepCounter{0, step0 + s0, step0 + s0};
+    e = cudaMemcpyAsync(ws.wall_cs, hw, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws.steps, plan->h_steps[slot], sizeof(StepCounter), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(plan->slot_ev[slot], s);
+    return status_from(e);
+}
+
+GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& pp,
+                  const pt_laser& lz, int D) {
+    GraphKey key;
+    key.D = D;
+    key.n = st->n;
+    const void* ptrs[7] = {st->x, st->y, st->z, st->vx, st->vy, st->vz, st->q};
+    memcpy(key.ptr, ptrs, sizeof ptrs);
+    key.pp = pp;
+    key.laser = lz;
+    key.profile = plan->profile;
+    return key;
+}
+
+// The step loop shared by pt_step (synchronous) and pt_step_async.
+int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_laser* laser,
+              double dt, int64_t n_steps, cudaStream_t s, bool sync) {
+    Workspace& ws = plan->ws;
+    pt_laser lz;
+    memset(&lz, 0, sizeof lz);
+    if (laser) lz = *laser;
+    const PushParams pp = make_push(trap, dt);
     const double t0 = st->t;
     const int64_t step0 = st->step;
     for (int64_t s0 = 0; s0 < n_steps; s0 += ws.wall_cap) {
         const int64_t k = (n_steps - s0) < ws.wall_cap ? (n_steps - s0) : ws.wall_cap;
         int D;
-        if (sync || plan->depth >= 0) {
-            int r = choose_depth(plan, st->n, st->x, st->y, st->z, s, &D);
-            if (r != PT_OK) return r;
-        } else {
-            if (plan->last_depth < 0) return PT_ERR_ARG;
-            D = plan->last_depth;
-        }
-        const int slot = plan->next_slot;
-        plan->next_slot = (slot + 1) % fmm_plan_s::kSlots;
-        cudaError_t e = cudaEventSynchronize(plan->slot_ev[slot]);  // slot free again
-        if (e != cudaSuccess) return status_from(e);
-        double* hw = plan->h_wall[slot];
-        for (int64_t j = 0; j < k; ++j) {
-            double tm = (t0 + (double)(s0 + j) * dt) + 0.5 * dt;
-            hw[2 * j] = cos(2.0 * trap->omega_r * tm);
-            hw[2 * j + 1] = sin(2.0 * trap->omega_r * tm);
-        }
-        *plan->h_steps[slot] = StepCounter{0, step0 + s0, step0 + s0};
-        e = cudaMemcpyAsync(ws.wall_cs, hw, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ws.steps, plan->h_steps[slot], sizeof(StepCounter),
-                                cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaEventRecord(plan->slot_ev[slot], s);
-        if (e != cudaSuccess) return status_from(e);
-        GraphKey key;
-        key.D = D;
-        key.n = st->n;
-        const void* ptrs[7] = {st->x, st->y, st->z, st->vx, st->vy, st->vz, st->q};
-        memcpy(key.ptr, ptrs, sizeof ptrs);
-        key.pp = pp;
-        key.laser = lz;
-        key.profile = plan->profile;
+        int r = prepare_chunk(plan, st, trap, dt, t0, step0, s0, k, sync, s, &D);
+        if (r != PT_OK) return r;
+        cudaError_t e;
+        const GraphKey key = make_key(plan, st, pp, lz, D);
         if (!plan->graph || !(key == plan->gkey)) {
             if (plan->graph) {
                 cudaGraphExecDestroy(plan->graph);
@@ -312,7 +407,7 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
         plan->last_depth = D;
         plan->last_n = st->n;
         if (sync) {
-            int r = check_err(plan, s);
+            r = check_err(plan, s);
             if (r != PT_OK) return r;
         }
     }
@@ -321,6 +416,35 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
     return PT_OK;
 }
 
+}  // namespace
+
+// Independent crystals stepped together: one CUDA graph holds every member's
+// time step as a parallel branch, so one graph launch advances the whole
+// ensemble by one step and the members' kernels share the GPU.
+struct pt_ensemble_s {
+    int device = 0;
+    std::vector<fmm_plan_s*> plans;      // not owned
+    std::vector<cudaStream_t> br;        // capture-time branch streams
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<GraphKey> keys;
+};
+
+namespace {
+void free_ensemble(pt_ensemble_s* e) {
+    if (!e) return;
+    cudaSetDevice(e->device);
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    for (cudaStream_t b : e->br)
+        if (b) cudaStreamDestroy(b);
+    for (cudaEvent_t j : e->join)
+        if (j) cudaEventDestroy(j);
+    if (e->fork) cudaEventDestroy(e->fork);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    delete e;
+}
 }  // namespace
 
 extern "C" {
@@ -424,9 +548,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
          dalloc(pl, ws.bbox_partial, sizeof(double) * 8 * ws.bbox_blocks) &&
          dalloc(pl, ws.ticket, sizeof(unsigned)) && dalloc(pl, ws.err, sizeof(int)) &&
          dalloc(pl, ws.steps, sizeof(StepCounter)) && dalloc(pl, ws.stats, sizeof(unsigned long long) * 8) &&
-         dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap) &&
-         dalloc(pl, ws.T_m2m, tsz * 8 * PP) && dalloc(pl, ws.T_l2l, tsz * 8 * PP) &&
-         dalloc(pl, ws.T_m2l, tsz * 343 * PP);
+         dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap);
     if (ok && is_tc(precision)) {
         ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
         int64_t tcap = 0;
@@ -436,8 +558,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
         ws.tc_part_floats = m2l_tc_part_floats(cells, ws.ld, ws.tc_splits_max, ws.tc_tiles_cap,
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
-        ok = ok && dalloc(pl, ws.T_m2l_tc, m2l_tc_operand_bytes(p, ws.tc_bf16 != 0)) &&
-             dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
+        ok = ok && dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
     }
     if (!ok) {
         free_plan(pl);
@@ -470,7 +591,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
             return PT_ERR_CUDA;
         }
     }
-    int r = build_operators(pl);
+    int r = acquire_ops(pl, tsz * PP);
     if (r != PT_OK) {
         free_plan(pl);
         return r;
@@ -632,6 +753,138 @@ int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, vo
     root[2] = rc.lo[2];
     root[3] = rc.side;
     return PT_OK;
+}
+
+int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
+    if (!out || !plans || n_members < 1) return PT_ERR_ARG;
+    *out = nullptr;
+    std::set<fmm_plan> seen;
+    for (int b = 0; b < n_members; ++b) {
+        if (!plans[b] || !seen.insert(plans[b]).second || plans[b]->device != plans[0]->device)
+            return PT_ERR_ARG;
+    }
+    pt_ensemble_s* e = new (std::nothrow) pt_ensemble_s;
+    if (!e) return PT_ERR_OOM;
+    e->device = plans[0]->device;
+    if (cudaSetDevice(e->device) != cudaSuccess) {
+        delete e;
+        return PT_ERR_CUDA;
+    }
+    e->plans.assign(plans, plans + n_members);
+    e->br.assign(n_members, nullptr);
+    e->join.assign(n_members, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; ok && b < n_members; ++b)
+        ok = cudaStreamCreateWithFlags(&e->br[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&e->join[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        free_ensemble(e);
+        return PT_ERR_CUDA;
+    }
+    *out = e;
+    return PT_OK;
+}
+
+int pt_ensemble_destroy(pt_ensemble ens) {
+    free_ensemble(ens);
+    return PT_OK;
+}
+
+int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
+                     const pt_laser* lasers, const double* dt, int64_t n_steps, void* stream) {
+    if (!ens || !states || !traps || !dt || n_steps < 0) return PT_ERR_ARG;
+    const int nm = (int)ens->plans.size();
+    for (int b = 0; b < nm; ++b) {
+        int r = step_args_ok(ens->plans[b], &states[b], &traps[b], lasers ? &lasers[b] : nullptr,
+                             dt[b], n_steps);
+        if (r != PT_OK) return r;
+    }
+    if (n_steps == 0) return PT_OK;
+    if (cudaSetDevice(ens->device) != cudaSuccess) return PT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<PushParams> pp(nm);
+    std::vector<pt_laser> lz(nm);
+    std::vector<double> t0(nm);
+    std::vector<int64_t> step0(nm);
+    for (int b = 0; b < nm; ++b) {
+        pp[b] = make_push(&traps[b], dt[b]);
+        memset(&lz[b], 0, sizeof(pt_laser));
+        if (lasers) lz[b] = lasers[b];
+        t0[b] = states[b].t;
+        step0[b] = states[b].step;
+    }
+    std::vector<int> D(nm);
+    std::vector<GraphKey> keys(nm);
+    for (int64_t s0 = 0; s0 < n_steps; s0 += kWallChunk) {
+        const int64_t k = (n_steps - s0) < kWallChunk ? (n_steps - s0) : kWallChunk;
+        for (int b = 0; b < nm; ++b) {
+            fmm_plan_s* pl = ens->plans[b];
+            // an automatic-depth plan that never chose a depth chooses it now
+            int r = prepare_chunk(pl, &states[b], &traps[b], dt[b], t0[b], step0[b], s0, k,
+                                  pl->depth < 0 && pl->last_depth < 0, s, &D[b]);
+            if (r != PT_OK) return r;
+            keys[b] = make_key(pl, &states[b], pp[b], lz[b], D[b]);
+        }
+        bool same = ens->graph != nullptr && ens->keys.size() == keys.size();
+        for (int b = 0; same && b < nm; ++b) same = keys[b] == ens->keys[b];
+        cudaError_t e;
+        if (!same) {
+            if (ens->graph) {
+                cudaGraphExecDestroy(ens->graph);
+                ens->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(ens->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return status_from(e);
+            cudaError_t e2 = cudaEventRecord(ens->fork, ens->cap);
+            for (int b = 0; e2 == cudaSuccess && b < nm; ++b) {
+                e2 = cudaStreamWaitEvent(ens->br[b], ens->fork, 0);
+                if (e2 == cudaSuccess)
+                    e2 = enqueue_step(ens->plans[b], states[b], pp[b], lz[b], D[b], ens->br[b]);
+                if (e2 == cudaSuccess) e2 = cudaEventRecord(ens->join[b], ens->br[b]);
+                if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(ens->cap, ens->join[b], 0);
+            }
+            e = cudaStreamEndCapture(ens->cap, &g);
+            if (e2 != cudaSuccess || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return status_from(e2 != cudaSuccess ? e2 : e);
+            }
+            e = cudaGraphInstantiate(&ens->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ens->graph = nullptr;
+                return status_from(e);
+            }
+            ens->keys = keys;
+        }
+        for (int64_t j = 0; j < k; ++j) {
+            e = cudaGraphLaunch(ens->graph, s);
+            if (e != cudaSuccess) return status_from(e);
+        }
+        for (int b = 0; b < nm; ++b) {
+            ens->plans[b]->last_depth = D[b];
+            ens->plans[b]->last_n = states[b].n;
+        }
+    }
+    for (int b = 0; b < nm; ++b) {
+        states[b].t = t0[b] + (double)n_steps * dt[b];
+        states[b].step = step0[b] + n_steps;
+    }
+    return PT_OK;
+}
+
+int pt_ensemble_sync(pt_ensemble ens, void* stream) {
+    if (!ens) return PT_ERR_ARG;
+    if (cudaSetDevice(ens->device) != cudaSuccess) return PT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PT_ERR_CUDA;
+    int first = PT_OK;
+    for (fmm_plan_s* pl : ens->plans) {
+        int r = check_err(pl, s);
+        if (r != PT_OK && first == PT_OK) first = r;
+    }
+    return first;
 }
 
 }  // extern "C"

@@ -131,7 +131,7 @@ cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
 size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap);
-// partial slabs of the M2L work items (a pool of 4 KB per ion, 256 MB to 8 GB)
+// partial slabs of the M2L work items (a pool of 16 KB per ion, 16 MB to 8 GB)
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max);
 size_t m2l_tc_part_floats(int64_t cells_max, int ld, int m2m_splits, int64_t tiles_cap,
                           int64_t slab_cap);

@@ -1133,10 +1133,11 @@ size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld) {
 }
 
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max) {
-    // 4 KB per ion, within [256 MB, 8 GB]: enough slabs for runs of
-    // kChainCap offsets up to about a million ions (beyond, runs lengthen)
-    double budget = 4096.0 * (double)n_max;
-    if (budget < 256.0 * 1024 * 1024) budget = 256.0 * 1024 * 1024;
+    // 16 KB per ion, within [16 MB, 8 GB]: enough slabs for runs of
+    // kChainCap offsets up to about a million ions at p <= 12 (beyond, runs
+    // lengthen), small for the small crystals of an ensemble
+    double budget = 16384.0 * (double)n_max;
+    if (budget < 16.0 * 1024 * 1024) budget = 16.0 * 1024 * 1024;
     if (budget > 8192.0 * 1024 * 1024) budget = 8192.0 * 1024 * 1024;
     int64_t s = (int64_t)(budget / ((double)kTcRows * ld * sizeof(float)));
     if (s > tiles_cap * 189) s = tiles_cap * 189;

@@ -1,0 +1,67 @@
+"""Batched ensembles through the C ABI: each member of an ensemble of uneven
+ion counts and shapes, stepped in one graph with the others, ends in the
+state that the same plan reaches when stepped alone, bit for bit (the kernels
+are deterministic and the members share nothing but the device)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2405_13973_gb300 as pt
+import workloads as W
+from paper_2405_13973_gb300 import autotune
+
+pytestmark = pytest.mark.gpu
+
+
+def members():
+    spec = [(150, 0.9), (700, 0.3), (2000, 0.5), (4000, 0.15), (300, 1.0)]
+    return [W.ensemble_member(n, a, seed=11 + k) for k, (n, a) in enumerate(spec)]
+
+
+def run(precision, p, steps_a, steps_b, together):
+    crs = members()
+    plans = [pt.Plan(len(c["q"]), p=p, leaf_max=32, depth=-1, precision=precision) for c in crs]
+    states = [pt.State.from_numpy(c["pos"], c["vel"], c["q"]) for c in crs]
+    traps = [pt.make_trap(c["trap"]) for c in crs]
+    lasers = [pt.make_laser(c["beams"], seed=5 + k, gamma0=W.GAMMA0) for k, c in enumerate(crs)]
+    dts = [c["dt"] for c in crs]
+    if together:
+        ens = pt.Ensemble(plans)
+        ens.step(states, traps, lasers, dts, steps_a)
+        ens.step(states, traps, lasers, dts, steps_b)
+        ens.sync()
+        ens.close()
+    else:
+        for pl, st, tr, lz, dt in zip(plans, states, traps, lasers, dts):
+            pl.step(st, tr, lz, dt, steps_a)
+            pl.step(st, tr, lz, dt, steps_b)
+    torch.cuda.synchronize()
+    out = [(s.pos().cpu().numpy(), s.vel().cpu().numpy(), s.t, s.step, pl.last_depth)
+           for s, pl in zip(states, plans)]
+    for pl in plans:
+        pl.close()
+    return out
+
+
+@pytest.mark.parametrize("precision,p", [("fp64", 6), ("bf16x3", 8)])
+def test_member_alone_equals_member_in_the_mix(precision, p):
+    mixed = run(precision, p, 5, 3, together=True)
+    alone = run(precision, p, 5, 3, together=False)
+    for (xm, vm, tm, sm, dm), (xa, va, ta, sa, da) in zip(mixed, alone):
+        assert dm == da
+        assert sm == sa == 8 and tm == ta
+        assert np.array_equal(xm, xa) and np.array_equal(vm, va)
+        assert np.all(np.isfinite(xm))
+
+
+def test_autotuned_depth_is_a_neighbour_of_the_automatic_one():
+    def crystal(n):
+        c = W.ensemble_member(n, 0.3, seed=3, cooling=False)
+        return c["pos"], c["vel"], c["q"], c["trap"], c["dt"]
+    d = autotune.tune_depth(3000, 8, "bf16x3", crystal, steps=4)
+    pos, vel, q, tr, dt = crystal(3000)
+    plan = pt.Plan(len(q), p=8, depth=-1, precision="bf16x3")
+    plan.step(pt.State.from_numpy(pos, vel, q), pt.make_trap(tr), None, dt, 1)
+    assert abs(d - plan.last_depth) <= 1
+    assert autotune.tune_depth(2500, 8, "bf16x3", crystal) == d   # same band: cached
+    plan.close()

@@ -187,3 +187,26 @@ def sphere_sweep(n, seed=3, density=2e14):
     a_ws = (3.0 / (4.0 * math.pi * density)) ** (1.0 / 3.0)
     pos = _unit_ball(rng, n) * radius + rng.normal(size=(n, 3)) * 0.01 * a_ws
     return {"name": f"sphere_sweep_N{n}", "pos": pos, "q": charges(n), "radius": radius}
+
+
+def ensemble_member(n, aspect, seed, temperature=10e-3, cooling=True):
+    """One crystal of a batched ensemble: n ions uniform at the rigid-rotor
+    density in a spheroid of the given aspect (the rotation frequency follows
+    from the shape law), rotating Maxwellian, the cooling beams."""
+    tr = trap(aspect=aspect)
+    n0 = rigid_rotor_density(tr["omega_r"])
+    a_r = (3.0 * n / (4.0 * math.pi * n0 * aspect)) ** (1.0 / 3.0)
+    pos = spheroid(n, a_r, aspect * a_r, seed)
+    vel = rotating_maxwellian(pos, tr["omega_r"], temperature, seed + 1000)
+    return {"name": f"member{seed}_N{n}_a{aspect:.2f}", "pos": pos, "vel": vel, "q": charges(n),
+            "trap": tr, "beams": cooling_beams() if cooling else [], "laser": cooling, "dt": DT,
+            "aspect": aspect}
+
+
+def ensemble_crystals(n_members=256, n_lo=100, n_hi=20000, seed=0):
+    """Batched ensemble: n_members crystals, N log-uniform in [n_lo, n_hi],
+    aspect uniform in [0.1, 1.0], seeds seed + k, cooling on."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_members)).astype(int)
+    aspects = rng.uniform(0.1, 1.0, n_members)
+    return [ensemble_member(int(n), float(a), seed + 7 * k) for k, (n, a) in enumerate(zip(ns, aspects))]
