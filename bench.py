@@ -273,6 +273,48 @@ def ensemble_arm(args, rank):
     return 0
 
 
+def serve_arm(args, rank):
+    """Serving: jobs with Poisson arrivals (mean args.serve_rate per s), N
+    log-uniform in [200, 50000], step counts log-uniform in args.serve_steps,
+    random aspect and seeds, cooling on; admitted by device-memory budget,
+    continuously batched.  Reports latency percentiles and throughput."""
+    import torch
+    from paper_2405_13973_gb300.serving import Job, Server, report
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(101 + rank)
+    m = args.serve
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, m))
+    ns = np.exp(rng.uniform(math.log(200), math.log(50000), m)).astype(int)
+    lo, hi = args.serve_steps
+    steps = np.exp(rng.uniform(math.log(lo), math.log(hi), m)).astype(int)
+    aspects = rng.uniform(0.1, 1.0, m)
+    jobs = []
+    for k in range(m):
+        c = W.ensemble_member(int(ns[k]), float(aspects[k]), seed=1000 + k)
+        jobs.append(Job(k, c["pos"], c["vel"], c["q"], c["trap"], c["beams"], 77 + k, c["dt"],
+                        int(steps[k]), arrival=float(arrivals[k]), gamma0=W.GAMMA0))
+    srv = Server(int(args.serve_budget_gb * 2**30), p=args.p, precision=args.precision,
+                 chunk=256)
+    t0 = time.perf_counter()
+    srv.run(jobs)
+    makespan = time.perf_counter() - t0
+    rep = report(jobs, makespan)
+    line = {"metric": "serving: job latency p50/p99 and aggregate ion-steps/s",
+            "value": rep["ion_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"{m} jobs, Poisson arrivals {args.serve_rate}/s, N log-uniform "
+                                   f"[200, 50000], steps log-uniform [{lo:g}, {hi:g}], aspect "
+                                   f"U[0.1, 1], cooling on, p={args.p}, dt=1ns",
+                       "hbm_budget_gb": args.serve_budget_gb},
+            "latency_s": {"p50": rep["p50_s"], "p99": rep["p99_s"], "max": rep["max_s"]},
+            "makespan_s": makespan, "ion_steps": rep["ion_steps"],
+            "peak_admitted_gb": srv.peak_bytes / 2**30, "graph_recaptures": srv.recaptures,
+            "chunks": srv.chunks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
     """K single steps, each timed with CUDA events, L2 flushed in between."""
     stream = torch.cuda.current_stream()
@@ -305,6 +347,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving measurement with this many Poisson-arriving jobs instead of the "
+                         "single-crystal step")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="mean arrivals per second")
+    ap.add_argument("--serve-steps", type=float, nargs=2, default=[100.0, 10000.0],
+                    help="job step counts, log-uniform in this range")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched-ensemble measurement with this many crystals instead of the "
                          "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
@@ -319,6 +368,8 @@ def main():
         return reference_arm(args, rank)
     if args.ensemble > 0:
         return ensemble_arm(args, rank)
+    if args.serve > 0:
+        return serve_arm(args, rank)
 
     import torch
     import paper_2405_13973_gb300 as pt

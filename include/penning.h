@@ -280,6 +280,19 @@ const char* pt_status_str(int status);
 int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * fmm_plan_footprint -- the device memory fmm_plan_create would allocate for
+ * these arguments, without allocating anything (no GPU needed): for admission
+ * control by memory budget.  The paper has no counterpart (a service of the
+ * library, like pt_energy_noalloc).
+ *   plan_bytes     : receives the plan's own workspace (octree, expansions,
+ *                    work list and partial slabs), at 512-byte granularity.
+ *   operator_bytes : receives the translation operators, which all plans of
+ *                    one (device, p, precision) share: counted once.
+ * Errors: PT_ERR_ARG (as fmm_plan_create), PT_ERR_UNSUPPORTED. */
+int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precision,
+                       int64_t* plan_bytes, int64_t* operator_bytes);
+
+/* ---------------------------------------------------------------------------
  * Ensembles: many independent crystals (e.g. trajectories of the stochastic
  * laser cooling of Sec. 2.2, or crystals of different ion counts and rotation
  * frequencies) advanced together.  Each member is the step of Eq. time_ev2

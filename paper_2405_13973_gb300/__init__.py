@@ -116,6 +116,8 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
+        L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
         L.pt_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.pt_ensemble_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                        ctypes.POINTER(pt_laser), ctypes.POINTER(_D), _I64, _VP]
@@ -340,6 +342,16 @@ def energy(state: State, trap, plan: Plan | None = None, stream=None):
     _check(load().pt_energy(plan._h if plan is not None else None, ctypes.byref(st),
                             ctypes.byref(tr), out, _stream(stream)), "pt_energy")
     return list(out)
+
+
+def plan_footprint(n_max: int, p: int, leaf_max: int = 32, depth: int = -1,
+                   precision="fp64") -> tuple[int, int]:
+    """(plan workspace bytes, shared operator bytes) that Plan(...) would take."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fmm_plan_footprint(int(n_max), int(p), int(leaf_max), int(depth), prec,
+                                     ctypes.byref(a), ctypes.byref(b)), "fmm_plan_footprint")
+    return a.value, b.value
 
 
 class Ensemble:

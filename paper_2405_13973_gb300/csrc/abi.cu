@@ -62,6 +62,8 @@ struct fmm_plan_s {
     static constexpr int kPhases = 6;
     cudaEvent_t ph_ev[kPhases + 1] = {nullptr};
     bool ops_held = false;     // holds a reference on the shared operator set
+    bool dry = false;          // sizing only (fmm_plan_footprint): nothing is allocated
+    size_t dry_bytes = 0;
 };
 
 namespace {
@@ -73,6 +75,11 @@ template <typename T>
 bool dalloc(fmm_plan_s* pl, T*& p, size_t bytes) {
     void* v = nullptr;
     if (bytes == 0) bytes = 16;
+    if (pl->dry) {  // count (at the allocator's 512-byte granularity), allocate nothing
+        pl->dry_bytes += (bytes + 511) / 512 * 512;
+        p = nullptr;
+        return true;
+    }
     if (cudaMalloc(&v, bytes) != cudaSuccess) return false;
     pl->allocs.push_back(v);
     p = (T*)v;
@@ -464,7 +471,23 @@ const char* pt_status_str(int status) {
     }
 }
 
+static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int precision,
+                            fmm_plan* out, bool dry, int64_t* dry_bytes, int64_t* op_bytes);
+
 int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision, fmm_plan* out) {
+    return plan_create_impl(n_max, p, leaf_max, depth, precision, out, false, nullptr, nullptr);
+}
+
+int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precision,
+                       int64_t* plan_bytes, int64_t* operator_bytes) {
+    if (!plan_bytes || !operator_bytes) return PT_ERR_ARG;
+    fmm_plan dummy = nullptr;
+    return plan_create_impl(n_max, p, leaf_max, depth, precision, &dummy, true, plan_bytes,
+                            operator_bytes);
+}
+
+static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int precision,
+                            fmm_plan* out, bool dry, int64_t* dry_bytes, int64_t* op_bytes) {
     if (!out || n_max < 1 || n_max > (int64_t)1 << 30 || p < 2 || p > kMaxOrder || leaf_max < 1 ||
         depth < -1 || depth > kMaxDepth)
         return PT_ERR_ARG;
@@ -472,11 +495,17 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     *out = nullptr;
     fmm_plan_s* pl = new (std::nothrow) fmm_plan_s;
     if (!pl) return PT_ERR_OOM;
-    if (cudaGetDevice(&pl->device) != cudaSuccess) {
+    pl->dry = dry;
+    if (dry) {
+        if (is_tc(precision) && m2l_tc_operand_bytes(p, precision == PT_MIXED_BF16X3) == 0) {
+            delete pl;
+            return PT_ERR_UNSUPPORTED;
+        }
+    } else if (cudaGetDevice(&pl->device) != cudaSuccess) {
         delete pl;
         return PT_ERR_CUDA;
     }
-    if (is_tc(precision)) {
+    if (!dry && is_tc(precision)) {
         cudaDeviceProp prop;
         if (cudaGetDeviceProperties(&prop, pl->device) != cudaSuccess) {
             delete pl;
@@ -521,7 +550,7 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     const size_t tsz = ws.fp64 ? sizeof(double) : sizeof(float);
     const size_t PP = (size_t)pl->P * pl->P;
     bool ok = true;
-    {
+    if (!dry) {
         // per-device tables and kernel attributes: a failure here is a CUDA
         // error, not a lack of memory
         std::lock_guard<std::mutex> g(g_tables_mu);
@@ -559,6 +588,13 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
         ok = ok && dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
+    }
+    if (dry) {
+        *dry_bytes = (int64_t)pl->dry_bytes;
+        *op_bytes = (int64_t)(tsz * (8 + 8 + 343) * PP +
+                              (is_tc(precision) ? m2l_tc_operand_bytes(p, ws.tc_bf16 != 0) : 0));
+        delete pl;
+        return PT_OK;
     }
     if (!ok) {
         free_plan(pl);
