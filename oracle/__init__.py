@@ -71,6 +71,8 @@ def lib():
             L.orc_step.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_double, _I64, _I64]
+            L.orc_step_damped.argtypes = L.orc_step.argtypes + [ctypes.c_double]
+            L.orc_temperatures.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D]
             L.orc_energy_rot.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double, _D]
             _lib = L
     return _lib
@@ -232,16 +234,32 @@ def laser_kick(pos, vel, beams, gamma0, mass, seed, step, dt):
 
 
 def step(pos, vel, q, trap, dt, n_steps, t0=0.0, step0=0, beams=(), gamma0=0.0, seed=0,
-         laser_on=False):
-    """Advance (pos, vel) by n_steps literal cyclotronic steps; returns copies."""
+         laser_on=False, damping=None):
+    """Advance (pos, vel) by n_steps literal cyclotronic steps; returns copies.
+    damping (1/s): rotating-frame velocities scaled by exp(-damping dt) after
+    every kick (None: the undamped step)."""
     st = [_f64(pos[:, a]).copy() for a in range(3)] + [_f64(vel[:, a]).copy() for a in range(3)]
     q = _f64(q)
     tr = trap_array(trap)
     b = beams_array(beams) if len(beams) else np.zeros(9)
-    lib().orc_step(len(q), *[_p(a) for a in st], _p(q), _p(tr), _p(b), len(beams), float(gamma0),
-                   int(seed) & (2**64 - 1), 1 if laser_on else 0, float(dt), float(t0), int(step0),
-                   int(n_steps))
+    args = (len(q), *[_p(a) for a in st], _p(q), _p(tr), _p(b), len(beams), float(gamma0),
+            int(seed) & (2**64 - 1), 1 if laser_on else 0, float(dt), float(t0), int(step0),
+            int(n_steps))
+    if damping is None:
+        lib().orc_step(*args)
+    else:
+        lib().orc_step_damped(*args, float(damping))
     return np.stack(st[:3], 1), np.stack(st[3:], 1)
+
+
+def temperatures(pos, vel, trap):
+    """(T_par, T_perp) in K of the rotating-frame motion."""
+    x, y = _f64(pos[:, 0]), _f64(pos[:, 1])
+    vx, vy, vz = (_f64(vel[:, a]) for a in range(3))
+    out = np.empty(2)
+    lib().orc_temperatures(len(x), _p(x), _p(y), _p(vx), _p(vy), _p(vz), _p(trap_array(trap)),
+                           _p(out))
+    return float(out[0]), float(out[1])
 
 
 def energy_rot(pos, vel, q, trap, t):

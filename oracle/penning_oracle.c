@@ -463,10 +463,39 @@ void orc_laser_kick(int64_t n, const double* beams, int n_beams, double gamma0, 
  * Trap parameters as above; beams as above (n_beams may be 0); laser_on
  * switches the kicks; t0 and step0 are the time and step index at entry.
  * ====================================================================== */
+/* The step above with optional artificial damping (Sec. 6: damping the
+ * ions' motion to find crystal equilibria): after the kick, each ion's
+ * velocity relative to the rigid rotation at w_r (the rotating-frame
+ * velocity w = (v_x - w_r y, v_y + w_r x, v_z) at the mid-step position) is
+ * scaled by f = exp(-gamma dt):  v <- (w_r y, -w_r x, 0) + f w.  f = 1 is the
+ * undamped step.  The rotating-frame energy (orc_energy_rot) then falls by
+ * gamma m |w|^2 per unit time (magnetic and Coriolis forces do no work), so
+ * the crystal relaxes to a minimum of the rotating-frame potential. */
+static void orc_step_impl(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                          double* vz, const double* q, const double* trap, const double* beams,
+                          int n_beams, double gamma0, uint64_t seed, int laser_on, double dt,
+                          double t0, int64_t step0, int64_t n_steps, double damp);
+
 void orc_step(int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
               const double* q, const double* trap, const double* beams, int n_beams,
               double gamma0, uint64_t seed, int laser_on, double dt, double t0, int64_t step0,
               int64_t n_steps) {
+    orc_step_impl(n, x, y, z, vx, vy, vz, q, trap, beams, n_beams, gamma0, seed, laser_on, dt, t0,
+                  step0, n_steps, 1.0);
+}
+
+void orc_step_damped(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                     double* vz, const double* q, const double* trap, const double* beams,
+                     int n_beams, double gamma0, uint64_t seed, int laser_on, double dt, double t0,
+                     int64_t step0, int64_t n_steps, double damping) {
+    orc_step_impl(n, x, y, z, vx, vy, vz, q, trap, beams, n_beams, gamma0, seed, laser_on, dt, t0,
+                  step0, n_steps, exp(-damping * dt));
+}
+
+static void orc_step_impl(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
+                          double* vz, const double* q, const double* trap, const double* beams,
+                          int n_beams, double gamma0, uint64_t seed, int laser_on, double dt,
+                          double t0, int64_t step0, int64_t n_steps, double damp) {
     double m = trap[T_M];
     double wc = trap[T_Q] * trap[T_B] / m;
     size_t sz = sizeof(double) * (size_t)(n > 0 ? n : 1);
@@ -488,6 +517,15 @@ void orc_step(int64_t n, double* x, double* y, double* z, double* vx, double* vy
             vx[i] = vx[i] + qm * (Ex[i] + Fx[i]) * dt + dvx[i];
             vy[i] = vy[i] + qm * (Ey[i] + Fy[i]) * dt + dvy[i];
             vz[i] = vz[i] + qm * (Ez[i] + Fz[i]) * dt + dvz[i];
+        }
+        if (damp != 1.0) {
+            const double wr = trap[T_WR];
+            for (int64_t i = 0; i < n; ++i) {
+                const double rx = wr * y[i], ry = -wr * x[i];
+                vx[i] = rx + damp * (vx[i] - rx);
+                vy[i] = ry + damp * (vy[i] - ry);
+                vz[i] = damp * vz[i];
+            }
         }
         orc_u0(n, 0.5 * dt, wc, x, y, z, vx, vy, vz);
     }
@@ -531,4 +569,26 @@ void orc_energy_rot(int64_t n, const double* x, const double* y, const double* z
     out[2] = acc_val(&ce);
     out[3] = out[0] + out[1] + out[2];
     free(Ex); free(Ey); free(Ez); free(phi);
+}
+
+/* ======================================================================
+ * Temperatures of the rotating-frame motion (Eqs. temp_ax, temp_pl):
+ *   T_par  = m sum_i w_z^2 / (N k_B),
+ *   T_perp = m sum_i (w_x^2 + w_y^2) / (2 N k_B),
+ * with w the velocity relative to the rigid rotation (w_x = v_x - w_r y,
+ * w_y = v_y + w_r x, w_z = v_z); the rotation into the rotating frame
+ * leaves w_x^2 + w_y^2 unchanged.  Instantaneous values (the paper's
+ * angle brackets are time averages of these).  out[2] = {T_par, T_perp} (K).
+ * ====================================================================== */
+void orc_temperatures(int64_t n, const double* x, const double* y, const double* vx,
+                      const double* vy, const double* vz, const double* trap, double out[2]) {
+    const double m = trap[T_M], wr = trap[T_WR], kb = 1.380649e-23;
+    orc_acc a = {0, 0}, b = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        const double wx = vx[i] - wr * y[i], wy = vy[i] + wr * x[i];
+        acc_add(&a, vz[i] * vz[i]);
+        acc_add(&b, wx * wx + wy * wy);
+    }
+    out[0] = m * acc_val(&a) / ((double)n * kb);
+    out[1] = m * acc_val(&b) / (2.0 * (double)n * kb);
 }
