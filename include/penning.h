@@ -280,6 +280,35 @@ const char* pt_status_str(int status);
 int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Diagnostics of a run (Sec. 5, Eqs. temps and rms_disp) and artificial
+ * damping toward equilibria (Sec. 6: the crystal evolves under the trap
+ * equations of motion while the ions' motion is slowly removed).
+ *
+ * pt_set_damping -- from the plan's next step on, after every kick each
+ *   ion's velocity relative to the rigid rotation at omega_r (the rotating-
+ *   frame velocity (v_x - w_r y, v_y + w_r x, v_z) at the mid-step
+ *   position) is scaled by exp(-gamma dt); gamma in 1/s, 0 (the default)
+ *   turns damping off and leaves the step exactly as without this call.
+ *   Errors: PT_ERR_ARG (NULL plan, gamma < 0 or NaN).
+ * pt_temperatures -- out[0] = T_par = m sum v_z^2 / (N k_B) (Eq. temp_ax),
+ *   out[1] = T_perp = m sum (w_x^2 + w_y^2) / (2 N k_B) (Eq. temp_pl), in K,
+ *   of the velocities relative to the rigid rotation (instantaneous; the
+ *   paper's angle brackets average these over time).  state: device
+ *   pointers (x, y, vx, vy, vz read); out: host, 2 doubles.  Uses a fixed
+ *   scratch array inside the library; calls are serialised by a host lock.
+ *   Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA.
+ * pt_position_moments -- accumulates the rotating-frame moments of every
+ *   ion at time state->t (x_r = R(w_r t) x as in Eq. rotation):
+ *   acc[i] += x_r, acc[n+i] += y_r, acc[2n+i] += z, acc[3n+i] += |x_r|^2.
+ *   acc: device, 4 n doubles owned and zeroed by the caller.  After K calls,
+ *   Delta r_rms of ion i = sqrt(acc[3n+i]/K - |(acc[i], acc[n+i],
+ *   acc[2n+i])/K|^2) (Eq. rms_disp).  Asynchronous.  Errors: PT_ERR_ARG,
+ *   PT_ERR_CUDA. */
+int pt_set_damping(fmm_plan plan, double gamma);
+int pt_temperatures(const pt_state* state, const pt_trap* trap, double* out, void* stream);
+int pt_position_moments(const pt_state* state, const pt_trap* trap, double* acc, void* stream);
+
+/* ---------------------------------------------------------------------------
  * fmm_plan_footprint -- the device memory fmm_plan_create would allocate for
  * these arguments, without allocating anything (no GPU needed): for admission
  * control by memory budget.  The paper has no counterpart (a service of the

@@ -118,6 +118,11 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(_I64), ctypes.POINTER(_I64)]
+        L.pt_set_damping.argtypes = [_VP, _D]
+        L.pt_temperatures.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                      ctypes.POINTER(_D), _VP]
+        L.pt_position_moments.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                          _VP, _VP]
         L.pt_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.pt_ensemble_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                        ctypes.POINTER(pt_laser), ctypes.POINTER(_D), _I64, _VP]
@@ -283,6 +288,10 @@ class Plan:
     def sync(self, stream=None):
         _check(load(False).pt_sync(self._h, _stream(stream)), "pt_sync")
 
+    def set_damping(self, gamma: float):
+        """Artificial damping rate (1/s) of the rotating-frame velocity; 0 = off."""
+        _check(load(False).pt_set_damping(self._h, float(gamma)), "pt_set_damping")
+
     def profile(self, enable: bool = True):
         _check(load(False).fmm_plan_profile(self._h, 1 if enable else 0), "fmm_plan_profile")
 
@@ -342,6 +351,41 @@ def energy(state: State, trap, plan: Plan | None = None, stream=None):
     _check(load().pt_energy(plan._h if plan is not None else None, ctypes.byref(st),
                             ctypes.byref(tr), out, _stream(stream)), "pt_energy")
     return list(out)
+
+
+def temperatures(state: State, trap, stream=None):
+    """(T_par, T_perp) in K of the motion relative to the rigid rotation."""
+    st = state._c()
+    tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+    out = (ctypes.c_double * 2)()
+    _check(load().pt_temperatures(ctypes.byref(st), ctypes.byref(tr), out, _stream(stream)),
+           "pt_temperatures")
+    return out[0], out[1]
+
+
+def position_moments(state: State, trap, acc, stream=None):
+    """acc (4, n) float64 CUDA += rotating-frame (x_r, y_r, z, |x_r|^2) at state.t."""
+    st = state._c()
+    tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+    _dev_f64(acc, (4, state.n))
+    _check(load().pt_position_moments(ctypes.byref(st), ctypes.byref(tr), _ptr(acc),
+                                      _stream(stream)), "pt_position_moments")
+    return acc
+
+
+def rms_displacement(acc, samples: int):
+    """Delta r_rms of every ion (Eq. rms_disp) from K = samples accumulations."""
+    mean = acc[:3] / samples
+    return torch.sqrt(torch.clamp(acc[3] / samples - (mean * mean).sum(0), min=0.0))
+
+
+def potential_temperature(state: State, trap, reference: State, plan: Plan | None = None):
+    """T_PE = (2/3) (PE - PE_0) / (N k_B) (Eq. temp_pe): rotating-frame potential
+    energy (external + Coulomb) of state minus that of the reference
+    configuration (each at its own time)."""
+    e = energy(state, trap, plan)
+    e0 = energy(reference, trap, plan)
+    return (2.0 / 3.0) * ((e[1] + e[2]) - (e0[1] + e0[2])) / (state.n * 1.380649e-23)
 
 
 def plan_footprint(n_max: int, p: int, leaf_max: int = 32, depth: int = -1,

@@ -42,6 +42,11 @@ struct fmm_plan_s {
     int64_t n_max = 0;
     int p = 0, P = 0, leaf_max = 32, depth = -1, precision = PT_FP64;
     int phases = PT_PHASE_ALL;
+    double damping = 0.0;      // artificial damping rate (1/s) of the push; 0 = off
+    // time anchor of the trajectory being stepped: step k's time is
+    // anc_t + (k - anc_step) dt, whatever calls the steps are split into
+    double anc_t = 0.0, anc_dt = 0.0, end_t = 0.0;
+    int64_t anc_step = 0, end_step = -1;
     int last_depth = -1;
     int64_t last_n = 0;
     Workspace ws;
@@ -309,7 +314,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
     return e;
 }
 
-PushParams make_push(const pt_trap* trap, double dt) {
+PushParams make_push(const pt_trap* trap, double dt, double damping) {
     PushParams pp;
     memset(&pp, 0, sizeof pp);
     pp.h = 0.5 * dt;
@@ -321,6 +326,8 @@ PushParams make_push(const pt_trap* trap, double dt) {
     pp.delta = trap->delta;
     pp.mass = trap->mass;
     pp.rk = 1.054571817e-34 / trap->mass;
+    pp.damp = damping > 0.0 ? exp(-damping * dt) : 1.0;
+    pp.wr = trap->omega_r;
     return pp;
 }
 
@@ -368,6 +375,26 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     return key;
 }
 
+// A call that continues exactly where the plan's last call left the state
+// (same step, same t, same dt) keeps the plan's time anchor; any other call
+// starts a new one at (state->t, state->step).  Step times then come from the
+// global step index alone, so a trajectory is bit for bit the same however
+// its steps are split into calls (the serving loop splits them at arbitrary
+// points).
+void anchor_time(fmm_plan_s* pl, double t0, int64_t step0, double dt) {
+    if (!(pl->end_step == step0 && pl->end_t == t0 && pl->anc_dt == dt)) {
+        pl->anc_t = t0;
+        pl->anc_step = step0;
+        pl->anc_dt = dt;
+    }
+}
+
+double anchored_end(fmm_plan_s* pl, int64_t step_end) {
+    pl->end_step = step_end;
+    pl->end_t = pl->anc_t + (double)(step_end - pl->anc_step) * pl->anc_dt;
+    return pl->end_t;
+}
+
 // The step loop shared by pt_step (synchronous) and pt_step_async.
 int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_laser* laser,
               double dt, int64_t n_steps, cudaStream_t s, bool sync) {
@@ -375,13 +402,15 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
     pt_laser lz;
     memset(&lz, 0, sizeof lz);
     if (laser) lz = *laser;
-    const PushParams pp = make_push(trap, dt);
-    const double t0 = st->t;
+    const PushParams pp = make_push(trap, dt, plan->damping);
     const int64_t step0 = st->step;
+    anchor_time(plan, st->t, step0, dt);
+    const int64_t off = step0 - plan->anc_step;
     for (int64_t s0 = 0; s0 < n_steps; s0 += ws.wall_cap) {
         const int64_t k = (n_steps - s0) < ws.wall_cap ? (n_steps - s0) : ws.wall_cap;
         int D;
-        int r = prepare_chunk(plan, st, trap, dt, t0, step0, s0, k, sync, s, &D);
+        int r = prepare_chunk(plan, st, trap, dt, plan->anc_t, plan->anc_step, off + s0, k, sync, s,
+                              &D);
         if (r != PT_OK) return r;
         cudaError_t e;
         const GraphKey key = make_key(plan, st, pp, lz, D);
@@ -418,7 +447,7 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
             if (r != PT_OK) return r;
         }
     }
-    st->t = t0 + (double)n_steps * dt;
+    st->t = anchored_end(plan, step0 + n_steps);
     st->step = step0 + n_steps;
     return PT_OK;
 }
@@ -841,14 +870,13 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<PushParams> pp(nm);
     std::vector<pt_laser> lz(nm);
-    std::vector<double> t0(nm);
     std::vector<int64_t> step0(nm);
     for (int b = 0; b < nm; ++b) {
-        pp[b] = make_push(&traps[b], dt[b]);
+        pp[b] = make_push(&traps[b], dt[b], ens->plans[b]->damping);
         memset(&lz[b], 0, sizeof(pt_laser));
         if (lasers) lz[b] = lasers[b];
-        t0[b] = states[b].t;
         step0[b] = states[b].step;
+        anchor_time(ens->plans[b], states[b].t, step0[b], dt[b]);
     }
     std::vector<int> D(nm);
     std::vector<GraphKey> keys(nm);
@@ -857,7 +885,8 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
         for (int b = 0; b < nm; ++b) {
             fmm_plan_s* pl = ens->plans[b];
             // an automatic-depth plan that never chose a depth chooses it now
-            int r = prepare_chunk(pl, &states[b], &traps[b], dt[b], t0[b], step0[b], s0, k,
+            int r = prepare_chunk(pl, &states[b], &traps[b], dt[b], pl->anc_t, pl->anc_step,
+                                  (step0[b] - pl->anc_step) + s0, k,
                                   pl->depth < 0 && pl->last_depth < 0, s, &D[b]);
             if (r != PT_OK) return r;
             keys[b] = make_key(pl, &states[b], pp[b], lz[b], D[b]);
@@ -904,7 +933,7 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
         }
     }
     for (int b = 0; b < nm; ++b) {
-        states[b].t = t0[b] + (double)n_steps * dt[b];
+        states[b].t = anchored_end(ens->plans[b], step0[b] + n_steps);
         states[b].step = step0[b] + n_steps;
     }
     return PT_OK;
@@ -921,6 +950,41 @@ int pt_ensemble_sync(pt_ensemble ens, void* stream) {
         if (r != PT_OK && first == PT_OK) first = r;
     }
     return first;
+}
+
+int pt_set_damping(fmm_plan plan, double gamma) {
+    if (!plan || !(gamma >= 0.0)) return PT_ERR_ARG;
+    plan->damping = gamma;
+    return PT_OK;
+}
+
+namespace {
+// scratch of the temperature reduction: {T_par, T_perp} and per-block partials
+static __device__ __align__(256) double g_diag_scratch[2 + 2 * 256];
+std::mutex g_diag_mu;
+}  // namespace
+
+int pt_temperatures(const pt_state* st, const pt_trap* trap, double* out, void* stream) {
+    if (!st || !trap || !out || st->n < 1 || !st->x || !st->y || !st->vx || !st->vy || !st->vz ||
+        !(trap->mass > 0))
+        return PT_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_diag_mu);
+    double* d = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&d, g_diag_scratch);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess) e = launch_temperatures(st->n, *st, *trap, d, s);
+    double h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from(e);
+    out[0] = h[0];
+    out[1] = h[1];
+    return PT_OK;
+}
+
+int pt_position_moments(const pt_state* st, const pt_trap* trap, double* acc, void* stream) {
+    if (!st || !trap || !acc || st->n < 1 || !st->x || !st->y || !st->z) return PT_ERR_ARG;
+    return status_from(launch_position_moments(st->n, *st, *trap, acc, (cudaStream_t)stream));
 }
 
 }  // extern "C"

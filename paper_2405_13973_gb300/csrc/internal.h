@@ -152,6 +152,8 @@ struct PushParams {
     double t0;         // time of the chunk's first step
     int64_t step0;     // its global index
     double rk;         // hbar / m
+    double damp;       // exp(-gamma dt) of the rotating-frame velocity; 1 = no damping
+    double wr;         // rotation frequency of the damping's rigid rotor
 };
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s);
@@ -164,5 +166,11 @@ cudaError_t launch_laser_kicks(const pt_laser& laser, double rk, int64_t n, cons
                                int32_t* counts, double* dv, cudaStream_t s);
 cudaError_t launch_energy_parts(int64_t n, const pt_state& st, const pt_trap& trap, double kz,
                                 const double* phi, double* d_out, cudaStream_t s);
+// {T_par, T_perp} into d_out[0..1]; d_out holds 2 + 2 * 256 doubles
+cudaError_t launch_temperatures(int64_t n, const pt_state& st, const pt_trap& trap, double* d_out,
+                                cudaStream_t s);
+// acc[0..n) += x_r, [n, 2n) += y_r, [2n, 3n) += z, [3n, 4n) += |x_r|^2 at time st.t
+cudaError_t launch_position_moments(int64_t n, const pt_state& st, const pt_trap& trap,
+                                    double* acc, cudaStream_t s);
 
 }  // namespace pt

@@ -220,6 +220,14 @@ __global__ void __launch_bounds__(128) k_kick_drift(int64_t n, double* x, double
         ux = ux + qm * (E[i] + Fx) * pp.dt + dx;
         uy = uy + qm * (E[n + i] + Fy) * pp.dt + dy;
         uz = uz + qm * (E[2 * n + i] + Fz) * pp.dt + dz;
+        if (pp.damp != 1.0) {
+            // artificial damping: the velocity relative to the rigid rotation
+            // at this (mid-step) position shrinks by exp(-gamma dt)
+            const double rx = pp.wr * py, ry = -pp.wr * px;
+            ux = rx + pp.damp * (ux - rx);
+            uy = ry + pp.damp * (uy - ry);
+            uz = pp.damp * uz;
+        }
         gyrate(pp, px, py, pz, ux, uy, uz);
         x[i] = px;
         y[i] = py;
@@ -335,6 +343,67 @@ cudaError_t launch_energy_parts(int64_t n, const pt_state& st, const pt_trap& tr
     double* partial = d_out + 4;  // caller provides 4 + 3 * kEnergyBlocks doubles
     k_energy_partial<<<kEnergyBlocks, 256, 0, s>>>(n, st, trap, kz, c, sn, phi, partial);
     k_energy_final<<<1, 32, 0, s>>>(partial, kEnergyBlocks, d_out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Temperatures of the rotating-frame motion (Eqs. temp_ax, temp_pl), the same
+// deterministic two-stage compensated reduction as the energy.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_temps_partial(int64_t n, pt_state st, double wr,
+                                                       double* partial) {
+    __shared__ double sh[2][256];
+    Neu2 a[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double wx = st.vx[i] - wr * st.y[i], wy = st.vy[i] + wr * st.x[i], vz = st.vz[i];
+        a[0].add(vz * vz);
+        a[1].add(wx * wx + wy * wy);
+    }
+    for (int k = 0; k < 2; ++k) sh[k][threadIdx.x] = a[k].s + a[k].c;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        Neu2 t;
+        for (int j = 0; j < (int)blockDim.x; ++j) t.add(sh[threadIdx.x][j]);
+        partial[blockIdx.x * 2 + threadIdx.x] = t.s + t.c;
+    }
+}
+
+__global__ void k_temps_final(const double* partial, int nb, double m, double nkb, double* out) {
+    if (threadIdx.x < 2) {
+        Neu2 t;
+        for (int b = 0; b < nb; ++b) t.add(partial[b * 2 + threadIdx.x]);
+        const double sum = t.s + t.c;
+        out[threadIdx.x] = threadIdx.x == 0 ? m * sum / nkb : m * sum / (2.0 * nkb);
+    }
+}
+
+cudaError_t launch_temperatures(int64_t n, const pt_state& st, const pt_trap& trap, double* d_out,
+                                cudaStream_t s) {
+    double* partial = d_out + 2;
+    k_temps_partial<<<kEnergyBlocks, 256, 0, s>>>(n, st, trap.omega_r, partial);
+    k_temps_final<<<1, 32, 0, s>>>(partial, kEnergyBlocks, trap.mass, (double)n * 1.380649e-23,
+                                   d_out);
+    return cudaGetLastError();
+}
+
+// Rotating-frame position moments (Eq. rms_disp accumulates these over time).
+__global__ void k_position_moments(int64_t n, pt_state st, double c, double s, double* acc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = st.x[i], y = st.y[i], z = st.z[i];
+        const double xr = c * x - s * y, yr = s * x + c * y;
+        acc[i] += xr;
+        acc[n + i] += yr;
+        acc[2 * n + i] += z;
+        acc[3 * n + i] += xr * xr + yr * yr + z * z;
+    }
+}
+
+cudaError_t launch_position_moments(int64_t n, const pt_state& st, const pt_trap& trap,
+                                    double* acc, cudaStream_t s) {
+    const double c = cos(trap.omega_r * st.t), sn = sin(trap.omega_r * st.t);
+    k_position_moments<<<grid_for(n, 256), 256, 0, s>>>(n, st, c, sn, acc);
     return cudaGetLastError();
 }
 

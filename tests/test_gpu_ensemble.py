@@ -65,3 +65,23 @@ def test_autotuned_depth_is_a_neighbour_of_the_automatic_one():
     assert abs(d - plan.last_depth) <= 1
     assert autotune.tune_depth(2500, 8, "bf16x3", crystal) == d   # same band: cached
     plan.close()
+
+
+@pytest.mark.parametrize("precision,p", [("fp64", 6), ("bf16x3", 8)])
+def test_a_trajectory_does_not_depend_on_how_its_steps_are_split(precision, p):
+    # step times come from the global step index and the trajectory's start,
+    # so 7 + 11 + 12 steps end exactly where 30 steps in one call end
+    c = W.ensemble_member(1200, 0.4, seed=21)
+    tr = pt.make_trap(c["trap"])
+    lz = pt.make_laser(c["beams"], seed=4, gamma0=W.GAMMA0)
+    out = []
+    for parts in ((30,), (7, 11, 12)):
+        plan = pt.Plan(1200, p=p, precision=precision)
+        st = pt.State.from_numpy(c["pos"], c["vel"], c["q"], t=2.5e-6, step=100)
+        for k in parts:
+            plan.step(st, tr, lz, c["dt"], k)
+        out.append((st.pos().cpu().numpy(), st.vel().cpu().numpy(), st.t, st.step))
+        plan.close()
+    (x1, v1, t1, s1), (x2, v2, t2, s2) = out
+    assert s1 == s2 == 130 and t1 == t2 == 2.5e-6 + 30 * c["dt"]
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
