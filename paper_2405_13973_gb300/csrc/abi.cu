@@ -617,6 +617,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
         ok = ok && dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
+        if (ws.tc_bf16) ok = ok && dalloc(pl, ws.M_pieces, sizeof(uint16_t) * 3 * ws.ld * cells);
     }
     if (dry) {
         *dry_bytes = (int64_t)pl->dry_bytes;

@@ -80,6 +80,7 @@ struct Workspace {
     void* T_l2l = nullptr;   // [8][P][P]
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
     void* T_m2l_tc = nullptr;   // tensor-core operand tiles (mixed modes)
+    uint16_t* M_pieces = nullptr;  // BF16x3: M split into bf16 hi/mid/lo, [cell][3][ld]
     int tc_bf16 = 0;            // tensor-core operand format: 0 TF32 hi/lo, 1 BF16 hi/mid/lo
     float* tc_part = nullptr;   // M2M split partials, then M2L item slabs (tc_part_floats)
     size_t tc_part_floats = 0;

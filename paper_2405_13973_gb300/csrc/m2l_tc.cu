@@ -195,6 +195,17 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t 
                  "r"(src_bytes)
                  : "memory");
 }
+// arrive on an mbarrier once all of this thread's earlier cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+// 8-byte global -> shared copy (cached path); src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -308,6 +319,7 @@ struct TcArgs {
     float* L;
     float* Mout;           // M2M output (= M, other level)
     float* part;           // M2M: [splits-1][cells][ld]; M2L: [item][128][ld] slabs
+    const uint16_t* Mp;    // BF16x3 M2L: M already split, [cell][3 pieces][ld] bf16
     int64_t part_stride;   // cells_max * ld
     const unsigned char* ops;  // [359][kchunks][pieces][Npad rows] swizzled
     int* err;
@@ -582,6 +594,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                         *abort_v = 1;
                         break;
                     }
+                    // pre-split A rows arrive by cp.async (generic proxy): order
+                    // them before the tensor core's reads
+                    if (MODE == MODE_M2L && BF16) fence_proxy_async();
                     tc_fence_after();
                     const uint32_t ah = smem_addr(base + st * stage_bytes);
                     if (BF16) {
@@ -618,6 +633,72 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             }
         }
     } else if (warp < kWarpEpi0) {
+        if (MODE == MODE_M2L && BF16) {
+            // ---- A producers, BF16x3 M2L: the sources' M rows are already
+            // split into bf16 pieces (k_split_m), so each thread copies its
+            // 4 values of each piece and row (8 bytes) by cp.async straight
+            // into the stage's swizzled layout, and the stage barrier counts
+            // its arrival once those copies land; no conversion here.
+            const int ta = tid - kWarpA0 * 32;
+            const int r0 = ta >> 3, c = ta & 7;
+            int g = 0;
+            for (int idx = first; idx < count && !*abort_v; idx += stride) {
+                TcWork w;
+                if (!tc_work<MODE>(a, li, idx, w)) continue;
+                const int n_it = (w.end - w.begin) * a.kchunks;
+                const int l = w.level, lim = 1 << l;
+                int tix[4], tiy[4], tiz[4], pg[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    tix[j] = tiy[j] = tiz[j] = 0;
+                    pg[j] = -1;
+                    if (r0 + 32 * j < w.rows) demorton3(a.code[w.base + r0 + 32 * j], tix[j], tiy[j], tiz[j]);
+                }
+                for (int it = 0; it < n_it; ++it) {
+                    const int gg = g + it;
+                    const int st = gg % NS, use = gg / NS;
+                    const int kc = it % a.kchunks;
+                    if (kc == 0) {
+                        const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
+                        const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            int gs = -1;
+                            const int sx = tix[j] - ox, sy = tiy[j] - oy, sz = tiz[j] - oz;
+                            if (r0 + 32 * j < w.rows &&
+                                tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
+                                sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
+                                gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
+                            pg[j] = gs;
+                        }
+                    }
+                    int okw = 1;
+                    if (lane == 0) okw = mbar_wait_or_abort(&empty_bar[st], (use & 1) ^ 1, abort_v) ? 1 : 0;
+                    okw = __shfl_sync(0xffffffffu, okw, 0);
+                    if (!okw) {
+                        *abort_v = 1;
+                        break;
+                    }
+                    unsigned char* sA = base + st * stage_bytes;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = r0 + 32 * j;
+                        const int off = (r >> 3) * 512 + (r & 7) * 64 +
+                                        (((c >> 1) ^ ((r & 7) >> 1)) << 4) + (c & 1) * 8;
+                        const int gs = pg[j];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const uint16_t* src =
+                                gs >= 0 ? a.Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 4 : a.Mp;
+                            cp_async8(sA + q * a_bytes + off, src, gs >= 0 ? 8u : 0u);
+                        }
+                    }
+                    cp_async_arrive(&fullA_bar[st]);
+                }
+                g += n_it;
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
         // ---- A producers: each thread owns rows r0 + 32 j (j < 4) and 16-byte unit c.
         // Its raw FP32 values travel by cp.async into its own slots of a ring
         // of a.raw chunks, a.raw - 1 iterations ahead of their split.
@@ -745,6 +826,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             g += n_it;
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
+        }
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the tile
         const int quad = warp & 3;
@@ -1258,6 +1340,7 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.part = ws.tc_part;
     a.part_stride = ws.cells_max * ws.ld;
     a.ops = static_cast<const unsigned char*>(ws.T_m2l_tc);
+    a.Mp = ws.M_pieces;
     a.err = ws.err;
     return a;
 }
@@ -1284,6 +1367,24 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
     return cudaGetLastError();
 }
 
+// M of every cell of levels 2..D as bf16 hi/mid/lo pieces (split_bf16x3, the
+// split the M2L producers would otherwise repeat for every target that
+// gathers the cell): Mp[(cell * 3 + q) * ld + k].
+__global__ void k_split_m(int lfirst, int D, int ld, const LevelInfo* linfo, const float* M,
+                          uint16_t* Mp) {
+    const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[D + 1];
+    for (int64_t e = g0 * ld + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g1 * ld;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / ld, k = e - cell * ld;
+        uint32_t h, m, l;
+        split_bf16x3(M[e], h, m, l);
+        uint16_t* row = Mp + cell * 3 * ld + k;
+        row[0] = (uint16_t)h;
+        row[ld] = (uint16_t)m;
+        row[2 * ld] = (uint16_t)l;
+    }
+}
+
 cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
@@ -1301,6 +1402,10 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
     k_tc_plan<<<(unsigned)tiles, kPlanThreads, tc_plan_smem_bytes(D), s>>>(a, tl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ws.tc_bf16) {
+        k_split_m<<<152 * 8, 256, 0, s>>>(2, D, ws.ld, ws.linfo, (const float*)ws.M, ws.M_pieces);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, (int)ws.tc_slab_cap, hdr, tl,
                                           items);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
