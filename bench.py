@@ -136,14 +136,15 @@ class ClockSampler:
 
 
 def launches_per_step(depth: int, precision: str) -> int:
-    # drift+cube, keys, 3 scan, scatter, 3 scan, leaf gather, near_far, kick
-    k = 12
+    # drift+cube, keys, leaf scan, scatter, cell scan, leaf gather, near_far,
+    # kick; each scan is one launch up to 65536 cells (depth <= 5), else three
+    k = 8 if depth <= 5 else 12
     if depth >= 2:
         k += 1 + (depth - 2)                 # P2M, M2M per level
         if precision in ("tf32x3", "bf16x3"):
             # M2M splits reduce per level, plan + items + M2L + tile reduce,
-            # L2L per level >= 3
-            k += (depth - 2) + 4 + (depth - 2)
+            # L2L per level >= 3, and (BF16x3) the split of M into pieces
+            k += (depth - 2) + 4 + (depth - 2) + (1 if precision == "bf16x3" else 0)
         else:
             k += depth - 1                   # M2L (+ folded L2L) per level
     return k

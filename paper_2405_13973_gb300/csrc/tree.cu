@@ -165,8 +165,62 @@ __global__ void k_scan_apply(Src src, int64_t total, const int32_t* block_sums) 
     if (blockIdx.x == 0 && threadIdx.x == 0) src.finish(block_sums[gridDim.x]);
 }
 
+// Small scans in one block of 1024 threads, tile by tile with a carry: one
+// launch instead of three (the three-phase scan of a few thousand cells is
+// all launch latency).
+constexpr int kScan1Threads = 1024;
+constexpr int kScan1Items = 8;
+constexpr int64_t kScan1Max = 65536;
+
+template <class Src>
+__global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t total) {
+    __shared__ int warp_tot[kScan1Threads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int carry = 0;
+    for (int64_t t0 = 0; t0 < total; t0 += (int64_t)kScan1Threads * kScan1Items) {
+        const int64_t base = t0 + (int64_t)threadIdx.x * kScan1Items;
+        int vals[kScan1Items];
+        int acc = 0;
+        for (int k = 0; k < kScan1Items; ++k) {
+            const int64_t i = base + k;
+            vals[k] = i < total ? src.load(i) : 0;
+            acc += vals[k];
+        }
+        int x = acc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        int ex = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - acc;
+        const int tot = warp_tot[kScan1Threads / 32 - 1];
+        for (int k = 0; k < kScan1Items; ++k) {
+            const int64_t i = base + k;
+            if (i < total) src.store(i, ex, vals[k]);
+            ex += vals[k];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) src.finish(carry);
+}
+
 template <class Src>
 static cudaError_t run_scan(Src src, int64_t total, Workspace& ws, cudaStream_t s) {
+    if (total <= kScan1Max) {
+        k_scan_single<<<1, kScan1Threads, 0, s>>>(src, total);
+        return cudaGetLastError();
+    }
     int nb = (int)((total + kScanTile - 1) / kScanTile);
     if (nb < 1) nb = 1;
     if (nb + 1 > ws.block_sums_cap) return cudaErrorInvalidValue;
