@@ -419,6 +419,17 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
             const bool active = ch < nch;
             const R me = sorted[ts + t0 + ti];
             T ex = 0, ey = 0, ez = 0, ph = 0, cex = 0, cey = 0, cez = 0, cph = 0;
+            if (far && active) {
+                // this chunk's share of the target's L2P: every nch-th column m
+                T fphi, gx, gy, gz, ux, uy, uz, uq;
+                Ion<T>::get(me, ux, uy, uz, uq);
+                l2p_eval_cols<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), ch, nch, fphi, gx,
+                                 gy, gz);
+                ex = -gx;
+                ey = -gy;
+                ez = -gz;
+                ph = fphi;
+            }
             for (int s0 = 0; s0 < ns; s0 += kNfSrc) {    // sources in passes of kNfSrc
                 const int nsb = min(kNfSrc, ns - s0);
                 __syncthreads();
@@ -475,16 +486,7 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
                     kb_add(sz, cz, part[th][2]);
                     kb_add(sp, cp, part[th][3]);
                 }
-                T fx = sx + cx, fy = sy + cy, fz = sz + cz, fp = sp + cp;
-                if (far) {
-                    T fphi, gx, gy, gz, ux, uy, uz, uq;
-                    Ion<T>::get(me, ux, uy, uz, uq);
-                    l2p_eval<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), fphi, gx, gy, gz);
-                    fx -= gx;
-                    fy -= gy;
-                    fz -= gz;
-                    fp += fphi;
-                }
+                const T fx = sx + cx, fy = sy + cy, fz = sz + cz, fp = sp + cp;
                 const int i = perm[ts + t0 + tid];
                 E[i] = fE * (double)fx;
                 E[n + i] = fE * (double)fy;
