@@ -200,9 +200,9 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
                  : "memory");
 }
-// 8-byte global -> shared copy (cached path); src_bytes = 0 fills zeros
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+// 16-byte global -> shared copy through L1; src_bytes = 0 fills zeros
+__device__ __forceinline__ void cp_async16ca(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
                  "r"(src_bytes)
                  : "memory");
 }
@@ -636,23 +636,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         if (MODE == MODE_M2L && BF16) {
             // ---- A producers, BF16x3 M2L: the sources' M rows are already
             // split into bf16 pieces (k_split_m), so each thread copies its
-            // 4 values of each piece and row (8 bytes) by cp.async straight
-            // into the stage's swizzled layout, and the stage barrier counts
-            // its arrival once those copies land; no conversion here.
+            // 16-byte unit (8 values) of each piece for two rows by cp.async
+            // straight into the stage's swizzled layout, and the stage barrier
+            // counts its arrival once those copies land; no conversion here.
             const int ta = tid - kWarpA0 * 32;
-            const int r0 = ta >> 3, c = ta & 7;
+            const int r0 = ta >> 2, c = ta & 3;
             int g = 0;
             for (int idx = first; idx < count && !*abort_v; idx += stride) {
                 TcWork w;
                 if (!tc_work<MODE>(a, li, idx, w)) continue;
                 const int n_it = (w.end - w.begin) * a.kchunks;
                 const int l = w.level, lim = 1 << l;
-                int tix[4], tiy[4], tiz[4], pg[4];
+                int tix[2], tiy[2], tiz[2], pg[2];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 2; ++j) {
                     tix[j] = tiy[j] = tiz[j] = 0;
                     pg[j] = -1;
-                    if (r0 + 32 * j < w.rows) demorton3(a.code[w.base + r0 + 32 * j], tix[j], tiy[j], tiz[j]);
+                    if (r0 + 64 * j < w.rows) demorton3(a.code[w.base + r0 + 64 * j], tix[j], tiy[j], tiz[j]);
                 }
                 for (int it = 0; it < n_it; ++it) {
                     const int gg = g + it;
@@ -662,10 +662,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                         const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
                         const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
+                        for (int j = 0; j < 2; ++j) {
                             int gs = -1;
                             const int sx = tix[j] - ox, sy = tiy[j] - oy, sz = tiz[j] - oz;
-                            if (r0 + 32 * j < w.rows &&
+                            if (r0 + 64 * j < w.rows &&
                                 tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
                                 sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
                                 gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
@@ -681,16 +681,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                     }
                     unsigned char* sA = base + st * stage_bytes;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int r = r0 + 32 * j;
-                        const int off = (r >> 3) * 512 + (r & 7) * 64 +
-                                        (((c >> 1) ^ ((r & 7) >> 1)) << 4) + (c & 1) * 8;
+                    for (int j = 0; j < 2; ++j) {
+                        const int r = r0 + 64 * j;
+                        const int off = (r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r & 7) >> 1)) << 4);
                         const int gs = pg[j];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             const uint16_t* src =
-                                gs >= 0 ? a.Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 4 : a.Mp;
-                            cp_async8(sA + q * a_bytes + off, src, gs >= 0 ? 8u : 0u);
+                                gs >= 0 ? a.Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 8 : a.Mp;
+                            cp_async16ca(sA + q * a_bytes + off, src, gs >= 0 ? 16u : 0u);
                         }
                     }
                     cp_async_arrive(&fullA_bar[st]);
