@@ -217,6 +217,15 @@ int fmm_plan_profile(fmm_plan plan, int enable);
 int fmm_plan_phase_times(fmm_plan plan, double* ms);
 int fmm_plan_stats(fmm_plan plan, int64_t* out, void* stream);
 
+/* fmm_plan_tc_stats: the tensor-core M2L work list of the last evaluation
+ * (host, 4 int64): {tiles (up to 128 target cells of one level), tile-offset
+ * products (each a dense 128-row translation by one operator, Eq. M2L),
+ * work items (runs of products of one tile), target rows (cells at levels
+ * >= 2)}.  All zero for the CUDA-core precisions and trees of depth < 2.
+ * Synchronises the stream.  Errors: PT_ERR_ARG (no evaluation yet),
+ * PT_ERR_CUDA. */
+int fmm_plan_tc_stats(fmm_plan plan, int64_t* out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * pt_laser_kicks -- the photon counts and recoil velocity change of one step
  * for a given midpoint state, without applying them.  Paper: Eqs.

@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_profile.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_phase_times.argtypes = [_VP, ctypes.POINTER(_D)]
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
+        L.fmm_plan_tc_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -308,6 +309,13 @@ class Plan:
         keys = ("n", "depth", "leaves", "cells", "m2l_pairs", "p2p_pairs", "l2l_shifts",
                 "m2m_shifts")
         return dict(zip(keys, [int(v) for v in out]))
+
+    def tc_stats(self, stream=None) -> dict:
+        """Tensor-core M2L work list of the last evaluation (zeros off the
+        tensor-core path): tiles, tile-offset products, work items, rows."""
+        out = (ctypes.c_int64 * 4)()
+        _check(load(False).fmm_plan_tc_stats(self._h, out, _stream(stream)), "fmm_plan_tc_stats")
+        return dict(zip(("tiles", "products", "items", "rows"), [int(v) for v in out]))
 
     def tree_info(self, n: int, device="cuda", stream=None):
         root = (ctypes.c_double * 4)()

@@ -574,7 +574,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
     ws.cells_max = cells;
     ws.dense_max = dense;
     ws.block_sums_cap = (dense + kScanTile - 1) / kScanTile + 16;
-    ws.bbox_blocks = 152 * 2;
+    ws.bbox_blocks = 152 * 4;
     ws.wall_cap = kWallChunk;
     const size_t tsz = ws.fp64 ? sizeof(double) : sizeof(float);
     const size_t PP = (size_t)pl->P * pl->P;
@@ -603,7 +603,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
          dalloc(pl, ws.L, tsz * ws.ld * cells) && dalloc(pl, ws.E, sizeof(double) * 3 * n_max) &&
          dalloc(pl, ws.block_sums, sizeof(int32_t) * ws.block_sums_cap) &&
          dalloc(pl, ws.root, sizeof(RootCube)) &&
-         dalloc(pl, ws.bbox_partial, sizeof(double) * 8 * ws.bbox_blocks) &&
+         dalloc(pl, ws.bbox_acc, sizeof(unsigned long long) * 8) &&
          dalloc(pl, ws.ticket, sizeof(unsigned)) && dalloc(pl, ws.err, sizeof(int)) &&
          dalloc(pl, ws.steps, sizeof(StepCounter)) && dalloc(pl, ws.stats, sizeof(unsigned long long) * 8) &&
          dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap);
@@ -636,6 +636,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
         cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ws.bbox_acc, 0, sizeof(unsigned long long) * 8) != cudaSuccess ||
         cudaMemset(ws.err, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ws.steps, 0, sizeof(StepCounter)) != cudaSuccess ||
         cudaMallocHost(&pl->h_err, sizeof(int)) != cudaSuccess ||
@@ -764,6 +765,15 @@ int fmm_plan_stats(fmm_plan plan, int64_t* out, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_tree_stats(plan->last_n, plan->last_depth, plan->ws, out, s);
     return status_from(e);
+}
+
+int fmm_plan_tc_stats(fmm_plan plan, int64_t* out, void* stream) {
+    if (!plan || !out || plan->last_depth < 0) return PT_ERR_ARG;
+    if (!is_tc(plan->precision) || plan->last_depth < 2) {
+        for (int k = 0; k < 4; ++k) out[k] = 0;
+        return PT_OK;
+    }
+    return status_from(m2l_tc_work_stats(plan->ws, out, (cudaStream_t)stream));
 }
 
 int pt_energy(fmm_plan plan, const pt_state* st, const pt_trap* trap, double* out, void* stream) {

@@ -1,7 +1,14 @@
-// bbox.cuh -- block reduction of the ions' bounding box and last-block
+// bbox.cuh -- reduction of the ions' bounding box and last-block
 // finalisation of the octree root cube (Sec. 2.3.2: the smallest cube that
 // contains all ions).  Shared by the tree build and the fused drift kernel.
-// Returns true in the one thread that finalised the cube.
+//
+// The extremes are reduced as integers: a double maps to a 64-bit key whose
+// unsigned order is the numeric order (sign bit set for x >= 0, all bits
+// flipped for x < 0), so a warp reduces with shuffles and integer compares,
+// and each warp folds its result into an 8-word accumulator in global memory
+// by atomicMax (the minimum is kept as the maximum of the complemented key,
+// so the identity of every word is 0).  The last block to finish reads and
+// clears the accumulator in one atomicExch per word and writes the cube.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -9,88 +16,95 @@
 
 namespace pt {
 
-__device__ __forceinline__ double warp_min(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+constexpr int kBboxWords = 8;  // [0..2] ~key of the minimum, [3..5] key of the maximum, [6] bad
+constexpr int kBboxThreads = 64;  // small blocks: the FP64 work of a pass spreads over every SM
+
+// blocks of a bounding-box pass over n points
+inline int bbox_grid(int64_t n, const Workspace& ws) {
+    int64_t g = (n + kBboxThreads - 1) / kBboxThreads;
+    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
+    return g > 0 ? (int)g : 1;
 }
 
-// Reduces the block's min/max into partial[blockIdx.x]; the last block to
-// finish combines all partials and writes the root cube exactly as
-//   side = max_a (max_a - min_a) (1 if zero); lo_a = (min_a+max_a)/2 - side/2.
-__device__ __forceinline__ bool bbox_block_and_finalise(double mn[3], double mx[3], int bad, double* partial,
-                                        unsigned* ticket, RootCube* root, int* err) {
-    __shared__ double smn[3][32], smx[3][32];
-    __shared__ int sbad[32];
-    __shared__ bool last;
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int a = 0; a < 3; ++a) {
-        double a0 = warp_min(mn[a]), a1 = warp_max(mx[a]);
-        if (lane == 0) { smn[a][wid] = a0; smx[a][wid] = a1; }
+__device__ __forceinline__ unsigned long long ord_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// per-thread extremes of the points it saw
+struct BboxAcc {
+    unsigned long long k[6] = {0, 0, 0, 0, 0, 0};
+    int bad = 0;
+    __device__ __forceinline__ void add(double x, double y, double z) {
+        const double p[3] = {x, y, z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bad |= !isfinite(p[a]);
+            const unsigned long long key = ord_key(p[a]);
+            k[a] = umax64(k[a], ~key);
+            k[3 + a] = umax64(k[3 + a], key);
+        }
     }
-    int wb = __any_sync(0xffffffffu, bad);
-    if (lane == 0) sbad[wid] = wb;
+};
+
+// Folds every thread's extremes into acc[] (all threads of the block call
+// it); the last block writes the root cube exactly as
+//   side = max_a (max_a - min_a) (1 if zero); lo_a = (min_a+max_a)/2 - side/2
+// and clears acc[] and the ticket.  Returns true in the one thread that
+// finalised the cube.
+__device__ __forceinline__ bool bbox_commit(BboxAcc& t, unsigned long long* acc, unsigned* ticket,
+                                            RootCube* root, int* err) {
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 0; w < 6; ++w)
+        for (int o = 16; o > 0; o >>= 1) t.k[w] = umax64(t.k[w], __shfl_xor_sync(0xffffffffu, t.k[w], o));
+    const int wb = __any_sync(0xffffffffu, t.bad);
+    if (lane == 0) {
+#pragma unroll
+        for (int w = 0; w < 6; ++w)
+            if (t.k[w] != 0ull) atomicMax(&acc[w], t.k[w]);
+        if (wb) atomicOr(&acc[6], 1ull);
+        __threadfence();
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double r[7];
-        for (int a = 0; a < 3; ++a) {
-            double u = smn[a][0], v = smx[a][0];
-            for (int w = 1; w < nw; ++w) { u = fmin(u, smn[a][w]); v = fmax(v, smx[a][w]); }
-            r[a] = u;
-            r[3 + a] = v;
-        }
-        int b = 0;
-        for (int w = 0; w < nw; ++w) b |= sbad[w];
-        for (int k = 0; k < 6; ++k) partial[blockIdx.x * 8 + k] = r[k];
-        partial[blockIdx.x * 8 + 6] = (double)b;
-        __threadfence();
-        unsigned t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
+        const unsigned tk = atomicAdd(ticket, 1u);
+        last = (tk == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last) return false;
+    if (!last || threadIdx.x != 0) return false;
     __threadfence();
-    // the last block combines every block's partial, all threads in parallel
-    double u[3], v[3];
-    int b = 0;
-    for (int a = 0; a < 3; ++a) { u[a] = INFINITY; v[a] = -INFINITY; }
-    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
-        const volatile double* pp = partial + k * 8;
-        for (int a = 0; a < 3; ++a) { u[a] = fmin(u[a], pp[a]); v[a] = fmax(v[a], pp[3 + a]); }
-        b |= (pp[6] != 0.0);
-    }
+    unsigned long long v[7];
+#pragma unroll
+    for (int w = 0; w < 7; ++w) v[w] = atomicExch(&acc[w], 0ull);
+    double u[3], hi[3];
     for (int a = 0; a < 3; ++a) {
-        double a0 = warp_min(u[a]), a1 = warp_max(v[a]);
-        if (lane == 0) { smn[a][wid] = a0; smx[a][wid] = a1; }
+        u[a] = ord_val(~v[a]);
+        hi[a] = ord_val(v[3 + a]);
     }
-    int wb2 = __any_sync(0xffffffffu, b);
-    __syncthreads();
-    if (lane == 0) sbad[wid] = wb2;
-    __syncthreads();
-    if (threadIdx.x != 0) return false;
-    for (int a = 0; a < 3; ++a) {
-        u[a] = smn[a][0];
-        v[a] = smx[a][0];
-        for (int w = 1; w < nw; ++w) { u[a] = fmin(u[a], smn[a][w]); v[a] = fmax(v[a], smx[a][w]); }
-    }
-    b = 0;
-    for (int w = 0; w < nw; ++w) b |= sbad[w];
+    const bool b = v[6] != 0ull;
+    if (v[0] == 0ull)  // no point at all: the unit cube at the origin
+        for (int a = 0; a < 3; ++a) u[a] = hi[a] = 0.0;
     double side = 0.0;
     for (int a = 0; a < 3; ++a) {
-        double e = __dsub_rn(v[a], u[a]);
+        double e = __dsub_rn(hi[a], u[a]);
         if (e > side) side = e;
     }
     if (!(side > 0.0)) side = 1.0;
     if (b || !isfinite(side)) {
         atomicOr(err, ERR_NONFINITE);
         side = 1.0;
-        for (int a = 0; a < 3; ++a) { u[a] = 0.0; v[a] = 0.0; }
+        for (int a = 0; a < 3; ++a) u[a] = hi[a] = 0.0;
     }
     for (int a = 0; a < 3; ++a)
-        root->lo[a] = __dsub_rn(__dmul_rn(0.5, __dadd_rn(u[a], v[a])), __dmul_rn(0.5, side));
+        root->lo[a] = __dsub_rn(__dmul_rn(0.5, __dadd_rn(u[a], hi[a])), __dmul_rn(0.5, side));
     root->side = side;
     *ticket = 0u;
     return true;

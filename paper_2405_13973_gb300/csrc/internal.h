@@ -67,7 +67,7 @@ struct Workspace {
     int32_t* block_sums = nullptr; // scan scratch
     int64_t block_sums_cap = 0;
     RootCube* root = nullptr;
-    double* bbox_partial = nullptr;  // [bbox blocks][6]
+    unsigned long long* bbox_acc = nullptr;  // bounding-box accumulator, 8 words, kept zero between passes
     int bbox_blocks = 0;
     unsigned* ticket = nullptr;      // last-block-done counter
     int* err = nullptr;              // device error flags (bit mask)
@@ -132,6 +132,7 @@ cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
 size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap);
+cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
 // partial slabs of the M2L work items (a pool of 16 KB per ion, 16 MB to 8 GB)
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max);
 size_t m2l_tc_part_floats(int64_t cells_max, int ld, int m2m_splits, int64_t tiles_cap,

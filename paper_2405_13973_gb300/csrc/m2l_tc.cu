@@ -49,6 +49,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <vector>
 
 #include "harmonics.cuh"
 #include "internal.h"
@@ -1424,6 +1425,30 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
         b.level = l;
         const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
         if ((e = tc_launch(b, (unsigned)t2, smem, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Work-list counts of the last M2L launch: {tiles, tile-offset products
+// (sum of the tiles' non-empty offsets), work items, target rows}.
+cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s) {
+    for (int k = 0; k < 4; ++k) out[k] = 0;
+    if (!ws.tc_work) return cudaSuccess;
+    TcPlanHdr h;
+    cudaError_t e = cudaMemcpyAsync(&h, ws.tc_work, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    if (h.n_tiles <= 0 || h.n_tiles > ws.tc_tiles_cap) return cudaSuccess;
+    std::vector<TcTile> t((size_t)h.n_tiles);
+    e = cudaMemcpyAsync(t.data(), (const TcPlanHdr*)ws.tc_work + 1, sizeof(TcTile) * t.size(),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    out[0] = h.n_tiles;
+    out[2] = h.n_items;
+    for (const TcTile& x : t) {
+        out[1] += x.cnt;
+        out[3] += x.rows;
     }
     return cudaSuccess;
 }

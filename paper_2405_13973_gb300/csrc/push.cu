@@ -65,13 +65,11 @@ __device__ double pt_exp(double x) {
     if (x < -745.2) return 0.0;
     double kf = floor(x * INV_LN2 + 0.5);
     double r = (x - kf * LN2_HI) - kf * LN2_LO;
-    double c[14];
-    double fact = 1.0;
-#pragma unroll
-    for (int j = 0; j <= 13; ++j) {
-        if (j > 0) fact = fact * (double)j;
-        c[j] = 1.0 / fact;
-    }
+    // Taylor coefficients 1/j! (every j! <= 13! is exact in double, so each
+    // constant is the correctly rounded quotient)
+    const double c[14] = {1.0, 1.0, 1.0 / 2.0, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0,
+                          1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0, 1.0 / 3628800.0,
+                          1.0 / 39916800.0, 1.0 / 479001600.0, 1.0 / 6227020800.0};
     double p = c[13];
 #pragma unroll
     for (int j = 12; j >= 0; --j) p = p * r + c[j];
@@ -111,7 +109,52 @@ __device__ __forceinline__ int poisson(double lambda, double u) {
     return k;
 }
 
-// Photon counts and recoil of ion i at its midpoint state (Eq. laser_kick).
+// Photon count of beam l for ion i at its midpoint state: the scattering
+// rate of Eq. scattering_rate times dt is the Poisson mean (Eq. laser_kick).
+__device__ __forceinline__ int beam_count(const pt_laser& L, int64_t i, int64_t step, double dt,
+                                          int l, double y, double z, double vx, double vy,
+                                          double vz) {
+    const pt_beam& b = L.beam[l];
+    double rate = scatter_rate(b, L.gamma0, y, z, vx, vy, vz);
+    double lam = rate * dt;
+    uint32_t blk[4];
+    stream_block(L.seed, step, i, l, 0u, blk);
+    return poisson(lam, u01(blk[0], blk[1]));
+}
+
+// Recoil of cnt > 0 photons of beam l (Eq. laser_kick): cnt absorptions
+// along the beam and cnt isotropic emissions (Marsaglia's disc method),
+// added in this order to (ax, ay, az).
+__device__ void beam_recoil(const pt_laser& L, double rk, int64_t i, int64_t step, int l, int cnt,
+                            double& ax, double& ay, double& az) {
+    const pt_beam& b = L.beam[l];
+    double kmag = sqrt((b.kx * b.kx + b.ky * b.ky) + b.kz * b.kz);
+    double fc = (double)cnt * rk;
+    ax = ax + fc * b.kx;
+    ay = ay + fc * b.ky;
+    az = az + fc * b.kz;
+    double em = rk * kmag;
+    uint32_t slot = 1;
+    uint32_t blk[4];
+    for (int j = 0; j < cnt; ++j) {
+        double v1 = 0.0, v2 = 0.0, s = 0.0;
+        for (int tr = 0; tr < kMaxTries; ++tr) {
+            stream_block(L.seed, step, i, l, slot, blk);
+            slot = slot + 1;
+            v1 = 2.0 * u01(blk[0], blk[1]) - 1.0;
+            v2 = 2.0 * u01(blk[2], blk[3]) - 1.0;
+            s = v1 * v1 + v2 * v2;
+            if (s < 1.0) break;
+        }
+        double w = 2.0 * sqrt(1.0 - s);
+        ax = ax + em * (v1 * w);
+        ay = ay + em * (v2 * w);
+        az = az + em * (1.0 - 2.0 * s);
+    }
+}
+
+// Photon counts and recoil of ion i at its midpoint state (Eq. laser_kick),
+// the beams in order.
 __device__ void laser_ion(const pt_laser& L, double rk, int64_t i, int64_t step, double dt,
                           double y, double z, double vx, double vy, double vz, int32_t* counts_row,
                           double& ax, double& ay, double& az) {
@@ -119,36 +162,10 @@ __device__ void laser_ion(const pt_laser& L, double rk, int64_t i, int64_t step,
     ay = 0.0;
     az = 0.0;
     for (int l = 0; l < L.n_beams; ++l) {
-        const pt_beam& b = L.beam[l];
-        double rate = scatter_rate(b, L.gamma0, y, z, vx, vy, vz);
-        double lam = rate * dt;
-        uint32_t blk[4];
-        stream_block(L.seed, step, i, l, 0u, blk);
-        int cnt = poisson(lam, u01(blk[0], blk[1]));
+        int cnt = beam_count(L, i, step, dt, l, y, z, vx, vy, vz);
         if (counts_row) counts_row[l] = cnt;
         if (cnt == 0) continue;
-        double kmag = sqrt((b.kx * b.kx + b.ky * b.ky) + b.kz * b.kz);
-        double fc = (double)cnt * rk;
-        ax = ax + fc * b.kx;
-        ay = ay + fc * b.ky;
-        az = az + fc * b.kz;
-        double em = rk * kmag;
-        uint32_t slot = 1;
-        for (int j = 0; j < cnt; ++j) {
-            double v1 = 0.0, v2 = 0.0, s = 0.0;
-            for (int tr = 0; tr < kMaxTries; ++tr) {
-                stream_block(L.seed, step, i, l, slot, blk);
-                slot = slot + 1;
-                v1 = 2.0 * u01(blk[0], blk[1]) - 1.0;
-                v2 = 2.0 * u01(blk[2], blk[3]) - 1.0;
-                s = v1 * v1 + v2 * v2;
-                if (s < 1.0) break;
-            }
-            double w = 2.0 * sqrt(1.0 - s);
-            ax = ax + em * (v1 * w);
-            ay = ay + em * (v2 * w);
-            az = az + em * (1.0 - 2.0 * s);
-        }
+        beam_recoil(L, rk, i, step, l, cnt, ax, ay, az);
     }
 }
 
@@ -165,13 +182,13 @@ __device__ __forceinline__ void gyrate(const PushParams& pp, double& x, double& 
 
 // First half-drift of a step, fused with the bounding cube of the midpoint
 // positions; the finalising thread also advances the step counter.
-__global__ void __launch_bounds__(256) k_drift_bbox(int64_t n, double* x, double* y, double* z,
-                                                    double* vx, double* vy, const double* vz,
-                                                    PushParams pp, double* partial,
-                                                    unsigned* ticket, RootCube* root, int* err,
-                                                    StepCounter* steps) {
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int bad = 0;
+__global__ void __launch_bounds__(kBboxThreads) k_drift_bbox(int64_t n, double* x, double* y,
+                                                             double* z, double* vx, double* vy,
+                                                             const double* vz, PushParams pp,
+                                                             unsigned long long* acc,
+                                                             unsigned* ticket, RootCube* root,
+                                                             int* err, StepCounter* steps) {
+    BboxAcc t;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i];
@@ -181,60 +198,71 @@ __global__ void __launch_bounds__(256) k_drift_bbox(int64_t n, double* x, double
         z[i] = pz;
         vx[i] = ux;
         vy[i] = uy;
-        double p[3] = {px, py, pz};
-        for (int a = 0; a < 3; ++a) {
-            bad |= !isfinite(p[a]);
-            mn[a] = fmin(mn[a], p[a]);
-            mx[a] = fmax(mx[a], p[a]);
-        }
+        t.add(px, py, pz);
     }
-    if (bbox_block_and_finalise(mn, mx, bad, partial, ticket, root, err)) {
+    if (bbox_commit(t, acc, ticket, root, err)) {
         steps->cur = steps->next;
         steps->next = steps->next + 1;
     }
 }
 
 // Kick (Eq. velocity_kick with the laser kicks of Eq. laser_kick) and the
-// second half-drift.
-__global__ void __launch_bounds__(128) k_kick_drift(int64_t n, double* x, double* y, double* z,
-                                                    double* vx, double* vy, double* vz,
-                                                    const double* __restrict__ q,
-                                                    const double* __restrict__ E, PushParams pp,
-                                                    pt_laser laser, const StepCounter* steps,
-                                                    const double* __restrict__ wall_cs) {
+// second half-drift.  A block takes 32 ions at a time with one warp per beam:
+// warp l draws beam l's photon counts (the rate and Poisson draw, the bulk
+// of the FP64 work), then warp 0 adds the recoils of the beams in order,
+// kicks and drifts, exactly the sequence of laser_ion per ion.
+constexpr int kKickIons = 32;
+__global__ void __launch_bounds__(32 * PT_MAX_BEAMS) k_kick_drift(
+    int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+    const double* __restrict__ q, const double* __restrict__ E, PushParams pp, pt_laser laser,
+    const StepCounter* steps, const double* __restrict__ wall_cs) {
+    __shared__ int s_cnt[PT_MAX_BEAMS][kKickIons];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool lasers = laser.enabled && laser.n_beams > 0;
     const int64_t step = steps->cur;
     const int64_t widx = step - steps->base;
     const double c = wall_cs[2 * widx], s = wall_cs[2 * widx + 1];
     const double kw = 0.5 * pp.kz * pp.delta;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i], uz = vz[i];
-        double etx = 0.5 * pp.kz * px, ety = 0.5 * pp.kz * py, etz = -pp.kz * pz;
-        double ewx = -kw * (px * c - py * s);
-        double ewy = -kw * (-py * c - px * s);
-        double Fx = etx + ewx, Fy = ety + ewy, Fz = etz;
-        double dx = 0.0, dy = 0.0, dz = 0.0;
-        if (laser.enabled && laser.n_beams > 0)
-            laser_ion(laser, pp.rk, i, step, pp.dt, py, pz, ux, uy, uz, nullptr, dx, dy, dz);
-        double qm = q[i] / pp.mass;
-        ux = ux + qm * (E[i] + Fx) * pp.dt + dx;
-        uy = uy + qm * (E[n + i] + Fy) * pp.dt + dy;
-        uz = uz + qm * (E[2 * n + i] + Fz) * pp.dt + dz;
-        if (pp.damp != 1.0) {
-            // artificial damping: the velocity relative to the rigid rotation
-            // at this (mid-step) position shrinks by exp(-gamma dt)
-            const double rx = pp.wr * py, ry = -pp.wr * px;
-            ux = rx + pp.damp * (ux - rx);
-            uy = ry + pp.damp * (uy - ry);
-            uz = pp.damp * uz;
+    for (int64_t g0 = (int64_t)blockIdx.x * kKickIons; g0 < n; g0 += (int64_t)gridDim.x * kKickIons) {
+        const int64_t i = g0 + lane;
+        if (lasers) {
+            if (w < laser.n_beams && i < n)
+                s_cnt[w][lane] = beam_count(laser, i, step, pp.dt, w, y[i], z[i], vx[i], vy[i], vz[i]);
+            __syncthreads();
         }
-        gyrate(pp, px, py, pz, ux, uy, uz);
-        x[i] = px;
-        y[i] = py;
-        z[i] = pz;
-        vx[i] = ux;
-        vy[i] = uy;
-        vz[i] = uz;
+        if (w == 0 && i < n) {
+            double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i], uz = vz[i];
+            double etx = 0.5 * pp.kz * px, ety = 0.5 * pp.kz * py, etz = -pp.kz * pz;
+            double ewx = -kw * (px * c - py * s);
+            double ewy = -kw * (-py * c - px * s);
+            double Fx = etx + ewx, Fy = ety + ewy, Fz = etz;
+            double dx = 0.0, dy = 0.0, dz = 0.0;
+            if (lasers)
+                for (int l = 0; l < laser.n_beams; ++l) {
+                    const int cnt = s_cnt[l][lane];
+                    if (cnt != 0) beam_recoil(laser, pp.rk, i, step, l, cnt, dx, dy, dz);
+                }
+            double qm = q[i] / pp.mass;
+            ux = ux + qm * (E[i] + Fx) * pp.dt + dx;
+            uy = uy + qm * (E[n + i] + Fy) * pp.dt + dy;
+            uz = uz + qm * (E[2 * n + i] + Fz) * pp.dt + dz;
+            if (pp.damp != 1.0) {
+                // artificial damping: the velocity relative to the rigid rotation
+                // at this (mid-step) position shrinks by exp(-gamma dt)
+                const double rx = pp.wr * py, ry = -pp.wr * px;
+                ux = rx + pp.damp * (ux - rx);
+                uy = ry + pp.damp * (uy - ry);
+                uz = pp.damp * uz;
+            }
+            gyrate(pp, px, py, pz, ux, uy, uz);
+            x[i] = px;
+            y[i] = py;
+            z[i] = pz;
+            vx[i] = ux;
+            vy[i] = uy;
+            vz[i] = uz;
+        }
+        if (lasers) __syncthreads();  // s_cnt is rewritten for the next 32 ions
     }
 }
 
@@ -261,18 +289,19 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s) {
-    int64_t g = (n + 255) / 256;
-    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
-    k_drift_bbox<<<g > 0 ? (int)g : 1, 256, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_partial,
-                                                      ws.ticket, ws.root, ws.err, ws.steps);
+    k_drift_bbox<<<bbox_grid(n, ws), kBboxThreads, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_acc,
+                                                          ws.ticket, ws.root, ws.err, ws.steps);
     return cudaGetLastError();
 }
 
 cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const double* q, const double* E, const PushParams& pp,
                               const pt_laser& laser, Workspace& ws, cudaStream_t s) {
-    k_kick_drift<<<grid_for(n, 128), 128, 0, s>>>(n, x, y, z, vx, vy, vz, q, E, pp, laser,
-                                                   ws.steps, ws.wall_cs);
+    const int nb = laser.enabled && laser.n_beams > 0 ? laser.n_beams : 1;
+    int64_t g = (n + kKickIons - 1) / kKickIons;
+    if (g > 152 * 16) g = 152 * 16;
+    k_kick_drift<<<g > 0 ? (int)g : 1, 32 * nb, 0, s>>>(n, x, y, z, vx, vy, vz, q, E, pp, laser,
+                                                         ws.steps, ws.wall_cs);
     return cudaGetLastError();
 }
 

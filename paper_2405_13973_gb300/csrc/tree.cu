@@ -36,28 +36,22 @@ DenseLayout dense_layout(int D) {
 // ---------------------------------------------------------------------------
 // 1. bounding cube
 // ---------------------------------------------------------------------------
-__global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, int64_t n, double* partial, unsigned* ticket,
-                       RootCube* root, int* err) {
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int bad = 0;
+__global__ void __launch_bounds__(kBboxThreads) k_bbox(const double* __restrict__ x,
+                                                      const double* __restrict__ y,
+                                                      const double* __restrict__ z, int64_t n,
+                                                      unsigned long long* acc, unsigned* ticket,
+                                                      RootCube* root, int* err) {
+    BboxAcc t;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double p[3] = {x[i], y[i], z[i]};
-        for (int a = 0; a < 3; ++a) {
-            bad |= !isfinite(p[a]);
-            mn[a] = fmin(mn[a], p[a]);
-            mx[a] = fmax(mx[a], p[a]);
-        }
-    }
-    bbox_block_and_finalise(mn, mx, bad, partial, ticket, root, err);
+         i += (int64_t)gridDim.x * blockDim.x)
+        t.add(x[i], y[i], z[i]);
+    bbox_commit(t, acc, ticket, root, err);
 }
 
 cudaError_t launch_bbox(const double* x, const double* y, const double* z, int64_t n,
                         Workspace& ws, cudaStream_t s) {
-    int64_t g = (n + 255) / 256;
-    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
-    k_bbox<<<g > 0 ? (int)g : 1, 256, 0, s>>>(x, y, z, n, ws.bbox_partial, ws.ticket, ws.root, ws.err);
+    k_bbox<<<bbox_grid(n, ws), kBboxThreads, 0, s>>>(x, y, z, n, ws.bbox_acc, ws.ticket, ws.root,
+                                                     ws.err);
     return cudaGetLastError();
 }
 
