@@ -130,6 +130,21 @@ void release_ops(fmm_plan_s* pl) {
     pl->ops_held = false;
 }
 
+// Stream priorities for calls outside a graph: the main chain of a step
+// high, the side stream (near field, M2L work list) low, so that freed SMs go
+// to the main chain first.  (Step graphs run at the priority of the stream
+// they are launched into: measured, node priorities did not help there.)
+int prio_high() {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    return hi;
+}
+int prio_low() {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    return lo;
+}
+
 void free_plan(fmm_plan_s* pl) {
     if (!pl) return;
     cudaSetDevice(pl->device);
@@ -138,6 +153,10 @@ void free_plan(fmm_plan_s* pl) {
     for (void* v : pl->allocs) cudaFree(v);
     release_ops(pl);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    Workspace& ws = pl->ws;
+    if (ws.side) cudaStreamDestroy(ws.side);
+    for (cudaEvent_t ev : {ws.ev_fork, ws.ev_p2m, ws.ev_items, ws.ev_near})
+        if (ev) cudaEventDestroy(ev);
     for (int k = 0; k < fmm_plan_s::kSlots; ++k) {
         if (pl->h_wall[k]) cudaFreeHost(pl->h_wall[k]);
         if (pl->h_steps[k]) cudaFreeHost(pl->h_steps[k]);
@@ -601,6 +620,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
          dalloc(pl, ws.cstart, sizeof(int32_t) * cells) && dalloc(pl, ws.ccount, sizeof(int32_t) * cells) &&
          dalloc(pl, ws.linfo, sizeof(LevelInfo)) && dalloc(pl, ws.M, tsz * ws.ld * cells) &&
          dalloc(pl, ws.L, tsz * ws.ld * cells) && dalloc(pl, ws.E, sizeof(double) * 3 * n_max) &&
+         dalloc(pl, ws.near, tsz * 4 * n_max) &&
          dalloc(pl, ws.block_sums, sizeof(int32_t) * ws.block_sums_cap) &&
          dalloc(pl, ws.root, sizeof(RootCube)) &&
          dalloc(pl, ws.bbox_acc, sizeof(unsigned long long) * 8) &&
@@ -640,7 +660,12 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
         cudaMemset(ws.err, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ws.steps, 0, sizeof(StepCounter)) != cudaSuccess ||
         cudaMallocHost(&pl->h_err, sizeof(int)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithPriority(&pl->cap_stream, cudaStreamNonBlocking, prio_high()) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ws.side, cudaStreamNonBlocking, prio_low()) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ws.ev_p2m, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ws.ev_items, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ws.ev_near, cudaEventDisableTiming) != cudaSuccess) {
         free_plan(pl);
         return PT_ERR_CUDA;
     }
@@ -849,10 +874,10 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
     e->plans.assign(plans, plans + n_members);
     e->br.assign(n_members, nullptr);
     e->join.assign(n_members, nullptr);
-    bool ok = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) == cudaSuccess &&
+    bool ok = cudaStreamCreateWithPriority(&e->cap, cudaStreamNonBlocking, prio_high()) == cudaSuccess &&
               cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int b = 0; ok && b < n_members; ++b)
-        ok = cudaStreamCreateWithFlags(&e->br[b], cudaStreamNonBlocking) == cudaSuccess &&
+        ok = cudaStreamCreateWithPriority(&e->br[b], cudaStreamNonBlocking, prio_high()) == cudaSuccess &&
              cudaEventCreateWithFlags(&e->join[b], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         free_ensemble(e);

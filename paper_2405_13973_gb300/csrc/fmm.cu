@@ -356,33 +356,26 @@ __device__ __forceinline__ void kb_add(T& s, T& c, T v) {
     s = t;
 }
 
-// L2P + P2P, one block per target leaf: the sources of the 27 adjacent
-// leaves are staged in shared memory in the target leaf's frame; thread
-// (target i, chunk c) sums every nchunk-th source; the chunk partials are
-// combined in a fixed order with compensated sums (deterministic), the far
-// field (L2P) is added, and the field is written in the original ion order,
-// scaled to SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
+// P2P, one block per target leaf: the sources of the 27 adjacent leaves are
+// staged in shared memory in the target leaf's frame; thread (target i,
+// chunk c) sums every nchunk-th source; the chunk partials are combined in a
+// fixed order with compensated sums (deterministic) into near[slot] =
+// (E_x, E_y, E_z, phi) in leaf units (k_e = 1, leaf side = 1).
 constexpr int kNfThreads = 128;
 constexpr int kNfSrc = 1024;   // staged sources per pass
 
 template <typename T>
-__global__ void __launch_bounds__(kNfThreads) k_near_far(
-    int64_t n, int D, int p, int ld, int phases, const RootCube* root, const LevelInfo* linfo,
-    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
+__global__ void __launch_bounds__(kNfThreads) k_p2p(
+    int D, const LevelInfo* linfo, const typename Ion<T>::rec* __restrict__ sorted,
     const uint32_t* __restrict__ code, const int32_t* __restrict__ cid_leaf,
-    const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
-    const T* __restrict__ L, double* E, double* phi) {
+    const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount, T* __restrict__ near) {
     using R = typename Ion<T>::rec;
     __shared__ R src[kNfSrc];
     __shared__ int nb_start[27], nb_count[27], nb_pre[28];
     __shared__ T part[kNfThreads][4];
     const int tid = threadIdx.x;
     const int lim = 1 << D;
-    const double sl = root->side / (double)lim;
-    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
-    const bool near = (phases & PT_PHASE_NEAR) != 0;
-    const bool far = (phases & PT_PHASE_FAR) && D >= 2;
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
         int ix, iy, iz;
@@ -391,7 +384,7 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
             const int dx = tid / 9 - 1, dy = (tid / 3) % 3 - 1, dz = tid % 3 - 1;
             const int nx = ix + dx, ny = iy + dy, nz = iz + dz;
             int st = 0, ct = 0;
-            if (near && nx >= 0 && ny >= 0 && nz >= 0 && nx < lim && ny < lim && nz < lim) {
+            if (nx >= 0 && ny >= 0 && nz >= 0 && nx < lim && ny < lim && nz < lim) {
                 const int gn = cid_leaf[morton3(nx, ny, nz)];
                 if (gn >= 0) {
                     st = cstart[gn];
@@ -419,17 +412,6 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
             const bool active = ch < nch;
             const R me = sorted[ts + t0 + ti];
             T ex = 0, ey = 0, ez = 0, ph = 0, cex = 0, cey = 0, cez = 0, cph = 0;
-            if (far && active) {
-                // this chunk's share of the target's L2P: every nch-th column m
-                T fphi, gx, gy, gz, ux, uy, uz, uq;
-                Ion<T>::get(me, ux, uy, uz, uq);
-                l2p_eval_cols<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), ch, nch, fphi, gx,
-                                 gy, gz);
-                ex = -gx;
-                ey = -gy;
-                ez = -gz;
-                ph = fphi;
-            }
             for (int s0 = 0; s0 < ns; s0 += kNfSrc) {    // sources in passes of kNfSrc
                 const int nsb = min(kNfSrc, ns - s0);
                 __syncthreads();
@@ -486,16 +468,85 @@ __global__ void __launch_bounds__(kNfThreads) k_near_far(
                     kb_add(sz, cz, part[th][2]);
                     kb_add(sp, cp, part[th][3]);
                 }
-                const T fx = sx + cx, fy = sy + cy, fz = sz + cz, fp = sp + cp;
-                const int i = perm[ts + t0 + tid];
-                E[i] = fE * (double)fx;
-                E[n + i] = fE * (double)fy;
-                E[2 * n + i] = fE * (double)fz;
-                if (phi) phi[i] = fP * (double)fp;
+                T* o = near + 4 * (int64_t)(ts + t0 + tid);
+                o[0] = sx + cx;
+                o[1] = sy + cy;
+                o[2] = sz + cz;
+                o[3] = sp + cp;
             }
             __syncthreads();
         }
         __syncthreads();
+    }
+}
+
+// L2P and the total field, one block per target leaf: thread (target i,
+// group c) evaluates every ngroup-th column m of the target's local expansion
+// (Eq. L2P); the group partials are combined in a fixed order with
+// compensated sums, the near field (if any) is added, and the field is
+// written in the original ion order scaled to SI (k_e / s^2 for E, k_e / s
+// for phi, s = leaf side).
+template <typename T>
+__global__ void __launch_bounds__(kNfThreads) k_l2p(
+    int64_t n, int D, int p, int ld, bool far, const RootCube* root, const LevelInfo* linfo,
+    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
+    const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
+    using R = typename Ion<T>::rec;
+    __shared__ T part[kNfThreads][4];
+    const int tid = threadIdx.x;
+    const int lim = 1 << D;
+    const double sl = root->side / (double)lim;
+    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
+    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+        const int ts = cstart[g], nt = ccount[g];
+        for (int t0 = 0; t0 < nt; t0 += kNfThreads) {
+            const int ntb = min(kNfThreads, nt - t0);
+            const int nch = kNfThreads / ntb;
+            const int ti = tid % ntb, ch = tid / ntb;
+            T ex = 0, ey = 0, ez = 0, ph = 0;
+            if (far && ch < nch) {
+                T fphi, gx, gy, gz, ux, uy, uz, uq;
+                Ion<T>::get(sorted[ts + t0 + ti], ux, uy, uz, uq);
+                l2p_eval_cols<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), ch, nch, fphi, gx,
+                                 gy, gz);
+                ex = -gx;
+                ey = -gy;
+                ez = -gz;
+                ph = fphi;
+            }
+            part[tid][0] = ex;
+            part[tid][1] = ey;
+            part[tid][2] = ez;
+            part[tid][3] = ph;
+            __syncthreads();
+            if (tid < ntb) {
+                T sx = 0, sy = 0, sz = 0, sp = 0, cx = 0, cy = 0, cz = 0, cp = 0;
+                for (int c = 0; c < nch; ++c) {
+                    const int th = c * ntb + tid;
+                    kb_add(sx, cx, part[th][0]);
+                    kb_add(sy, cy, part[th][1]);
+                    kb_add(sz, cz, part[th][2]);
+                    kb_add(sp, cp, part[th][3]);
+                }
+                double fx = (double)(sx + cx), fy = (double)(sy + cy), fz = (double)(sz + cz),
+                       fp = (double)(sp + cp);
+                if (near) {
+                    const T* o = near + 4 * (int64_t)(ts + t0 + tid);
+                    fx += (double)o[0];
+                    fy += (double)o[1];
+                    fz += (double)o[2];
+                    fp += (double)o[3];
+                }
+                const int i = perm[ts + t0 + tid];
+                E[i] = fE * fx;
+                E[n + i] = fE * fy;
+                E[2 * n + i] = fE * fz;
+                if (phi) phi[i] = fP * fp;
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -506,13 +557,43 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     DenseLayout dl = dense_layout(D);
     T* M = (T*)ws.M;
     T* L = (T*)ws.L;
+    T* near = (T*)ws.near;
     const bool far = (phases & PT_PHASE_FAR) && D >= 2;
+    const bool nf = (phases & PT_PHASE_NEAR) != 0;
+    const int64_t leaves = n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D));
+    const int leaf_grid = (int)(leaves < 152 * 16 ? (leaves > 0 ? leaves : 1) : 152 * 16);
+    // The near field and the M2L work list depend on the tree only: with a
+    // side stream they run there, beside the upward pass.
+    const bool fork = far && nf && ws.side != nullptr;
+    cudaStream_t sn = fork ? ws.side : s;
     cudaError_t e;
+    if (fork) {
+        if ((e = cudaEventRecord(ws.ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(sn, ws.ev_fork, 0)) != cudaSuccess) return e;
+    }
+    if (far && use_tc) {
+        if ((e = launch_m2l_tc_worklist(n, D, ws, sn)) != cudaSuccess) return e;
+        if (fork && (e = cudaEventRecord(ws.ev_items, sn)) != cudaSuccess) return e;
+    }
     if (far) {
-        int leaves_max = (int)(n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D)));
-        int grid = leaves_max < 152 * 16 ? leaves_max : 152 * 16;
-        k_p2m<T><<<grid > 0 ? grid : 1, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
+        int grid = leaf_grid;
+        k_p2m<T><<<grid, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
             D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (nf) {
+        if (fork) {
+            // after P2M, which wants every SM
+            if ((e = cudaEventRecord(ws.ev_p2m, s)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(sn, ws.ev_p2m, 0)) != cudaSuccess) return e;
+        }
+        k_p2p<T><<<leaf_grid, kNfThreads, 0, sn>>>(D, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
+                                              ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount,
+                                              near);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (fork && (e = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return e;
+    }
+    if (far) {
         for (int l = D - 1; l >= 2; --l) {
             if (use_tc) {
                 if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
@@ -529,16 +610,8 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     if (ev && (e = cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
     if (far && use_tc) {
-        // one launch for every level's M2L; splits fill the SMs on small trees
-        int64_t tiles = 0;
-        for (int l = 2; l <= D; ++l) {
-            int64_t cl = (int64_t)1 << (3 * l);
-            tiles += ((n < cl ? n : cl) + 127) / 128 + 8;
-        }
-        int splits = (int)((2 * 152 + tiles - 1) / tiles);
-        if (splits < 1) splits = 1;
-        if (splits > ws.tc_splits_max) splits = ws.tc_splits_max;
-        if ((e = launch_m2l_tc_all(n, D, ws, splits, s)) != cudaSuccess) return e;
+        if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
+        if ((e = launch_m2l_tc_run(n, D, ws, s)) != cudaSuccess) return e;
     } else if (far) {
         for (int l = 2; l <= D; ++l) {
             int64_t cl = (int64_t)1 << (3 * l);
@@ -551,11 +624,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     }
     if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
-    int64_t leaves = n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D));
-    int grid = (int)(leaves < 152 * 16 ? leaves : 152 * 16);
-    k_near_far<T><<<grid > 0 ? grid : 1, kNfThreads, 0, s>>>(
-        n, D, p, ws.ld, phases, ws.root, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
-        ws.perm, ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount, L, E, phi);
+    if (fork && (e = cudaStreamWaitEvent(s, ws.ev_near, 0)) != cudaSuccess) return e;
+    k_l2p<T><<<leaf_grid, kNfThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
+                                              (const typename Ion<T>::rec*)ws.sorted, ws.perm,
+                                              ws.cstart, ws.ccount, L, nf ? near : nullptr, E, phi);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;

@@ -64,6 +64,11 @@ struct Workspace {
     void* M = nullptr;             // [cells_max][ld] multipole coefficients (padding zero)
     void* L = nullptr;             // [cells_max][ld] local coefficients
     double* E = nullptr;           // [3n] Coulomb field of the last evaluation (SoA, SI)
+    void* near = nullptr;          // [n][4] P2P field and potential per sorted slot (leaf units)
+    // side stream (lowest priority) of the near field and the M2L work list,
+    // which overlap the upward pass; events of the fork and the joins
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_p2m = nullptr, ev_items = nullptr, ev_near = nullptr;
     int32_t* block_sums = nullptr; // scan scratch
     int64_t block_sums_cap = 0;
     RootCube* root = nullptr;
@@ -124,10 +129,11 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
                           cudaStream_t s);
 
 // ---- tensor-core M2L (m2l_tc.cu) ---------------------------------------------
-cudaError_t launch_m2l_tc(int level, int D, Workspace& ws, cudaStream_t s);
-// M2L of every level on the tensor cores, then per level the split partials
-// and the L2L shift of the parent (so L is complete on return).
-cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int splits, cudaStream_t s);
+// The M2L work list of the current tree (reads the tree only), then the M2L
+// of every level on the tensor cores with the slab reduction and the L2L
+// shifts level by level (L is complete once the second has run).
+cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, cudaStream_t s);
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);

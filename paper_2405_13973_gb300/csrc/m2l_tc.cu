@@ -1385,15 +1385,25 @@ __global__ void k_split_m(int lfirst, int D, int ld, const LevelInfo* linfo, con
     }
 }
 
-cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, cudaStream_t s) {
-    if (D < 2) return cudaSuccess;
-    const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
-    int64_t tiles = 0;
+// The M2L work list of the current tree (tiles, their non-empty offsets,
+// the work items); it reads the tree only.
+static bool tc_worklist_layout(int64_t n, int D, Workspace& ws, int64_t& tiles, TcPlanHdr*& hdr,
+                               TcTile*& tl, TcItem*& items) {
+    tiles = 0;
     for (int l = 2; l <= D; ++l) tiles += (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
-    if (tiles > ws.tc_tiles_cap) return cudaErrorInvalidValue;
-    TcPlanHdr* hdr = (TcPlanHdr*)ws.tc_work;
-    TcTile* tl = (TcTile*)(hdr + 1);
-    TcItem* items = (TcItem*)(tl + ws.tc_tiles_cap);
+    hdr = (TcPlanHdr*)ws.tc_work;
+    tl = (TcTile*)(hdr + 1);
+    items = (TcItem*)(tl + ws.tc_tiles_cap);
+    return tiles <= ws.tc_tiles_cap;
+}
+
+cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    int64_t tiles;
+    TcPlanHdr* hdr;
+    TcTile* tl;
+    TcItem* items;
+    if (!tc_worklist_layout(n, D, ws, tiles, hdr, tl, items)) return cudaErrorInvalidValue;
     TcArgs a = base_args(n, D, ws, 1);
     a.mode = MODE_M2L;
     a.tiles = tl;
@@ -1402,13 +1412,29 @@ cudaError_t launch_m2l_tc_all(int64_t n, int D, Workspace& ws, int /*splits*/, c
     k_tc_plan<<<(unsigned)tiles, kPlanThreads, tc_plan_smem_bytes(D), s>>>(a, tl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, (int)ws.tc_slab_cap, hdr, tl,
+                                          items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
+    int64_t tiles;
+    TcPlanHdr* hdr;
+    TcTile* tl;
+    TcItem* items;
+    if (!tc_worklist_layout(n, D, ws, tiles, hdr, tl, items)) return cudaErrorInvalidValue;
+    TcArgs a = base_args(n, D, ws, 1);
+    a.mode = MODE_M2L;
+    a.tiles = tl;
+    a.items = items;
+    a.hdr = hdr;
+    cudaError_t e;
     if (ws.tc_bf16) {
         k_split_m<<<152 * 8, 256, 0, s>>>(2, D, ws.ld, ws.linfo, (const float*)ws.M, ws.M_pieces);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_tc_items<<<1, kItemThreads, 0, s>>>(D, ws.linfo, (int)tiles, (int)ws.tc_slab_cap, hdr, tl,
-                                          items);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // persistent: one CTA per SM walks the work list
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -1457,7 +1483,5 @@ size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap) {
     return sizeof(TcPlanHdr) + (size_t)tiles_cap * sizeof(TcTile) +
            (size_t)(tiles_cap + slab_cap) * sizeof(TcItem);
 }
-
-cudaError_t launch_m2l_tc(int, int, Workspace&, cudaStream_t) { return cudaErrorNotSupported; }
 
 }  // namespace pt
