@@ -98,6 +98,21 @@ int fmm_plan_destroy(fmm_plan plan);
  * both (default).  For testing each stage against its definition. */
 int fmm_plan_set_phases(fmm_plan plan, int phases);
 
+/* How the tensor-core precisions obtain the expansions of the cells above
+ * the leaves (Sec. 2.3.1):
+ *   PT_EXPAND_TREE   (default) the passes: P2M at the leaves, M2M shifts up,
+ *                    M2L, L2L shifts down, L2P at the leaves;
+ *   PT_EXPAND_DIRECT P2M of every ion about each of its ancestor cells and
+ *                    L2P of each ancestor's own M2L sum at the ion -- equal
+ *                    to the passes up to rounding, since M2M and L2L shift
+ *                    truncated expansions exactly.  It costs D - 1
+ *                    expansions per ion and serves as a cross-check of the
+ *                    shifts (slower than the passes on the 10k-ion crystal).
+ * The CUDA-core precisions always use the passes.  Errors: PT_ERR_ARG. */
+#define PT_EXPAND_TREE 0
+#define PT_EXPAND_DIRECT 1
+int fmm_plan_set_expansion(fmm_plan plan, int mode);
+
 /* Depth used by the last fmm_forces / pt_step call on this plan (or -1). */
 int fmm_plan_last_depth(fmm_plan plan);
 

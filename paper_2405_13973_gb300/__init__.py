@@ -25,6 +25,7 @@ PT_ERR_NONFINITE, PT_ERR_ESCAPED, PT_ERR_TIMEOUT, PT_ERR_COINCIDENT, PT_ERR_UNSU
     -4, -5, -6, -7, -8)
 PT_FP64, PT_MIXED_TF32X3, PT_MIXED_BF16X3, PT_FP32 = 0, 1, 2, 3
 PT_PHASE_NEAR, PT_PHASE_FAR, PT_PHASE_ALL = 1, 2, 3
+EXPAND_TREE, EXPAND_DIRECT = 0, 1
 PT_MAX_BEAMS = 8
 PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "bf16x3": PT_MIXED_BF16X3,
               "fp32": PT_FP32}
@@ -115,6 +116,7 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_phase_times.argtypes = [_VP, ctypes.POINTER(_D)]
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.fmm_plan_tc_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
+        L.fmm_plan_set_expansion.argtypes = [_VP, ctypes.c_int]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -244,6 +246,12 @@ class Plan:
 
     def set_phases(self, phases: int):
         _check(load(False).fmm_plan_set_phases(self._h, int(phases)), "fmm_plan_set_phases")
+
+    def set_expansion(self, mode: int):
+        """EXPAND_TREE (default: the M2M / L2L passes) or EXPAND_DIRECT (every
+        ion expanded about, and evaluated in, each ancestor cell) for the
+        tensor-core precisions."""
+        _check(load(False).fmm_plan_set_expansion(self._h, int(mode)), "fmm_plan_set_expansion")
 
     @property
     def last_depth(self) -> int:

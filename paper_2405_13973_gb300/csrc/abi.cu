@@ -29,8 +29,10 @@ struct GraphKey {
     PushParams pp{};
     pt_laser laser{};
     bool profile = false;
+    int expand = 0;
     bool operator==(const GraphKey& o) const {
-        return D == o.D && n == o.n && profile == o.profile && memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
+        return D == o.D && n == o.n && profile == o.profile && expand == o.expand &&
+               memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
                memcmp(&pp, &o.pp, sizeof pp) == 0 && memcmp(&laser, &o.laser, sizeof laser) == 0;
     }
 };
@@ -391,6 +393,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.pp = pp;
     key.laser = lz;
     key.profile = plan->profile;
+    key.expand = plan->ws.expand;
     return key;
 }
 
@@ -694,6 +697,12 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
 
 int fmm_plan_destroy(fmm_plan plan) {
     free_plan(plan);
+    return PT_OK;
+}
+
+int fmm_plan_set_expansion(fmm_plan plan, int mode) {
+    if (!plan || (mode != PT_EXPAND_TREE && mode != PT_EXPAND_DIRECT)) return PT_ERR_ARG;
+    plan->ws.expand = mode;
     return PT_OK;
 }
 

@@ -114,6 +114,37 @@ struct Ion<float> {
     }
 };
 
+// s + v with the rounding error carried in c (Kahan-Babuska / Neumaier).
+template <typename T>
+__device__ __forceinline__ void kb_add(T& s, T& c, T v) {
+    T t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+}
+
+// Position of a sorted ion in the frame of its ancestor s levels above its
+// leaf: o = the leaf's integer position inside the ancestor (0 .. 2^s - 1
+// per axis), u_anc = (u_leaf + o + 1/2 - 2^s / 2) / 2^s, in ancestor units.
+__device__ __forceinline__ void ion_in_ancestor(const Ion<float>::rec& r, int s, int ox, int oy,
+                                                int oz, float& x, float& y, float& z, float& q) {
+    const float sc = __int_as_float((127 - 30 - s) << 23);  // 2^-(30+s)
+    const int half = 1 << s;
+    const long long u = 1ll << 29;  // 1/2 in 30-bit fixed point
+    x = __ll2float_rn((long long)r.x + (long long)(2 * ox + 1 - half) * u) * sc;
+    y = __ll2float_rn((long long)r.y + (long long)(2 * oy + 1 - half) * u) * sc;
+    z = __ll2float_rn((long long)r.z + (long long)(2 * oz + 1 - half) * u) * sc;
+    q = __int_as_float(r.w);
+}
+__device__ __forceinline__ void ion_in_ancestor(const Ion<double>::rec& r, int s, int ox, int oy,
+                                                int oz, double& x, double& y, double& z, double& q) {
+    const double sc = ldexp(1.0, -s), c = 0.5 - 0.5 * (double)(1 << s);
+    x = (r.x + ((double)ox + c)) * sc;
+    y = (r.y + ((double)oy + c)) * sc;
+    z = (r.z + ((double)oz + c)) * sc;
+    q = r.w;
+}
+
 constexpr int kP2mThreads = 128;
 constexpr int kP2mIons = 32;
 
@@ -165,6 +196,69 @@ __global__ void __launch_bounds__(kP2mThreads) k_p2m(int D, int p, int ld, const
         for (int r = 0; r < NA; ++r) {
             const int c = threadIdx.x + r * kP2mThreads;
             if (c < P) M[(int64_t)g * ld + c] = acc[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Direct ancestor multipoles (PT_EXPAND_DIRECT): P2M of every ion about each
+// of its cells at levels lmin..D, one block per cell, as k_p2m but with u in
+// the cell's frame and units and compensated sums (an ancestor's
+// coefficients sum thousands of terms of both signs).  A cell's ions are the
+// contiguous slots of its leaves.  Equal to P2M at the leaves followed by the
+// M2M shifts, which shift a truncated expansion exactly.
+// ---------------------------------------------------------------------------
+constexpr int kP2mAncIons = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kP2mThreads) k_p2m_anc(
+    int D, int lmin, int p, int ld, const LevelInfo* linfo, const uint32_t* __restrict__ code,
+    const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_of,
+    const typename Ion<T>::rec* __restrict__ sorted, T* __restrict__ M) {
+    extern __shared__ unsigned char p2m_smem[];
+    const int P = (p + 1) * (p + 1);
+    T* terms = reinterpret_cast<T*>(p2m_smem);  // [kP2mAncIons][P]
+    const HarmTables<T>& t = tab<T>();
+    const int g0 = linfo->gbase[lmin], g1 = linfo->gbase[D + 1];
+    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+        int l = lmin;
+        while (l < D && g >= linfo->gbase[l + 1]) ++l;
+        const int sh = D - l, mask = (1 << sh) - 1;
+        const uint32_t c = code[g];
+        const int s = leaf_start[(int64_t)c << (3 * sh)];
+        const int k = leaf_start[((int64_t)c + 1) << (3 * sh)] - s;
+        constexpr int NA = (kMaxOrder + 1) * (kMaxOrder + 1) / kP2mThreads + 1;
+        T acc[NA], cmp[NA];
+#pragma unroll
+        for (int r = 0; r < NA; ++r) acc[r] = cmp[r] = T(0);
+        for (int i0 = 0; i0 < k; i0 += kP2mAncIons) {
+            const int ni = min(kP2mAncIons, k - i0);
+            __syncthreads();
+            if (threadIdx.x < ni) {
+                T x, y, z, q;
+                const int slot = s + i0 + threadIdx.x;
+                int ix, iy, iz;
+                demorton3(code[leaf_of[slot]], ix, iy, iz);
+                ion_in_ancestor(sorted[slot], sh, ix & mask, iy & mask, iz & mask, x, y, z, q);
+                T* row = terms + threadIdx.x * P;
+                for_each_ups<T>(p, x, y, z, t, [&](int n, int m, T re, T im) {
+                    const int idx = re_idx(n, m);
+                    row[idx] = q * re;
+                    if (m > 0) row[idx + 1] = -q * im;
+                });
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < NA; ++r) {
+                const int cc = threadIdx.x + r * kP2mThreads;
+                if (cc < P)
+                    for (int i = 0; i < ni; ++i) kb_add(acc[r], cmp[r], terms[i * P + cc]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+            const int cc = threadIdx.x + r * kP2mThreads;
+            if (cc < P) M[(int64_t)g * ld + cc] = acc[r] + cmp[r];
         }
     }
 }
@@ -347,14 +441,6 @@ __device__ __forceinline__ double inv_sqrt<double>(double r2) {
     return 1.0 / sqrt(r2);
 }
 
-// s + v with the rounding error carried in c (Kahan-Babuska / Neumaier).
-template <typename T>
-__device__ __forceinline__ void kb_add(T& s, T& c, T v) {
-    T t = s + v;
-    if (fabs(s) >= fabs(v)) c += (s - t) + v;
-    else c += (v - t) + s;
-    s = t;
-}
 
 // P2P, one block per target leaf: the sources of the 27 adjacent leaves are
 // staged in shared memory in the target leaf's frame; thread (target i,
@@ -550,6 +636,87 @@ __global__ void __launch_bounds__(kNfThreads) k_l2p(
     }
 }
 
+// Direct ancestor local expansions (PT_EXPAND_DIRECT): as k_l2p, but every
+// thread evaluates its columns of the M2L-only local expansions of the
+// target's cells at levels lmin..D, each at the ion in that cell's frame,
+// scaled to leaf units; equal to shifting them down by L2L (which shifts a
+// truncated local expansion exactly) and evaluating the leaf's.
+template <typename T>
+__global__ void __launch_bounds__(kNfThreads) k_l2p_anc(
+    int64_t n, int D, int lmin, int p, int ld, const RootCube* root, const LevelInfo* linfo,
+    const uint32_t* __restrict__ code, const int32_t* __restrict__ cid,
+    const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
+    const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
+    __shared__ T part[kNfThreads][4];
+    const int tid = threadIdx.x;
+    const int lim = 1 << D;
+    const double sl = root->side / (double)lim;
+    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
+    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+        const int ts = cstart[g], nt = ccount[g];
+        const uint32_t cl = code[g];
+        int ix, iy, iz;
+        demorton3(cl, ix, iy, iz);
+        for (int t0 = 0; t0 < nt; t0 += kNfThreads) {
+            const int ntb = min(kNfThreads, nt - t0);
+            const int nch = kNfThreads / ntb;
+            const int ti = tid % ntb, ch = tid / ntb;
+            T ex = 0, ey = 0, ez = 0, ph = 0;
+            if (ch < nch) {
+                const typename Ion<T>::rec me = sorted[ts + t0 + ti];
+                for (int l = lmin; l <= D; ++l) {
+                    const int sh = D - l, mask = (1 << sh) - 1;
+                    // dense maps of levels 2.. concatenated: level l starts at (8^l - 64) / 7
+                    const int ga =
+                        sh == 0 ? g : cid[(((1ll << (3 * l)) - 64) / 7) + (cl >> (3 * sh))];
+                    T fphi, gx, gy, gz, ux, uy, uz, uq;
+                    ion_in_ancestor(me, sh, ix & mask, iy & mask, iz & mask, ux, uy, uz, uq);
+                    l2p_eval_cols<T>(p, L + (int64_t)ga * ld, ux, uy, uz, tab<T>(), ch, nch, fphi,
+                                     gx, gy, gz);
+                    // level-l units -> leaf units: phi / 2^sh, E / 4^sh (exact)
+                    const T fp1 = (T)1 / (T)(1 << sh), fe1 = fp1 * fp1;
+                    ex -= fe1 * gx;
+                    ey -= fe1 * gy;
+                    ez -= fe1 * gz;
+                    ph += fp1 * fphi;
+                }
+            }
+            part[tid][0] = ex;
+            part[tid][1] = ey;
+            part[tid][2] = ez;
+            part[tid][3] = ph;
+            __syncthreads();
+            if (tid < ntb) {
+                T sx = 0, sy = 0, sz = 0, sp = 0, cx = 0, cy = 0, cz = 0, cp = 0;
+                for (int c = 0; c < nch; ++c) {
+                    const int th = c * ntb + tid;
+                    kb_add(sx, cx, part[th][0]);
+                    kb_add(sy, cy, part[th][1]);
+                    kb_add(sz, cz, part[th][2]);
+                    kb_add(sp, cp, part[th][3]);
+                }
+                double fx = (double)(sx + cx), fy = (double)(sy + cy), fz = (double)(sz + cz),
+                       fp = (double)(sp + cp);
+                if (near) {
+                    const T* o = near + 4 * (int64_t)(ts + t0 + tid);
+                    fx += (double)o[0];
+                    fy += (double)o[1];
+                    fz += (double)o[2];
+                    fp += (double)o[3];
+                }
+                const int i = perm[ts + t0 + tid];
+                E[i] = fE * fx;
+                E[n + i] = fE * fy;
+                E[2 * n + i] = fE * fz;
+                if (phi) phi[i] = fP * fp;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
                            double* phi, cudaStream_t s, cudaEvent_t* ev) {
@@ -566,6 +733,9 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     // side stream they run there, beside the upward pass.
     const bool fork = far && nf && ws.side != nullptr;
     cudaStream_t sn = fork ? ws.side : s;
+    // ancestor expansions of the tensor-core path directly from the ions
+    // instead of the M2M / L2L shifts (an option: a cross-check of the shifts)
+    const bool direct = far && use_tc && ws.expand == PT_EXPAND_DIRECT;
     cudaError_t e;
     if (fork) {
         if ((e = cudaEventRecord(ws.ev_fork, s)) != cudaSuccess) return e;
@@ -575,7 +745,15 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         if ((e = launch_m2l_tc_worklist(n, D, ws, sn)) != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(ws.ev_items, sn)) != cudaSuccess) return e;
     }
-    if (far) {
+    if (direct) {
+        int64_t cells = 0;
+        for (int l = 2; l <= D; ++l) cells += n < ((int64_t)1 << (3 * l)) ? n : ((int64_t)1 << (3 * l));
+        const int grid = (int)(cells < 152 * 16 ? cells : 152 * 16);
+        k_p2m_anc<T><<<grid, kP2mThreads, kP2mAncIons * P * sizeof(T), s>>>(
+            D, 2, p, ws.ld, ws.linfo, ws.code, ws.leaf_start, ws.leaf_of,
+            (const typename Ion<T>::rec*)ws.sorted, M);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if (far) {
         int grid = leaf_grid;
         k_p2m<T><<<grid, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
             D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M);
@@ -593,7 +771,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return e;
     }
-    if (far) {
+    if (far && !direct) {
         for (int l = D - 1; l >= 2; --l) {
             if (use_tc) {
                 if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
@@ -611,7 +789,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         return e;
     if (far && use_tc) {
         if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
-        if ((e = launch_m2l_tc_run(n, D, ws, s)) != cudaSuccess) return e;
+        if ((e = launch_m2l_tc_run(n, D, ws, !direct, s)) != cudaSuccess) return e;
     } else if (far) {
         for (int l = 2; l <= D; ++l) {
             int64_t cl = (int64_t)1 << (3 * l);
@@ -625,9 +803,16 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
     if (fork && (e = cudaStreamWaitEvent(s, ws.ev_near, 0)) != cudaSuccess) return e;
-    k_l2p<T><<<leaf_grid, kNfThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
-                                              (const typename Ion<T>::rec*)ws.sorted, ws.perm,
-                                              ws.cstart, ws.ccount, L, nf ? near : nullptr, E, phi);
+    if (direct)
+        k_l2p_anc<T><<<leaf_grid, kNfThreads, 0, s>>>(
+            n, D, 2, p, ws.ld, ws.root, ws.linfo, ws.code, ws.cid,
+            (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
+            nf ? near : nullptr, E, phi);
+    else
+        k_l2p<T><<<leaf_grid, kNfThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
+                                                  (const typename Ion<T>::rec*)ws.sorted, ws.perm,
+                                                  ws.cstart, ws.ccount, L, nf ? near : nullptr, E,
+                                                  phi);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;
@@ -790,6 +975,12 @@ cudaError_t upload_harmonic_tables() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_p2m<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kP2mIons * pmax * (int)sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2m_anc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kP2mAncIons * pmax * (int)sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_p2m_anc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kP2mAncIons * pmax * (int)sizeof(float));
     return e;
 }
 

@@ -93,6 +93,7 @@ struct Workspace {
     int64_t tc_slab_cap = 1;    // M2L items of rank > 0 (partial slabs)
     void* tc_work = nullptr;    // M2L work list (tiles, items)
     int64_t tc_tiles_cap = 0;
+    int expand = 0;             // PT_EXPAND_*: ancestor expansions of the tensor-core paths
 };
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
@@ -133,7 +134,7 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
 // of every level on the tensor cores with the slab reduction and the L2L
 // shifts level by level (L is complete once the second has run).
 cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, cudaStream_t s);
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s);
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
