@@ -26,6 +26,10 @@ namespace pt {
 
 __constant__ HarmTables<double> c_tab_d;
 __constant__ HarmTables<float> c_tab_f;
+// the same tables in global memory, for kernels whose lanes read them at
+// different m (constant memory would serialise those reads)
+__device__ HarmTables<double> g_tab_d;
+__device__ HarmTables<float> g_tab_f;
 // M2L source offsets per target octant: packed (ox+3)*49 + (oy+3)*7 + (oz+3),
 // o = target - source, o_a in [b_a - 3, b_a + 2] with b the octant bits,
 // excluding the 27 neighbours.
@@ -566,72 +570,163 @@ __global__ void __launch_bounds__(kNfThreads) k_p2p(
     }
 }
 
-// L2P and the total field, one block per target leaf: thread (target i,
-// group c) evaluates every ngroup-th column m of the target's local expansion
-// (Eq. L2P); the group partials are combined in a fixed order with
-// compensated sums, the near field (if any) is added, and the field is
-// written in the original ion order scaled to SI (k_e / s^2 for E, k_e / s
-// for phi, s = leaf side).
+// L2P (Eq. L2P) and the total field, one block per target leaf, one target
+// per 16-lane half-warp, lane m holding column m of the harmonics:
+//   * the diagonal Y^_m^m = prod_{k<=m} (x + i y) c_k is an inclusive prefix
+//     product over the lanes (4 shuffle steps instead of m serial ones);
+//   * all lanes then walk n = 0..p together, lane m stepping its column
+//     recurrence once n >= m, and adding the (n, m) terms of the potential
+//     and the gradient; L_{n+1,m+1} and L_{n+1,m-1} come from lanes m +- 1,
+//     which load L_{n+1,m'} for their own column anyway;
+//   * the column sums are added by a fixed shuffle tree (deterministic).
+// The leaf's local expansion is staged in shared memory; the near field (if
+// any) is added and the field written in the original ion order scaled to
+// SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
+constexpr int kL2pThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(kNfThreads) k_l2p(
+__device__ __forceinline__ const HarmTables<T>& gtab();
+template <>
+__device__ __forceinline__ const HarmTables<double>& gtab<double>() { return g_tab_d; }
+template <>
+__device__ __forceinline__ const HarmTables<float>& gtab<float>() { return g_tab_f; }
+
+template <typename T>
+__global__ void __launch_bounds__(kL2pThreads) k_l2p(
     int64_t n, int D, int p, int ld, bool far, const RootCube* root, const LevelInfo* linfo,
     const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
     const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
-    using R = typename Ion<T>::rec;
-    __shared__ T part[kNfThreads][4];
-    const int tid = threadIdx.x;
+    __shared__ T sL[(kMaxOrder + 1) * (kMaxOrder + 1)];
+    __shared__ HarmTables<T> t;
+    {
+        const int* src = reinterpret_cast<const int*>(&gtab<T>());
+        int* dst = reinterpret_cast<int*>(&t);
+        for (int i = threadIdx.x; i < (int)(sizeof(HarmTables<T>) / sizeof(int)); i += kL2pThreads)
+            dst[i] = src[i];
+    }
+    const int lane = threadIdx.x & 31, m = lane & 15;
+    const int slot_in_pass = threadIdx.x >> 4;        // target of this half-warp
+    constexpr int kPerPass = kL2pThreads / 16;
+    const unsigned hw_mask = 0xffffu << (lane & 16);  // this half-warp's lanes
+    const int P = (p + 1) * (p + 1);
     const int lim = 1 << D;
-    const double sl = root->side / (double)lim;
-    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
+    // SI scale factors, once per block: FP64 division is slow on this GPU,
+    // and every thread computing them cost more than the L2P itself
+    __shared__ double s_f[2];
+    if (threadIdx.x == 0) {
+        const double sl = root->side / (double)lim;
+        s_f[0] = kCoulomb / (sl * sl);
+        s_f[1] = kCoulomb / sl;
+    }
+    __syncthreads();
+    const T tE = (T)s_f[0], tP = (T)s_f[1];
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
-        for (int t0 = 0; t0 < nt; t0 += kNfThreads) {
-            const int ntb = min(kNfThreads, nt - t0);
-            const int nch = kNfThreads / ntb;
-            const int ti = tid % ntb, ch = tid / ntb;
+        __syncthreads();
+        if (far)
+            for (int c = threadIdx.x; c < P; c += kL2pThreads) sL[c] = L[(int64_t)g * ld + c];
+        __syncthreads();
+        for (int t0 = 0; t0 < nt; t0 += kPerPass) {
+            const int ti = t0 + slot_in_pass;
+            if (ti >= nt) continue;  // whole half-warps only: the shuffles stay within one
             T ex = 0, ey = 0, ez = 0, ph = 0;
-            if (far && ch < nch) {
-                T fphi, gx, gy, gz, ux, uy, uz, uq;
-                Ion<T>::get(sorted[ts + t0 + ti], ux, uy, uz, uq);
-                l2p_eval_cols<T>(p, L + (int64_t)g * ld, ux, uy, uz, tab<T>(), ch, nch, fphi, gx,
-                                 gy, gz);
-                ex = -gx;
-                ey = -gy;
-                ez = -gz;
-                ph = fphi;
-            }
-            part[tid][0] = ex;
-            part[tid][1] = ey;
-            part[tid][2] = ez;
-            part[tid][3] = ph;
-            __syncthreads();
-            if (tid < ntb) {
-                T sx = 0, sy = 0, sz = 0, sp = 0, cx = 0, cy = 0, cz = 0, cp = 0;
-                for (int c = 0; c < nch; ++c) {
-                    const int th = c * ntb + tid;
-                    kb_add(sx, cx, part[th][0]);
-                    kb_add(sy, cy, part[th][1]);
-                    kb_add(sz, cz, part[th][2]);
-                    kb_add(sp, cp, part[th][3]);
+            if (far) {
+                T x, y, z, q;
+                Ion<T>::get(sorted[ts + ti], x, y, z, q);
+                // diagonal: inclusive prefix product of (x + i y) c_k over k = 1..m
+                T dre = m == 0 ? T(1) : x * t.c[m <= p ? m : 0];
+                T dim = m == 0 ? T(0) : y * t.c[m <= p ? m : 0];
+#pragma unroll
+                for (int off = 1; off < 16; off <<= 1) {
+                    const T ore = __shfl_up_sync(hw_mask, dre, off, 16);
+                    const T oim = __shfl_up_sync(hw_mask, dim, off, 16);
+                    if (m >= off) {
+                        const T r = ore * dre - oim * dim;
+                        dim = ore * dim + oim * dre;
+                        dre = r;
+                    }
                 }
-                double fx = (double)(sx + cx), fy = (double)(sy + cy), fz = (double)(sz + cz),
-                       fp = (double)(sp + cp);
+                const T r2 = x * x + y * y + z * z;
+                const T w = m > 0 ? T(2) : T(1);
+                T yr = 0, yi = 0, y1r = 0, y1i = 0;  // Y_n^m and Y_{n-1}^m
+                T ax = 0, ay = 0, az = 0;
+                T lr = 0, li = 0;                    // L_{n,m}, carried from the previous n
+                if (m == 0) lr = sL[0];
+                for (int nn = 0; nn <= p; ++nn) {
+                    // this lane's column: L_{n+1,m}
+                    T l1r = 0, l1i = 0;
+                    if (nn + 1 <= p && m <= nn + 1 && m <= p) {
+                        const int k1 = re_idx(nn + 1, m);
+                        l1r = sL[k1];
+                        l1i = m > 0 ? sL[k1 + 1] : T(0);
+                    }
+                    // neighbours' columns: L_{n+1,m+1} and L_{n+1,m-1}
+                    const T l2r = __shfl_down_sync(hw_mask, l1r, 1, 16);
+                    const T l2i = __shfl_down_sync(hw_mask, l1i, 1, 16);
+                    const T l3r = __shfl_up_sync(hw_mask, l1r, 1, 16);
+                    const T l3i = __shfl_up_sync(hw_mask, l1i, 1, 16);
+                    if (m <= nn && m <= p) {
+                        // Y_n^m by the column recurrence
+                        T cr, ci;
+                        if (nn == m) {
+                            cr = dre;
+                            ci = dim;
+                        } else if (nn == m + 1) {
+                            cr = z * t.d[m] * yr;
+                            ci = z * t.d[m] * yi;
+                        } else {
+                            const T a = t.a[nn][m] * z, b = t.b[nn][m] * r2;
+                            cr = a * yr - b * y1r;
+                            ci = a * yi - b * y1i;
+                        }
+                        y1r = yr;
+                        y1i = yi;
+                        yr = cr;
+                        yi = ci;
+                        ph += w * (lr * yr + li * yi);
+                        if (nn + 1 <= p) {
+                            az += w * t.e[nn][m] * (l1r * yr + l1i * yi);
+                            ax += t.f[nn][m] * (l2r * yr + l2i * yi);
+                            ay += t.f[nn][m] * (l2i * yr - l2r * yi);
+                            if (m >= 1) {
+                                ax -= t.g[nn][m] * (l3r * yr + l3i * yi);
+                                ay -= t.g[nn][m] * (l3r * yi - l3i * yr);
+                            }
+                        }
+                    }
+                    lr = l1r;
+                    li = l1i;
+                }
+                ex = -ax;
+                ey = -ay;
+                ez = -az;
+            }
+            // column sums: a fixed shuffle tree over the half-warp
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                ex += __shfl_xor_sync(hw_mask, ex, off, 16);
+                ey += __shfl_xor_sync(hw_mask, ey, off, 16);
+                ez += __shfl_xor_sync(hw_mask, ez, off, 16);
+                ph += __shfl_xor_sync(hw_mask, ph, off, 16);
+            }
+            if (m == 0) {
+                // near + far and the SI scale in T: in FP32 one conversion per
+                // stored component (FP64 instructions are scarce on this GPU)
                 if (near) {
-                    const T* o = near + 4 * (int64_t)(ts + t0 + tid);
-                    fx += (double)o[0];
-                    fy += (double)o[1];
-                    fz += (double)o[2];
-                    fp += (double)o[3];
+                    const T* o = near + 4 * (int64_t)(ts + ti);
+                    ex += o[0];
+                    ey += o[1];
+                    ez += o[2];
+                    ph += o[3];
                 }
-                const int i = perm[ts + t0 + tid];
-                E[i] = fE * fx;
-                E[n + i] = fE * fy;
-                E[2 * n + i] = fE * fz;
-                if (phi) phi[i] = fP * fp;
+                const int i = perm[ts + ti];
+                E[i] = (double)(tE * ex);
+                E[n + i] = (double)(tE * ey);
+                E[2 * n + i] = (double)(tE * ez);
+                if (phi) phi[i] = (double)(tP * ph);
             }
-            __syncthreads();
         }
     }
 }
@@ -651,8 +746,16 @@ __global__ void __launch_bounds__(kNfThreads) k_l2p_anc(
     __shared__ T part[kNfThreads][4];
     const int tid = threadIdx.x;
     const int lim = 1 << D;
-    const double sl = root->side / (double)lim;
-    const double fE = kCoulomb / (sl * sl), fP = kCoulomb / sl;
+    // SI scale factors, once per block: FP64 division is slow on this GPU,
+    // and every thread computing them cost more than the L2P itself
+    __shared__ double s_f[2];
+    if (threadIdx.x == 0) {
+        const double sl = root->side / (double)lim;
+        s_f[0] = kCoulomb / (sl * sl);
+        s_f[1] = kCoulomb / sl;
+    }
+    __syncthreads();
+    const double fE = s_f[0], fP = s_f[1];
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
@@ -809,7 +912,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
             (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
             nf ? near : nullptr, E, phi);
     else
-        k_l2p<T><<<leaf_grid, kNfThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
+        k_l2p<T><<<leaf_grid, kL2pThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
                                                   (const typename Ion<T>::rec*)ws.sorted, ws.perm,
                                                   ws.cstart, ws.ccount, L, nf ? near : nullptr, E,
                                                   phi);
@@ -967,6 +1070,8 @@ cudaError_t upload_harmonic_tables() {
     }
     cudaError_t e = cudaMemcpyToSymbol(c_tab_d, &hd, sizeof hd);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_f, &hf, sizeof hf);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tab_d, &hd, sizeof hd);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tab_f, &hf, sizeof hf);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_m2l_off, off, sizeof off);
     const int pmax = (kMaxOrder + 1) * (kMaxOrder + 1);
     if (e == cudaSuccess)
