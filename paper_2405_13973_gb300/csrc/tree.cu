@@ -175,11 +175,13 @@ __global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t 
         const int64_t base = t0 + (int64_t)threadIdx.x * kScan1Items;
         int vals[kScan1Items];
         int acc = 0;
-        for (int k = 0; k < kScan1Items; ++k) {
+#pragma unroll
+        for (int k = 0; k < kScan1Items; ++k) {  // all loads in flight at once
             const int64_t i = base + k;
             vals[k] = i < total ? src.load(i) : 0;
-            acc += vals[k];
         }
+#pragma unroll
+        for (int k = 0; k < kScan1Items; ++k) acc += vals[k];
         int x = acc;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t 
         __syncthreads();
         int ex = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - acc;
         const int tot = warp_tot[kScan1Threads / 32 - 1];
+#pragma unroll
         for (int k = 0; k < kScan1Items; ++k) {
             const int64_t i = base + k;
             if (i < total) src.store(i, ex, vals[k]);
@@ -250,8 +253,9 @@ struct CellCompaction {
         while (l < D && v >= off[l + 1]) ++l;
         int64_t j = v - off[l];
         if (l == 0) { c = 0; return; }
-        int64_t per = (int64_t)1 << (3 * (l - 1));
-        uint32_t oct = (uint32_t)(j / per), par = (uint32_t)(j % per);
+        // j = oct * 8^(l-1) + par (octant-major order)
+        const int sh = 3 * (l - 1);
+        uint32_t oct = (uint32_t)(j >> sh), par = (uint32_t)(j & (((int64_t)1 << sh) - 1));
         c = (par << 3) | oct;
     }
     __device__ int range(int l, uint32_t c, int& first) const {
@@ -284,8 +288,8 @@ struct CellCompaction {
         }
         if (j == 0) linfo->gbase[l] = ex;
         if (l >= 1) {
-            int64_t per = (int64_t)1 << (3 * (l - 1));
-            if (j % per == 0) linfo->oct_start[l][j / per] = ex;
+            const int sh = 3 * (l - 1);
+            if ((j & (((int64_t)1 << sh) - 1)) == 0) linfo->oct_start[l][j >> sh] = ex;
         } else {
             for (int o = 0; o < 8; ++o) linfo->oct_start[0][o] = ex;
         }
