@@ -100,8 +100,9 @@ int fmm_plan_set_phases(fmm_plan plan, int phases);
 
 /* How the tensor-core precisions obtain the expansions of the cells above
  * the leaves (Sec. 2.3.1):
- *   PT_EXPAND_TREE   (default) the passes: P2M at the leaves, M2M shifts up,
- *                    M2L, L2L shifts down, L2P at the leaves;
+ *   PT_EXPAND_TREE   (default) the passes: P2M at the leaves and at their
+ *                    parents, M2M shifts up from there, M2L, L2L shifts
+ *                    down, L2P at the leaves;
  *   PT_EXPAND_DIRECT P2M of every ion about each of its ancestor cells and
  *                    L2P of each ancestor's own M2L sum at the ion -- equal
  *                    to the passes up to rounding, since M2M and L2L shift

@@ -248,9 +248,10 @@ class Plan:
         _check(load(False).fmm_plan_set_phases(self._h, int(phases)), "fmm_plan_set_phases")
 
     def set_expansion(self, mode: int):
-        """EXPAND_TREE (default: the M2M / L2L passes) or EXPAND_DIRECT (every
-        ion expanded about, and evaluated in, each ancestor cell) for the
-        tensor-core precisions."""
+        """EXPAND_TREE (default: P2M at the leaves and their parents, the
+        M2M / L2L passes above) or EXPAND_DIRECT (every ion expanded about,
+        and evaluated in, each ancestor cell) for the tensor-core
+        precisions."""
         _check(load(False).fmm_plan_set_expansion(self._h, int(mode)), "fmm_plan_set_expansion")
 
     @property

@@ -832,8 +832,8 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     const bool nf = (phases & PT_PHASE_NEAR) != 0;
     const int64_t leaves = n < ((int64_t)1 << (3 * D)) ? n : ((int64_t)1 << (3 * D));
     const int leaf_grid = (int)(leaves < 152 * 16 ? (leaves > 0 ? leaves : 1) : 152 * 16);
-    // The near field and the M2L work list depend on the tree only: with a
-    // side stream they run there, beside the upward pass.
+    // The M2L work list and the near field depend on the tree only: with a
+    // side stream they run there, beside the main chain.
     const bool fork = far && nf && ws.side != nullptr;
     cudaStream_t sn = fork ? ws.side : s;
     // ancestor expansions of the tensor-core path directly from the ions
@@ -848,12 +848,18 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         if ((e = launch_m2l_tc_worklist(n, D, ws, sn)) != cudaSuccess) return e;
         if (fork && (e = cudaEventRecord(ws.ev_items, sn)) != cudaSuccess) return e;
     }
-    if (direct) {
+    // Multipoles from the ions: at the leaves, and on the tensor-core path also
+    // at their parents (a parent holds about eight leaves' ions, cheaper to
+    // expand directly than one more M2M launch and its reduction), or at every
+    // level >= 2 in the direct mode; M2M shifts the rest up.
+    const int lmin_p2m = direct ? 2 : (far && use_tc && D >= 3 ? D - 1 : D);
+    if (far && lmin_p2m < D) {
         int64_t cells = 0;
-        for (int l = 2; l <= D; ++l) cells += n < ((int64_t)1 << (3 * l)) ? n : ((int64_t)1 << (3 * l));
+        for (int l = lmin_p2m; l <= D; ++l)
+            cells += n < ((int64_t)1 << (3 * l)) ? n : ((int64_t)1 << (3 * l));
         const int grid = (int)(cells < 152 * 16 ? cells : 152 * 16);
         k_p2m_anc<T><<<grid, kP2mThreads, kP2mAncIons * P * sizeof(T), s>>>(
-            D, 2, p, ws.ld, ws.linfo, ws.code, ws.leaf_start, ws.leaf_of,
+            D, lmin_p2m, p, ws.ld, ws.linfo, ws.code, ws.leaf_start, ws.leaf_of,
             (const typename Ion<T>::rec*)ws.sorted, M);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (far) {
@@ -862,20 +868,27 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
             D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (nf) {
-        if (fork) {
-            // after P2M, which wants every SM
-            if ((e = cudaEventRecord(ws.ev_p2m, s)) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(sn, ws.ev_p2m, 0)) != cudaSuccess) return e;
-        }
-        k_p2p<T><<<leaf_grid, kNfThreads, 0, sn>>>(D, ws.linfo, (const typename Ion<T>::rec*)ws.sorted,
-                                              ws.code, ws.cid + dl.off[D], ws.cstart, ws.ccount,
-                                              near);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (fork && (e = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return e;
+    // P2P on the side stream: after P2M on the CUDA-core paths (beside their
+    // M2L); on the tensor-core path after the M2L kernel, which needs every
+    // SM, beside the slab reduction and the L2L launches, which use few
+    auto launch_near = [&](bool after_event) -> cudaError_t {
+        cudaError_t r;
+        if (fork && after_event && (r = cudaStreamWaitEvent(sn, ws.ev_p2m, 0)) != cudaSuccess)
+            return r;
+        k_p2p<T><<<leaf_grid, kNfThreads, 0, sn>>>(D, ws.linfo,
+                                                  (const typename Ion<T>::rec*)ws.sorted, ws.code,
+                                                  ws.cid + dl.off[D], ws.cstart, ws.ccount, near);
+        if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        if (fork && (r = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return r;
+        return cudaSuccess;
+    };
+    const bool near_late = fork && use_tc;
+    if (nf && !near_late) {
+        if (fork && (e = cudaEventRecord(ws.ev_p2m, s)) != cudaSuccess) return e;
+        if ((e = launch_near(true)) != cudaSuccess) return e;
     }
-    if (far && !direct) {
-        for (int l = D - 1; l >= 2; --l) {
+    if (far) {
+        for (int l = lmin_p2m - 1; l >= 2; --l) {
             if (use_tc) {
                 if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
                 continue;
@@ -892,7 +905,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         return e;
     if (far && use_tc) {
         if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
-        if ((e = launch_m2l_tc_run(n, D, ws, !direct, s)) != cudaSuccess) return e;
+        if ((e = launch_m2l_tc_run(n, D, ws, !direct, s, near_late ? ws.ev_p2m : nullptr)) !=
+            cudaSuccess)
+            return e;
+        if (nf && near_late && (e = launch_near(true)) != cudaSuccess) return e;
     } else if (far) {
         for (int l = 2; l <= D; ++l) {
             int64_t cl = (int64_t)1 << (3 * l);

@@ -65,8 +65,9 @@ struct Workspace {
     void* L = nullptr;             // [cells_max][ld] local coefficients
     double* E = nullptr;           // [3n] Coulomb field of the last evaluation (SoA, SI)
     void* near = nullptr;          // [n][4] P2P field and potential per sorted slot (leaf units)
-    // side stream (lowest priority) of the near field and the M2L work list,
-    // which overlap the upward pass; events of the fork and the joins
+    // side stream (lowest priority) of the M2L work list and the near field,
+    // which overlap the main chain; events of the fork and the joins
+    // (ev_p2m: when the near field may start)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_p2m = nullptr, ev_items = nullptr, ev_near = nullptr;
     int32_t* block_sums = nullptr; // scan scratch
@@ -134,7 +135,9 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
 // of every level on the tensor cores with the slab reduction and the L2L
 // shifts level by level (L is complete once the second has run).
 cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s);
+// after_m2l (optional) is recorded on s right after the M2L kernel.
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s,
+                              cudaEvent_t after_m2l = nullptr);
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);

@@ -1417,7 +1417,8 @@ cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s) {
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s,
+                              cudaEvent_t after_m2l) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
     int64_t tiles;
@@ -1440,6 +1441,7 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStr
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if ((e = tc_launch(a, (unsigned)(sms > 0 ? sms : 152), smem, s)) != cudaSuccess) return e;
+    if (after_m2l && (e = cudaEventRecord(after_m2l, s)) != cudaSuccess) return e;
     const int64_t rg = tiles * kRedSlices;
     k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 16 ? rg : 152 * 16), 256, 0, s>>>(
         ws.ld, hdr, tl, (const float4*)ws.tc_part, (float4*)ws.L);
