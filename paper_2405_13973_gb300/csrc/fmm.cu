@@ -570,19 +570,23 @@ __global__ void __launch_bounds__(kNfThreads) k_p2p(
     }
 }
 
-// L2P (Eq. L2P) and the total field, one block per target leaf, one target
-// per 16-lane half-warp, lane m holding column m of the harmonics:
-//   * the diagonal Y^_m^m = prod_{k<=m} (x + i y) c_k is an inclusive prefix
-//     product over the lanes (4 shuffle steps instead of m serial ones);
-//   * all lanes then walk n = 0..p together, lane m stepping its column
-//     recurrence once n >= m, and adding the (n, m) terms of the potential
-//     and the gradient; L_{n+1,m+1} and L_{n+1,m-1} come from lanes m +- 1,
-//     which load L_{n+1,m'} for their own column anyway;
-//   * the column sums are added by a fixed shuffle tree (deterministic).
-// The leaf's local expansion is staged in shared memory; the near field (if
-// any) is added and the field written in the original ion order scaled to
-// SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
+// L2P (Eq. L2P) and the total field, one block per target leaf.
+//   * Per leaf, four derived expansions are formed in shared memory from the
+//     leaf's local expansion L: for every (n, m) a pair D_k(n, m) such that
+//     the potential and the three gradient components are sums over (n, m)
+//     of Re D_k Y^_n^m + Im D_k Im Y^_n^m -- the terms of l2p_eval regrouped
+//     by the harmonic they multiply (D_phi = w L_{n,m}; D_z = w e L_{n+1,m};
+//     D_x, D_y from f L_{n+1,m+1} and g L_{n+1,m-1}).  The leaf's ~10 targets
+//     share them.
+//   * One target per 16-lane half-warp, lane m holding column m: the
+//     diagonal Y^_m^m = prod_{k<=m} (x + i y) c_k is an inclusive prefix
+//     product over the lanes (4 shuffle steps), then lane m runs its column
+//     recurrence n = m..p adding four dot products per step; a fixed shuffle
+//     tree sums the columns (deterministic).
+// The near field (if any) is added and the field written in the original ion
+// order scaled to SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
 constexpr int kL2pThreads = 256;
+constexpr int kPmax = (kMaxOrder + 1) * (kMaxOrder + 1);
 
 template <typename T>
 __device__ __forceinline__ const HarmTables<T>& gtab();
@@ -597,36 +601,77 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
     const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
-    __shared__ T sL[(kMaxOrder + 1) * (kMaxOrder + 1)];
+    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    if (g0 + (int)blockIdx.x >= g1) return;  // no leaf for this block
+    __shared__ T sL[kPmax];
+    __shared__ T sD[4][kPmax];  // derived expansions: phi, grad x, grad y, grad z
     __shared__ HarmTables<T> t;
+    __shared__ double s_f[2];
     {
         const int* src = reinterpret_cast<const int*>(&gtab<T>());
         int* dst = reinterpret_cast<int*>(&t);
         for (int i = threadIdx.x; i < (int)(sizeof(HarmTables<T>) / sizeof(int)); i += kL2pThreads)
             dst[i] = src[i];
     }
-    const int lane = threadIdx.x & 31, m = lane & 15;
-    const int slot_in_pass = threadIdx.x >> 4;        // target of this half-warp
-    constexpr int kPerPass = kL2pThreads / 16;
-    const unsigned hw_mask = 0xffffu << (lane & 16);  // this half-warp's lanes
-    const int P = (p + 1) * (p + 1);
-    const int lim = 1 << D;
     // SI scale factors, once per block: FP64 division is slow on this GPU,
     // and every thread computing them cost more than the L2P itself
-    __shared__ double s_f[2];
     if (threadIdx.x == 0) {
-        const double sl = root->side / (double)lim;
+        const double sl = root->side / (double)(1 << D);
         s_f[0] = kCoulomb / (sl * sl);
         s_f[1] = kCoulomb / sl;
     }
     __syncthreads();
     const T tE = (T)s_f[0], tP = (T)s_f[1];
-    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+    const int lane = threadIdx.x & 31, m = lane & 15;
+    const int slot_in_pass = threadIdx.x >> 4;        // target of this half-warp
+    constexpr int kPerPass = kL2pThreads / 16;
+    const unsigned hw_mask = 0xffffu << (lane & 16);  // this half-warp's lanes
+    const int C = p + 1, P = C * C;
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
-        __syncthreads();
+        __syncthreads();  // sL, sD free from the previous leaf
         if (far)
             for (int c = threadIdx.x; c < P; c += kL2pThreads) sL[c] = L[(int64_t)g * ld + c];
+        __syncthreads();
+        if (far)
+            for (int q = threadIdx.x; q < C * C; q += kL2pThreads) {
+                const int nn = q / C, mm = q % C;
+                if (mm > nn) continue;
+                const int k = re_idx(nn, mm);
+                const T w = mm > 0 ? T(2) : T(1);
+                T d0r = w * sL[k], d0i = mm > 0 ? w * sL[k + 1] : T(0);
+                T dxr = 0, dxi = 0, dyr = 0, dyi = 0, dzr = 0, dzi = 0;
+                if (nn + 1 <= p) {
+                    const int k1 = re_idx(nn + 1, mm);
+                    const T e = w * t.e[nn][mm];
+                    dzr = e * sL[k1];
+                    dzi = mm > 0 ? e * sL[k1 + 1] : T(0);
+                    const int k2 = re_idx(nn + 1, mm + 1);
+                    const T f = t.f[nn][mm], l2r = sL[k2], l2i = sL[k2 + 1];
+                    dxr = f * l2r;
+                    dxi = f * l2i;
+                    dyr = f * l2i;
+                    dyi = -f * l2r;
+                    if (mm >= 1) {
+                        const int k3 = re_idx(nn + 1, mm - 1);
+                        const T gg = t.g[nn][mm], l3r = sL[k3], l3i = mm - 1 > 0 ? sL[k3 + 1] : T(0);
+                        dxr -= gg * l3r;
+                        dxi -= gg * l3i;
+                        dyr += gg * l3i;
+                        dyi -= gg * l3r;
+                    }
+                }
+                sD[0][k] = d0r;
+                sD[1][k] = dxr;
+                sD[2][k] = dyr;
+                sD[3][k] = dzr;
+                if (mm > 0) {  // for m = 0 the imaginary parts meet Im Y = 0
+                    sD[0][k + 1] = d0i;
+                    sD[1][k + 1] = dxi;
+                    sD[2][k + 1] = dyi;
+                    sD[3][k + 1] = dzi;
+                }
+            }
         __syncthreads();
         for (int t0 = 0; t0 < nt; t0 += kPerPass) {
             const int ti = t0 + slot_in_pass;
@@ -648,60 +693,40 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
                         dre = r;
                     }
                 }
-                const T r2 = x * x + y * y + z * z;
-                const T w = m > 0 ? T(2) : T(1);
-                T yr = 0, yi = 0, y1r = 0, y1i = 0;  // Y_n^m and Y_{n-1}^m
-                T ax = 0, ay = 0, az = 0;
-                T lr = 0, li = 0;                    // L_{n,m}, carried from the previous n
-                if (m == 0) lr = sL[0];
-                for (int nn = 0; nn <= p; ++nn) {
-                    // this lane's column: L_{n+1,m}
-                    T l1r = 0, l1i = 0;
-                    if (nn + 1 <= p && m <= nn + 1 && m <= p) {
-                        const int k1 = re_idx(nn + 1, m);
-                        l1r = sL[k1];
-                        l1i = m > 0 ? sL[k1 + 1] : T(0);
-                    }
-                    // neighbours' columns: L_{n+1,m+1} and L_{n+1,m-1}
-                    const T l2r = __shfl_down_sync(hw_mask, l1r, 1, 16);
-                    const T l2i = __shfl_down_sync(hw_mask, l1i, 1, 16);
-                    const T l3r = __shfl_up_sync(hw_mask, l1r, 1, 16);
-                    const T l3i = __shfl_up_sync(hw_mask, l1i, 1, 16);
-                    if (m <= nn && m <= p) {
-                        // Y_n^m by the column recurrence
-                        T cr, ci;
-                        if (nn == m) {
-                            cr = dre;
-                            ci = dim;
-                        } else if (nn == m + 1) {
-                            cr = z * t.d[m] * yr;
-                            ci = z * t.d[m] * yi;
-                        } else {
+                if (m <= p) {
+                    const T r2 = x * x + y * y + z * z;
+                    T yr = dre, yi = dim, y1r = 0, y1i = 0;  // Y_n^m, Y_{n-1}^m
+                    T ax = 0, ay = 0, az = 0;
+                    for (int nn = m; nn <= p; ++nn) {
+                        if (nn == m + 1) {
+                            y1r = yr;
+                            y1i = yi;
+                            yr = z * t.d[m] * y1r;
+                            yi = z * t.d[m] * y1i;
+                        } else if (nn > m + 1) {
                             const T a = t.a[nn][m] * z, b = t.b[nn][m] * r2;
-                            cr = a * yr - b * y1r;
-                            ci = a * yi - b * y1i;
+                            const T cr = a * yr - b * y1r, ci = a * yi - b * y1i;
+                            y1r = yr;
+                            y1i = yi;
+                            yr = cr;
+                            yi = ci;
                         }
-                        y1r = yr;
-                        y1i = yi;
-                        yr = cr;
-                        yi = ci;
-                        ph += w * (lr * yr + li * yi);
-                        if (nn + 1 <= p) {
-                            az += w * t.e[nn][m] * (l1r * yr + l1i * yi);
-                            ax += t.f[nn][m] * (l2r * yr + l2i * yi);
-                            ay += t.f[nn][m] * (l2i * yr - l2r * yi);
-                            if (m >= 1) {
-                                ax -= t.g[nn][m] * (l3r * yr + l3i * yi);
-                                ay -= t.g[nn][m] * (l3r * yi - l3i * yr);
-                            }
+                        const int k = re_idx(nn, m);
+                        ph += sD[0][k] * yr;
+                        ax += sD[1][k] * yr;
+                        ay += sD[2][k] * yr;
+                        az += sD[3][k] * yr;
+                        if (m > 0) {
+                            ph += sD[0][k + 1] * yi;
+                            ax += sD[1][k + 1] * yi;
+                            ay += sD[2][k + 1] * yi;
+                            az += sD[3][k + 1] * yi;
                         }
                     }
-                    lr = l1r;
-                    li = l1i;
+                    ex = -ax;
+                    ey = -ay;
+                    ez = -az;
                 }
-                ex = -ax;
-                ey = -ay;
-                ez = -az;
             }
             // column sums: a fixed shuffle tree over the half-warp
 #pragma unroll
