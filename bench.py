@@ -136,16 +136,19 @@ class ClockSampler:
 
 
 def launches_per_step(depth: int, precision: str) -> int:
-    # drift+cube, keys, leaf scan, scatter, cell scan, leaf gather, P2P, L2P,
-    # kick; each scan is one launch up to 65536 cells (depth <= 5), else three
-    k = 9 if depth <= 5 else 13
+    tc = precision in ("tf32x3", "bf16x3")
+    # drift + cube, keys, scatter, leaf gather, P2P, L2P, kick; the leaf and
+    # cell scans: one launch together while both fit one block (depth <= 5),
+    # else three each
+    k = 7 + (1 if depth <= 5 else 6)
     if depth >= 2:
-        k += 1 + (depth - 2)                 # P2M, M2M per level
-        if precision in ("tf32x3", "bf16x3"):
-            # M2M splits reduce per level, plan + items + M2L + tile reduce,
-            # L2L per level >= 3, and (BF16x3) the split of M into pieces
-            k += (depth - 2) + 4 + (depth - 2) + (1 if precision == "bf16x3" else 0)
+        if tc:
+            m2m = max(depth - 3, 0)          # P2M covers the leaves and their parents
+            k += 1 + 2 * m2m                 # P2M; M2M and its reduction per level
+            k += 4 + (depth - 2)             # plan, items, M2L, tile reduction; L2L per level
+            k += 1 if precision == "bf16x3" else 0   # split of M into bf16 pieces
         else:
+            k += 1 + (depth - 2)             # P2M, M2M per level
             k += depth - 1                   # M2L (+ folded L2L) per level
     return k
 

@@ -167,7 +167,7 @@ constexpr int kScan1Items = 8;
 constexpr int64_t kScan1Max = 65536;
 
 template <class Src>
-__global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t total) {
+__device__ __forceinline__ void scan_single_body(const Src& src, int64_t total) {
     __shared__ int warp_tot[kScan1Threads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int carry = 0;
@@ -210,6 +210,21 @@ __global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t 
         __syncthreads();
     }
     if (threadIdx.x == 0) src.finish(carry);
+}
+
+template <class Src>
+__global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t total) {
+    scan_single_body(src, total);
+}
+
+// Two dependent single-block scans in one launch: b's loads read what a's
+// stores wrote (made visible to the block by the barrier between them).
+template <class SrcA, class SrcB>
+__global__ void __launch_bounds__(kScan1Threads) k_scan_single2(SrcA a, int64_t total_a, SrcB b,
+                                                                 int64_t total_b) {
+    scan_single_body(a, total_a);
+    __syncthreads();
+    scan_single_body(b, total_b);
 }
 
 template <class Src>
@@ -370,9 +385,6 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
     k_keys<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(x, y, z, n, D, ws.root, ws.key, ws.rank,
                                                          ws.leaf_count);
     LeafCountScan ls{ws.leaf_count, ws.leaf_start, ncells};
-    if ((e = run_scan(ls, ncells, ws, s)) != cudaSuccess) return e;
-    k_scatter<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(ws.key, ws.rank, ws.leaf_start, n,
-                                                            ws.perm_tmp);
     DenseLayout dl = dense_layout(D);
     CellCompaction cc;
     cc.leaf_start = ws.leaf_start;
@@ -384,7 +396,17 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
     cc.D = D;
     cc.lmin = dl.lmin;
     for (int l = 0; l < kMaxDepth + 2; ++l) cc.off[l] = dl.off[l];
-    if ((e = run_scan(cc, dl.total, ws, s)) != cudaSuccess) return e;
+    // the cell compaction reads only the leaf starts: both scans in one
+    // single-block launch when they fit, then the scatter
+    if (ncells <= kScan1Max && dl.total <= kScan1Max) {
+        k_scan_single2<<<1, kScan1Threads, 0, s>>>(ls, ncells, cc, dl.total);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+        if ((e = run_scan(ls, ncells, ws, s)) != cudaSuccess) return e;
+        if ((e = run_scan(cc, dl.total, ws, s)) != cudaSuccess) return e;
+    }
+    k_scatter<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(ws.key, ws.rank, ws.leaf_start, n,
+                                                            ws.perm_tmp);
     const int grid_leaves = 152 * 8;
     if (ws.fp64)
         k_leaf_gather<double4_32a><<<grid_leaves, 128, 0, s>>>(
