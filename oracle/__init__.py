@@ -74,6 +74,9 @@ def lib():
             L.orc_step_damped.argtypes = L.orc_step.argtypes + [ctypes.c_double]
             L.orc_temperatures.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D]
             L.orc_energy_rot.argtypes = [_I64, _D, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double, _D]
+            L.orc_mh_scans.argtypes = [_I64, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                       _I64, _I64, _D]
             _lib = L
     return _lib
 
@@ -270,3 +273,16 @@ def energy_rot(pos, vel, q, trap, t):
     out = np.empty(4)
     lib().orc_energy_rot(len(q), *[_p(c) for c in cols], _p(q), _p(tr), float(t), _p(out))
     return out
+
+
+def mh_scans(pos, q, trap, temp, dx, seed, scan0, n_scans, wall_cs):
+    """Metropolis-Hastings potential-energy scans (returns new positions,
+    accepted moves, sum of the accepted energy changes in J).  wall_cs =
+    (cos w_r t, sin w_r t) of the state's time."""
+    x, y, z = (np.ascontiguousarray(pos[:, a], dtype=np.float64).copy() for a in range(3))
+    q = _f64(q)
+    out = np.empty(2)
+    lib().orc_mh_scans(len(q), _p(x), _p(y), _p(z), _p(q), _p(trap_array(trap)),
+                       float(wall_cs[0]), float(wall_cs[1]), float(temp), float(dx),
+                       int(seed) & (2**64 - 1), int(scan0), int(n_scans), _p(out))
+    return np.stack([x, y, z], axis=1), int(out[0]), float(out[1])

@@ -592,3 +592,97 @@ void orc_temperatures(int64_t n, const double* x, const double* y, const double*
     out[0] = m * acc_val(&a) / ((double)n * kb);
     out[1] = m * acc_val(&b) / (2.0 * (double)n * kb);
 }
+
+/* ======================================================================
+ * Metropolis-Hastings potential-energy initialisation (Sec. 4, the laser-
+ * cooling initialisation following Shankar et al. 2020): ions are visited in
+ * order; ion i is displaced by a distance uniform in [0, dx) in a uniformly
+ * random direction; with dE the change of the crystal's potential energy
+ * the move is kept if dE < 0, or else if u < exp(-dE / (k_B T)), u uniform in
+ * [0, 1); otherwise the ion goes back.  One scan visits every ion once.
+ *
+ * Potential energy (rotating frame at the state's time, wall phase given as
+ * (c, s) = (cos w_r t, sin w_r t)): per ion
+ *   U(x) = q k_z (2 z^2 - x^2 - y^2)/4 + (q B w_r - m w_r^2)(x^2 + y^2)/2
+ *        + q k_z delta (x_r^2 - y_r^2)/4,   x_r = c x - s y, y_r = s x + c y,
+ * plus the Coulomb pair energy; moving ion i from a to b changes it by
+ *   dE = (U(b) - U(a)) + k_e q_i sum_{j != i} q_j (1/|b - x_j| - 1/|a - x_j|)
+ * (the j sum in index order).
+ *
+ * Random numbers: the Philox stream of the photon kicks with the beam field
+ * set to 0xFF (no beam uses it), the scan index in place of the step:
+ *   ctr = (ion, 0xFF | (slot << 8), scan low, scan high), key = seed;
+ * slot 0: words (0,1) -> the distance fraction, words (2,3) -> u;
+ * slots 1, 2, ...: one (v1, v2) pair each for Marsaglia's disc pick of the
+ * direction (v in (-1,1)^2 until s = v1^2 + v2^2 < 1; direction
+ * (2 v1 sqrt(1-s), 2 v2 sqrt(1-s), 1 - 2 s)), at most 64 tries.
+ * The proposal depends on |b - a| only, so it is symmetric and the plain
+ * Metropolis test samples exp(-E / k_B T).
+ *
+ * Positions are updated in place; out[0] = accepted moves, out[1] = the sum
+ * of the accepted dE (J).
+ * ====================================================================== */
+void orc_mh_scans(int64_t n, double* x, double* y, double* z, const double* q,
+                  const double* trap, double c, double s, double temp, double dx, uint64_t seed,
+                  int64_t scan0, int64_t n_scans, double out[2]) {
+    const double m = trap[T_M], wr = trap[T_WR], B = trap[T_B], delta = trap[T_DELTA];
+    const double kz = m * trap[T_WZ] * trap[T_WZ] / trap[T_Q];
+    const double ke = orc_ke(), kb = 1.380649e-23;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    int64_t acc = 0;
+    double de_sum = 0.0;
+    for (int64_t sc = 0; sc < n_scans; ++sc) {
+        const uint64_t scan = (uint64_t)(scan0 + sc);
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t ctr[4] = {(uint32_t)i, 0xFFu, (uint32_t)scan, (uint32_t)(scan >> 32)};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            const double r = dx * orc_u01(w[0], w[1]);
+            const double u = orc_u01(w[2], w[3]);
+            double v1 = 0.0, v2 = 0.0, ss = 0.0;
+            for (uint32_t slot = 1; slot <= 64; ++slot) {
+                uint32_t c2[4] = {(uint32_t)i, 0xFFu | (slot << 8), (uint32_t)scan,
+                                  (uint32_t)(scan >> 32)};
+                orc_philox4x32_10(c2, key, w);
+                v1 = 2.0 * orc_u01(w[0], w[1]) - 1.0;
+                v2 = 2.0 * orc_u01(w[2], w[3]) - 1.0;
+                ss = v1 * v1 + v2 * v2;
+                if (ss < 1.0) break;
+            }
+            const double f = 2.0 * sqrt(1.0 - ss);
+            const double ax = x[i], ay = y[i], az = z[i];
+            const double bx = ax + r * (v1 * f), by = ay + r * (v2 * f), bz = az + r * (1.0 - 2.0 * ss);
+            /* external part */
+            double ua, ub;
+            {
+                const double xr = c * ax - s * ay, yr = s * ax + c * ay, r2 = ax * ax + ay * ay;
+                ua = 0.25 * q[i] * kz * (2.0 * az * az - r2) + 0.5 * (q[i] * B * wr - m * wr * wr) * r2 +
+                     0.25 * q[i] * kz * delta * (xr * xr - yr * yr);
+            }
+            {
+                const double xr = c * bx - s * by, yr = s * bx + c * by, r2 = bx * bx + by * by;
+                ub = 0.25 * q[i] * kz * (2.0 * bz * bz - r2) + 0.5 * (q[i] * B * wr - m * wr * wr) * r2 +
+                     0.25 * q[i] * kz * delta * (xr * xr - yr * yr);
+            }
+            /* Coulomb part, j in index order */
+            double sum = 0.0;
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const double dbx = bx - x[j], dby = by - y[j], dbz = bz - z[j];
+                const double dax = ax - x[j], day = ay - y[j], daz = az - z[j];
+                sum += q[j] * (1.0 / sqrt(dbx * dbx + dby * dby + dbz * dbz) -
+                               1.0 / sqrt(dax * dax + day * day + daz * daz));
+            }
+            const double dE = (ub - ua) + ke * q[i] * sum;
+            if (dE < 0.0 || u < orc_exp(-dE / (kb * temp))) {
+                x[i] = bx;
+                y[i] = by;
+                z[i] = bz;
+                ++acc;
+                de_sum += dE;
+            }
+        }
+    }
+    out[0] = (double)acc;
+    out[1] = de_sum;
+}
