@@ -305,6 +305,29 @@ const char* pt_status_str(int status);
 int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * pt_mh_scans -- Metropolis-Hastings initialisation of the potential energy
+ * (Sec. 4, the laser-cooling initialisation): n_scans scans; in each, ion i =
+ * 0..n-1 in turn is displaced by a distance uniform in [0, dx) in a uniformly
+ * random direction (Marsaglia's disc pick), and the move is kept if the
+ * crystal's rotating-frame potential energy (Eq. pe_rot at the state's time
+ * t, trap + rotating wall + Coulomb) falls, or else if u < exp(-dE /
+ * (k_B temperature)); otherwise the ion goes back.  Random numbers: the
+ * Philox stream of pt_laser_kicks with beam field 0xFF and the scan index
+ * scan0 + s in place of the step (resume = pass the next scan0).
+ *   st          : positions x, y, z updated in place (device); q read;
+ *                 velocities untouched.
+ *   temperature : K (> 0); dx: m (>= 0).
+ *   accepted    : host, the number of accepted moves, or NULL.
+ *   de_sum      : host, the sum of the accepted energy changes (J), or NULL.
+ * One 1024-thread block, FP64; the Coulomb change is summed over the other
+ * ions in parallel.  Synchronises the stream; calls on one device are
+ * serialised (they share a small device scratch).
+ * Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int pt_mh_scans(const pt_state* st, const pt_trap* trap, double temperature, double dx,
+                uint64_t seed, int64_t scan0, int64_t n_scans, int64_t* accepted, double* de_sum,
+                void* stream);
+
+/* ---------------------------------------------------------------------------
  * Diagnostics of a run (Sec. 5, Eqs. temps and rms_disp) and artificial
  * damping toward equilibria (Sec. 6: the crystal evolves under the trap
  * equations of motion while the ions' motion is slowly removed).

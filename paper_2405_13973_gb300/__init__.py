@@ -126,6 +126,9 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(_D), _VP]
         L.pt_position_moments.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                           _VP, _VP]
+        L.pt_mh_scans.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap), _D, _D,
+                                  ctypes.c_uint64, _I64, _I64, ctypes.POINTER(_I64),
+                                  ctypes.POINTER(_D), _VP]
         L.pt_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]
         L.pt_ensemble_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                        ctypes.POINTER(pt_laser), ctypes.POINTER(_D), _I64, _VP]
@@ -378,6 +381,21 @@ def temperatures(state: State, trap, stream=None):
     _check(load().pt_temperatures(ctypes.byref(st), ctypes.byref(tr), out, _stream(stream)),
            "pt_temperatures")
     return out[0], out[1]
+
+
+def mh_scans(state: State, trap, temperature: float, dx: float, seed: int, scan0: int,
+             n_scans: int, stream=None):
+    """Metropolis-Hastings potential-energy scans on the state's positions (in
+    place); returns (accepted moves, sum of the accepted energy changes in J)."""
+    st = state._c()
+    tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+    acc = _I64(0)
+    de = _D(0.0)
+    _check(load().pt_mh_scans(ctypes.byref(st), ctypes.byref(tr), float(temperature), float(dx),
+                              int(seed) & (2**64 - 1), int(scan0), int(n_scans),
+                              ctypes.byref(acc), ctypes.byref(de), _stream(stream)),
+           "pt_mh_scans")
+    return int(acc.value), float(de.value)
 
 
 def position_moments(state: State, trap, acc, stream=None):

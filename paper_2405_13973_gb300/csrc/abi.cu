@@ -1027,6 +1027,43 @@ int pt_temperatures(const pt_state* st, const pt_trap* trap, double* out, void* 
     return PT_OK;
 }
 
+int pt_mh_scans(const pt_state* st, const pt_trap* trap, double temperature, double dx,
+                uint64_t seed, int64_t scan0, int64_t n_scans, int64_t* accepted, double* de_sum,
+                void* stream) {
+    if (!st || !trap || st->n < 1 || !st->x || !st->y || !st->z || !st->q || !(trap->mass > 0) ||
+        trap->charge == 0.0 || !(temperature > 0) || !(dx >= 0) || n_scans < 0 || scan0 < 0)
+        return PT_ERR_ARG;
+    MhParams mp;
+    mp.c = cos(trap->omega_r * st->t);
+    mp.s = sin(trap->omega_r * st->t);
+    mp.kz = trap->mass * trap->omega_z * trap->omega_z / trap->charge;
+    mp.B = trap->B;
+    mp.wr = trap->omega_r;
+    mp.m = trap->mass;
+    mp.delta = trap->delta;
+    mp.ke = 1.0 / (4.0 * 3.14159265358979323846 * 8.8541878128e-12);
+    mp.kb = 1.380649e-23;
+    mp.temp = temperature;
+    mp.dx = dx;
+    mp.seed = seed;
+    std::lock_guard<std::mutex> g(g_diag_mu);
+    double* d = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&d, g_diag_scratch);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (e == cudaSuccess)
+        e = launch_mh_scans(st->n, st->x, st->y, st->z, st->q, mp, scan0, n_scans,
+                            (unsigned long long*)d, d + 1, s);
+    double h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_from(e);
+    unsigned long long a;
+    memcpy(&a, &h[0], sizeof a);
+    if (accepted) *accepted = (int64_t)a;
+    if (de_sum) *de_sum = h[1];
+    return PT_OK;
+}
+
 int pt_position_moments(const pt_state* st, const pt_trap* trap, double* acc, void* stream) {
     if (!st || !trap || !acc || st->n < 1 || !st->x || !st->y || !st->z) return PT_ERR_ARG;
     return status_from(launch_position_moments(st->n, *st, *trap, acc, (cudaStream_t)stream));

@@ -167,6 +167,18 @@ struct PushParams {
     double damp;       // exp(-gamma dt) of the rotating-frame velocity; 1 = no damping
     double wr;         // rotation frequency of the damping's rigid rotor
 };
+// ---- Metropolis-Hastings initialisation (mh.cu) --------------------------------
+struct MhParams {
+    double c, s;            // wall phase cos, sin(w_r t)
+    double kz, B, wr, m, delta;
+    double ke, kb;          // Coulomb and Boltzmann constants (J m / C^2, J / K)
+    double temp, dx;        // temperature (K), largest displacement (m)
+    uint64_t seed;
+};
+cudaError_t launch_mh_scans(int64_t n, double* x, double* y, double* z, const double* q,
+                            const MhParams& mp, int64_t scan0, int64_t n_scans,
+                            unsigned long long* acc_out, double* de_out, cudaStream_t s);
+
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s);
 cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
