@@ -1048,14 +1048,19 @@ int pt_mh_scans(const pt_state* st, const pt_trap* trap, double temperature, dou
     mp.seed = seed;
     std::lock_guard<std::mutex> g(g_diag_mu);
     double* d = nullptr;
+    double* scratch = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&d, g_diag_scratch);
     cudaStream_t s = (cudaStream_t)stream;
+    const size_t sb = mh_scratch_bytes(st->n);
+    if (e == cudaSuccess && sb > 0 && cudaMalloc((void**)&scratch, sb) != cudaSuccess)
+        return PT_ERR_OOM;
     if (e == cudaSuccess)
         e = launch_mh_scans(st->n, st->x, st->y, st->z, st->q, mp, scan0, n_scans,
-                            (unsigned long long*)d, d + 1, s);
+                            (unsigned long long*)d, d + 1, scratch, s);
     double h[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (scratch) cudaFree(scratch);
     if (e != cudaSuccess) return status_from(e);
     unsigned long long a;
     memcpy(&a, &h[0], sizeof a);

@@ -175,9 +175,12 @@ struct MhParams {
     double temp, dx;        // temperature (K), largest displacement (m)
     uint64_t seed;
 };
+// scratch: mh_scratch_bytes(n) of device memory (none needed for large n)
+size_t mh_scratch_bytes(int64_t n);
 cudaError_t launch_mh_scans(int64_t n, double* x, double* y, double* z, const double* q,
                             const MhParams& mp, int64_t scan0, int64_t n_scans,
-                            unsigned long long* acc_out, double* de_out, cudaStream_t s);
+                            unsigned long long* acc_out, double* de_out, double* scratch,
+                            cudaStream_t s);
 
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s);

@@ -6,7 +6,8 @@ energy are the same IEEE sequences on both sides; the Coulomb change is a
 parallel FP64 sum on the GPU and a sequential one in the oracle, so the two
 dE differ in the last bits only and every accept decision agrees unless a
 uniform falls within ~1e-16 of its threshold.  So positions and accept counts
-are compared exactly, and the sums of accepted energy changes to 1e-9.
+are compared exactly, and the sums of accepted energy changes to 1e-9.  Both
+kernels are covered: the 8-CTA cluster (up to 4096 ions) and one block.
 """
 import math
 
@@ -29,7 +30,7 @@ def crystal(n):
     return w["pos"], w["q"], dict(cr["trap"], delta=0.02)
 
 
-@pytest.mark.parametrize("n,scans", [(300, 3), (1500, 1)])
+@pytest.mark.parametrize("n,scans", [(300, 3), (1500, 2), (5000, 1)])  # cluster path up to 4096
 def test_mh_scans_match_the_oracle(n, scans):
     pos, q, trap = crystal(n)
     t = 3.7e-7
