@@ -22,7 +22,8 @@
  *   - the photon-scattering rate, Poisson counts and recoil kicks
  *     (Eqs. scattering_rate, laser_kick; Sec. 2.2);
  *   - the literal cyclotronic step U0(dt/2) Ukick U0(dt/2) (Eq. time_ev2);
- *   - the rotating-frame energy (Eq. rotation and Eq. pe_rot).
+ *   - the rotating-frame energy (Eq. rotation and Eq. pe_rot);
+ *   - the Metropolis-Hastings potential-energy initialisation (Sec. 4).
  *
  * Parity status: every function below is pinned by tests/test_oracle_*.py
  * against closed forms, a library routine, or brute force (see the tests).
