@@ -25,10 +25,13 @@
 // swizzled K-major shared-memory image of each 32-wide K chunk (128-byte
 // rows and swizzle for TF32, 64-byte rows and swizzle for BF16), so one
 // cp.async.bulk per (offset, chunk) brings every piece of B.  A rows are
-// gathered by all threads, split and stored into the same layout.  Up to
-// four stages: the loads of later chunks overlap the MMAs of chunk i.  One
-// thread issues tcgen05.mma (M = 128, N = P rounded up to 16, 32 bytes of K
-// per instruction) and commits to an mbarrier per stage.
+// gathered by 256 producer threads: for the BF16x3 M2L, M is split into its
+// bf16 pieces once per step (k_split_m) and the producers copy 16-byte units
+// of the pieces by cp.async.cg straight into the swizzled stage; in the
+// other modes they copy FP32 rows into a per-thread ring, split them and
+// store the pieces.  Up to four stages: the loads of later chunks overlap the
+// MMAs of chunk i.  One thread issues tcgen05.mma (M = 128, N = P rounded up
+// to 16, 32 bytes of K per instruction) and commits to an mbarrier per stage.
 //
 // The same gathered product serves the two other dense translations:
 //   M2M (upward pass): a tile of parents, 8 terms (child octants), A = the
@@ -36,9 +39,13 @@
 //   L2L (downward pass): a tile of children of one octant, 1 term, A = the
 //     parent's L, B = the octant's L2L operator, and the epilogue adds the
 //     child's own M2L result (and the split partials).
-// Parallelism: one M2L launch covers every level; the 189 offsets of a tile
-// are split S ways across CTAs.  Split 0 writes L; splits 1.. write partial
-// buffers that the L2L launches add, level by level.
+// Parallelism: one persistent M2L launch (a CTA per SM) covers every level
+// and walks a device work list: per tile its non-empty offsets (k_tc_plan)
+// cut into runs of at most four (k_tc_items; the tensor-core accumulation
+// rounds with a bias that grows with the products summed into one
+// accumulator).  The first run of a tile writes L, the others write partial
+// slabs that k_tc_reduce_tiles adds in run order (deterministic); then the
+// L2L launches shift level by level.
 //
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // ERR_TIMEOUT, stops issuing, waits (bounded) for its own work in flight,
