@@ -1,6 +1,8 @@
-// fmm.cu -- the FMM stages on the CUDA cores (Sec. 2.3.2).
+// fmm.cu -- the FMM stages on the CUDA cores (Sec. 2.3.2) and the order of
+// one evaluation's launches (run_fmm: main chain and side stream).
 //
-// Upward pass: P2M at the leaves (Eq. FMM_coul2), M2M to the parents.
+// Upward pass: P2M at the leaves (Eq. FMM_coul2; on the tensor-core path
+// also at the leaves' parents, straight from their ions), M2M to the parents.
 // Downward pass: at every level l >= 2 the local expansion of a cell is the
 // L2L shift of its parent's plus the M2L conversion (Eq. FMM_local) of the
 // multipole expansions of the 189 cells that are children of the parent's
