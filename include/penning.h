@@ -319,10 +319,12 @@ int fmm_tree_info(fmm_plan plan, double* root, int32_t* perm, uint32_t* keys, vo
  *   temperature : K (> 0); dx: m (>= 0).
  *   accepted    : host, the number of accepted moves, or NULL.
  *   de_sum      : host, the sum of the accepted energy changes (J), or NULL.
- * One 1024-thread block, FP64; the Coulomb change is summed over the other
- * ions in parallel.  Synchronises the stream; calls on one device are
- * serialised (they share a small device scratch).
- * Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+ * FP64.  Up to 4096 ions: a cluster of 8 CTAs (the Coulomb change of each
+ * move summed over the other ions by all of them), with a device scratch of
+ * 40 B per ion allocated for the call; larger crystals: one 1024-thread
+ * block.  Synchronises the stream; calls on one device are serialised (they
+ * share a small device result buffer).
+ * Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
 int pt_mh_scans(const pt_state* st, const pt_trap* trap, double temperature, double dx,
                 uint64_t seed, int64_t scan0, int64_t n_scans, int64_t* accepted, double* de_sum,
                 void* stream);
