@@ -45,7 +45,7 @@ typedef enum {
     PT_ERR_ESCAPED = -5,     /* reserved: ion outside the plan's domain */
     PT_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
     PT_ERR_COINCIDENT = -7,  /* reserved: two ions at the same point */
-    PT_ERR_UNSUPPORTED = -8  /* this build or device lacks the feature */
+    PT_ERR_UNSUPPORTED = -8  /* the library or the device lacks the feature */
 } pt_status;
 
 /* Arithmetic of the FMM (positions, velocities and the push are FP64 in
