@@ -597,16 +597,117 @@ __device__ __forceinline__ const HarmTables<double>& gtab<double>() { return g_t
 template <>
 __device__ __forceinline__ const HarmTables<float>& gtab<float>() { return g_tab_f; }
 
+// the derived expansions of one local expansion Lr (see k_l2p) into D4[4][P]
+template <typename T>
+__device__ __forceinline__ void l2p_derive(int p, const T* Lr, const HarmTables<T>& t, T (*D4)[kPmax]) {
+    const int C = p + 1;
+    for (int q = threadIdx.x; q < C * C; q += kL2pThreads) {
+        const int nn = q / C, mm = q % C;
+        if (mm > nn) continue;
+        const int k = re_idx(nn, mm);
+        const T w = mm > 0 ? T(2) : T(1);
+        T d0r = w * Lr[k], d0i = mm > 0 ? w * Lr[k + 1] : T(0);
+        T dxr = 0, dxi = 0, dyr = 0, dyi = 0, dzr = 0, dzi = 0;
+        if (nn + 1 <= p) {
+            const int k1 = re_idx(nn + 1, mm);
+            const T e = w * t.e[nn][mm];
+            dzr = e * Lr[k1];
+            dzi = mm > 0 ? e * Lr[k1 + 1] : T(0);
+            const int k2 = re_idx(nn + 1, mm + 1);
+            const T f = t.f[nn][mm], l2r = Lr[k2], l2i = Lr[k2 + 1];
+            dxr = f * l2r;
+            dxi = f * l2i;
+            dyr = f * l2i;
+            dyi = -f * l2r;
+            if (mm >= 1) {
+                const int k3 = re_idx(nn + 1, mm - 1);
+                const T gg = t.g[nn][mm], l3r = Lr[k3], l3i = mm - 1 > 0 ? Lr[k3 + 1] : T(0);
+                dxr -= gg * l3r;
+                dxi -= gg * l3i;
+                dyr += gg * l3i;
+                dyi -= gg * l3r;
+            }
+        }
+        D4[0][k] = d0r;
+        D4[1][k] = dxr;
+        D4[2][k] = dyr;
+        D4[3][k] = dzr;
+        if (mm > 0) {  // for m = 0 the imaginary parts meet Im Y = 0
+            D4[0][k + 1] = d0i;
+            D4[1][k + 1] = dxi;
+            D4[2][k + 1] = dyi;
+            D4[3][k + 1] = dzi;
+        }
+    }
+}
+
+// column m of the potential and gradient at (x, y, z) from derived
+// expansions D4; every lane of the half-warp calls it (the prefix product
+// shuffles), lanes m > p return zeros
+template <typename T>
+__device__ __forceinline__ void l2p_columns(int p, int m, unsigned hw_mask, T x, T y, T z,
+                                            const HarmTables<T>& t, const T (*D4)[kPmax], T& ph,
+                                            T& ax, T& ay, T& az) {
+    // diagonal: inclusive prefix product of (x + i y) c_k over k = 1..m
+    T dre = m == 0 ? T(1) : x * t.c[m <= p ? m : 0];
+    T dim = m == 0 ? T(0) : y * t.c[m <= p ? m : 0];
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        const T ore = __shfl_up_sync(hw_mask, dre, off, 16);
+        const T oim = __shfl_up_sync(hw_mask, dim, off, 16);
+        if (m >= off) {
+            const T r = ore * dre - oim * dim;
+            dim = ore * dim + oim * dre;
+            dre = r;
+        }
+    }
+    ph = ax = ay = az = T(0);
+    if (m > p) return;
+    const T r2 = x * x + y * y + z * z;
+    T yr = dre, yi = dim, y1r = 0, y1i = 0;  // Y_n^m, Y_{n-1}^m
+    for (int nn = m; nn <= p; ++nn) {
+        if (nn == m + 1) {
+            y1r = yr;
+            y1i = yi;
+            yr = z * t.d[m] * y1r;
+            yi = z * t.d[m] * y1i;
+        } else if (nn > m + 1) {
+            const T a = t.a[nn][m] * z, b = t.b[nn][m] * r2;
+            const T cr = a * yr - b * y1r, ci = a * yi - b * y1i;
+            y1r = yr;
+            y1i = yi;
+            yr = cr;
+            yi = ci;
+        }
+        const int k = re_idx(nn, m);
+        ph += D4[0][k] * yr;
+        ax += D4[1][k] * yr;
+        ay += D4[2][k] * yr;
+        az += D4[3][k] * yr;
+        if (m > 0) {
+            ph += D4[0][k + 1] * yi;
+            ax += D4[1][k + 1] * yi;
+            ay += D4[2][k + 1] * yi;
+            az += D4[3][k + 1] * yi;
+        }
+    }
+}
+
+// nlev = 2: the leaf's expansion holds its own M2L sum only, and the
+// parent's complete expansion is evaluated at the ion in the parent's frame
+// (equal to the L2L shift into the leaf, which shifts a truncated expansion
+// exactly), saving the last L2L launch.
 template <typename T>
 __global__ void __launch_bounds__(kL2pThreads) k_l2p(
-    int64_t n, int D, int p, int ld, bool far, const RootCube* root, const LevelInfo* linfo,
+    int64_t n, int D, int p, int ld, bool far, int nlev, const RootCube* root,
+    const LevelInfo* linfo, const uint32_t* __restrict__ code, const int32_t* __restrict__ cid,
     const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
     const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
     if (g0 + (int)blockIdx.x >= g1) return;  // no leaf for this block
-    __shared__ T sL[kPmax];
-    __shared__ T sD[4][kPmax];  // derived expansions: phi, grad x, grad y, grad z
+    __shared__ T sL[2][kPmax];
+    __shared__ T sD[2][4][kPmax];  // derived expansions: phi, grad x, grad y, grad z
     __shared__ HarmTables<T> t;
     __shared__ double s_f[2];
     {
@@ -628,107 +729,38 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     const int slot_in_pass = threadIdx.x >> 4;        // target of this half-warp
     constexpr int kPerPass = kL2pThreads / 16;
     const unsigned hw_mask = 0xffffu << (lane & 16);  // this half-warp's lanes
-    const int C = p + 1, P = C * C;
+    const int P = (p + 1) * (p + 1);
+    const int levs = far ? nlev : 0;
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
+        const uint32_t cl = code[g];
+        int ix, iy, iz;
+        demorton3(cl, ix, iy, iz);
         __syncthreads();  // sL, sD free from the previous leaf
-        if (far)
-            for (int c = threadIdx.x; c < P; c += kL2pThreads) sL[c] = L[(int64_t)g * ld + c];
+        for (int lv = 0; lv < levs; ++lv) {
+            // dense maps of levels 2.. concatenated: level l starts at (8^l - 64) / 7
+            const int ga = lv == 0 ? g : cid[(((1ll << (3 * (D - 1))) - 64) / 7) + (cl >> 3)];
+            for (int c = threadIdx.x; c < P; c += kL2pThreads) sL[lv][c] = L[(int64_t)ga * ld + c];
+        }
         __syncthreads();
-        if (far)
-            for (int q = threadIdx.x; q < C * C; q += kL2pThreads) {
-                const int nn = q / C, mm = q % C;
-                if (mm > nn) continue;
-                const int k = re_idx(nn, mm);
-                const T w = mm > 0 ? T(2) : T(1);
-                T d0r = w * sL[k], d0i = mm > 0 ? w * sL[k + 1] : T(0);
-                T dxr = 0, dxi = 0, dyr = 0, dyi = 0, dzr = 0, dzi = 0;
-                if (nn + 1 <= p) {
-                    const int k1 = re_idx(nn + 1, mm);
-                    const T e = w * t.e[nn][mm];
-                    dzr = e * sL[k1];
-                    dzi = mm > 0 ? e * sL[k1 + 1] : T(0);
-                    const int k2 = re_idx(nn + 1, mm + 1);
-                    const T f = t.f[nn][mm], l2r = sL[k2], l2i = sL[k2 + 1];
-                    dxr = f * l2r;
-                    dxi = f * l2i;
-                    dyr = f * l2i;
-                    dyi = -f * l2r;
-                    if (mm >= 1) {
-                        const int k3 = re_idx(nn + 1, mm - 1);
-                        const T gg = t.g[nn][mm], l3r = sL[k3], l3i = mm - 1 > 0 ? sL[k3 + 1] : T(0);
-                        dxr -= gg * l3r;
-                        dxi -= gg * l3i;
-                        dyr += gg * l3i;
-                        dyi -= gg * l3r;
-                    }
-                }
-                sD[0][k] = d0r;
-                sD[1][k] = dxr;
-                sD[2][k] = dyr;
-                sD[3][k] = dzr;
-                if (mm > 0) {  // for m = 0 the imaginary parts meet Im Y = 0
-                    sD[0][k + 1] = d0i;
-                    sD[1][k + 1] = dxi;
-                    sD[2][k + 1] = dyi;
-                    sD[3][k + 1] = dzi;
-                }
-            }
+        for (int lv = 0; lv < levs; ++lv) l2p_derive<T>(p, sL[lv], t, sD[lv]);
         __syncthreads();
         for (int t0 = 0; t0 < nt; t0 += kPerPass) {
             const int ti = t0 + slot_in_pass;
             if (ti >= nt) continue;  // whole half-warps only: the shuffles stay within one
             T ex = 0, ey = 0, ez = 0, ph = 0;
-            if (far) {
+            const typename Ion<T>::rec me = sorted[ts + ti];
+            for (int lv = 0; lv < levs; ++lv) {
                 T x, y, z, q;
-                Ion<T>::get(sorted[ts + ti], x, y, z, q);
-                // diagonal: inclusive prefix product of (x + i y) c_k over k = 1..m
-                T dre = m == 0 ? T(1) : x * t.c[m <= p ? m : 0];
-                T dim = m == 0 ? T(0) : y * t.c[m <= p ? m : 0];
-#pragma unroll
-                for (int off = 1; off < 16; off <<= 1) {
-                    const T ore = __shfl_up_sync(hw_mask, dre, off, 16);
-                    const T oim = __shfl_up_sync(hw_mask, dim, off, 16);
-                    if (m >= off) {
-                        const T r = ore * dre - oim * dim;
-                        dim = ore * dim + oim * dre;
-                        dre = r;
-                    }
-                }
-                if (m <= p) {
-                    const T r2 = x * x + y * y + z * z;
-                    T yr = dre, yi = dim, y1r = 0, y1i = 0;  // Y_n^m, Y_{n-1}^m
-                    T ax = 0, ay = 0, az = 0;
-                    for (int nn = m; nn <= p; ++nn) {
-                        if (nn == m + 1) {
-                            y1r = yr;
-                            y1i = yi;
-                            yr = z * t.d[m] * y1r;
-                            yi = z * t.d[m] * y1i;
-                        } else if (nn > m + 1) {
-                            const T a = t.a[nn][m] * z, b = t.b[nn][m] * r2;
-                            const T cr = a * yr - b * y1r, ci = a * yi - b * y1i;
-                            y1r = yr;
-                            y1i = yi;
-                            yr = cr;
-                            yi = ci;
-                        }
-                        const int k = re_idx(nn, m);
-                        ph += sD[0][k] * yr;
-                        ax += sD[1][k] * yr;
-                        ay += sD[2][k] * yr;
-                        az += sD[3][k] * yr;
-                        if (m > 0) {
-                            ph += sD[0][k + 1] * yi;
-                            ax += sD[1][k + 1] * yi;
-                            ay += sD[2][k + 1] * yi;
-                            az += sD[3][k + 1] * yi;
-                        }
-                    }
-                    ex = -ax;
-                    ey = -ay;
-                    ez = -az;
-                }
+                ion_in_ancestor(me, lv, ix & lv, iy & lv, iz & lv, x, y, z, q);
+                T cph, cax, cay, caz;
+                l2p_columns<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
+                // level units -> leaf units: phi / 2^lv, E / 4^lv (exact)
+                const T fp1 = lv == 0 ? T(1) : T(0.5), fe1 = fp1 * fp1;
+                ph += fp1 * cph;
+                ex -= fe1 * cax;
+                ey -= fe1 * cay;
+                ez -= fe1 * caz;
             }
             // column sums: a fixed shuffle tree over the half-warp
 #pragma unroll
@@ -932,8 +964,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         return e;
     if (far && use_tc) {
         if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
-        if ((e = launch_m2l_tc_run(n, D, ws, !direct, s, near_late ? ws.ev_p2m : nullptr)) !=
-            cudaSuccess)
+        // L2L down to the leaves' parents; the leaves' L2P evaluates the
+        // parent's expansion itself (direct mode: no L2L at all)
+        if ((e = launch_m2l_tc_run(n, D, ws, direct ? 2 : D - 1, s,
+                                   near_late ? ws.ev_p2m : nullptr)) != cudaSuccess)
             return e;
         if (nf && near_late && (e = launch_near(true)) != cudaSuccess) return e;
     } else if (far) {
@@ -955,10 +989,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
             (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
             nf ? near : nullptr, E, phi);
     else
-        k_l2p<T><<<leaf_grid, kL2pThreads, 0, s>>>(n, D, p, ws.ld, far, ws.root, ws.linfo,
-                                                  (const typename Ion<T>::rec*)ws.sorted, ws.perm,
-                                                  ws.cstart, ws.ccount, L, nf ? near : nullptr, E,
-                                                  phi);
+        k_l2p<T><<<leaf_grid, kL2pThreads, 0, s>>>(
+            n, D, p, ws.ld, far, use_tc && D >= 3 ? 2 : 1, ws.root, ws.linfo, ws.code, ws.cid,
+            (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
+            nf ? near : nullptr, E, phi);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;

@@ -1424,7 +1424,7 @@ cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStream_t s,
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s,
                               cudaEvent_t after_m2l) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
@@ -1453,8 +1453,9 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, bool l2l, cudaStr
     k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 16 ? rg : 152 * 16), 256, 0, s>>>(
         ws.ld, hdr, tl, (const float4*)ws.tc_part, (float4*)ws.L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // L2L shifts level by level (level 2 has no parent expansion)
-    for (int l = 3; l2l && l <= D; ++l) {
+    // L2L shifts level by level, levels 3 .. l2l_last (level 2 has no parent
+    // expansion)
+    for (int l = 3; l <= l2l_last && l <= D; ++l) {
         TcArgs b = base_args(n, D, ws, 1);
         b.mode = MODE_L2L;
         b.level = l;
