@@ -145,7 +145,8 @@ def launches_per_step(depth: int, precision: str) -> int:
         if tc:
             m2m = max(depth - 3, 0)          # P2M covers the leaves and their parents
             k += 1 + 2 * m2m                 # P2M; M2M and its reduction per level
-            k += 4 + (depth - 2)             # plan, items, M2L, tile reduction; L2L per level
+            k += 4 + max(depth - 3, 0)       # plan, items, M2L, tile reduction; L2L per level
+                                             # down to the leaves' parents
             k += 1 if precision == "bf16x3" else 0   # split of M into bf16 pieces
         else:
             k += 1 + (depth - 2)             # P2M, M2M per level
