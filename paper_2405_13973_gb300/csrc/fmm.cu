@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kNfThreads) k_p2p(
 //   * Per leaf, four derived expansions are formed in shared memory from the
 //     leaf's local expansion L: for every (n, m) a pair D_k(n, m) such that
 //     the potential and the three gradient components are sums over (n, m)
-//     of Re D_k Y^_n^m + Im D_k Im Y^_n^m -- the terms of l2p_eval regrouped
+//     of Re D_k Y^_n^m + Im D_k Im Y^_n^m -- the terms of l2p_eval_cols regrouped
 //     by the harmonic they multiply (D_phi = w L_{n,m}; D_z = w e L_{n+1,m};
 //     D_x, D_y from f L_{n+1,m+1} and g L_{n+1,m-1}).  The leaf's ~10 targets
 //     share them.

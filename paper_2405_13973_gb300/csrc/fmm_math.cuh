@@ -78,17 +78,9 @@ PT_HD void for_each_ups_cols(int p, T x, T y, T z, const HarmTables<T>& t, int m
     }
 }
 
-template <typename T>
-PT_HD void p2m_ion(int p, T x, T y, T z, T q, const HarmTables<T>& t, T* Mh) {
-    for_each_ups(p, x, y, z, t, [&](int n, int m, T re, T im) {
-        int k = re_idx(n, m);
-        Mh[k] += q * re;
-        if (m > 0) Mh[k + 1] -= q * im;
-    });
-}
-
 // L2P over the columns m0, m0 + mstep, ... of the local expansion (see
-// for_each_ups_cols); summing the mstep parts gives l2p_eval.
+// for_each_ups_cols); summing the mstep parts gives the whole L2P (Eq. L2P):
+// the potential and the gradient of the local expansion at (x, y, z).
 template <typename T>
 PT_HD void l2p_eval_cols(int p, const T* Lh, T x, T y, T z, const HarmTables<T>& t, int m0,
                          int mstep, T& phi, T& gx, T& gy, T& gz) {
@@ -109,39 +101,6 @@ PT_HD void l2p_eval_cols(int p, const T* Lh, T x, T y, T z, const HarmTables<T>&
             if (m >= 1) {
                 int k3 = re_idx(n + 1, m - 1);
                 T l3r = Lh[k3], l3i = (m - 1) > 0 ? Lh[k3 + 1] : T(0);
-                ax -= t.g[n][m] * (l3r * yr + l3i * yi);
-                ay -= t.g[n][m] * (l3r * yi - l3i * yr);
-            }
-        }
-    });
-    phi = ph;
-    gx = ax;
-    gy = ay;
-    gz = az;
-}
-
-template <typename T>
-PT_HD void l2p_eval(int p, const T* Lh, T x, T y, T z, const HarmTables<T>& t, T& phi, T& gx,
-                    T& gy, T& gz) {
-    T ph = 0, ax = 0, ay = 0, az = 0;
-    for_each_ups(p, x, y, z, t, [&](int n, int m, T yr, T yi) {
-        int k = re_idx(n, m);
-        T lr = Lh[k], li = m > 0 ? Lh[k + 1] : T(0);
-        T w = m > 0 ? T(2) : T(1);
-        ph += w * (lr * yr + li * yi);
-        if (n + 1 <= p) {
-            int k1 = re_idx(n + 1, m);
-            T l1r = Lh[k1], l1i = m > 0 ? Lh[k1 + 1] : T(0);
-            az += w * t.e[n][m] * (l1r * yr + l1i * yi);
-            int k2 = re_idx(n + 1, m + 1);
-            T l2r = Lh[k2], l2i = Lh[k2 + 1];
-            // L2 conj(Y)
-            ax += t.f[n][m] * (l2r * yr + l2i * yi);
-            ay += t.f[n][m] * (l2i * yr - l2r * yi);
-            if (m >= 1) {
-                int k3 = re_idx(n + 1, m - 1);
-                T l3r = Lh[k3], l3i = (m - 1) > 0 ? Lh[k3 + 1] : T(0);
-                // - conj(L3) Y
                 ax -= t.g[n][m] * (l3r * yr + l3i * yi);
                 ay -= t.g[n][m] * (l3r * yi - l3i * yr);
             }
