@@ -14,6 +14,14 @@ on the launching stream, with a 512 MiB write between steps to flush the
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|tf32x3|bf16x3|fp64] [--p P] [--p10-steps K10]
+                  [--forces N] [--config1-steps K1] [--sweep N1,N2,...]
+
+The default line also carries, as extra keys, the 1,000-ion FP64 run
+(1,000 steps at p = 8, oracle timed in the same run: "config1") and the
+single-evaluation sweep over ion counts, orders and precisions with errors
+against the FP64 direct sum ("sweep").  --forces N times only single force
+evaluations of the N-ion sweep sphere (--p, --precision) and prints their
+line (the command the kernel profiles are taken with).
 
 --impl reference times the FP64 CPU oracle (direct O(N^2) Coulomb sum and
 the literal step) on the host cores, one oracle step per benchmark step.
@@ -320,6 +328,151 @@ def serve_arm(args, rank):
     return 0
 
 
+def sweep_reference(pt, torch, w, n_sample=512):
+    """FP64 reference field of a sweep sphere: the GPU direct sum (pinned to
+    the oracle's to 1e-13) up to 1e5 ions, else the oracle's direct sum at a
+    seeded sample of n_sample ions.  Returns (E_ref (n_s, 3), sample index or
+    None, what)."""
+    pos, q = w["pos"], w["q"]
+    n = len(q)
+    if n <= 100000:
+        pd = torch.tensor(np.ascontiguousarray(pos.T), dtype=torch.float64, device="cuda")
+        qd = torch.tensor(q, dtype=torch.float64, device="cuda")
+        E, _ = pt.direct(pd, qd, want_phi=False)
+        return E.cpu().numpy().T, None, "FP64 GPU direct sum, every ion"
+    import oracle
+    idx = np.sort(np.random.default_rng(7).choice(n, n_sample, replace=False))
+    Eo, _ = oracle.coulomb_targets(pos, q, idx, want_phi=False)
+    return Eo, idx, f"FP64 oracle direct sum at {n_sample} sampled ions"
+
+
+def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=1):
+    """Single force evaluations (config-3 sweep point): mean CUDA-event time
+    of `steps` evaluations (L2 flushed before each) and the relative RMS force
+    error against ref."""
+    pos, q = w["pos"], w["q"]
+    n = len(q)
+    pd = torch.tensor(np.ascontiguousarray(pos.T), dtype=torch.float64, device="cuda")
+    qd = torch.tensor(q, dtype=torch.float64, device="cuda")
+    try:
+        plan = pt.Plan(n, p=p, leaf_max=32, depth=-1, precision=precision)
+    except pt.PenningError as exc:
+        return {"status": str(exc)}
+    E = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        plan.forces(pd, qd, E=E, want_phi=False)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.forces(pd, qd, E=E, want_phi=False)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    out = {"ms": float(np.mean(ms)), "evals_per_s": 1e3 / float(np.mean(ms)),
+           "ion_evals_per_s": n * 1e3 / float(np.mean(ms)), "depth": plan.last_depth}
+    if ref is not None:
+        Er, idx, _ = ref
+        e = E.cpu().numpy().T
+        if idx is not None:
+            e = e[idx]
+        out["force_err"] = float(np.sqrt(((e - Er) ** 2).sum() / (Er ** 2).sum()))
+    plan.close()
+    return out
+
+
+def sweep_arm(pt, torch, ns, ps, precisions, flush, steps=2):
+    """Config-3 sweep: N uniform in a sphere at 2e14 m^-3 plus 1% jitter, one
+    force evaluation per point, errors against sweep_reference."""
+    res = {}
+    for n in ns:
+        w = W.sphere_sweep(n)
+        ref = sweep_reference(pt, torch, w)
+        row = {"reference": ref[2]}
+        for p in ps:
+            for prec in precisions:
+                k = steps if n <= 100000 or prec != "fp64" else 1
+                row[f"{prec}_p{p}"] = force_eval_point(pt, torch, w, p, prec, k, flush, ref)
+        res[str(n)] = row
+        torch.cuda.empty_cache()
+    return res
+
+
+def config1_arm(pt, torch, steps, flush, with_oracle=True):
+    """Config 1: N = 1,000 uniform in a 100 um sphere, rotating 10 mK
+    Maxwellian, FP64, p = 8, leaf <= 32, dt = 1 ns, cooling off; `steps`
+    steps timed on the GPU (one replayed step graph per step) beside the same
+    steps of the FP64 oracle on the host cores.  Checked: the initial force
+    error against the oracle's direct sum and the energies of the two final
+    states (Error_en, Eq. rms_en)."""
+    import oracle
+    cr = W.crystal_sphere_1k()
+    pos, vel, q, tr = cr["pos"], cr["vel"], cr["q"], cr["trap"]
+    n = len(q)
+    plan = pt.Plan(n, p=8, leaf_max=32, depth=-1, precision="fp64")
+    pd = torch.tensor(np.ascontiguousarray(pos.T), dtype=torch.float64, device="cuda")
+    qd = torch.tensor(q, dtype=torch.float64, device="cuda")
+    E, _ = plan.forces(pd, qd, want_phi=False)
+    Eo, _ = oracle.coulomb_direct(pos, q, want_phi=False)
+    ferr = float(np.sqrt(((E.cpu().numpy().T - Eo) ** 2).sum() / (Eo ** 2).sum()))
+    st = pt.State.from_numpy(pos, vel, q)
+    trap = pt.make_trap(tr)
+    plan.step(st, trap, None, cr["dt"], 1)       # captures the step graph
+    st = pt.State.from_numpy(pos, vel, q)
+    flush()
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plan.step_async(st, trap, None, cr["dt"], steps)
+    b.record(stream)
+    b.synchronize()
+    plan.sync()
+    ms = a.elapsed_time(b)
+    out = {"workload": f"sphere 100 um, N={n}, FP64, p=8, leaf<=32, dt=1ns, cooling off, "
+                       f"{steps} steps", "value": n * steps / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms / steps, "force_err_vs_oracle": ferr, "depth": plan.last_depth}
+    if with_oracle:
+        t0 = time.perf_counter()
+        po, vo = oracle.step(pos, vel, q, tr, cr["dt"], steps)
+        el = time.perf_counter() - t0
+        eg = pt.energy(st, trap)[3]
+        eo = oracle.energy_rot(po, vo, q, tr, steps * cr["dt"])[3]
+        out["oracle"] = {"value": n * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
+                         "seconds": el, "kind": "oracle (direct O(N^2) FP64 sum, literal step)"}
+        out["error_en"] = abs(eg - eo) / abs(eo)
+        out["max_pos_diff_m"] = float(np.abs(st.pos().cpu().numpy() - po).max())
+    plan.close()
+    return out
+
+
+def forces_arm(args):
+    """Only single force evaluations of the N-ion sweep sphere (one JSON line)."""
+    import torch
+    import paper_2405_13973_gb300 as pt
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+    w = W.sphere_sweep(args.forces)
+    ref = sweep_reference(pt, torch, w) if not args.no_ref else None
+    r = force_eval_point(pt, torch, w, args.p, args.precision, args.steps, flush, ref,
+                         warmup=args.warmup)
+    line = {"metric": "single force evaluations/s (sweep sphere, 2e14 m^-3)",
+            "value": r.get("evals_per_s"), "unit": "evaluations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"sphere N={args.forces}, 2e14 m^-3 + 1% jitter, p={args.p}",
+                       "l2": "flushed between timed evaluations (512 MiB write)"},
+            "result": r, "reference": ref[2] if ref else None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
     """K single steps, each timed with CUDA events, L2 flushed in between."""
     stream = torch.cuda.current_stream()
@@ -362,7 +515,16 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched-ensemble measurement with this many crystals instead of the "
                          "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
+    ap.add_argument("--forces", type=int, default=0,
+                    help="only single force evaluations of this many ions (sweep sphere)")
+    ap.add_argument("--no-ref", action="store_true", help="--forces without the error reference")
+    ap.add_argument("--config1-steps", type=int, default=1000,
+                    help="steps of the 1,000-ion FP64 run carried by the default line (0: skip)")
+    ap.add_argument("--sweep", default="10000,100000,1000000",
+                    help="ion counts of the single-evaluation sweep in the default line ('' skips)")
     args = ap.parse_args()
+    if args.forces > 0:
+        return forces_arm(args)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -526,6 +688,17 @@ def main():
                          "depth": pl.last_depth}
             pl.close()
         out["p10"] = p10
+
+    # config 1 (1,000 ions, FP64, p = 8) and the single-evaluation sweep
+    if rank == 0 and args.config1_steps > 0:
+        out["config1"] = config1_arm(pt, torch, args.config1_steps, flush,
+                                     with_oracle=not args.no_cpu)
+    if rank == 0 and args.sweep:
+        ns = [int(float(x)) for x in args.sweep.split(",") if x]
+        out["sweep"] = {"workload": "sphere at 2e14 m^-3 + 1% jitter, one force evaluation, "
+                                    "leaf<=32, automatic depth",
+                        "points": sweep_arm(pt, torch, ns, (4, 6, 8, 10, 12, 16),
+                                            ("fp64", "fp32", "bf16x3"), flush)}
 
     # end to end through the public API: every step copies the state in from
     # pinned host memory, advances it (pt_step_async) and copies it back; the
