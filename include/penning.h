@@ -272,20 +272,23 @@ int pt_energy(fmm_plan plan, const pt_state* state, const pt_trap* trap, double*
 
 /* ---------------------------------------------------------------------------
  * pt_energy_noalloc -- pt_energy with the exact FP64 direct sum (as with a
- * NULL plan), for callers that cannot allocate device memory: code running
- * inside a CUDA stream capture (where cudaMalloc is not allowed), real-time
- * loops that cannot afford cudaMalloc's implicit device synchronisation, and
- * programs whose device memory is reserved up front by their own allocator.
- * The paper has no counterpart; this is a library-service variant.
+ * NULL plan), for callers that cannot allocate device memory: real-time
+ * loops that cannot afford cudaMalloc's implicit device synchronisation in
+ * the middle of a run, and programs whose device memory is reserved up
+ * front by their own allocator (a fixed pool that leaves nothing for a
+ * library to take).  The paper has no counterpart; this is a service of the
+ * library.
  *   state, trap, out, stream : as pt_energy.
  * Allocates nothing: its scratch is a fixed array inside the library
  * (3.5 MiB, held by every GPU that loads the library until exit), which
  * limits state->n to 65536 (larger: PT_ERR_ARG, nothing queued).  The first
- * call on a device looks the array up and should come before any stream
- * capture.  All calls on a device share the array: calls that overlap on
- * the GPU (other streams or threads) race and must be serialised.  Each
- * call overwrites all the scratch it reads, so no clearing is needed.
- * Synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+ * call on a device looks the array's device address up once (the set-up);
+ * make that first call before any stream capture on the device.  All calls
+ * on a device share the array and it keeps the last call's contents: calls
+ * that overlap on the GPU (other streams or threads) race and must be
+ * serialised.  Each call overwrites all the scratch it reads, so nothing
+ * needs clearing.  Copies the four results to `out` on the host and
+ * synchronises the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
 int pt_energy_noalloc(const pt_state* state, const pt_trap* trap, double* out, void* stream);
 
 /* Human-readable text for a status code (static storage). */
@@ -357,6 +360,32 @@ int pt_mh_scans(const pt_state* st, const pt_trap* trap, double temperature, dou
 int pt_set_damping(fmm_plan plan, double gamma);
 int pt_temperatures(const pt_state* state, const pt_trap* trap, double* out, void* stream);
 int pt_position_moments(const pt_state* state, const pt_trap* trap, double* acc, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pt_rms_displacement -- Delta r_rms of every ion (Sec. 5, Eq. rms_disp: the
+ * RMS displacement of an ion about its mean rotating-frame position over K
+ * samples) from the moments pt_position_moments accumulated K times:
+ *   out[i] = sqrt(max(0, acc[3n+i]/K - sum_a (acc[a n+i]/K)^2)).
+ *   n       : ions.
+ *   acc     : device, 4n doubles (layout of pt_position_moments), read only.
+ *   samples : K >= 1.
+ *   out     : device, n doubles written (m).
+ * Asynchronous on the stream.  Errors: PT_ERR_ARG, PT_ERR_CUDA. */
+int pt_rms_displacement(int64_t n, const double* acc, int64_t samples, double* out,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------
+ * pt_potential_temperature -- T_PE = (2/3)(PE - PE_0)/(N k_B) (Sec. 5, Eq.
+ * temp_pe): PE the rotating-frame potential energy (external: trap, rotating
+ * wall and rotation terms, plus Coulomb) of `state` and PE_0 that of the
+ * reference configuration `ref` (the paper's is a minimised equilibrium),
+ * each at its own time, both from pt_energy with `plan` (NULL: the exact
+ * direct sum).
+ *   out : host, 1 double written (K).
+ * Synchronises the stream.  Errors: as pt_energy; PT_ERR_ARG if the ion
+ * counts differ. */
+int pt_potential_temperature(fmm_plan plan, const pt_state* state, const pt_state* ref,
+                             const pt_trap* trap, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * fmm_plan_footprint -- the device memory fmm_plan_create would allocate for

@@ -126,6 +126,10 @@ def load(build_if_missing: bool = True):
                                       ctypes.POINTER(_D), _VP]
         L.pt_position_moments.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                           _VP, _VP]
+        L.pt_rms_displacement.argtypes = [_I64, _VP, _I64, _VP, _VP]
+        L.pt_potential_temperature.argtypes = [_VP, ctypes.POINTER(pt_state),
+                                               ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
+                                               ctypes.POINTER(_D), _VP]
         L.pt_mh_scans.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap), _D, _D,
                                   ctypes.c_uint64, _I64, _I64, ctypes.POINTER(_I64),
                                   ctypes.POINTER(_D), _VP]
@@ -408,19 +412,31 @@ def position_moments(state: State, trap, acc, stream=None):
     return acc
 
 
-def rms_displacement(acc, samples: int):
-    """Delta r_rms of every ion (Eq. rms_disp) from K = samples accumulations."""
-    mean = acc[:3] / samples
-    return torch.sqrt(torch.clamp(acc[3] / samples - (mean * mean).sum(0), min=0.0))
+def rms_displacement(acc, samples: int, out=None, stream=None):
+    """Delta r_rms (n,) of every ion (Eq. rms_disp) from K = samples
+    accumulations of position_moments (pt_rms_displacement)."""
+    _dev_f64(acc)
+    n = acc.shape[1]
+    _dev_f64(acc, (4, n))
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=acc.device)
+    _check(load().pt_rms_displacement(n, _ptr(acc), int(samples), _ptr(out), _stream(stream)),
+           "pt_rms_displacement")
+    return out
 
 
-def potential_temperature(state: State, trap, reference: State, plan: Plan | None = None):
-    """T_PE = (2/3) (PE - PE_0) / (N k_B) (Eq. temp_pe): rotating-frame potential
-    energy (external + Coulomb) of state minus that of the reference
-    configuration (each at its own time)."""
-    e = energy(state, trap, plan)
-    e0 = energy(reference, trap, plan)
-    return (2.0 / 3.0) * ((e[1] + e[2]) - (e0[1] + e0[2])) / (state.n * 1.380649e-23)
+def potential_temperature(state: State, trap, reference: State, plan: Plan | None = None,
+                          stream=None):
+    """T_PE in K (Eq. temp_pe) of state against the reference configuration
+    (pt_potential_temperature)."""
+    st, ref = state._c(), reference._c()
+    tr = trap if isinstance(trap, pt_trap) else make_trap(trap)
+    out = _D(0.0)
+    _check(load().pt_potential_temperature(plan._h if plan is not None else None,
+                                           ctypes.byref(st), ctypes.byref(ref),
+                                           ctypes.byref(tr), ctypes.byref(out), _stream(stream)),
+           "pt_potential_temperature")
+    return float(out.value)
 
 
 def plan_footprint(n_max: int, p: int, leaf_max: int = 32, depth: int = -1,

@@ -1074,4 +1074,22 @@ int pt_position_moments(const pt_state* st, const pt_trap* trap, double* acc, vo
     return status_from(launch_position_moments(st->n, *st, *trap, acc, (cudaStream_t)stream));
 }
 
+int pt_rms_displacement(int64_t n, const double* acc, int64_t samples, double* out,
+                        void* stream) {
+    if (n < 1 || !acc || !out || samples < 1) return PT_ERR_ARG;
+    return status_from(launch_rms_displacement(n, acc, samples, out, (cudaStream_t)stream));
+}
+
+int pt_potential_temperature(fmm_plan plan, const pt_state* st, const pt_state* ref,
+                             const pt_trap* trap, double* out, void* stream) {
+    if (!st || !ref || !out || st->n < 1 || ref->n != st->n) return PT_ERR_ARG;
+    double e[4], e0[4];
+    int r = pt_energy(plan, st, trap, e, stream);
+    if (r != PT_OK) return r;
+    if ((r = pt_energy(plan, ref, trap, e0, stream)) != PT_OK) return r;
+    const double kb = 1.380649e-23;
+    *out = (2.0 / 3.0) * ((e[1] + e[2]) - (e0[1] + e0[2])) / ((double)st->n * kb);
+    return PT_OK;
+}
+
 }  // extern "C"

@@ -3,13 +3,13 @@
 //
 // pt_energy(NULL plan, ...) obtains its scratch (a packed copy of the
 // positions, the field, the potential and the reduction partials) from
-// cudaMalloc on every call.  Some callers cannot do that: code that runs
-// while a CUDA graph is being captured (device allocation is not allowed
-// there), real-time loops that must not pay cudaMalloc's implicit device
-// synchronisation, and host programs whose device memory is reserved up
+// cudaMalloc on every call.  Some callers cannot do that: real-time loops
+// that must not pay cudaMalloc's implicit device synchronisation in the
+// middle of a run, and host programs whose device memory is reserved up
 // front by their own allocator.  This entry point serves them: its scratch
 // is the file-scope array below, which every GPU that loads the library
-// holds from module load until process exit.
+// holds from module load until process exit.  The call ends with a copy of
+// the four results to the host and a synchronisation of the stream.
 //
 // Contract of the scratch array:
 //   * it is sized for at most kNoAllocMaxIons ions; larger states are
@@ -41,9 +41,10 @@ std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device
-// address).  The lookup may load the module, so the first call on a device
-// must not happen inside a stream capture.
+// per device with that device current (the host-side symbol is only a
+// stand-in, never a device address).  This set-up runs in the first call on
+// a device; the lookup may load the module, so that first call should come
+// before any stream capture on the device.
 cudaError_t scratch_on_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

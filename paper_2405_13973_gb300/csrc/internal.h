@@ -200,5 +200,8 @@ cudaError_t launch_temperatures(int64_t n, const pt_state& st, const pt_trap& tr
 // acc[0..n) += x_r, [n, 2n) += y_r, [2n, 3n) += z, [3n, 4n) += |x_r|^2 at time st.t
 cudaError_t launch_position_moments(int64_t n, const pt_state& st, const pt_trap& trap,
                                     double* acc, cudaStream_t s);
+// out[i] = Delta r_rms of ion i from `samples` accumulations of acc (above)
+cudaError_t launch_rms_displacement(int64_t n, const double* acc, int64_t samples, double* out,
+                                    cudaStream_t s);
 
 }  // namespace pt

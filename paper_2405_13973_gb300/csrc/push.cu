@@ -375,4 +375,23 @@ cudaError_t launch_position_moments(int64_t n, const pt_state& st, const pt_trap
     return cudaGetLastError();
 }
 
+// Delta r_rms of every ion (Eq. rms_disp) from K accumulations of the
+// rotating-frame moments: sqrt(<|x_r|^2> - |<x_r>|^2), the variance clamped
+// at zero against rounding.
+__global__ void k_rms_displacement(int64_t n, const double* __restrict__ acc, double inv_k,
+                                   double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double mx = acc[i] * inv_k, my = acc[n + i] * inv_k, mz = acc[2 * n + i] * inv_k;
+        const double v = acc[3 * n + i] * inv_k - (mx * mx + my * my + mz * mz);
+        out[i] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+}
+
+cudaError_t launch_rms_displacement(int64_t n, const double* acc, int64_t samples, double* out,
+                                    cudaStream_t s) {
+    k_rms_displacement<<<grid_for(n, 256), 256, 0, s>>>(n, acc, 1.0 / (double)samples, out);
+    return cudaGetLastError();
+}
+
 }  // namespace pt

@@ -6,7 +6,7 @@ exp(-dE / k_B T)).
 Each pin ties it to something other than itself:
   * energy bookkeeping: the accepted energy changes add up to the change of
     the rotating-frame potential energy computed independently by
-    orc_energy_rot (itself pinned in test_oracle_energy), with the wall on and
+    orc_energy_rot (itself pinned in test_oracle_push.py), with the wall on and
     an arbitrary wall phase -- a dropped, mis-signed or self-including term in
     dE breaks it;
   * T -> 0: only downhill moves survive, so the potential energy never rises

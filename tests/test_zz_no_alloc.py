@@ -1,5 +1,6 @@
 """pt_energy_noalloc: the rotating-frame energy for callers that cannot
-allocate device memory (inside a graph capture, in real-time loops, or under
+allocate device memory (real-time loops that cannot take cudaMalloc's device
+synchronisation mid-run, programs whose device memory is all reserved by
 their own allocator).  Its scratch is a fixed array inside the library, so
 it must give the same energies as pt_energy with the direct sum, call after
 call, and refuse states larger than that array.
