@@ -143,7 +143,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def launches_per_step(depth: int, precision: str) -> int:
+def launches_per_step(depth: int, precision: str, schedule: str = "tiles") -> int:
     tc = precision in ("tf32x3", "bf16x3")
     # drift + cube, keys, scatter, leaf gather, P2P, L2P, kick; the leaf and
     # cell scans: one launch together while both fit one block (depth <= 5),
@@ -153,8 +153,10 @@ def launches_per_step(depth: int, precision: str) -> int:
         if tc:
             m2m = max(depth - 3, 0)          # P2M covers the leaves and their parents
             k += 1 + 2 * m2m                 # P2M; M2M and its reduction per level
-            k += 4 + max(depth - 3, 0)       # plan, items, M2L, tile reduction; L2L per level
-                                             # down to the leaves' parents
+            if schedule == "pairs":          # counts, scans, pairs, M2L, pair reduction
+                k += 5 + max(depth - 3, 0)   # (+ one memset node); L2L per level
+            else:                            # plan, items, M2L, tile reduction; L2L per level
+                k += 4 + max(depth - 3, 0)   # down to the leaves' parents
             k += 1 if precision == "bf16x3" else 0   # split of M into bf16 pieces
         else:
             k += 1 + (depth - 2)             # P2M, M2M per level
@@ -346,7 +348,7 @@ def sweep_reference(pt, torch, w, n_sample=512):
     return Eo, idx, f"FP64 oracle direct sum at {n_sample} sampled ions"
 
 
-def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=1):
+def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=1, schedule=""):
     """Single force evaluations (config-3 sweep point): mean CUDA-event time
     of `steps` evaluations (L2 flushed before each) and the relative RMS force
     error against ref."""
@@ -356,6 +358,8 @@ def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=
     qd = torch.tensor(q, dtype=torch.float64, device="cuda")
     try:
         plan = pt.Plan(n, p=p, leaf_max=32, depth=-1, precision=precision)
+        if schedule and precision in ("tf32x3", "bf16x3"):
+            plan.set_m2l_schedule(schedule)
     except pt.PenningError as exc:
         return {"status": str(exc)}
     E = torch.empty((3, n), dtype=torch.float64, device="cuda")
@@ -374,6 +378,8 @@ def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=
         ms.append(a.elapsed_time(b))
     out = {"ms": float(np.mean(ms)), "evals_per_s": 1e3 / float(np.mean(ms)),
            "ion_evals_per_s": n * 1e3 / float(np.mean(ms)), "depth": plan.last_depth}
+    if precision in ("tf32x3", "bf16x3"):
+        out["m2l_schedule"] = plan.m2l_schedule
     if ref is not None:
         Er, idx, _ = ref
         e = E.cpu().numpy().T
@@ -461,7 +467,7 @@ def forces_arm(args):
     w = W.sphere_sweep(args.forces)
     ref = sweep_reference(pt, torch, w) if not args.no_ref else None
     r = force_eval_point(pt, torch, w, args.p, args.precision, args.steps, flush, ref,
-                         warmup=args.warmup)
+                         warmup=args.warmup, schedule=args.schedule)
     line = {"metric": "single force evaluations/s (sweep sphere, 2e14 m^-3)",
             "value": r.get("evals_per_s"), "unit": "evaluations/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -473,7 +479,7 @@ def forces_arm(args):
     return 0
 
 
-def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
+def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True, kernels=False):
     """K single steps, each timed with CUDA events, L2 flushed in between."""
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -486,7 +492,10 @@ def timed_steps(pt, torch, plan, st, trap, laser, dt, K, flush, profile=True):
         ev[k][1].record(stream)
         if profile:
             ev[k][1].synchronize()
-            phases.append(plan.phase_times())
+            ph = plan.phase_times()
+            if kernels:
+                ph.update(plan.kernel_times())
+            phases.append(ph)
     torch.cuda.synchronize()
     plan.sync()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -515,6 +524,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched-ensemble measurement with this many crystals instead of the "
                          "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
+    ap.add_argument("--schedule", default="", choices=["", "tiles", "pairs"],
+                    help="M2L schedule of the tensor-core precisions (default: the library's)")
     ap.add_argument("--forces", type=int, default=0,
                     help="only single force evaluations of this many ions (sweep sphere)")
     ap.add_argument("--no-ref", action="store_true", help="--forces without the error reference")
@@ -567,8 +578,20 @@ def main():
         E, _ = plan.forces(pos0, st0.q, want_phi=False)
         return float(torch.sqrt(((E - Ed) ** 2).sum() / (Ed ** 2).sum()))
 
+    def force_err_oracle(plan):
+        """Err_F of the plan's field against the FP64 CPU oracle's direct sum."""
+        import oracle
+        Eo, _ = oracle.coulomb_direct(cr["pos"], cr["q"], want_phi=False)
+        E, _ = plan.forces(pos0, st0.q, want_phi=False)
+        e = E.cpu().numpy().T
+        return float(np.sqrt(((e - Eo) ** 2).sum() / (Eo ** 2).sum()))
+
     plan = pt.Plan(n, p=args.p, leaf_max=32, depth=-1, precision=args.precision)
+    if args.schedule and args.precision in ("tf32x3", "bf16x3"):
+        plan.set_m2l_schedule(args.schedule)
+    schedule = plan.m2l_schedule if args.precision in ("tf32x3", "bf16x3") else "cuda-core"
     ferr = force_err(plan)
+    ferr_oracle = force_err_oracle(plan) if rank == 0 and not args.no_cpu else None
     st = pt.State.from_numpy(cr["pos"], cr["vel"], cr["q"])
     plan.profile(False)
     plan.step(st, trap, laser, dt, args.warmup)           # warm-up; chooses the depth
@@ -596,19 +619,30 @@ def main():
     # so the headline above is timed without them)
     plan.profile(True)
     plan.step(st, trap, laser, dt, 1)                     # recaptures with the events
-    ms_prof, phases = timed_steps(pt, torch, plan, st, trap, laser, dt, args.steps, flush)
+    ms_prof, phases = timed_steps(pt, torch, plan, st, trap, laser, dt, args.steps, flush,
+                                  kernels=True)
     plan.profile(False)
 
     # phase breakdown and the roofline of the dominant kernel
     ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
+    kern = {k: ph.pop(k) for k in ("m2l_kernel", "p2p_kernel") if k in ph}
     P = (args.p + 1) ** 2
     m2l_flops = 2.0 * P * P * (stats["m2l_pairs"] + stats["l2l_shifts"])
     p2p_flops = 20.0 * stats["p2p_pairs"]
     pk, pk_src = peaks()
     dom = max(ph, key=ph.get)
-    roof = {"kernel": dom, "phases_ms": ph, "phases_pass_ms_per_step": float(np.mean(ms_prof))}
+    roof = {"kernel": dom, "phases_ms": ph, "kernels_ms": kern,
+            "phases_pass_ms_per_step": float(np.mean(ms_prof))}
     if dom == "m2l":
-        achieved = m2l_flops / (ph["m2l"] * 1e-3) / 1e12
+        # the dominant kernel: the M2L launch alone (events right before and
+        # after it, in the profiled pass); the phase (split, M2L, reduction,
+        # L2L) beside it
+        m2l_only = 2.0 * P * P * stats["m2l_pairs"]
+        achieved = m2l_only / (kern["m2l_kernel"] * 1e-3) / 1e12
+        roof["kernel"] = "M2L kernel (k_m2l_tc)" if args.precision in ("tf32x3", "bf16x3") \
+            else "M2L kernels (k_m2l_simt, all levels)"
+        roof["kernel_ms"] = kern["m2l_kernel"]
+        roof["phase_achieved"] = m2l_flops / (ph["m2l"] * 1e-3) / 1e12
         if args.precision == "tf32x3":
             peak = pk["bf16_tflops"] * TF32_OVER_BF16 / 3.0
             roof.update(bound="tensor", peak_note=f"TF32 rate / 3 (3 products per FP32-accurate "
@@ -624,7 +658,10 @@ def main():
             peak = FP64_TFLOPS
             roof.update(bound="alu", peak_note="nominal dense FP64")
         roof.update(achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                    work=f"2 P^2 x ({stats['m2l_pairs']} M2L + {stats['l2l_shifts']} L2L) flop")
+                    work=f"2 P^2 x {stats['m2l_pairs']} M2L translations per launch",
+                    phase_frac=roof["phase_achieved"] / peak,
+                    phase_work=f"2 P^2 x ({stats['m2l_pairs']} M2L + {stats['l2l_shifts']} L2L) "
+                               f"flop")
         if tc["products"]:
             # what the tensor cores execute: 128-row products of the work list
             roof["tensor_work"] = dict(tc, row_fill=stats["m2l_pairs"] / (128.0 * tc["products"]))
@@ -651,13 +688,15 @@ def main():
                                                              "fp64": "f64"}[args.precision],
            "data": "synthetic",
            "config": {"workload": workload_name(args.p), "precision": args.precision, "p": args.p,
-                      "depth": depth, "n": n, "l2": "flushed between timed steps (512 MiB write)",
+                      "depth": depth, "n": n, "m2l_schedule": schedule,
+                      "l2": "flushed between timed steps (512 MiB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
-           "force_err": ferr, "force_err_note": "relative RMS vs the FP64 direct sum, initial state",
+           "force_err": ferr, "force_err_note": "relative RMS vs the FP64 GPU direct sum, initial state",
+           "force_err_vs_oracle": ferr_oracle,
            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                           "max": float(max(ms))},
            "stats": stats, "roofline": roof, "clocks": clk,
-           "gpu_launches": launches_per_step(depth, args.precision) * args.steps,
+           "gpu_launches": launches_per_step(depth, args.precision, schedule) * args.steps,
            "wall_s_timed_region": t_wall}
 
     # the plain FP64 GPU path beside it (same workload, fewer steps)

@@ -114,6 +114,36 @@ int fmm_plan_set_phases(fmm_plan plan, int phases);
 #define PT_EXPAND_DIRECT 1
 int fmm_plan_set_expansion(fmm_plan plan, int mode);
 
+/* How M2L is scheduled (Eq. FMM_local; Sec. 2.3.2's interaction list of 189
+ * source cells per target, at most 316 distinct offsets o = target - source
+ * per level).  The translation operator depends on the offset only
+ * (expansions are stored scaled by the cell size), so:
+ *   PT_M2L_TILES  tensor cores: tiles of 128 target cells of one level and
+ *                 child octant, per non-empty offset one dense product of
+ *                 all 128 rows (rows whose source is empty multiply zeros),
+ *                 summed in tensor memory over runs of up to four offsets;
+ *                 CUDA cores: per level, tiles of 32 targets of one octant
+ *                 looping over their 189 offsets (and the L2L shift);
+ *   PT_M2L_PAIRS  the (target, source) pairs of each offset, gathered over
+ *                 all levels, fill products of 128 pairs (tensor cores) or
+ *                 64 x 64 SIMT tiles (CUDA cores); each pair's result row is
+ *                 a partial local expansion, and each target's partials are
+ *                 summed in increasing offset order (deterministic).  Fewer,
+ *                 fuller products on small or flat crystals, at the price of
+ *                 a pool of partial rows: about 189 x 9.2 n / leaf_max pairs
+ *                 (exact bound with a fixed depth) x (P rounded up to 16 on
+ *                 the tensor cores, the row stride of M and L on the CUDA
+ *                 cores) values.  A step whose pairs exceed the pool returns
+ *                 PT_ERR_OOM.
+ * Default: PT_M2L_PAIRS for n_max <= 65536, else PT_M2L_TILES.  Selecting
+ * the other schedule allocates what it needs.
+ * Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
+#define PT_M2L_TILES 0
+#define PT_M2L_PAIRS 1
+int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule);
+/* The plan's M2L schedule (PT_M2L_*), or -1 for a NULL plan. */
+int fmm_plan_m2l_schedule(fmm_plan plan);
+
 /* Depth used by the last fmm_forces / pt_step call on this plan (or -1). */
 int fmm_plan_last_depth(fmm_plan plan);
 
@@ -231,6 +261,12 @@ int pt_sync(fmm_plan plan, void* stream);
  *   L2L shifts, M2M shifts}.  Synchronises the stream. */
 int fmm_plan_profile(fmm_plan plan, int enable);
 int fmm_plan_phase_times(fmm_plan plan, double* ms);
+/* fmm_plan_kernel_times: device milliseconds, in the last executed profiled
+ *   step, of the M2L kernel alone (host ms[0]: the tensor-core M2L launch,
+ *   or the CUDA-core M2L launches of all levels) and of the near-field (P2P)
+ *   kernel (ms[1]), each between events recorded right before and after the
+ *   launch on its own stream.  Errors: PT_ERR_ARG (profiling off). */
+int fmm_plan_kernel_times(fmm_plan plan, double* ms);
 int fmm_plan_stats(fmm_plan plan, int64_t* out, void* stream);
 
 /* fmm_plan_tc_stats: the tensor-core M2L work list of the last evaluation

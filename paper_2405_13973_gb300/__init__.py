@@ -26,6 +26,7 @@ PT_ERR_NONFINITE, PT_ERR_ESCAPED, PT_ERR_TIMEOUT, PT_ERR_COINCIDENT, PT_ERR_UNSU
 PT_FP64, PT_MIXED_TF32X3, PT_MIXED_BF16X3, PT_FP32 = 0, 1, 2, 3
 PT_PHASE_NEAR, PT_PHASE_FAR, PT_PHASE_ALL = 1, 2, 3
 EXPAND_TREE, EXPAND_DIRECT = 0, 1
+M2L_TILES, M2L_PAIRS = 0, 1
 PT_MAX_BEAMS = 8
 PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "bf16x3": PT_MIXED_BF16X3,
               "fp32": PT_FP32}
@@ -114,9 +115,12 @@ def load(build_if_missing: bool = True):
         L.pt_sync.argtypes = [_VP, _VP]
         L.fmm_plan_profile.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_phase_times.argtypes = [_VP, ctypes.POINTER(_D)]
+        L.fmm_plan_kernel_times.argtypes = [_VP, ctypes.POINTER(_D)]
         L.fmm_plan_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.fmm_plan_tc_stats.argtypes = [_VP, ctypes.POINTER(_I64), _VP]
         L.fmm_plan_set_expansion.argtypes = [_VP, ctypes.c_int]
+        L.fmm_plan_set_m2l_schedule.argtypes = [_VP, ctypes.c_int]
+        L.fmm_plan_m2l_schedule.argtypes = [_VP]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -261,6 +265,18 @@ class Plan:
         precisions."""
         _check(load(False).fmm_plan_set_expansion(self._h, int(mode)), "fmm_plan_set_expansion")
 
+    def set_m2l_schedule(self, schedule):
+        """M2L_TILES or M2L_PAIRS ("tiles" / "pairs") for the tensor-core
+        precisions (fmm_plan_set_m2l_schedule)."""
+        if isinstance(schedule, str):
+            schedule = {"tiles": M2L_TILES, "pairs": M2L_PAIRS}[schedule]
+        _check(load(False).fmm_plan_set_m2l_schedule(self._h, int(schedule)),
+               "fmm_plan_set_m2l_schedule")
+
+    @property
+    def m2l_schedule(self) -> str:
+        return {M2L_TILES: "tiles", M2L_PAIRS: "pairs"}[int(load(False).fmm_plan_m2l_schedule(self._h))]
+
     @property
     def last_depth(self) -> int:
         return int(load(False).fmm_plan_last_depth(self._h))
@@ -318,6 +334,13 @@ class Plan:
         out = (ctypes.c_double * 6)()
         _check(load(False).fmm_plan_phase_times(self._h, out), "fmm_plan_phase_times")
         return dict(zip(self.PHASES, list(out)))
+
+    def kernel_times(self) -> dict:
+        """Device ms of the M2L kernel and the P2P kernel alone in the last
+        profiled step."""
+        out = (ctypes.c_double * 2)()
+        _check(load(False).fmm_plan_kernel_times(self._h, out), "fmm_plan_kernel_times")
+        return {"m2l_kernel": out[0], "p2p_kernel": out[1]}
 
     def stats(self, stream=None) -> dict:
         out = (ctypes.c_int64 * 8)()

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpenning.so")
 BUILD = os.path.join(HERE, "_build")
 
-SOURCES = ["abi.cu", "tree.cu", "fmm.cu", "push.cu", "m2l_tc.cu", "energy_noalloc.cu", "mh.cu"]
+SOURCES = ["abi.cu", "tree.cu", "fmm.cu", "push.cu", "m2l_tc.cu", "m2l_pairs.cu",
+           "energy_noalloc.cu", "mh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
           "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", CSRC,

@@ -21,6 +21,8 @@ using namespace pt;
 namespace {
 
 constexpr int kWallChunk = 4096;  // steps per wall-phase table upload
+// tensor-core plans up to this many ions use the pair-packed M2L schedule
+constexpr int64_t kPairsDefaultIons = 65536;
 
 struct GraphKey {
     int D = -1;
@@ -30,8 +32,10 @@ struct GraphKey {
     pt_laser laser{};
     bool profile = false;
     int expand = 0;
+    int sched = 0;
     bool operator==(const GraphKey& o) const {
         return D == o.D && n == o.n && profile == o.profile && expand == o.expand &&
+               sched == o.sched &&
                memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
                memcmp(&pp, &o.pp, sizeof pp) == 0 && memcmp(&laser, &o.laser, sizeof laser) == 0;
     }
@@ -68,6 +72,7 @@ struct fmm_plan_s {
     bool profile = false;
     static constexpr int kPhases = 6;
     cudaEvent_t ph_ev[kPhases + 1] = {nullptr};
+    cudaEvent_t k_ev[4] = {nullptr};   // kernel timing of profiled steps (Workspace::kev)
     bool ops_held = false;     // holds a reference on the shared operator set
     bool dry = false;          // sizing only (fmm_plan_footprint): nothing is allocated
     size_t dry_bytes = 0;
@@ -166,6 +171,8 @@ void free_plan(fmm_plan_s* pl) {
     }
     for (int k = 0; k <= fmm_plan_s::kPhases; ++k)
         if (pl->ph_ev[k]) cudaEventDestroy(pl->ph_ev[k]);
+    for (cudaEvent_t ev : pl->k_ev)
+        if (ev) cudaEventDestroy(ev);
     if (pl->h_err) cudaFreeHost(pl->h_err);
     delete pl;
 }
@@ -274,6 +281,7 @@ int check_err(fmm_plan_s* pl, cudaStream_t s) {
         cudaStreamSynchronize(s);
         if (v & ERR_NONFINITE) return PT_ERR_NONFINITE;
         if (v & ERR_TIMEOUT) return PT_ERR_TIMEOUT;
+        if (v & ERR_CAPACITY) return PT_ERR_OOM;
     }
     return PT_OK;
 }
@@ -317,6 +325,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
                          const pt_laser& laser, int D, cudaStream_t s) {
     Workspace& ws = pl->ws;
     const int64_t n = st.n;
+    for (int k = 0; k < 4; ++k) ws.kev[k] = pl->profile ? pl->k_ev[k] : nullptr;
     auto mark = [&](int k) -> cudaError_t {
         return pl->profile ? cudaEventRecordWithFlags(pl->ph_ev[k], s, cudaEventRecordExternal)
                            : cudaSuccess;
@@ -332,6 +341,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
     if (e == cudaSuccess)
         e = launch_kick_drift(n, st.x, st.y, st.z, st.vx, st.vy, st.vz, st.q, ws.E, pp, laser, ws, s);
     if (e == cudaSuccess) e = mark(6);
+    for (int k = 0; k < 4; ++k) ws.kev[k] = nullptr;
     return e;
 }
 
@@ -394,6 +404,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.laser = lz;
     key.profile = plan->profile;
     key.expand = plan->ws.expand;
+    key.sched = plan->ws.m2l_pairs;
     return key;
 }
 
@@ -529,6 +540,95 @@ int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision
     return plan_create_impl(n_max, p, leaf_max, depth, precision, out, false, nullptr, nullptr);
 }
 
+// Pair-packed M2L schedule: the pool of partial rows holds every (target,
+// source) pair of a step.  With a fixed depth D the bound is exact (189
+// sources per cell of levels 2..D).  With the automatic depth, D is the
+// smallest depth whose leaves hold at most leaf_max ions on average, so level
+// D - 1 has fewer than n / leaf_max cells and level D at most 8 times as many:
+// pairs < 189 (8 + 1 + 1/7) n / leaf_max, bounded here by 189 x 9.2 n /
+// leaf_max plus a margin for the tree's drift between depth choices.
+static int alloc_pairs(fmm_plan_s* pl) {
+    Workspace& ws = pl->ws;
+    if (ws.pp_work) return PT_OK;
+    const int dcap = pl->depth >= 0 ? pl->depth : ws.depth_max;
+    int64_t exact = 0;
+    for (int l = 2; l <= dcap; ++l) exact += 189 * (pow8(l) < pl->n_max ? pow8(l) : pl->n_max);
+    int64_t cap = exact;
+    if (pl->depth < 0) {
+        const int64_t autob = (int64_t)(189.0 * 9.2 * (double)pl->n_max / pl->leaf_max) + 8192;
+        if (autob < cap) cap = autob;
+    }
+    ws.pp_slot_cap = cap > 0 ? cap : 1;
+    ws.pp_item_cap = ws.pp_slot_cap / 128 + 344;
+    ws.pp_stride = is_tc(pl->precision) ? m2l_tc_npad(pl->p) : ws.ld;
+    bool ok = dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) &&
+              dalloc(pl, ws.pp_part, m2l_pp_part_bytes(ws));
+    if (!ok) {
+        ws.pp_work = nullptr;
+        ws.pp_part = nullptr;
+        return PT_ERR_OOM;
+    }
+    if (!pl->dry && cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess)
+        return PT_ERR_CUDA;
+    return PT_OK;
+}
+
+// The tile schedule's full pool of partial slabs (plans created for the pair
+// schedule hold the minimum).
+static int alloc_tile_slabs(fmm_plan_s* pl) {
+    Workspace& ws = pl->ws;
+    const int64_t want = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, pl->n_max);
+    if (ws.tc_slab_cap >= want) return PT_OK;
+    const size_t floats = m2l_tc_part_floats(ws.cells_max, ws.ld, ws.tc_splits_max,
+                                             ws.tc_tiles_cap, want);
+    void *work = nullptr, *part = nullptr;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+    if (cudaMalloc(&work, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(float) * floats) != cudaSuccess) {
+        cudaFree(work);
+        return PT_ERR_OOM;
+    }
+    if (cudaMemset(work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
+        cudaMemset(part, 0, sizeof(float) * floats) != cudaSuccess) {
+        cudaFree(work);
+        cudaFree(part);
+        return PT_ERR_CUDA;
+    }
+    for (void*& v : pl->allocs) {
+        if (v == ws.tc_work) {
+            cudaFree(v);
+            v = work;
+        } else if (v == (void*)ws.tc_part) {
+            cudaFree(v);
+            v = part;
+        }
+    }
+    ws.tc_work = work;
+    ws.tc_part = (float*)part;
+    ws.tc_slab_cap = want;
+    ws.tc_part_floats = floats;
+    if (pl->graph) {  // captured with the old buffers
+        cudaGraphExecDestroy(pl->graph);
+        pl->graph = nullptr;
+        pl->gkey = GraphKey{};
+    }
+    return PT_OK;
+}
+
+int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule) {
+    if (!plan || (schedule != PT_M2L_TILES && schedule != PT_M2L_PAIRS)) return PT_ERR_ARG;
+    if (cudaSetDevice(plan->device) != cudaSuccess) return PT_ERR_CUDA;
+    int r = schedule == PT_M2L_PAIRS ? alloc_pairs(plan)
+            : is_tc(plan->precision) ? alloc_tile_slabs(plan) : PT_OK;
+    if (r != PT_OK) return r;
+    plan->ws.m2l_pairs = schedule == PT_M2L_PAIRS ? 1 : 0;
+    return PT_OK;
+}
+
+int fmm_plan_m2l_schedule(fmm_plan plan) {
+    return plan ? (plan->ws.m2l_pairs ? PT_M2L_PAIRS : PT_M2L_TILES) : -1;
+}
+
 int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precision,
                        int64_t* plan_bytes, int64_t* operator_bytes) {
     if (!plan_bytes || !operator_bytes) return PT_ERR_ARG;
@@ -635,12 +735,24 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
         int64_t tcap = 0;
         for (int l = 2; l <= ws.depth_max; ++l) tcap += ((pow8(l) < n_max ? pow8(l) : n_max) + 127) / 128 + 8;
         ws.tc_tiles_cap = tcap > 0 ? tcap : 1;
-        ws.tc_slab_cap = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, n_max);
+        // the pair-packed schedule by default up to kPairsDefaultIons; the
+        // tile schedule's partial slabs then only at their minimum until it
+        // is selected
+        const bool pairs = n_max <= kPairsDefaultIons;
+        ws.tc_slab_cap = pairs ? 1 : m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, n_max);
         ws.tc_part_floats = m2l_tc_part_floats(cells, ws.ld, ws.tc_splits_max, ws.tc_tiles_cap,
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
         ok = ok && dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
         if (ws.tc_bf16) ok = ok && dalloc(pl, ws.M_pieces, sizeof(uint16_t) * 3 * ws.ld * cells);
+        if (ok && pairs) {
+            ok = alloc_pairs(pl) == PT_OK;
+            ws.m2l_pairs = ok ? 1 : 0;
+        }
+    } else if (ok && n_max <= kPairsDefaultIons) {
+        // CUDA-core precisions: the pair-packed M2L by default as well
+        ok = alloc_pairs(pl) == PT_OK;
+        ws.m2l_pairs = ok ? 1 : 0;
     }
     if (dry) {
         *dry_bytes = (int64_t)pl->dry_bytes;
@@ -682,6 +794,12 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
     }
     for (int k = 0; k <= fmm_plan_s::kPhases; ++k) {
         if (cudaEventCreate(&pl->ph_ev[k]) != cudaSuccess) {
+            free_plan(pl);
+            return PT_ERR_CUDA;
+        }
+    }
+    for (cudaEvent_t& ev : pl->k_ev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
             free_plan(pl);
             return PT_ERR_CUDA;
         }
@@ -780,6 +898,17 @@ int pt_sync(fmm_plan plan, void* stream) {
 int fmm_plan_profile(fmm_plan plan, int enable) {
     if (!plan) return PT_ERR_ARG;
     plan->profile = enable != 0;
+    return PT_OK;
+}
+
+int fmm_plan_kernel_times(fmm_plan plan, double* ms) {
+    if (!plan || !ms || !plan->profile) return PT_ERR_ARG;
+    for (int k = 0; k < 2; ++k) {
+        float v = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&v, plan->k_ev[2 * k], plan->k_ev[2 * k + 1]);
+        if (e != cudaSuccess) return status_from(e);
+        ms[k] = v;
+    }
     return PT_OK;
 }
 

@@ -903,8 +903,13 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         if ((e = cudaEventRecord(ws.ev_fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(sn, ws.ev_fork, 0)) != cudaSuccess) return e;
     }
-    if (far && use_tc) {
-        if ((e = launch_m2l_tc_worklist(n, D, ws, sn)) != cudaSuccess) return e;
+    // the M2L work list: the tensor-core schedules, and the pair-packed
+    // schedule of the CUDA-core paths
+    const bool pairs_simt = far && !use_tc && ws.m2l_pairs;
+    if (far && (use_tc || pairs_simt)) {
+        if ((e = use_tc ? launch_m2l_tc_worklist(n, D, ws, sn)
+                        : launch_m2l_pairs_worklist(n, D, ws, sn)) != cudaSuccess)
+            return e;
         if (fork && (e = cudaEventRecord(ws.ev_items, sn)) != cudaSuccess) return e;
     }
     // Multipoles from the ions: at the leaves, and on the tensor-core path also
@@ -934,10 +939,16 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         cudaError_t r;
         if (fork && after_event && (r = cudaStreamWaitEvent(sn, ws.ev_p2m, 0)) != cudaSuccess)
             return r;
+        if (ws.kev[2] && (r = cudaEventRecordWithFlags(ws.kev[2], sn, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return r;
         k_p2p<T><<<leaf_grid, kNfThreads, 0, sn>>>(D, ws.linfo,
                                                   (const typename Ion<T>::rec*)ws.sorted, ws.code,
                                                   ws.cid + dl.off[D], ws.cstart, ws.ccount, near);
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
+        if (ws.kev[3] && (r = cudaEventRecordWithFlags(ws.kev[3], sn, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return r;
         if (fork && (r = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return r;
         return cudaSuccess;
     };
@@ -970,7 +981,15 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                                    near_late ? ws.ev_p2m : nullptr)) != cudaSuccess)
             return e;
         if (nf && near_late && (e = launch_near(true)) != cudaSuccess) return e;
+    } else if (pairs_simt) {
+        if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
+        // M2L products of the work list, the per-target sums, L2L down to
+        // the leaves (their L2P evaluates their own expansion)
+        if ((e = launch_m2l_pairs_simt(n, D, ws, direct ? 2 : D, s)) != cudaSuccess) return e;
     } else if (far) {
+        if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return e;
         for (int l = 2; l <= D; ++l) {
             int64_t cl = (int64_t)1 << (3 * l);
             int cells = (int)(n < cl ? n : cl);
@@ -979,6 +998,9 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                                                l >= 3 ? dl.off[l - 1] : 0, M, L,
                                                (const T*)ws.T_m2l, (const T*)ws.T_l2l);
         }
+        if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return e;
     }
     if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;

@@ -95,9 +95,22 @@ struct Workspace {
     void* tc_work = nullptr;    // M2L work list (tiles, items)
     int64_t tc_tiles_cap = 0;
     int expand = 0;             // PT_EXPAND_*: ancestor expansions of the tensor-core paths
+    // pair-packed M2L schedule (PT_M2L_PAIRS, m2l_pairs.h): work list and the
+    // partial rows of every (target, source) pair, [slot][pp_stride] in the
+    // path's type (FP32: P rounded up to 16 on the tensor cores, ld on the
+    // CUDA cores; FP64: ld)
+    int m2l_pairs = 0;
+    // kernel timing (profiled steps only, else null): recorded right before
+    // and after the M2L kernel(s) [0, 1] and the near-field kernel [2, 3]
+    cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* pp_work = nullptr;
+    void* pp_part = nullptr;
+    int pp_stride = 0;
+    int64_t pp_slot_cap = 0;    // pairs the pool holds
+    int64_t pp_item_cap = 0;    // work items (runs of up to 128 pairs of one offset)
 };
 
-enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2, ERR_CAPACITY = 4 };
 
 // Offsets of the concatenated dense maps: levels lmin..D.
 struct DenseLayout {
@@ -143,6 +156,23 @@ cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);
 size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap);
+// ---- pair-packed M2L schedule (m2l_pairs.cu) -----------------------------------
+// work-list and partial-row bytes for the workspace's cells_max, pp_slot_cap,
+// pp_item_cap and pp_stride
+size_t m2l_pp_work_bytes(const Workspace& ws);
+size_t m2l_pp_part_bytes(const Workspace& ws);
+// the work list of the current tree (reads the tree only)
+cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
+// L of every cell of levels 2..D = the sum of its pairs' partial rows
+// (`width` columns)
+cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s);
+// CUDA-core paths: the M2L products of the work list, the reduction and the
+// L2L shifts into levels 3 .. l2l_last
+cudaError_t launch_m2l_pairs_simt(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s);
+// {offsets with pairs, work items, work items, pairs} of the last work list
+cudaError_t m2l_pairs_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
+// the tensor-core partial-row width (P rounded up to 16)
+int m2l_tc_npad(int p);
 cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
 // partial slabs of the M2L work items (a pool of 16 KB per ion, 16 MB to 8 GB)
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max);

@@ -1,0 +1,541 @@
+// m2l_pairs.cu -- the pair-packed M2L schedule (see m2l_pairs.h): its work
+// list, the per-target reduction of the partial rows, the CUDA-core M2L
+// product of every work item (FP64 and FP32 paths) and the CUDA-core L2L
+// shifts that follow it.
+//
+// Work list, per step (reads the tree only):
+//   k_pp_count  one warp per target: presence of its 216 candidate offsets
+//               (the 189 of its octant plus the 27 neighbours, always
+//               absent), its pair count and the per-offset counts;
+//   k_pp_scan   one block: target slot bases, offset pair bases, the items
+//               (each offset's pairs in runs of kPairRows, offsets in
+//               increasing order) and the pool check;
+//   k_pp_fill   one block per offset: its pairs in target order with their
+//               sources and slots.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "harmonics.cuh"
+#include "m2l_pairs.h"
+
+namespace pt {
+
+namespace {
+
+struct PpArgs {
+    int D;
+    const LevelInfo* linfo;
+    const uint32_t* code;
+    const int32_t* cid;
+    int64_t off[kMaxDepth + 2];
+};
+
+__device__ __forceinline__ void stage_linfo(const LevelInfo* g, LevelInfo* s) {
+    const int* src = reinterpret_cast<const int*>(g);
+    int* dst = reinterpret_cast<int*>(s);
+    for (int i = threadIdx.x; i < (int)(sizeof(LevelInfo) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+}
+
+// Targets are the cells of levels 2..D (global ids gbase[2] .. gbase[D+1]),
+// t = g - gbase[2].  Candidate offsets of a target in child octant b are the
+// 216 offsets o with o_a in [b_a - 3, b_a + 2] (index c = 36 (o_x - b_x + 3)
+// + 6 (o_y - b_y + 3) + (o_z - b_z + 3), increasing with the operator index
+// (o_x+3)*49 + (o_y+3)*7 + (o_z+3)); the 27 with |o_a| <= 1 are neighbours.
+// A candidate is present when its source cell t - o holds ions.
+constexpr int kPpCand = 216;
+constexpr int kPpWords = 7;   // 32-bit presence words per target
+
+__device__ __forceinline__ int pp_level(const LevelInfo& li, int D, int g) {
+    int l = 2;
+    while (l < D && g >= li.gbase[l + 1]) ++l;
+    return l;
+}
+
+// source of candidate c of the target at (x, y, z) of level l, or -1
+__device__ __forceinline__ int pp_source(const PpArgs& a, int l, int x, int y, int z, int c,
+                                         int* op) {
+    const int ox = (x & 1) - 3 + c / 36, oy = (y & 1) - 3 + (c / 6) % 6, oz = (z & 1) - 3 + c % 6;
+    *op = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return -1;
+    const int sx = x - ox, sy = y - oy, sz = z - oz, lim = 1 << l;
+    if (sx < 0 || sy < 0 || sz < 0 || sx >= lim || sy >= lim || sz >= lim) return -1;
+    return a.cid[a.off[l] + morton3(sx, sy, sz)];
+}
+
+// One warp per target: presence words of its 216 candidates, its pair count,
+// and the per-offset pair counts (block histogram, then global).
+constexpr int kPpThreads = 256;
+__global__ void __launch_bounds__(kPpThreads) k_pp_count(PpArgs a, uint32_t* tmask, int* tcount,
+                                                         int* ocnt) {
+    __shared__ int hist[343];
+    __shared__ LevelInfo li;
+    stage_linfo(a.linfo, &li);
+    for (int i = threadIdx.x; i < 343; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int g0 = li.gbase[2], g1 = li.gbase[a.D + 1];
+    const int wpb = blockDim.x >> 5;
+    for (int g = g0 + blockIdx.x * wpb + (threadIdx.x >> 5); g < g1; g += gridDim.x * wpb) {
+        const int l = pp_level(li, a.D, g);
+        int x, y, z;
+        demorton3(a.code[g], x, y, z);
+        int cnt = 0;
+#pragma unroll
+        for (int w = 0; w < kPpWords; ++w) {
+            const int c = 32 * w + lane;
+            int op = 0, src = -1;
+            if (c < kPpCand) src = pp_source(a, l, x, y, z, c, &op);
+            const unsigned bal = __ballot_sync(0xffffffffu, src >= 0);
+            if (src >= 0) atomicAdd(&hist[op], 1);
+            if (lane == 0) tmask[(int64_t)(g - g0) * kPpWords + w] = bal;
+            cnt += __popc(bal);
+        }
+        if (lane == 0) tcount[g - g0] = cnt;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 343; i += blockDim.x)
+        if (hist[i]) atomicAdd(&ocnt[i], hist[i]);
+}
+
+// One block: slot bases of the targets (exclusive scan of their counts; tbase
+// has n_targets + 1 entries), pair bases of the offsets, and the work items
+// (each offset's pairs in runs of 128, offsets in increasing order).
+constexpr int kPpScanThreads = 1024;
+__global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelInfo* linfo,
+                                                             int64_t slot_cap, int item_cap,
+                                                             const int* tcount, int* tbase,
+                                                             const int* ocnt, int* obase,
+                                                             M2lPairHdr* hdr, M2lPairItem* items,
+                                                             int* err) {
+    __shared__ int wsum[32];
+    __shared__ int s_carry;
+    __shared__ int s_ibase[344];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nt = linfo->gbase[D + 1] - linfo->gbase[2];
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nt; c0 += kPpScanThreads) {
+        const int i = c0 + tid;
+        const int v = i < nt ? tcount[i] : 0;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        if (i < nt) tbase[i] = s_carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+        __syncthreads();
+        if (tid == 0) s_carry += wsum[31];
+        __syncthreads();
+    }
+    const int total = s_carry;
+    if (tid == 0) {
+        tbase[nt] = total;
+        // offsets: pair bases and item bases (343 entries, serial)
+        int pb = 0, ib = 0, nof = 0;
+        for (int o = 0; o < 343; ++o) {
+            obase[o] = pb;
+            s_ibase[o] = ib;
+            pb += ocnt[o];
+            ib += (ocnt[o] + kPairRows - 1) / kPairRows;
+            nof += ocnt[o] > 0;
+        }
+        obase[343] = pb;
+        s_ibase[343] = ib;
+        const bool over = (int64_t)total > slot_cap || ib > item_cap || pb != total;
+        hdr->overflow = over ? 1 : 0;
+        if (over) atomicOr(err, ERR_CAPACITY);
+        hdr->n_items = over ? 0 : ib;
+        hdr->n_pairs = total;
+        hdr->n_targets = nt;
+        hdr->n_offsets = nof;
+    }
+    __syncthreads();
+    if ((int64_t)total > slot_cap || s_ibase[343] > item_cap) return;
+    for (int o = tid; o < 343; o += kPpScanThreads) {
+        const int c = ocnt[o];
+        for (int k = 0; k * kPairRows < c; ++k) {
+            M2lPairItem it;
+            it.op = o;
+            it.begin = obase[o] + k * kPairRows;
+            it.rows = min(kPairRows, c - k * kPairRows);
+            it.pad = 0;
+            items[s_ibase[o] + k] = it;
+        }
+    }
+}
+
+// One block per offset: its pairs in target order (a block-wide scan of the
+// targets' presence bits), each with its source and its slot (the target's
+// slot base plus the rank of the offset among the target's present ones).
+__global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t* tmask,
+                                                         const int* tbase, const int* obase,
+                                                         const M2lPairHdr* hdr, M2lPair* pairs) {
+    __shared__ int wsum[kPpThreads / 32];
+    __shared__ int s_carry;
+    __shared__ LevelInfo li;
+    const int op = blockIdx.x;
+    const int ox = op / 49 - 3, oy = (op / 7) % 7 - 3, oz = op % 7 - 3;
+    if (hdr->overflow) return;
+    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return;
+    if (obase[op + 1] == obase[op]) return;  // uniform: no pairs at this offset
+    stage_linfo(a.linfo, &li);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    const int g0 = li.gbase[2], nt = li.gbase[a.D + 1] - g0;
+    for (int c0 = 0; c0 < nt; c0 += kPpThreads) {
+        const int t = c0 + tid;
+        bool pres = false;
+        int c = 0, x = 0, y = 0, z = 0, l = 2;
+        uint32_t wbits[kPpWords];
+        if (t < nt) {
+            demorton3(a.code[g0 + t], x, y, z);
+            const int bx = x & 1, by = y & 1, bz = z & 1;
+            const int cx = ox - bx + 3, cy = oy - by + 3, cz = oz - bz + 3;
+            if (cx >= 0 && cx < 6 && cy >= 0 && cy < 6 && cz >= 0 && cz < 6) {
+                c = 36 * cx + 6 * cy + cz;
+#pragma unroll
+                for (int w = 0; w < kPpWords; ++w) wbits[w] = tmask[(int64_t)t * kPpWords + w];
+                pres = (wbits[c >> 5] >> (c & 31)) & 1u;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pres);
+        if (lane == 0) wsum[wid] = __popc(bal);
+        __syncthreads();
+        if (pres) {
+            int pos = s_carry + __popc(bal & ((1u << lane) - 1u));
+            for (int v = 0; v < wid; ++v) pos += wsum[v];
+            int rank = __popc(wbits[c >> 5] & ((1u << (c & 31)) - 1u));
+            for (int w = 0; w < (c >> 5); ++w) rank += __popc(wbits[w]);
+            l = pp_level(li, a.D, g0 + t);
+            int opc;
+            M2lPair pr;
+            pr.src = pp_source(a, l, x, y, z, c, &opc);
+            pr.slot = tbase[t] + rank;
+            pairs[obase[op] + pos] = pr;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int v = 0; v < kPpThreads / 32; ++v) tot += wsum[v];
+            s_carry += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// L of every target = the sum of its partial rows in slot order (increasing
+// offset), one warp per target, lanes over 16-byte column groups (FP32) or
+// single columns (FP64); `width` columns are written.  Targets without pairs
+// get zeros.  On a pool overflow nothing is summed (the call reports it).
+__global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride, int width,
+                                                       const LevelInfo* linfo,
+                                                       const M2lPairHdr* hdr, const int* tbase,
+                                                       const float4* __restrict__ part, float* L) {
+    const int lane = threadIdx.x & 31;
+    const int g0 = linfo->gbase[2], nt = linfo->gbase[D + 1] - g0;
+    const int s4 = stride / 4, w4 = width / 4;
+    const bool over = hdr->overflow != 0;
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += gridDim.x * (blockDim.x >> 5)) {
+        const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
+        for (int u = lane; u < w4; u += 32) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int s = s0;
+            for (; s + 4 <= s1; s += 4) {
+                float4 q[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k] = part[(int64_t)(s + k) * s4 + u];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
+                }
+            }
+            for (; s < s1; ++s) {
+                const float4 q = part[(int64_t)s * s4 + u];
+                v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+            }
+            *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pp_reduce(int D, int ld, int stride, int width,
+                                                    const LevelInfo* linfo, const M2lPairHdr* hdr,
+                                                    const int* tbase, const T* __restrict__ part,
+                                                    T* L) {
+    const int lane = threadIdx.x & 31;
+    const int g0 = linfo->gbase[2], nt = linfo->gbase[D + 1] - g0;
+    const bool over = hdr->overflow != 0;
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += gridDim.x * (blockDim.x >> 5)) {
+        const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
+        for (int u = lane; u < width; u += 32) {
+            T v = T(0);
+            for (int s = s0; s < s1; ++s) v += part[(int64_t)s * stride + u];
+            L[(int64_t)(g0 + t) * ld + u] = v;
+        }
+    }
+}
+
+// CUDA-core M2L of the work items: per item (offset o, up to 128 pairs) the
+// product D[pairs x P] = A[pairs x P] B[P x P], A row r = M of pair r's
+// source, B[k][n] = T_o[n][k], written to the pairs' slot rows (columns < P).
+// Block tile 64 pairs x 64 outputs, K in chunks of 16 through shared
+// memory, 4 x 4 outputs per thread; blocks walk (item, row half, column
+// block) units.
+constexpr int kSimtRows = 64, kSimtCols = 64, kSimtK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2l_pairs_simt(int P, int ld, int stride,
+                                                         const M2lPairHdr* hdr,
+                                                         const M2lPairItem* items,
+                                                         const M2lPair* pairs,
+                                                         const T* __restrict__ M,
+                                                         const T* __restrict__ Tm2l, T* part) {
+    __shared__ __align__(16) T As[kSimtK][kSimtRows];
+    __shared__ __align__(16) T Bs[kSimtK][kSimtCols];
+    __shared__ int s_src[kSimtRows], s_slot[kSimtRows];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int cb_n = (P + kSimtCols - 1) / kSimtCols;
+    const int units = hdr->n_items * 2 * cb_n;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int item = u / (2 * cb_n), rh = (u / cb_n) & 1, cb = u % cb_n;
+        const M2lPairItem it = items[item];
+        const int r0 = rh * kSimtRows, rows = min(kSimtRows, it.rows - r0);
+        if (rows <= 0) continue;  // uniform over the block
+        __syncthreads();
+        if (tid < kSimtRows) {
+            const bool live = tid < rows;
+            s_src[tid] = live ? pairs[it.begin + r0 + tid].src : -1;
+            s_slot[tid] = live ? pairs[it.begin + r0 + tid].slot : -1;
+        }
+        __syncthreads();
+        const T* To = Tm2l + (int64_t)it.op * P * P;
+        const int c0 = cb * kSimtCols;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        for (int k0 = 0; k0 < P; k0 += kSimtK) {
+#pragma unroll
+            for (int e = 0; e < (kSimtRows * kSimtK) / 256; ++e) {
+                const int idx = tid + 256 * e;
+                const int r = idx / kSimtK, kk = idx % kSimtK;
+                const int src = s_src[r];
+                As[kk][r] = (src >= 0 && k0 + kk < P) ? M[(int64_t)src * ld + k0 + kk] : T(0);
+                const int c = c0 + r;
+                Bs[kk][r] = (c < P && k0 + kk < P) ? To[(int64_t)c * P + k0 + kk] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < kSimtK; ++kk) {
+                T a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i;
+            if (r >= rows) continue;
+            T* out = part + (int64_t)s_slot[r] * stride;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + tx * 4 + j;
+                if (c < P) out[c] = acc[i][j];
+            }
+        }
+    }
+}
+
+// CUDA-core L2L of level l (after the reduction, which wrote every cell's
+// own M2L sum into L): L_child += T_l2l[octant] L_parent, one warp per
+// child, lanes over output coefficients, the parent's L staged per warp.
+template <typename T>
+__global__ void __launch_bounds__(128) k_l2l_simt(int l, int P, int ld, const LevelInfo* linfo,
+                                                  const uint32_t* __restrict__ code,
+                                                  const int32_t* __restrict__ cid,
+                                                  int64_t off_parent, const T* __restrict__ Tl2l,
+                                                  T* L) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sL = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * P;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int g0 = linfo->gbase[l], g1 = linfo->gbase[l + 1];
+    for (int g = g0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g1; g += warps) {
+        const uint32_t c = code[g];
+        const int gp = cid[off_parent + (c >> 3)];
+        __syncwarp();
+        for (int k = lane; k < P; k += 32) sL[k] = gp >= 0 ? L[(int64_t)gp * ld + k] : T(0);
+        __syncwarp();
+        const T* To = Tl2l + (int64_t)(c & 7u) * P * P;
+        for (int row = lane; row < P; row += 32) {
+            T acc = L[(int64_t)g * ld + row];
+            const T* tr = To + (int64_t)row * P;
+            for (int k = 0; k < P; ++k) acc += tr[k] * sL[k];
+            L[(int64_t)g * ld + row] = acc;
+        }
+    }
+}
+
+}  // namespace
+
+PairList pair_list(const Workspace& ws, size_t* bytes) {
+    PairList L;
+    unsigned char* b = static_cast<unsigned char*>(ws.pp_work);
+    size_t o = 0;
+    auto take = [&](size_t sz) {
+        unsigned char* r = b ? b + o : nullptr;
+        o += (sz + 255) & ~(size_t)255;
+        return r;
+    };
+    L.hdr = (M2lPairHdr*)take(sizeof(M2lPairHdr));
+    L.ocnt = (int*)take(sizeof(int) * 343);
+    L.obase = (int*)take(sizeof(int) * 344);
+    L.tbase = (int*)take(sizeof(int) * (ws.cells_max + 1));
+    L.tcount = (int*)take(sizeof(int) * ws.cells_max);
+    L.tmask = (uint32_t*)take(sizeof(uint32_t) * kPpWords * ws.cells_max);
+    L.items = (M2lPairItem*)take(sizeof(M2lPairItem) * ws.pp_item_cap);
+    L.pairs = (M2lPair*)take(sizeof(M2lPair) * ws.pp_slot_cap);
+    if (bytes) *bytes = o;
+    return L;
+}
+
+size_t m2l_pp_work_bytes(const Workspace& ws) {
+    Workspace w = ws;
+    w.pp_work = nullptr;
+    size_t b = 0;
+    pair_list(w, &b);
+    return b;
+}
+
+size_t m2l_pp_part_bytes(const Workspace& ws) {
+    return (size_t)ws.pp_slot_cap * ws.pp_stride * (ws.fp64 ? sizeof(double) : sizeof(float));
+}
+
+static int64_t target_cells_bound(int64_t n, int D) {
+    int64_t t = 0;
+    for (int l = 2; l <= D; ++l) {
+        const int64_t cl = (int64_t)1 << (3 * l);
+        t += n < cl ? n : cl;
+    }
+    return t > 0 ? t : 1;
+}
+
+cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    PpArgs a;
+    a.D = D;
+    a.linfo = ws.linfo;
+    a.code = ws.code;
+    a.cid = ws.cid;
+    const DenseLayout dl = dense_layout(D);
+    for (int l = 0; l < kMaxDepth + 2; ++l) a.off[l] = dl.off[l];
+    PairList L = pair_list(ws);
+    cudaError_t e = cudaMemsetAsync(L.ocnt, 0, sizeof(int) * 343, s);
+    if (e != cudaSuccess) return e;
+    const int64_t tb = target_cells_bound(n, D);
+    const int64_t warps = kPpThreads / 32;
+    const unsigned gc = (unsigned)std::min<int64_t>((tb + warps - 1) / warps, 152 * 8);
+    k_pp_count<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tcount, L.ocnt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pp_scan<<<1, kPpScanThreads, 0, s>>>(D, ws.linfo, ws.pp_slot_cap, (int)ws.pp_item_cap,
+                                            L.tcount, L.tbase, L.ocnt, L.obase, L.hdr, L.items,
+                                            ws.err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pp_fill<<<343, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.hdr, L.pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    PairList L = pair_list(ws);
+    const int64_t tb = target_cells_bound(n, D);
+    const unsigned gr = (unsigned)std::min<int64_t>((tb + 7) / 8, 152 * 16);
+    if (ws.fp64) {
+        k_pp_reduce<double><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
+                                               L.tbase, (const double*)ws.pp_part, (double*)ws.L);
+    } else if (width % 4 == 0 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
+        k_pp_reduce_f4<<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr, L.tbase,
+                                          (const float4*)ws.pp_part, (float*)ws.L);
+    } else {
+        k_pp_reduce<float><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
+                                              L.tbase, (const float*)ws.pp_part, (float*)ws.L);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t simt_pairs(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s) {
+    const int P = ws.P;
+    PairList L = pair_list(ws);
+    cudaError_t e;
+    if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+                         cudaSuccess)
+        return e;
+    const int64_t units = ws.pp_item_cap * 2 * ((P + kSimtCols - 1) / kSimtCols);
+    const unsigned grid = (unsigned)std::min<int64_t>(units, 152 * 8);
+    k_m2l_pairs_simt<T><<<grid, 256, 0, s>>>(P, ws.ld, ws.pp_stride, L.hdr, L.items, L.pairs,
+                                             (const T*)ws.M, (const T*)ws.T_m2l, (T*)ws.pp_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+                         cudaSuccess)
+        return e;
+    if ((e = launch_m2l_pairs_reduce(n, D, ws, P, s)) != cudaSuccess) return e;
+    const DenseLayout dl = dense_layout(D);
+    for (int l = 3; l <= l2l_last && l <= D; ++l) {
+        const int64_t cl = (int64_t)1 << (3 * l);
+        const int64_t cells = n < cl ? n : cl;
+        const unsigned g = (unsigned)std::min<int64_t>((cells + 3) / 4, 152 * 16);
+        k_l2l_simt<T><<<g, 128, 4 * P * sizeof(T), s>>>(l, P, ws.ld, ws.linfo, ws.code, ws.cid,
+                                                        dl.off[l - 1], (const T*)ws.T_l2l,
+                                                        (T*)ws.L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_m2l_pairs_simt(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s) {
+    if (D < 2) return cudaSuccess;
+    return ws.fp64 ? simt_pairs<double>(n, D, ws, l2l_last, s)
+                   : simt_pairs<float>(n, D, ws, l2l_last, s);
+}
+
+cudaError_t m2l_pairs_stats(const Workspace& ws, int64_t* out, cudaStream_t s) {
+    for (int k = 0; k < 4; ++k) out[k] = 0;
+    if (!ws.pp_work) return cudaSuccess;
+    M2lPairHdr h;
+    cudaError_t e = cudaMemcpyAsync(&h, pair_list(ws).hdr, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    out[0] = h.n_offsets;
+    out[1] = h.n_items;
+    out[2] = h.n_items;
+    out[3] = h.n_pairs;
+    return cudaSuccess;
+}
+
+}  // namespace pt

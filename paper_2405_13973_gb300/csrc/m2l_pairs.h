@@ -1,0 +1,45 @@
+// m2l_pairs.h -- the pair-packed M2L work list shared by the tensor-core and
+// the CUDA-core M2L kernels.  Not part of the ABI.
+//
+// M2L (Eq. FMM_local) at every level l >= 2 adds to a target cell t the
+// translation T_o M_{t-o} of each source cell t - o of its interaction list
+// (Sec. 2.3.2: children of the parent's neighbours that are not neighbours
+// of t; 189 offsets o per child octant, 316 distinct ones).  Expansions are
+// stored scaled by the cell size, so T_o depends on o only, not on the level:
+// the (target, source) pairs of one offset, gathered over every level, form
+// one dense product [pairs x P] x [P x P].  Each pair's result row is a
+// partial local expansion, stored in the target's slot row (a target's pairs
+// take consecutive slots in increasing offset order), and the target's L is
+// the sum of its slot rows in that order (deterministic).
+#pragma once
+#include "internal.h"
+
+namespace pt {
+
+constexpr int kPairRows = 128;   // pairs per work item (one tensor-core product)
+
+struct M2lPair {
+    int32_t src;   // global compact id of the source cell
+    int32_t slot;  // row of the partial-result array
+};
+struct M2lPairItem {
+    int32_t op, begin, rows, pad;  // offset index, first pair, pairs (<= kPairRows)
+};
+struct M2lPairHdr {
+    int n_items, n_pairs, n_targets, overflow;
+    int n_offsets, pad[3];
+};
+
+// The work list in ws.pp_work: header, per-offset counts and pair bases,
+// per-target slot bases, counts and candidate-presence words, the items and
+// the pairs.
+struct PairList {
+    M2lPairHdr* hdr;
+    int *ocnt, *obase, *tbase, *tcount;
+    uint32_t* tmask;
+    M2lPairItem* items;
+    M2lPair* pairs;
+};
+PairList pair_list(const Workspace& ws, size_t* bytes = nullptr);
+
+}  // namespace pt

@@ -55,11 +55,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "harmonics.cuh"
 #include "internal.h"
+#include "m2l_pairs.h"
 
 namespace pt {
 
@@ -311,7 +313,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2 };
+enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2, MODE_PAIR = 3 };
+
 constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator indices
 
 struct TcArgs {
@@ -335,6 +338,11 @@ struct TcArgs {
     const struct TcTile* tiles;
     const struct TcItem* items;
     const struct TcPlanHdr* hdr;
+    // pair-packed M2L work list (k_pp_*) and its partial rows [slot][Npad]
+    const M2lPair* pairs;
+    const M2lPairItem* pitems;
+    const M2lPairHdr* phdr;
+    float* ppart;
 };
 
 // One M2L tile (up to 128 targets of one level) and its non-empty offsets,
@@ -420,7 +428,7 @@ constexpr int kEpiThreads = 128;
 // of 128 target cells.  rank > 0 runs of M2L (and split > 0 of M2M) write
 // partial sums that a reduction adds afterwards.
 struct TcWork {
-    int level, oct, base, rows, begin, end, rank, tile, slot;
+    int level, oct, base, rows, begin, end, rank, tile, slot, op, pbegin;
 };
 
 // Work item idx of this launch: M2L reads the device work list; M2M and L2L
@@ -428,6 +436,21 @@ struct TcWork {
 template <int MODE>
 __device__ __forceinline__ bool tc_work(const TcArgs& a, const LevelInfo& li, int idx, TcWork& w) {
     w.rows = 0;
+    if (MODE == MODE_PAIR) {
+        const M2lPairItem it = a.pitems[idx];
+        w.op = it.op;
+        w.pbegin = it.begin;
+        w.rows = it.rows;
+        w.begin = 0;
+        w.end = 1;
+        w.rank = 0;
+        w.tile = -1;
+        w.slot = idx;
+        w.level = 0;
+        w.oct = 0;
+        w.base = 0;
+        return w.rows > 0;
+    }
     if (MODE == MODE_M2L) {
         const TcItem it = a.items[idx];
         const TcTile& tl = a.tiles[it.tile];
@@ -478,6 +501,7 @@ __device__ __forceinline__ bool tc_work(const TcArgs& a, const LevelInfo& li, in
 // packed operator index of term j of a work item
 template <int MODE>
 __device__ __forceinline__ int tc_op(const TcArgs& a, const TcWork& w, int j) {
+    if (MODE == MODE_PAIR) return w.op;
     if (MODE == MODE_M2L) return a.tiles[w.tile].terms[j];
     if (MODE == MODE_M2M) return kOpM2M + j;
     return kOpL2L + w.oct;
@@ -514,8 +538,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     const int NS = a.stages;
     // work items of this CTA: idx = first, first + stride, ... < count
     int count, first, stride;
-    if (MODE == MODE_M2L) {
-        count = a.hdr->n_items;
+    if (MODE == MODE_M2L || MODE == MODE_PAIR) {
+        count = MODE == MODE_PAIR ? a.phdr->n_items : a.hdr->n_items;
         first = blockIdx.x;
         stride = gridDim.x;
     } else {
@@ -604,7 +628,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                     }
                     // pre-split A rows arrive by cp.async (generic proxy): order
                     // them before the tensor core's reads
-                    if (MODE == MODE_M2L && BF16) fence_proxy_async();
+                    if ((MODE == MODE_M2L || MODE == MODE_PAIR) && BF16) fence_proxy_async();
                     tc_fence_after();
                     const uint32_t ah = smem_addr(base + st * stage_bytes);
                     if (BF16) {
@@ -641,7 +665,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             }
         }
     } else if (warp < kWarpEpi0) {
-        if (MODE == MODE_M2L && BF16) {
+        if ((MODE == MODE_M2L || MODE == MODE_PAIR) && BF16) {
             // ---- A producers, BF16x3 M2L: the sources' M rows are already
             // split into bf16 pieces (k_split_m), so each thread copies its
             // 16-byte unit (8 values) of each piece for two rows by cp.async
@@ -660,13 +684,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 for (int j = 0; j < 2; ++j) {
                     tix[j] = tiy[j] = tiz[j] = 0;
                     pg[j] = -1;
-                    if (r0 + 64 * j < w.rows) demorton3(a.code[w.base + r0 + 64 * j], tix[j], tiy[j], tiz[j]);
+                    if (MODE == MODE_M2L && r0 + 64 * j < w.rows)
+                        demorton3(a.code[w.base + r0 + 64 * j], tix[j], tiy[j], tiz[j]);
                 }
                 for (int it = 0; it < n_it; ++it) {
                     const int gg = g + it;
                     const int st = gg % NS, use = gg / NS;
                     const int kc = it % a.kchunks;
-                    if (kc == 0) {
+                    if (MODE == MODE_PAIR && it == 0) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            pg[j] = r0 + 64 * j < w.rows ? a.pairs[w.pbegin + r0 + 64 * j].src : -1;
+                    } else if (MODE == MODE_M2L && kc == 0) {
                         const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
                         const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
 #pragma unroll
@@ -727,7 +756,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 const int r = r0 + 32 * j;
                 tcode[j] = 0;
                 tix[j] = tiy[j] = tiz[j] = 0;
-                if (r < w.rows) {
+                if (MODE != MODE_PAIR && r < w.rows) {
                     tcode[j] = a.code[w.base + r];
                     demorton3(tcode[j], tix[j], tiy[j], tiz[j]);
                 }
@@ -742,7 +771,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 for (int j = 0; j < 4; ++j) {
                     int gs = -1;
                     if (r0 + 32 * j < w.rows) {
-                        if (MODE == MODE_M2L) {
+                        if (MODE == MODE_PAIR) {
+                            gs = a.pairs[w.pbegin + r0 + 32 * j].src;
+                        } else if (MODE == MODE_M2L) {
                             // a mixed tile's rows differ in octant: each takes its own offsets
                             const int sx = tix[j] - ox, sy = tiy[j] - oy, sz = tiz[j] - oz;
                             if (tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
@@ -845,7 +876,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             const int n_it = (w.end - w.begin) * a.kchunks;
             float* out;
             int64_t orow;
-            if (MODE == MODE_M2L && w.rank > 0) {
+            if (MODE == MODE_PAIR) {
+                out = a.ppart;
+                orow = row < w.rows ? (int64_t)a.pairs[w.pbegin + row].slot : 0;
+            } else if (MODE == MODE_M2L && w.rank > 0) {
                 out = a.part + (int64_t)w.slot * kTcRows * a.ld;  // this item's partial slab
                 orow = row;
             } else if (MODE == MODE_M2M && w.rank > 0) {
@@ -869,7 +903,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             // cell's own M2L result are all issued before the group's stores.
             // Columns P .. Npad-1 hold exact zeros (zero operator rows), so
             // whole 16-byte units are written.
-            float* orow_p = out + orow * a.ld;
+            float* orow_p = out + orow * (MODE == MODE_PAIR ? a.Npad : a.ld);
             const float* own_p = a.L + orow * a.ld;
             const bool live = row < w.rows;
             for (int cb0 = 0; cb0 * 16 < a.Npad; cb0 += 4) {
@@ -1206,6 +1240,8 @@ __global__ void k_tc_reduce(int lfirst, int llast, int ld, int nparts, const Lev
 
 void host_m2l_offsets(int16_t out[8][189]);
 
+int m2l_tc_npad(int p) { return tc_geom(p, true).Npad; }
+
 size_t m2l_tc_operand_bytes(int p, bool bf16) {
     if (!tc_supported(p, bf16)) return 0;
     TcGeom g = tc_geom(p, bf16);
@@ -1288,6 +1324,7 @@ static cudaError_t tc_launch_mode(const TcArgs& a, unsigned grid, int smem, cuda
     return cudaGetLastError();
 }
 static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
+    if (a.mode == MODE_PAIR) return tc_launch_mode<MODE_PAIR>(a, grid, smem, s);
     if (a.mode == MODE_M2L) return tc_launch_mode<MODE_M2L>(a, grid, smem, s);
     if (a.mode == MODE_M2M) return tc_launch_mode<MODE_M2M>(a, grid, smem, s);
     return tc_launch_mode<MODE_L2L>(a, grid, smem, s);
@@ -1308,6 +1345,8 @@ cudaError_t m2l_tc_init() {
     };
     set((const void*)k_m2l_tc<MODE_M2L, 0>);
     set((const void*)k_m2l_tc<MODE_M2L, 1>);
+    set((const void*)k_m2l_tc<MODE_PAIR, 0>);
+    set((const void*)k_m2l_tc<MODE_PAIR, 1>);
     set((const void*)k_m2l_tc<MODE_M2M, 0>);
     set((const void*)k_m2l_tc<MODE_M2M, 1>);
     set((const void*)k_m2l_tc<MODE_L2L, 0>);
@@ -1404,8 +1443,21 @@ static bool tc_worklist_layout(int64_t n, int D, Workspace& ws, int64_t& tiles, 
     return tiles <= ws.tc_tiles_cap;
 }
 
+
+static TcArgs pair_args(int64_t n, int D, Workspace& ws) {
+    TcArgs a = base_args(n, D, ws, 1);
+    a.mode = MODE_PAIR;
+    PairList L = pair_list(ws);
+    a.pairs = L.pairs;
+    a.pitems = L.items;
+    a.phdr = L.hdr;
+    a.ppart = (float*)ws.pp_part;
+    return a;
+}
+
 cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
+    if (ws.m2l_pairs) return launch_m2l_pairs_worklist(n, D, ws, s);
     int64_t tiles;
     TcPlanHdr* hdr;
     TcTile* tl;
@@ -1424,10 +1476,50 @@ cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t
     return cudaGetLastError();
 }
 
+// L2L shifts level by level, levels 3 .. l2l_last (level 2 has no parent
+// expansion); each adds the cell's own M2L result already in L.
+static cudaError_t launch_l2l_levels(int64_t n, int D, Workspace& ws, int l2l_last, int smem,
+                                     cudaStream_t s) {
+    for (int l = 3; l <= l2l_last && l <= D; ++l) {
+        TcArgs b = base_args(n, D, ws, 1);
+        b.mode = MODE_L2L;
+        b.level = l;
+        const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
+        cudaError_t e = tc_launch(b, (unsigned)t2, smem, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static int sm_count() {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 152;
+}
+
 cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s,
                               cudaEvent_t after_m2l) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
+    if (ws.m2l_pairs) {
+        TcArgs a = pair_args(n, D, ws);
+        cudaError_t e;
+        if (ws.tc_bf16) {
+            k_split_m<<<152 * 8, 256, 0, s>>>(2, D, ws.ld, ws.linfo, (const float*)ws.M, ws.M_pieces);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return e;
+        if ((e = tc_launch(a, (unsigned)sm_count(), smem, s)) != cudaSuccess) return e;
+        if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+                             cudaSuccess)
+            return e;
+        if (after_m2l && (e = cudaEventRecord(after_m2l, s)) != cudaSuccess) return e;
+        if ((e = launch_m2l_pairs_reduce(n, D, ws, a.Npad, s)) != cudaSuccess) return e;
+        return launch_l2l_levels(n, D, ws, l2l_last, smem, s);
+    }
     int64_t tiles;
     TcPlanHdr* hdr;
     TcTile* tl;
@@ -1444,31 +1536,26 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cud
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // persistent: one CTA per SM walks the work list
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = tc_launch(a, (unsigned)(sms > 0 ? sms : 152), smem, s)) != cudaSuccess) return e;
+    if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+                         cudaSuccess)
+        return e;
+    if ((e = tc_launch(a, (unsigned)sm_count(), smem, s)) != cudaSuccess) return e;
+    if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+                         cudaSuccess)
+        return e;
     if (after_m2l && (e = cudaEventRecord(after_m2l, s)) != cudaSuccess) return e;
     const int64_t rg = tiles * kRedSlices;
     k_tc_reduce_tiles<<<(unsigned)(rg < 152 * 16 ? rg : 152 * 16), 256, 0, s>>>(
         ws.ld, hdr, tl, (const float4*)ws.tc_part, (float4*)ws.L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // L2L shifts level by level, levels 3 .. l2l_last (level 2 has no parent
-    // expansion)
-    for (int l = 3; l <= l2l_last && l <= D; ++l) {
-        TcArgs b = base_args(n, D, ws, 1);
-        b.mode = MODE_L2L;
-        b.level = l;
-        const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
-        if ((e = tc_launch(b, (unsigned)t2, smem, s)) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return launch_l2l_levels(n, D, ws, l2l_last, smem, s);
 }
 
 // Work-list counts of the last M2L launch: {tiles, tile-offset products
 // (sum of the tiles' non-empty offsets), work items, target rows}.
 cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s) {
     for (int k = 0; k < 4; ++k) out[k] = 0;
+    if (ws.m2l_pairs) return m2l_pairs_stats(ws, out, s);
     if (!ws.tc_work) return cudaSuccess;
     TcPlanHdr h;
     cudaError_t e = cudaMemcpyAsync(&h, ws.tc_work, sizeof h, cudaMemcpyDeviceToHost, s);

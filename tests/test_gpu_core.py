@@ -128,6 +128,30 @@ def test_tensor_core_m2l_matches_cuda_core_m2l(sphere4k, depth, tc):
     assert rel(out[tc], out["fp32"]) < {"tf32x3": 1e-5, "bf16x3": 5e-6}[tc]
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "fp32", "fp64"])
+@pytest.mark.parametrize("depth", [2, 3, 4, 5])
+def test_pair_schedule_equals_tile_schedule(sphere4k, depth, prec):
+    # The two M2L schedules compute the same translations and differ only in
+    # the order of the sums (tensor cores: FP32 in tensor memory over runs of
+    # offsets vs one partial per pair, summed in offset order; CUDA cores:
+    # per-target loops over the offsets vs the same per-pair partials): the
+    # far fields agree to the arithmetic's rounding, and the pair schedule is
+    # deterministic (bitwise equal on a second evaluation).
+    pos, q, Eo, _ = sphere4k
+    out = {}
+    for sched in ("tiles", "pairs"):
+        plan = pt.Plan(len(q), p=10, depth=depth, precision=prec)
+        plan.set_m2l_schedule(sched)
+        plan.set_phases(pt.PT_PHASE_FAR)
+        E, _ = plan.forces(dev_pos(pos), dev_vec(q))
+        out[sched] = E.cpu().numpy().T
+        if sched == "pairs":
+            E2, _ = plan.forces(dev_pos(pos), dev_vec(q))
+            assert np.array_equal(E2.cpu().numpy().T, out[sched])
+        plan.close()
+    assert rel(out["pairs"], out["tiles"]) < (1e-12 if prec == "fp64" else 2e-6)
+
+
 def test_field_of_one_and_two_ions():
     for precision in ("fp64", "fp32", "tf32x3", "bf16x3"):
         plan = pt.Plan(2, p=6, precision=precision)
@@ -139,7 +163,7 @@ def test_field_of_one_and_two_ions():
         ke = 1 / (4 * math.pi * W.EPS0)
         want = ke * W.E_CHARGE / r**2
         e = E.cpu().numpy()
-        tol = 1e-14 if precision == "fp64" else 2e-6
+        tol = 1e-14 if precision == "fp64" else 1e-6
         assert abs(e[0, 1] - want) < tol * want and abs(e[0, 0] + want) < tol * want
         plan.close()
 

@@ -13,7 +13,9 @@ Definitions counted:
   * tensor-core tiles: per level, cells in (child octant, parent Morton code)
     order, cut into 128-row tiles, per octant on levels holding at least 512
     cells and across octants below; a tile's products are the offsets with at
-    least one admitted target row whose source cell holds ions.
+    least one admitted target row whose source cell holds ions;
+  * pair-packed products: per offset, its pairs over every level, cut into
+    runs of 128.
 """
 import numpy as np
 import pytest
@@ -41,6 +43,7 @@ def decode(codes, l):
 def expected_counts(pos, D):
     keys, _, _ = oracle.leaf_keys(pos, D)
     out = {"cells": 0, "m2l_pairs": 0, "shifts": 0, "tiles": 0, "products": 0, "rows": 0}
+    per_offset = np.zeros(len(offs), np.int64)
     offs = [(ox, oy, oz) for ox in range(-3, 4) for oy in range(-3, 4) for oz in range(-3, 4)
             if max(abs(ox), abs(oy), abs(oz)) > 1]
     for l in range(2, D + 1):
@@ -59,6 +62,7 @@ def expected_counts(pos, D):
             adm = np.all((o >= b - 3) & (o <= b + 2), axis=1)
             s = xyz - o + 3
             valid[:, k] = adm & occ[s[:, 0], s[:, 1], s[:, 2]]
+        per_offset += valid.sum(0)
         out["cells"] += len(codes)
         out["m2l_pairs"] += int(valid.sum())
         out["shifts"] += len(codes) if l >= 3 else 0
@@ -81,6 +85,8 @@ def expected_counts(pos, D):
         p2p += m * nb - m
     out["p2p_pairs"] = p2p
     out["leaves"] = len(cnt)
+    out["pair_offsets"] = int((per_offset > 0).sum())
+    out["pair_products"] = int(((per_offset + ROWS - 1) // ROWS).sum())
     return out
 
 
@@ -93,11 +99,18 @@ def test_interaction_and_work_list_counts(crystal, D):
     n = len(pos)
     q = np.full(n, W.E_CHARGE)
     plan = pt.Plan(n, p=12, depth=D, precision="bf16x3")
+    plan.set_m2l_schedule("tiles")
     pd = torch.tensor(np.ascontiguousarray(pos.T), dtype=torch.float64, device=DEV)
     plan.forces(pd, torch.tensor(q, dtype=torch.float64, device=DEV), want_phi=False)
     st, tc = plan.stats(), plan.tc_stats()
+    plan.set_m2l_schedule("pairs")
+    plan.forces(pd, torch.tensor(q, dtype=torch.float64, device=DEV), want_phi=False)
+    tp = plan.tc_stats()
     plan.close()
     ex = expected_counts(pos, D)
+    # pair-packed work list: offsets with pairs, 128-row runs per offset, every pair once
+    assert tp == {"tiles": ex["pair_offsets"], "products": ex["pair_products"],
+                  "items": ex["pair_products"], "rows": ex["m2l_pairs"]}
     assert (st["n"], st["depth"], st["leaves"], st["cells"]) == (n, D, ex["leaves"], ex["cells"])
     assert st["m2l_pairs"] == ex["m2l_pairs"]
     assert st["p2p_pairs"] == ex["p2p_pairs"]
