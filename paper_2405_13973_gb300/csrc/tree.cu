@@ -346,33 +346,38 @@ __device__ __forceinline__ double4_32a make4<double4_32a>(double a, double b, do
     return make_double4_32a(a, b, c, d);
 }
 
+// One thread per sorted slot: the slot's ion (in arrival order within its
+// leaf) takes the rank of its index among the leaf's ions, so every leaf
+// lists its ions by original index (deterministic whatever the atomic order
+// of k_keys); the leaf's ions are read from the few cache lines the
+// neighbouring threads share.
 template <typename T4>
 __global__ void k_leaf_gather(const double* __restrict__ x, const double* __restrict__ y,
-                              const double* __restrict__ z, const double* __restrict__ q, int D,
-                              const RootCube* root, const LevelInfo* linfo,
-                              const uint32_t* __restrict__ code, const int32_t* __restrict__ cstart,
-                              const int32_t* __restrict__ ccount, const int32_t* __restrict__ perm_tmp,
-                              int32_t* perm, int32_t* slot_of, int32_t* leaf_of, T4* sorted) {
-    const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
+                              const double* __restrict__ z, const double* __restrict__ q, int64_t n,
+                              int D, const RootCube* root, const uint32_t* __restrict__ key,
+                              const int32_t* __restrict__ leaf_start,
+                              const int32_t* __restrict__ cid_leaf,
+                              const int32_t* __restrict__ perm_tmp, int32_t* perm,
+                              int32_t* slot_of, int32_t* leaf_of, T4* sorted) {
     const double lo0 = root->lo[0], lo1 = root->lo[1], lo2 = root->lo[2], side = root->side;
     const double scale = (double)(1 << D);
-    for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
-        const int s = cstart[g], k = ccount[g];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int idx = perm_tmp[i];
+        const uint32_t c = key[idx];
+        const int s = leaf_start[c], k = leaf_start[c + 1] - s;
+        int r = 0;
+        for (int u = 0; u < k; ++u) r += (perm_tmp[s + u] < idx);
+        const int slot = s + r;
         int ix, iy, iz;
-        demorton3(code[g], ix, iy, iz);
-        for (int t = threadIdx.x; t < k; t += blockDim.x) {
-            const int idx = perm_tmp[s + t];
-            int r = 0;
-            for (int u = 0; u < k; ++u) r += (perm_tmp[s + u] < idx);
-            const int slot = s + r;
-            perm[slot] = idx;
-            slot_of[idx] = slot;
-            leaf_of[slot] = g;
-            double ux = (x[idx] - lo0) / side * scale - (ix + 0.5);
-            double uy = (y[idx] - lo1) / side * scale - (iy + 0.5);
-            double uz = (z[idx] - lo2) / side * scale - (iz + 0.5);
-            sorted[slot] = make4<T4>(ux, uy, uz, q[idx]);
-        }
+        demorton3(c, ix, iy, iz);
+        perm[slot] = idx;
+        slot_of[idx] = slot;
+        leaf_of[slot] = cid_leaf[c];
+        const double ux = (x[idx] - lo0) / side * scale - (ix + 0.5);
+        const double uy = (y[idx] - lo1) / side * scale - (iy + 0.5);
+        const double uz = (z[idx] - lo2) / side * scale - (iz + 0.5);
+        sorted[slot] = make4<T4>(ux, uy, uz, q[idx]);
     }
 }
 
@@ -407,14 +412,15 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
     }
     k_scatter<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(ws.key, ws.rank, ws.leaf_start, n,
                                                             ws.perm_tmp);
-    const int grid_leaves = 152 * 8;
+    const int g = grid_ions > 0 ? grid_ions : 1;
+    const int32_t* cid_leaf = ws.cid + dl.off[D];
     if (ws.fp64)
-        k_leaf_gather<double4_32a><<<grid_leaves, 128, 0, s>>>(
-            x, y, z, q, D, ws.root, ws.linfo, ws.code, ws.cstart, ws.ccount, ws.perm_tmp, ws.perm,
+        k_leaf_gather<double4_32a><<<g, 256, 0, s>>>(
+            x, y, z, q, n, D, ws.root, ws.key, ws.leaf_start, cid_leaf, ws.perm_tmp, ws.perm,
             ws.slot_of, ws.leaf_of, (double4_32a*)ws.sorted);
     else
-        k_leaf_gather<int4><<<grid_leaves, 128, 0, s>>>(
-            x, y, z, q, D, ws.root, ws.linfo, ws.code, ws.cstart, ws.ccount, ws.perm_tmp, ws.perm,
+        k_leaf_gather<int4><<<g, 256, 0, s>>>(
+            x, y, z, q, n, D, ws.root, ws.key, ws.leaf_start, cid_leaf, ws.perm_tmp, ws.perm,
             ws.slot_of, ws.leaf_of, (int4*)ws.sorted);
     return cudaGetLastError();
 }
@@ -424,17 +430,28 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
 // ---------------------------------------------------------------------------
 __global__ void k_level_nonempty(const int32_t* __restrict__ leaf_start, int Dm,
                                  int32_t* counts) {
-    // thread per (level, cell) pair over levels 0..Dm
+    // thread per (level, cell) pair over levels 0..Dm; per-thread counts per
+    // level, summed over the warp before one atomic per level and warp
     int64_t total = 0;
     for (int l = 0; l <= Dm; ++l) total += (int64_t)1 << (3 * l);
+    int mine[kMaxDepth + 1];
+#pragma unroll
+    for (int l = 0; l <= kMaxDepth; ++l) mine[l] = 0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total;
          v += (int64_t)gridDim.x * blockDim.x) {
         int l = 0;
         int64_t base = 0;
         while (v >= base + ((int64_t)1 << (3 * l))) { base += (int64_t)1 << (3 * l); ++l; }
-        int64_t c = v - base;
-        int sh = 3 * (Dm - l);
-        if (leaf_start[(c + 1) << sh] - leaf_start[c << sh] > 0) atomicAdd(&counts[l], 1);
+        const int64_t c = v - base;
+        const int sh = 3 * (Dm - l);
+        const int ne = leaf_start[(c + 1) << sh] - leaf_start[c << sh] > 0 ? 1 : 0;
+#pragma unroll
+        for (int k = 0; k <= kMaxDepth; ++k) mine[k] += (k == l) ? ne : 0;
+    }
+#pragma unroll
+    for (int l = 0; l <= kMaxDepth; ++l) {
+        const int w = __reduce_add_sync(0xffffffffu, mine[l]);
+        if ((threadIdx.x & 31) == 0 && w > 0) atomicAdd(&counts[l], w);
     }
 }
 
