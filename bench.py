@@ -358,7 +358,7 @@ def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=
     qd = torch.tensor(q, dtype=torch.float64, device="cuda")
     try:
         plan = pt.Plan(n, p=p, leaf_max=32, depth=-1, precision=precision)
-        if schedule and precision in ("tf32x3", "bf16x3"):
+        if schedule:
             plan.set_m2l_schedule(schedule)
     except pt.PenningError as exc:
         return {"status": str(exc)}
@@ -378,8 +378,7 @@ def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=
         ms.append(a.elapsed_time(b))
     out = {"ms": float(np.mean(ms)), "evals_per_s": 1e3 / float(np.mean(ms)),
            "ion_evals_per_s": n * 1e3 / float(np.mean(ms)), "depth": plan.last_depth}
-    if precision in ("tf32x3", "bf16x3"):
-        out["m2l_schedule"] = plan.m2l_schedule
+    out["m2l_schedule"] = plan.m2l_schedule
     if ref is not None:
         Er, idx, _ = ref
         e = E.cpu().numpy().T
@@ -524,8 +523,8 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched-ensemble measurement with this many crystals instead of the "
                          "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
-    ap.add_argument("--schedule", default="", choices=["", "tiles", "pairs"],
-                    help="M2L schedule of the tensor-core precisions (default: the library's)")
+    ap.add_argument("--schedule", default="", choices=["", "tiles", "pairs", "rotation"],
+                    help="M2L schedule (default: the library's for the plan)")
     ap.add_argument("--forces", type=int, default=0,
                     help="only single force evaluations of this many ions (sweep sphere)")
     ap.add_argument("--no-ref", action="store_true", help="--forces without the error reference")
@@ -709,7 +708,7 @@ def main():
                               profile=False)
         out["fp64_path"] = {"value": n * args.fp64_steps / (sum(ms64) * 1e-3),
                             "ms_per_step": sum(ms64) / args.fp64_steps, "force_err": e64,
-                            "depth": plan64.last_depth}
+                            "depth": plan64.last_depth, "m2l_schedule": plan64.m2l_schedule}
         plan64.close()
 
     # order p = 10 beside the headline (both tensor-core operand formats)

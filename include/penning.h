@@ -118,28 +118,39 @@ int fmm_plan_set_expansion(fmm_plan plan, int mode);
  * source cells per target, at most 316 distinct offsets o = target - source
  * per level).  The translation operator depends on the offset only
  * (expansions are stored scaled by the cell size), so:
- *   PT_M2L_TILES  tensor cores: tiles of 128 target cells of one level and
- *                 child octant, per non-empty offset one dense product of
- *                 all 128 rows (rows whose source is empty multiply zeros),
- *                 summed in tensor memory over runs of up to four offsets;
- *                 CUDA cores: per level, tiles of 32 targets of one octant
- *                 looping over their 189 offsets (and the L2L shift);
- *   PT_M2L_PAIRS  the (target, source) pairs of each offset, gathered over
- *                 all levels, fill products of 128 pairs (tensor cores) or
- *                 64 x 64 SIMT tiles (CUDA cores); each pair's result row is
- *                 a partial local expansion, and each target's partials are
- *                 summed in increasing offset order (deterministic).  Fewer,
- *                 fuller products on small or flat crystals, at the price of
- *                 a pool of partial rows: about 189 x 9.2 n / leaf_max pairs
- *                 (exact bound with a fixed depth) x (P rounded up to 16 on
- *                 the tensor cores, the row stride of M and L on the CUDA
- *                 cores) values.  A step whose pairs exceed the pool returns
- *                 PT_ERR_OOM.
- * Default: PT_M2L_PAIRS for n_max <= 65536, else PT_M2L_TILES.  Selecting
- * the other schedule allocates what it needs.
- * Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
+ *   PT_M2L_TILES     tensor cores: tiles of 128 target cells of one level
+ *                    and child octant, per non-empty offset one dense
+ *                    product of all 128 rows (rows whose source is empty
+ *                    multiply zeros), summed in tensor memory over runs of
+ *                    up to four offsets; CUDA cores: per level, tiles of 32
+ *                    targets of one octant looping over their 189 offsets
+ *                    (and the L2L shift);
+ *   PT_M2L_PAIRS     the (target, source) pairs of each offset, gathered
+ *                    over all levels, fill products of 128 pairs (tensor
+ *                    cores) or 64 x 64 SIMT tiles (CUDA cores); each pair's
+ *                    result row is a partial local expansion, and each
+ *                    target's partials are summed in increasing offset order
+ *                    (deterministic).  Fewer, fuller products on small or flat
+ *                    crystals, at the price of a pool of partial rows: about
+ *                    189 x 9.2 n / leaf_max pairs (exact bound with a fixed
+ *                    depth) x (P rounded up to 16 on the tensor cores, the row
+ *                    stride of M and L on the CUDA cores) values.  A step
+ *                    whose pairs exceed the pool returns PT_ERR_OOM;
+ *   PT_M2L_ROTATION  CUDA-core precisions, p <= 16: the pair work list, each
+ *                    translation done by rotating the multipole so that the
+ *                    offset points along +z, translating along z (orders m
+ *                    do not mix) and rotating back (the point-and-shoot
+ *                    factorisation of the dense operator, exact up to
+ *                    rounding): O(p^3) instead of (p+1)^4 multiply-adds per
+ *                    translation (7.3k instead of 28.6k at p = 12).
+ * Default: PT_M2L_ROTATION for FP64 and PT_M2L_PAIRS for the other
+ * precisions up to n_max = 65536, PT_M2L_TILES above.  Selecting another
+ * schedule allocates what it needs.
+ * Errors: PT_ERR_ARG, PT_ERR_UNSUPPORTED (rotation on the tensor-core
+ * precisions or beyond p = 16), PT_ERR_OOM, PT_ERR_CUDA. */
 #define PT_M2L_TILES 0
 #define PT_M2L_PAIRS 1
+#define PT_M2L_ROTATION 2
 int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule);
 /* The plan's M2L schedule (PT_M2L_*), or -1 for a NULL plan. */
 int fmm_plan_m2l_schedule(fmm_plan plan);

@@ -26,7 +26,7 @@ PT_ERR_NONFINITE, PT_ERR_ESCAPED, PT_ERR_TIMEOUT, PT_ERR_COINCIDENT, PT_ERR_UNSU
 PT_FP64, PT_MIXED_TF32X3, PT_MIXED_BF16X3, PT_FP32 = 0, 1, 2, 3
 PT_PHASE_NEAR, PT_PHASE_FAR, PT_PHASE_ALL = 1, 2, 3
 EXPAND_TREE, EXPAND_DIRECT = 0, 1
-M2L_TILES, M2L_PAIRS = 0, 1
+M2L_TILES, M2L_PAIRS, M2L_ROTATION = 0, 1, 2
 PT_MAX_BEAMS = 8
 PRECISIONS = {"fp64": PT_FP64, "tf32x3": PT_MIXED_TF32X3, "bf16x3": PT_MIXED_BF16X3,
               "fp32": PT_FP32}
@@ -266,16 +266,17 @@ class Plan:
         _check(load(False).fmm_plan_set_expansion(self._h, int(mode)), "fmm_plan_set_expansion")
 
     def set_m2l_schedule(self, schedule):
-        """M2L_TILES or M2L_PAIRS ("tiles" / "pairs") for the tensor-core
-        precisions (fmm_plan_set_m2l_schedule)."""
+        """M2L_TILES, M2L_PAIRS or M2L_ROTATION ("tiles" / "pairs" /
+        "rotation") (fmm_plan_set_m2l_schedule)."""
         if isinstance(schedule, str):
-            schedule = {"tiles": M2L_TILES, "pairs": M2L_PAIRS}[schedule]
+            schedule = {"tiles": M2L_TILES, "pairs": M2L_PAIRS, "rotation": M2L_ROTATION}[schedule]
         _check(load(False).fmm_plan_set_m2l_schedule(self._h, int(schedule)),
                "fmm_plan_set_m2l_schedule")
 
     @property
     def m2l_schedule(self) -> str:
-        return {M2L_TILES: "tiles", M2L_PAIRS: "pairs"}[int(load(False).fmm_plan_m2l_schedule(self._h))]
+        return {M2L_TILES: "tiles", M2L_PAIRS: "pairs",
+                M2L_ROTATION: "rotation"}[int(load(False).fmm_plan_m2l_schedule(self._h))]
 
     @property
     def last_depth(self) -> int:

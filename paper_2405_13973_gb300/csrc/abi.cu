@@ -119,6 +119,7 @@ struct OpSet {
     void* T_l2l = nullptr;
     void* T_m2l = nullptr;
     void* T_m2l_tc = nullptr;
+    void* T_rot = nullptr;   // rotation-based M2L operators (CUDA-core precisions)
 };
 std::mutex g_ops_mu;
 std::map<std::tuple<int, int, int>, OpSet> g_ops;
@@ -132,6 +133,7 @@ void release_ops(fmm_plan_s* pl) {
         cudaFree(it->second.T_l2l);
         cudaFree(it->second.T_m2l);
         if (it->second.T_m2l_tc) cudaFree(it->second.T_m2l_tc);
+        if (it->second.T_rot) cudaFree(it->second.T_rot);
         g_ops.erase(it);
     }
     pl->ops_held = false;
@@ -218,6 +220,28 @@ int build_operators(fmm_plan_s* pl) {
     cudaError_t e = pl->ws.fp64 ? upload_ops<double>(pl, m2m, l2l, m2l)
                                 : upload_ops<float>(pl, m2m, l2l, m2l);
     if (e != cudaSuccess) return status_from(e);
+    if (pl->ws.T_rot) {
+        // rotation-based M2L operators of every offset index (neighbours zero)
+        const int nv = pl->ws.rot_op_vals;
+        std::vector<double> rot((size_t)343 * nv, 0.0);
+        for (int ox = -3; ox <= 3; ++ox)
+            for (int oy = -3; oy <= 3; ++oy)
+                for (int oz = -3; oz <= 3; ++oz) {
+                    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+                    const int idx = (ox + 3) * 49 + (oy + 3) * 7 + (oz + 3);
+                    if (!ops::build_m2l_rotation(p, ox, oy, oz, &rot[(size_t)idx * nv]))
+                        return PT_ERR_CUDA;
+                }
+        if (pl->ws.fp64) {
+            e = cudaMemcpy(pl->ws.T_rot, rot.data(), rot.size() * sizeof(double),
+                           cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> rf(rot.begin(), rot.end());
+            e = cudaMemcpy(pl->ws.T_rot, rf.data(), rf.size() * sizeof(float),
+                           cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return status_from(e);
+    }
     if (is_tc(pl->precision)) {
         const bool bf16 = pl->precision == PT_MIXED_BF16X3;
         std::vector<unsigned char> packed(m2l_tc_operand_bytes(p, bf16));
@@ -226,6 +250,17 @@ int build_operators(fmm_plan_s* pl) {
         if (e != cudaSuccess) return status_from(e);
     }
     return PT_OK;
+}
+
+// Rotation-based M2L operators: CUDA-core precisions whose operators fit the
+// kernel's shared memory.
+size_t rot_operator_bytes(const fmm_plan_s* pl) {
+    if (is_tc(pl->precision)) return 0;
+    const size_t tsz = pl->precision == PT_FP64 ? sizeof(double) : sizeof(float);
+    Workspace w = pl->ws;
+    w.rot_op_vals = ops::rot_op_vals(pl->p);
+    if (m2l_rot_tile(w) == 0) return 0;
+    return (size_t)343 * w.rot_op_vals * tsz;
 }
 
 // Points the plan at the shared operator set of its (device, p, precision),
@@ -238,26 +273,31 @@ int acquire_ops(fmm_plan_s* pl, size_t op_bytes) {
     if (it == g_ops.end()) {
         OpSet o;
         const size_t tc = is_tc(pl->precision) ? m2l_tc_operand_bytes(pl->p, ws.tc_bf16 != 0) : 0;
+        const size_t rot = rot_operator_bytes(pl);
         if (cudaMalloc(&o.T_m2m, 8 * op_bytes) != cudaSuccess ||
             cudaMalloc(&o.T_l2l, 8 * op_bytes) != cudaSuccess ||
             cudaMalloc(&o.T_m2l, 343 * op_bytes) != cudaSuccess ||
-            (tc && cudaMalloc(&o.T_m2l_tc, tc) != cudaSuccess)) {
+            (tc && cudaMalloc(&o.T_m2l_tc, tc) != cudaSuccess) ||
+            (rot && cudaMalloc(&o.T_rot, rot) != cudaSuccess)) {
             cudaFree(o.T_m2m);
             cudaFree(o.T_l2l);
             cudaFree(o.T_m2l);
+            cudaFree(o.T_m2l_tc);
             return PT_ERR_OOM;
         }
         ws.T_m2m = o.T_m2m;
         ws.T_l2l = o.T_l2l;
         ws.T_m2l = o.T_m2l;
         ws.T_m2l_tc = o.T_m2l_tc;
+        ws.T_rot = o.T_rot;
         int r = build_operators(pl);
         if (r != PT_OK) {
             cudaFree(o.T_m2m);
             cudaFree(o.T_l2l);
             cudaFree(o.T_m2l);
             if (o.T_m2l_tc) cudaFree(o.T_m2l_tc);
-            ws.T_m2m = ws.T_l2l = ws.T_m2l = ws.T_m2l_tc = nullptr;
+            if (o.T_rot) cudaFree(o.T_rot);
+            ws.T_m2m = ws.T_l2l = ws.T_m2l = ws.T_m2l_tc = ws.T_rot = nullptr;
             return r;
         }
         it = g_ops.emplace(key, o).first;
@@ -267,6 +307,7 @@ int acquire_ops(fmm_plan_s* pl, size_t op_bytes) {
     ws.T_l2l = it->second.T_l2l;
     ws.T_m2l = it->second.T_m2l;
     ws.T_m2l_tc = it->second.T_m2l_tc;
+    ws.T_rot = it->second.T_rot;
     pl->ops_held = true;
     return PT_OK;
 }
@@ -404,7 +445,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.laser = lz;
     key.profile = plan->profile;
     key.expand = plan->ws.expand;
-    key.sched = plan->ws.m2l_pairs;
+    key.sched = plan->ws.m2l_pairs + 2 * plan->ws.m2l_rot;
     return key;
 }
 
@@ -616,17 +657,24 @@ static int alloc_tile_slabs(fmm_plan_s* pl) {
 }
 
 int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule) {
-    if (!plan || (schedule != PT_M2L_TILES && schedule != PT_M2L_PAIRS)) return PT_ERR_ARG;
+    if (!plan || (schedule != PT_M2L_TILES && schedule != PT_M2L_PAIRS &&
+                  schedule != PT_M2L_ROTATION))
+        return PT_ERR_ARG;
+    if (schedule == PT_M2L_ROTATION && (is_tc(plan->precision) || !plan->ws.T_rot))
+        return PT_ERR_UNSUPPORTED;
     if (cudaSetDevice(plan->device) != cudaSuccess) return PT_ERR_CUDA;
-    int r = schedule == PT_M2L_PAIRS ? alloc_pairs(plan)
+    int r = schedule != PT_M2L_TILES ? alloc_pairs(plan)
             : is_tc(plan->precision) ? alloc_tile_slabs(plan) : PT_OK;
     if (r != PT_OK) return r;
-    plan->ws.m2l_pairs = schedule == PT_M2L_PAIRS ? 1 : 0;
+    plan->ws.m2l_pairs = schedule != PT_M2L_TILES ? 1 : 0;
+    plan->ws.m2l_rot = schedule == PT_M2L_ROTATION ? 1 : 0;
     return PT_OK;
 }
 
 int fmm_plan_m2l_schedule(fmm_plan plan) {
-    return plan ? (plan->ws.m2l_pairs ? PT_M2L_PAIRS : PT_M2L_TILES) : -1;
+    if (!plan) return -1;
+    if (plan->ws.m2l_rot) return PT_M2L_ROTATION;
+    return plan->ws.m2l_pairs ? PT_M2L_PAIRS : PT_M2L_TILES;
 }
 
 int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precision,
@@ -681,6 +729,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
     ws.fp64 = (precision == PT_FP64);
     ws.tc_bf16 = (precision == PT_MIXED_BF16X3) ? 1 : 0;
     ws.ld = ws.fp64 ? pl->P : ((pl->P + 31) / 32) * 32;
+    ws.rot_op_vals = rot_operator_bytes(pl) > 0 ? ops::rot_op_vals(p) : 0;
     if (depth >= 0) {
         ws.depth_max = depth;
     } else {
@@ -706,7 +755,8 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
         // error, not a lack of memory
         std::lock_guard<std::mutex> g(g_tables_mu);
         if (!g_tables_dev.count(pl->device)) {
-            if (upload_harmonic_tables() != cudaSuccess || m2l_tc_init() != cudaSuccess) {
+            if (upload_harmonic_tables() != cudaSuccess || m2l_tc_init() != cudaSuccess ||
+                m2l_rot_init() != cudaSuccess) {
                 free_plan(pl);
                 return PT_ERR_CUDA;
             }
@@ -750,14 +800,18 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
             ws.m2l_pairs = ok ? 1 : 0;
         }
     } else if (ok && n_max <= kPairsDefaultIons) {
-        // CUDA-core precisions: the pair-packed M2L by default as well
+        // CUDA-core precisions: the pair work list by default as well, with
+        // the rotation-based M2L for FP64 (a quarter of the dense
+        // translation's FP64 operations at p = 12)
         ok = alloc_pairs(pl) == PT_OK;
         ws.m2l_pairs = ok ? 1 : 0;
+        ws.m2l_rot = ok && ws.fp64 && ws.rot_op_vals > 0 ? 1 : 0;
     }
     if (dry) {
         *dry_bytes = (int64_t)pl->dry_bytes;
         *op_bytes = (int64_t)(tsz * (8 + 8 + 343) * PP +
-                              (is_tc(precision) ? m2l_tc_operand_bytes(p, ws.tc_bf16 != 0) : 0));
+                              (is_tc(precision) ? m2l_tc_operand_bytes(p, ws.tc_bf16 != 0) : 0) +
+                              rot_operator_bytes(pl));
         delete pl;
         return PT_OK;
     }

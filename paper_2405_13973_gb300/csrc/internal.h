@@ -100,6 +100,12 @@ struct Workspace {
     // path's type (FP32: P rounded up to 16 on the tensor cores, ld on the
     // CUDA cores; FP64: ld)
     int m2l_pairs = 0;
+    // rotation-based M2L of the CUDA-core paths (PT_M2L_ROTATION, with the
+    // pair work list): per offset index [R^M | R^L | Z_re | Z_im], rot_op_vals
+    // values of the path's type
+    int m2l_rot = 0;
+    void* T_rot = nullptr;
+    int rot_op_vals = 0;
     // kernel timing (profiled steps only, else null): recorded right before
     // and after the M2L kernel(s) [0, 1] and the near-field kernel [2, 3]
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -171,6 +177,10 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
 cudaError_t launch_m2l_pairs_simt(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s);
 // {offsets with pairs, work items, work items, pairs} of the last work list
 cudaError_t m2l_pairs_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
+// rotation-based M2L: pairs per shared-memory tile (0: the operators of
+// this order do not fit), per-device kernel set-up
+int m2l_rot_tile(const Workspace& ws);
+cudaError_t m2l_rot_init();
 // the tensor-core partial-row width (P rounded up to 16)
 int m2l_tc_npad(int p);
 cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s);

@@ -401,6 +401,107 @@ __global__ void __launch_bounds__(128) k_l2l_simt(int l, int P, int ld, const Le
     }
 }
 
+// Rotation-based M2L of the work items (CUDA cores): per pair, the source's
+// multipole rotated so that the offset points along +z (R^M, degree blocks),
+// translated along z (one coupling per order m, Re and Im apart), rotated
+// back (R^L(Q^T)), in three passes through shared memory over a tile of np
+// pairs; the offset's packed operator [R^M | R^L | Z_re | Z_im] is staged
+// once per item.  sum_n (2n+1)^2 x 2 + sum_m (p+1-m)^2 (x 2 for m > 0)
+// multiply-adds per pair instead of (p+1)^4.
+__device__ __forceinline__ int deg_of(int i) {
+    int n = (int)sqrtf((float)i + 0.5f);
+    while (n * n > i) --n;
+    while ((n + 1) * (n + 1) <= i) ++n;
+    return n;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2l_rot(int p, int P, int ld, int stride, int np,
+                                                  const M2lPairHdr* hdr,
+                                                  const M2lPairItem* items, const M2lPair* pairs,
+                                                  const T* __restrict__ M,
+                                                  const T* __restrict__ ops, int op_vals,
+                                                  T* part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = (p + 1) * (4 * (p + 1) * (p + 1) - 1) / 3;
+    const int nz = op_vals / 2 - nb;
+    const int lp = P | 1;  // odd row stride of the pair tiles
+    T* sOp = reinterpret_cast<T*>(smem_raw);
+    T* sA = sOp + op_vals;
+    T* sB = sA + np * lp;
+    __shared__ int s_src[64], s_slot[64];
+    const T* RM = sOp;
+    const T* RL = sOp + nb;
+    const T* ZR = sOp + 2 * nb;
+    const T* ZI = ZR + nz;
+    const int tid = threadIdx.x;
+    const int S1 = (p + 1) * (p + 2) * (2 * p + 3) / 6;  // sum_{q<=p+1} q^2
+    for (int itx = blockIdx.x; itx < hdr->n_items; itx += gridDim.x) {
+        const M2lPairItem it = items[itx];
+        __syncthreads();
+        const T* op = ops + (int64_t)it.op * op_vals;
+        for (int e = tid; e < op_vals; e += blockDim.x) sOp[e] = op[e];
+        for (int r0 = 0; r0 < it.rows; r0 += np) {
+            const int rows = min(np, it.rows - r0);
+            __syncthreads();
+            if (tid < np) {
+                const bool live = tid < rows;
+                s_src[tid] = live ? pairs[it.begin + r0 + tid].src : -1;
+                s_slot[tid] = live ? pairs[it.begin + r0 + tid].slot : -1;
+            }
+            __syncthreads();
+            for (int e = tid; e < np * P; e += blockDim.x) {
+                const int r = e / P, k = e - r * P;
+                const int src = s_src[r];
+                sA[r * lp + k] = src >= 0 ? M[(int64_t)src * ld + k] : T(0);
+            }
+            __syncthreads();
+            // rotate the multipoles: sB = R^M sA (degree blocks)
+            for (int e = tid; e < np * P; e += blockDim.x) {
+                const int i = e / np, r = e - i * np;
+                const int n = deg_of(i), w = i - n * n, k = 2 * n + 1;
+                const T* row = RM + n * (4 * n * n - 1) / 3 + w * k;
+                const T* a = sA + r * lp + n * n;
+                T acc = T(0);
+                for (int u = 0; u < k; ++u) acc += row[u] * a[u];
+                sB[r * lp + i] = acc;
+            }
+            __syncthreads();
+            // translate along z: sA = Z sB (order m couples degrees l, j >= m)
+            for (int e = tid; e < np * P; e += blockDim.x) {
+                const int i = e / np, r = e - i * np;
+                const int l = deg_of(i), w = i - l * l;
+                const int m = (w + 1) >> 1;
+                const int im = (w > 0 && !(w & 1)) ? 1 : 0;
+                const int width = p + 1 - m;
+                const int q = p + 1 - m;  // zoff(m) = S(p+1) - S(p+1-m)
+                const int zo = S1 - q * (q + 1) * (2 * q + 1) / 6;
+                const T* row = (im ? ZI : ZR) + zo + (l - m) * width;
+                const T* b = sB + r * lp + (m == 0 ? 0 : 2 * m - 1) + im;
+                T acc = T(0);
+                for (int j = m; j <= p; ++j) acc += row[j - m] * b[j * j];
+                sA[r * lp + i] = acc;
+            }
+            __syncthreads();
+            // rotate back: sB = R^L(Q^T) sA
+            for (int e = tid; e < np * P; e += blockDim.x) {
+                const int i = e / np, r = e - i * np;
+                const int n = deg_of(i), w = i - n * n, k = 2 * n + 1;
+                const T* row = RL + n * (4 * n * n - 1) / 3 + w * k;
+                const T* a = sA + r * lp + n * n;
+                T acc = T(0);
+                for (int u = 0; u < k; ++u) acc += row[u] * a[u];
+                sB[r * lp + i] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < rows * P; e += blockDim.x) {
+                const int r = e / P, k = e - r * P;
+                part[(int64_t)s_slot[r] * stride + k] = sB[r * lp + k];
+            }
+        }
+    }
+}
+
 }  // namespace
 
 PairList pair_list(const Workspace& ws, size_t* bytes) {
@@ -488,6 +589,42 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
     return cudaGetLastError();
 }
 
+// shared-memory bytes of k_m2l_rot for np pairs per tile
+static size_t rot_smem(const Workspace& ws, int np) {
+    const size_t tsz = ws.fp64 ? sizeof(double) : sizeof(float);
+    return tsz * ((size_t)ws.rot_op_vals + 2 * (size_t)np * (ws.P | 1));
+}
+
+int m2l_rot_tile(const Workspace& ws) {
+    for (int np = 64; np >= 8; np /= 2)
+        if (rot_smem(ws, np) <= 200 * 1024) return np;
+    return 0;
+}
+
+cudaError_t m2l_rot_init() {
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_rot<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_m2l_rot<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024);
+    return e;
+}
+
+template <typename T>
+static cudaError_t rot_pairs(int64_t n, int D, Workspace& ws, cudaStream_t s) {
+    PairList L = pair_list(ws);
+    const int np = m2l_rot_tile(ws);
+    if (np == 0) return cudaErrorNotSupported;
+    const unsigned grid = (unsigned)std::min<int64_t>(ws.pp_item_cap, 152 * 4);
+    k_m2l_rot<T><<<grid, 256, rot_smem(ws, np), s>>>(ws.p, ws.P, ws.ld, ws.pp_stride, np, L.hdr,
+                                                     L.items, L.pairs, (const T*)ws.M,
+                                                     (const T*)ws.T_rot, ws.rot_op_vals,
+                                                     (T*)ws.pp_part);
+    (void)n;
+    (void)D;
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t simt_pairs(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s) {
     const int P = ws.P;
@@ -496,11 +633,16 @@ static cudaError_t simt_pairs(int64_t n, int D, Workspace& ws, int l2l_last, cud
     if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
                          cudaSuccess)
         return e;
-    const int64_t units = ws.pp_item_cap * 2 * ((P + kSimtCols - 1) / kSimtCols);
-    const unsigned grid = (unsigned)std::min<int64_t>(units, 152 * 8);
-    k_m2l_pairs_simt<T><<<grid, 256, 0, s>>>(P, ws.ld, ws.pp_stride, L.hdr, L.items, L.pairs,
-                                             (const T*)ws.M, (const T*)ws.T_m2l, (T*)ws.pp_part);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ws.m2l_rot) {
+        if ((e = rot_pairs<T>(n, D, ws, s)) != cudaSuccess) return e;
+    } else {
+        const int64_t units = ws.pp_item_cap * 2 * ((P + kSimtCols - 1) / kSimtCols);
+        const unsigned grid = (unsigned)std::min<int64_t>(units, 152 * 8);
+        k_m2l_pairs_simt<T><<<grid, 256, 0, s>>>(P, ws.ld, ws.pp_stride, L.hdr, L.items, L.pairs,
+                                                 (const T*)ws.M, (const T*)ws.T_m2l,
+                                                 (T*)ws.pp_part);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
                          cudaSuccess)
         return e;

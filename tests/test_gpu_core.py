@@ -137,19 +137,25 @@ def test_pair_schedule_equals_tile_schedule(sphere4k, depth, prec):
     # per-target loops over the offsets vs the same per-pair partials): the
     # far fields agree to the arithmetic's rounding, and the pair schedule is
     # deterministic (bitwise equal on a second evaluation).
+    # The rotation schedule (CUDA cores) factors every translation as rotate,
+    # translate along z, rotate back: equal to the dense operator up to
+    # rounding.
     pos, q, Eo, _ = sphere4k
     out = {}
-    for sched in ("tiles", "pairs"):
+    scheds = ("tiles", "pairs") if prec in ("tf32x3", "bf16x3") else ("tiles", "pairs", "rotation")
+    for sched in scheds:
         plan = pt.Plan(len(q), p=10, depth=depth, precision=prec)
         plan.set_m2l_schedule(sched)
+        assert plan.m2l_schedule == sched
         plan.set_phases(pt.PT_PHASE_FAR)
         E, _ = plan.forces(dev_pos(pos), dev_vec(q))
         out[sched] = E.cpu().numpy().T
-        if sched == "pairs":
+        if sched != "tiles":
             E2, _ = plan.forces(dev_pos(pos), dev_vec(q))
             assert np.array_equal(E2.cpu().numpy().T, out[sched])
         plan.close()
-    assert rel(out["pairs"], out["tiles"]) < (1e-12 if prec == "fp64" else 2e-6)
+    for sched in scheds[1:]:
+        assert rel(out[sched], out["tiles"]) < (1e-12 if prec == "fp64" else 2e-6), sched
 
 
 def test_field_of_one_and_two_ions():

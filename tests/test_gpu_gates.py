@@ -48,10 +48,12 @@ def spheroid10k():
     return cr["pos"], cr["q"], Eo
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "fp64"])
-def test_benchmark_crystal_force_error_at_most_1e6(spheroid10k, precision):
+@pytest.mark.parametrize("precision,schedule", [("bf16x3", "pairs"), ("bf16x3", "tiles"),
+                                                 ("fp64", "rotation"), ("fp64", "pairs")])
+def test_benchmark_crystal_force_error_at_most_1e6(spheroid10k, precision, schedule):
     pos, q, Eo = spheroid10k
     plan = pt.Plan(len(q), p=12, leaf_max=32, depth=-1, precision=precision)
+    plan.set_m2l_schedule(schedule)
     E, _ = plan.forces(dev_pos(pos), dev_vec(q), want_phi=False)
     err = rel(E.cpu().numpy().T, Eo)
     plan.close()
