@@ -458,6 +458,11 @@ int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precis
  *           them and must not destroy or use them elsewhere while the
  *           ensemble is stepping them.
  *   out   : receives the ensemble.
+ * While grouped, each member's persistent tensor-core M2L kernel takes one
+ * CTA per 256 ions (at least 2) instead of one per SM, so that the members'
+ * M2L kernels share the SMs; results do not depend on it (every work item
+ * is computed by one CTA whatever the grid).  pt_ensemble_destroy restores
+ * the plans.
  * Errors: PT_ERR_ARG (NULL, duplicate plans, mixed devices), PT_ERR_OOM,
  * PT_ERR_CUDA. */
 typedef struct pt_ensemble_s* pt_ensemble;

@@ -33,9 +33,10 @@ struct GraphKey {
     bool profile = false;
     int expand = 0;
     int sched = 0;
+    int ctas = 0;
     bool operator==(const GraphKey& o) const {
         return D == o.D && n == o.n && profile == o.profile && expand == o.expand &&
-               sched == o.sched &&
+               sched == o.sched && ctas == o.ctas &&
                memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
                memcmp(&pp, &o.pp, sizeof pp) == 0 && memcmp(&laser, &o.laser, sizeof laser) == 0;
     }
@@ -446,6 +447,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.profile = plan->profile;
     key.expand = plan->ws.expand;
     key.sched = plan->ws.m2l_pairs + 2 * plan->ws.m2l_rot;
+    key.ctas = plan->ws.m2l_ctas;
     return key;
 }
 
@@ -1064,6 +1066,13 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
         return PT_ERR_CUDA;
     }
     e->plans.assign(plans, plans + n_members);
+    // each member's persistent M2L kernel takes CTAs in proportion to its
+    // ions (one per 256, at least 2): the members' M2L kernels run side by
+    // side on the SMs instead of each waiting for all of them
+    for (int b = 0; b < n_members; ++b) {
+        const int64_t c = (plans[b]->n_max + 255) / 256;
+        plans[b]->ws.m2l_ctas = (int)(c < 2 ? 2 : (c > 1024 ? 1024 : c));
+    }
     e->br.assign(n_members, nullptr);
     e->join.assign(n_members, nullptr);
     bool ok = cudaStreamCreateWithPriority(&e->cap, cudaStreamNonBlocking, prio_high()) == cudaSuccess &&
@@ -1080,6 +1089,8 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
 }
 
 int pt_ensemble_destroy(pt_ensemble ens) {
+    if (ens)
+        for (fmm_plan_s* pl : ens->plans) pl->ws.m2l_ctas = 0;  // plans alone again
     free_ensemble(ens);
     return PT_OK;
 }

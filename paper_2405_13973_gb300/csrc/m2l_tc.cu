@@ -1498,6 +1498,12 @@ static int sm_count() {
     return sms > 0 ? sms : 152;
 }
 
+// CTAs of the persistent M2L launch: one per SM, or the plan's cap
+static unsigned m2l_grid(const Workspace& ws) {
+    const int sms = sm_count();
+    return (unsigned)(ws.m2l_ctas > 0 && ws.m2l_ctas < sms ? ws.m2l_ctas : sms);
+}
+
 cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s,
                               cudaEvent_t after_m2l) {
     if (D < 2) return cudaSuccess;
@@ -1512,7 +1518,7 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cud
         if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
                              cudaSuccess)
             return e;
-        if ((e = tc_launch(a, (unsigned)sm_count(), smem, s)) != cudaSuccess) return e;
+        if ((e = tc_launch(a, m2l_grid(ws), smem, s)) != cudaSuccess) return e;
         if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
                              cudaSuccess)
             return e;
@@ -1539,7 +1545,7 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cud
     if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
                          cudaSuccess)
         return e;
-    if ((e = tc_launch(a, (unsigned)sm_count(), smem, s)) != cudaSuccess) return e;
+    if ((e = tc_launch(a, m2l_grid(ws), smem, s)) != cudaSuccess) return e;
     if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
                          cudaSuccess)
         return e;
