@@ -15,11 +15,14 @@ on the launching stream, with a 512 MiB write between steps to flush the
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|tf32x3|bf16x3|fp64] [--p P] [--p10-steps K10]
                   [--forces N] [--config1-steps K1] [--sweep N1,N2,...]
+                  [--ensemble-extra M] [--serve-extra J]
 
 The default line also carries, as extra keys, the 1,000-ion FP64 run
 (1,000 steps at p = 8, oracle timed in the same run: "config1") and the
 single-evaluation sweep over ion counts, orders and precisions with errors
-against the FP64 direct sum ("sweep").  --forces N times only single force
+against the FP64 direct sum ("sweep"), a 256-crystal batched ensemble
+(10 steps, "ensemble") and a 24-job serving run ("serving").  --forces N
+times only single force
 evaluations of the N-ion sweep sphere (--p, --precision) and prints their
 line (the command the kernel profiles are taken with).
 
@@ -233,33 +236,40 @@ def reference_arm(args, rank):
 def ensemble_arm(args, rank):
     """Batched ensemble: every crystal its own plan (depth from the autotuner
     for its ion-count band), all advanced by one graph launch per step."""
+    line = ensemble_measure(args.ensemble, args.p, args.precision, args.steps, args.warmup, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def ensemble_measure(members, p, precision, steps, warmup, rank=0):
     import torch
     import paper_2405_13973_gb300 as pt
     from paper_2405_13973_gb300 import autotune
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    crs = W.ensemble_crystals(args.ensemble, seed=17 * rank)
+    crs = W.ensemble_crystals(members, seed=17 * rank)
 
     def crystal(n):
         c = W.ensemble_member(n, 0.3, seed=3, cooling=False)
         return c["pos"], c["vel"], c["q"], c["trap"], c["dt"]
 
     t_tune = time.perf_counter()
-    depths = [autotune.tune_depth(len(c["q"]), args.p, args.precision, crystal) for c in crs]
+    depths = [autotune.tune_depth(len(c["q"]), p, precision, crystal) for c in crs]
     t_tune = time.perf_counter() - t_tune
-    plans = [pt.Plan(len(c["q"]), p=args.p, leaf_max=32, depth=d, precision=args.precision)
+    plans = [pt.Plan(len(c["q"]), p=p, leaf_max=32, depth=d, precision=precision)
              for c, d in zip(crs, depths)]
     states = [pt.State.from_numpy(c["pos"], c["vel"], c["q"]) for c in crs]
     traps = [pt.make_trap(c["trap"]) for c in crs]
     lasers = [pt.make_laser(c["beams"], seed=1 + k, gamma0=W.GAMMA0) for k, c in enumerate(crs)]
     dts = [c["dt"] for c in crs]
     ens = pt.Ensemble(plans)
-    ens.step(states, traps, lasers, dts, args.warmup)
+    ens.step(states, traps, lasers, dts, warmup)
     ens.sync()
     ions = sum(len(c["q"]) for c in crs)
     flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush_buf.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -271,11 +281,11 @@ def ensemble_arm(args, rank):
     ens.sync()
     total = float(sum(ms))
     line = {"metric": "ion-steps/s (batched ensemble of independent crystals)",
-            "value": ions * args.steps / (total * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
-            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"{args.ensemble} crystals, N log-uniform [100, 20000], "
-                                   f"aspect U[0.1, 1], cooling on, p={args.p}, dt=1ns",
+            "value": ions * steps / (total * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": total / steps,
+            "higher_is_better": True, "dtype": precision, "data": "synthetic",
+            "config": {"workload": f"{members} crystals, N log-uniform [100, 20000], "
+                                   f"aspect U[0.1, 1], cooling on, p={p}, dt=1ns",
                        "ions": ions, "depths": sorted(set(depths)),
                        "l2": "flushed between timed steps (512 MiB write)"},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
@@ -283,9 +293,9 @@ def ensemble_arm(args, rank):
     ens.close()
     for pl in plans:
         pl.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    del flush_buf
+    torch.cuda.empty_cache()
+    return line
 
 
 def serve_arm(args, rank):
@@ -293,14 +303,21 @@ def serve_arm(args, rank):
     log-uniform in [200, 50000], step counts log-uniform in args.serve_steps,
     random aspect and seeds, cooling on; admitted by device-memory budget,
     continuously batched.  Reports latency percentiles and throughput."""
+    line = serve_measure(args.serve, args.serve_rate, args.serve_steps, args.serve_budget_gb,
+                         args.p, args.precision, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_measure(m, rate, step_range, budget_gb, p, precision, rank=0):
     import torch
     from paper_2405_13973_gb300.serving import Job, Server, report
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rng = np.random.default_rng(101 + rank)
-    m = args.serve
-    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, m))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, m))
     ns = np.exp(rng.uniform(math.log(200), math.log(50000), m)).astype(int)
-    lo, hi = args.serve_steps
+    lo, hi = step_range
     steps = np.exp(rng.uniform(math.log(lo), math.log(hi), m)).astype(int)
     aspects = rng.uniform(0.1, 1.0, m)
     jobs = []
@@ -308,7 +325,7 @@ def serve_arm(args, rank):
         c = W.ensemble_member(int(ns[k]), float(aspects[k]), seed=1000 + k)
         jobs.append(Job(k, c["pos"], c["vel"], c["q"], c["trap"], c["beams"], 77 + k, c["dt"],
                         int(steps[k]), arrival=float(arrivals[k]), gamma0=W.GAMMA0))
-    srv = Server(int(args.serve_budget_gb * 2**30), p=args.p, precision=args.precision,
+    srv = Server(int(budget_gb * 2**30), p=p, precision=precision,
                  chunk=256)
     t0 = time.perf_counter()
     srv.run(jobs)
@@ -316,18 +333,16 @@ def serve_arm(args, rank):
     rep = report(jobs, makespan)
     line = {"metric": "serving: job latency p50/p99 and aggregate ion-steps/s",
             "value": rep["ion_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"{m} jobs, Poisson arrivals {args.serve_rate}/s, N log-uniform "
+            "higher_is_better": True, "dtype": precision, "data": "synthetic",
+            "config": {"workload": f"{m} jobs, Poisson arrivals {rate}/s, N log-uniform "
                                    f"[200, 50000], steps log-uniform [{lo:g}, {hi:g}], aspect "
-                                   f"U[0.1, 1], cooling on, p={args.p}, dt=1ns",
-                       "hbm_budget_gb": args.serve_budget_gb},
+                                   f"U[0.1, 1], cooling on, p={p}, dt=1ns",
+                       "hbm_budget_gb": budget_gb},
             "latency_s": {"p50": rep["p50_s"], "p99": rep["p99_s"], "max": rep["max_s"]},
             "makespan_s": makespan, "ion_steps": rep["ion_steps"],
             "peak_admitted_gb": srv.peak_bytes / 2**30, "graph_recaptures": srv.recaptures,
             "chunks": srv.chunks}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def sweep_reference(pt, torch, w, n_sample=512):
@@ -465,13 +480,13 @@ def forces_arm(args):
         flush_buf.fill_(1.0)
     w = W.sphere_sweep(args.forces)
     ref = sweep_reference(pt, torch, w) if not args.no_ref else None
-    r = force_eval_point(pt, torch, w, args.p, args.precision, args.steps, flush, ref,
+    r = force_eval_point(pt, torch, w, p, precision, args.steps, flush, ref,
                          warmup=args.warmup, schedule=args.schedule)
     line = {"metric": "single force evaluations/s (sweep sphere, 2e14 m^-3)",
             "value": r.get("evals_per_s"), "unit": "evaluations/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"sphere N={args.forces}, 2e14 m^-3 + 1% jitter, p={args.p}",
+            "dtype": precision, "data": "synthetic",
+            "config": {"workload": f"sphere N={args.forces}, 2e14 m^-3 + 1% jitter, p={p}",
                        "l2": "flushed between timed evaluations (512 MiB write)"},
             "result": r, "reference": ref[2] if ref else None}
     print(json.dumps(line), flush=True)
@@ -530,6 +545,10 @@ def main():
     ap.add_argument("--no-ref", action="store_true", help="--forces without the error reference")
     ap.add_argument("--config1-steps", type=int, default=1000,
                     help="steps of the 1,000-ion FP64 run carried by the default line (0: skip)")
+    ap.add_argument("--ensemble-extra", type=int, default=256,
+                    help="crystals of the ensemble run carried by the default line (0: skip)")
+    ap.add_argument("--serve-extra", type=int, default=24,
+                    help="jobs of the serving run carried by the default line (0: skip)")
     ap.add_argument("--sweep", default="10000,100000,1000000",
                     help="ion counts of the single-evaluation sweep in the default line ('' skips)")
     args = ap.parse_args()
@@ -737,6 +756,13 @@ def main():
                                     "leaf<=32, automatic depth",
                         "points": sweep_arm(pt, torch, ns, (4, 6, 8, 10, 12, 16),
                                             ("fp64", "fp32", "bf16x3"), flush)}
+
+    # batched ensemble and serving, each a short run of its own measurement
+    if rank == 0 and args.ensemble_extra > 0:
+        out["ensemble"] = ensemble_measure(args.ensemble_extra, args.p, args.precision, 10, 3)
+    if rank == 0 and args.serve_extra > 0:
+        out["serving"] = serve_measure(args.serve_extra, 50.0, (100.0, 2000.0), 40.0, args.p,
+                                       args.precision)
 
     # end to end through the public API: every step copies the state in from
     # pinned host memory, advances it (pt_step_async) and copies it back; the

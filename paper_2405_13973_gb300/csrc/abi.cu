@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "m2l_pairs.h"
 #include "operators.h"
 
 using namespace pt;
@@ -34,9 +35,10 @@ struct GraphKey {
     int expand = 0;
     int sched = 0;
     int ctas = 0;
+    int pool = 0;
     bool operator==(const GraphKey& o) const {
         return D == o.D && n == o.n && profile == o.profile && expand == o.expand &&
-               sched == o.sched && ctas == o.ctas &&
+               sched == o.sched && ctas == o.ctas && pool == o.pool &&
                memcmp(ptr, o.ptr, sizeof ptr) == 0 &&
                memcmp(&pp, &o.pp, sizeof pp) == 0 && memcmp(&laser, &o.laser, sizeof laser) == 0;
     }
@@ -76,6 +78,7 @@ struct fmm_plan_s {
     cudaEvent_t k_ev[4] = {nullptr};   // kernel timing of profiled steps (Workspace::kev)
     bool ops_held = false;     // holds a reference on the shared operator set
     bool dry = false;          // sizing only (fmm_plan_footprint): nothing is allocated
+    bool pp_counted = false;   // the pair pool was checked against a real tree
     size_t dry_bytes = 0;
 };
 
@@ -177,6 +180,7 @@ void free_plan(fmm_plan_s* pl) {
     for (cudaEvent_t ev : pl->k_ev)
         if (ev) cudaEventDestroy(ev);
     if (pl->h_err) cudaFreeHost(pl->h_err);
+    if (ws.h_pp_hdr) cudaFreeHost(ws.h_pp_hdr);
     delete pl;
 }
 
@@ -350,8 +354,135 @@ int choose_depth(fmm_plan_s* pl, int64_t n, const double* x, const double* y, co
     return PT_OK;
 }
 
+// Pair-packed M2L schedule: the pool of partial rows holds every (target,
+// source) pair of a step; 189 sources per cell of levels 2..D bound them.
+static int alloc_pairs(fmm_plan_s* pl) {
+    Workspace& ws = pl->ws;
+    if (ws.pp_work) return PT_OK;
+    const int dcap = pl->depth >= 0 ? pl->depth : ws.depth_max;
+    int64_t exact = 0;
+    for (int l = 2; l <= dcap; ++l) exact += 189 * (pow8(l) < pl->n_max ? pow8(l) : pl->n_max);
+    // initial pool: the exact bound, or about twelve pairs per ion if less
+    // (the 10,000-ion spheroid has ten); the first call counts its pairs and
+    // every later call checks the count of the last step (ensure_pairs)
+    int64_t cap = std::min<int64_t>(exact, 12 * pl->n_max + 4096);
+    ws.pp_slot_cap = cap > 0 ? cap : 1;
+    ws.pp_item_cap = ws.pp_slot_cap / 128 + 344;
+    ws.pp_stride = is_tc(pl->precision) ? m2l_tc_npad(pl->p) : ws.ld;
+    bool ok = dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) &&
+              dalloc(pl, ws.pp_part, m2l_pp_part_bytes(ws));
+    if (!ok) {
+        ws.pp_work = nullptr;
+        ws.pp_part = nullptr;
+        return PT_ERR_OOM;
+    }
+    if (!pl->dry && cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess)
+        return PT_ERR_CUDA;
+    if (!pl->dry && !ws.h_pp_hdr) {
+        if (cudaMallocHost(&ws.h_pp_hdr, sizeof(M2lPairHdr)) != cudaSuccess) return PT_ERR_CUDA;
+        memset(ws.h_pp_hdr, 0, sizeof(M2lPairHdr));
+    }
+    return PT_OK;
+}
+
+// Replaces the pool by one of `cap` pairs (device idle first; graphs that
+// captured the old buffers are recaptured through the pool generation).
+static int regrow_pairs(fmm_plan_s* pl, int64_t cap) {
+    Workspace& ws = pl->ws;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+    for (auto it = pl->allocs.begin(); it != pl->allocs.end();) {
+        if (*it == ws.pp_work || *it == ws.pp_part) {
+            cudaFree(*it);
+            it = pl->allocs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    ws.pp_work = nullptr;
+    ws.pp_part = nullptr;
+    ws.pp_slot_cap = cap;
+    ws.pp_item_cap = cap / 128 + 344;
+    if (!dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) ||
+        !dalloc(pl, ws.pp_part, m2l_pp_part_bytes(ws)))
+        return PT_ERR_OOM;
+    if (cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess) return PT_ERR_CUDA;
+    memset(ws.h_pp_hdr, 0, sizeof(M2lPairHdr));
+    ++ws.pp_gen;
+    return PT_OK;
+}
+
+// Pool check of the pair-packed schedule before a call enqueues work: the
+// plan's first call counts the pairs of its tree (one synchronising work-list
+// pass); later calls read the count that the last step left in pinned host
+// memory, and the pool grows by half again once a step used more than 80 %
+// of it (a step that overflowed reported PT_ERR_OOM and is counted too).
+static int ensure_pairs(fmm_plan_s* pl, int64_t n, const double* x, const double* y,
+                        const double* z, const double* q, int D, cudaStream_t s) {
+    Workspace& ws = pl->ws;
+    if (!ws.m2l_pairs || !ws.h_pp_hdr || D < 2) return PT_OK;
+    if (!pl->pp_counted) {
+        cudaError_t e = launch_bbox(x, y, z, n, ws, s);
+        if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, ws, s);
+        if (e == cudaSuccess) e = launch_m2l_pairs_worklist(n, D, ws, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return status_from(e);
+        int r = check_err(pl, s);  // an overflow of this count is not an error
+        if (r != PT_OK && r != PT_ERR_OOM) return r;
+        pl->pp_counted = true;
+    }
+    const M2lPairHdr* h = (const M2lPairHdr*)ws.h_pp_hdr;
+    const int64_t used = h->n_pairs;
+    if (used > 0 && (h->overflow || 10 * used > 8 * ws.pp_slot_cap))
+        return regrow_pairs(pl, used + used / 2 + 4096);
+    return PT_OK;
+}
+
+// The tile schedule's full pool of partial slabs (plans created for the pair
+// schedule hold the minimum).
+static int alloc_tile_slabs(fmm_plan_s* pl) {
+    Workspace& ws = pl->ws;
+    const int64_t want = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, pl->n_max);
+    if (ws.tc_slab_cap >= want) return PT_OK;
+    const size_t floats = m2l_tc_part_floats(ws.cells_max, ws.ld, ws.tc_splits_max,
+                                             ws.tc_tiles_cap, want);
+    void *work = nullptr, *part = nullptr;
+    if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
+    if (cudaMalloc(&work, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(float) * floats) != cudaSuccess) {
+        cudaFree(work);
+        return PT_ERR_OOM;
+    }
+    if (cudaMemset(work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
+        cudaMemset(part, 0, sizeof(float) * floats) != cudaSuccess) {
+        cudaFree(work);
+        cudaFree(part);
+        return PT_ERR_CUDA;
+    }
+    for (void*& v : pl->allocs) {
+        if (v == ws.tc_work) {
+            cudaFree(v);
+            v = work;
+        } else if (v == (void*)ws.tc_part) {
+            cudaFree(v);
+            v = part;
+        }
+    }
+    ws.tc_work = work;
+    ws.tc_part = (float*)part;
+    ws.tc_slab_cap = want;
+    ws.tc_part_floats = floats;
+    if (pl->graph) {  // captured with the old buffers
+        cudaGraphExecDestroy(pl->graph);
+        pl->graph = nullptr;
+        pl->gkey = GraphKey{};
+    }
+    return PT_OK;
+}
+
 int forces_impl(fmm_plan_s* pl, int64_t n, const double* x, const double* y, const double* z,
                 const double* q, double* E, double* phi, cudaStream_t s, int D) {
+    int r = ensure_pairs(pl, n, x, y, z, q, D, s);
+    if (r != PT_OK) return r;
     cudaError_t e = launch_bbox(x, y, z, n, pl->ws, s);
     if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, pl->ws, s);
     if (e == cudaSuccess)
@@ -417,6 +548,8 @@ int prepare_chunk(fmm_plan_s* plan, const pt_state* st, const pt_trap* trap, dou
         if (plan->last_depth < 0) return PT_ERR_ARG;
         *D = plan->last_depth;
     }
+    int rp = ensure_pairs(plan, st->n, st->x, st->y, st->z, st->q, *D, s);
+    if (rp != PT_OK) return rp;
     const int slot = plan->next_slot;
     plan->next_slot = (slot + 1) % fmm_plan_s::kSlots;
     cudaError_t e = cudaEventSynchronize(plan->slot_ev[slot]);  // slot free again
@@ -448,6 +581,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.expand = plan->ws.expand;
     key.sched = plan->ws.m2l_pairs + 2 * plan->ws.m2l_rot;
     key.ctas = plan->ws.m2l_ctas;
+    key.pool = plan->ws.pp_gen;
     return key;
 }
 
@@ -581,81 +715,6 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
 
 int fmm_plan_create(int64_t n_max, int p, int leaf_max, int depth, int precision, fmm_plan* out) {
     return plan_create_impl(n_max, p, leaf_max, depth, precision, out, false, nullptr, nullptr);
-}
-
-// Pair-packed M2L schedule: the pool of partial rows holds every (target,
-// source) pair of a step.  With a fixed depth D the bound is exact (189
-// sources per cell of levels 2..D).  With the automatic depth, D is the
-// smallest depth whose leaves hold at most leaf_max ions on average, so level
-// D - 1 has fewer than n / leaf_max cells and level D at most 8 times as many:
-// pairs < 189 (8 + 1 + 1/7) n / leaf_max, bounded here by 189 x 9.2 n /
-// leaf_max plus a margin for the tree's drift between depth choices.
-static int alloc_pairs(fmm_plan_s* pl) {
-    Workspace& ws = pl->ws;
-    if (ws.pp_work) return PT_OK;
-    const int dcap = pl->depth >= 0 ? pl->depth : ws.depth_max;
-    int64_t exact = 0;
-    for (int l = 2; l <= dcap; ++l) exact += 189 * (pow8(l) < pl->n_max ? pow8(l) : pl->n_max);
-    int64_t cap = exact;
-    if (pl->depth < 0) {
-        const int64_t autob = (int64_t)(189.0 * 9.2 * (double)pl->n_max / pl->leaf_max) + 8192;
-        if (autob < cap) cap = autob;
-    }
-    ws.pp_slot_cap = cap > 0 ? cap : 1;
-    ws.pp_item_cap = ws.pp_slot_cap / 128 + 344;
-    ws.pp_stride = is_tc(pl->precision) ? m2l_tc_npad(pl->p) : ws.ld;
-    bool ok = dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) &&
-              dalloc(pl, ws.pp_part, m2l_pp_part_bytes(ws));
-    if (!ok) {
-        ws.pp_work = nullptr;
-        ws.pp_part = nullptr;
-        return PT_ERR_OOM;
-    }
-    if (!pl->dry && cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess)
-        return PT_ERR_CUDA;
-    return PT_OK;
-}
-
-// The tile schedule's full pool of partial slabs (plans created for the pair
-// schedule hold the minimum).
-static int alloc_tile_slabs(fmm_plan_s* pl) {
-    Workspace& ws = pl->ws;
-    const int64_t want = m2l_tc_slab_cap(ws.ld, ws.tc_tiles_cap, pl->n_max);
-    if (ws.tc_slab_cap >= want) return PT_OK;
-    const size_t floats = m2l_tc_part_floats(ws.cells_max, ws.ld, ws.tc_splits_max,
-                                             ws.tc_tiles_cap, want);
-    void *work = nullptr, *part = nullptr;
-    if (cudaDeviceSynchronize() != cudaSuccess) return PT_ERR_CUDA;
-    if (cudaMalloc(&work, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
-        cudaMalloc(&part, sizeof(float) * floats) != cudaSuccess) {
-        cudaFree(work);
-        return PT_ERR_OOM;
-    }
-    if (cudaMemset(work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, want)) != cudaSuccess ||
-        cudaMemset(part, 0, sizeof(float) * floats) != cudaSuccess) {
-        cudaFree(work);
-        cudaFree(part);
-        return PT_ERR_CUDA;
-    }
-    for (void*& v : pl->allocs) {
-        if (v == ws.tc_work) {
-            cudaFree(v);
-            v = work;
-        } else if (v == (void*)ws.tc_part) {
-            cudaFree(v);
-            v = part;
-        }
-    }
-    ws.tc_work = work;
-    ws.tc_part = (float*)part;
-    ws.tc_slab_cap = want;
-    ws.tc_part_floats = floats;
-    if (pl->graph) {  // captured with the old buffers
-        cudaGraphExecDestroy(pl->graph);
-        pl->graph = nullptr;
-        pl->gkey = GraphKey{};
-    }
-    return PT_OK;
 }
 
 int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule) {

@@ -115,6 +115,8 @@ struct Workspace {
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
     void* pp_work = nullptr;
     void* pp_part = nullptr;
+    void* h_pp_hdr = nullptr;       // pinned copy of the last work list's header (pairs, overflow)
+    int pp_gen = 0;                 // bumped whenever the pool is reallocated
     int pp_stride = 0;
     int64_t pp_slot_cap = 0;    // pairs the pool holds
     int64_t pp_item_cap = 0;    // work items (runs of up to 128 pairs of one offset)

@@ -568,7 +568,12 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
                                             ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_pp_fill<<<343, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.hdr, L.pairs);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the header (pair count, overflow flag) to pinned host memory, for the
+    // host's pool check at the next call
+    if (ws.h_pp_hdr)
+        e = cudaMemcpyAsync(ws.h_pp_hdr, L.hdr, sizeof(M2lPairHdr), cudaMemcpyDeviceToHost, s);
+    return e;
 }
 
 cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s) {
