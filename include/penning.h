@@ -131,11 +131,16 @@ int fmm_plan_set_expansion(fmm_plan plan, int mode);
  *                    result row is a partial local expansion, and each
  *                    target's partials are summed in increasing offset order
  *                    (deterministic).  Fewer, fuller products on small or flat
- *                    crystals, at the price of a pool of partial rows: about
- *                    189 x 9.2 n / leaf_max pairs (exact bound with a fixed
- *                    depth) x (P rounded up to 16 on the tensor cores, the row
- *                    stride of M and L on the CUDA cores) values.  A step
- *                    whose pairs exceed the pool returns PT_ERR_OOM;
+ *                    crystals, at the price of a pool of partial rows (P
+ *                    rounded up to 16 values on the tensor cores, the row
+ *                    stride of M and L on the CUDA cores, per pair).  The
+ *                    pool starts at 12 n_max + 4096 pairs (or the exact bound
+ *                    189 x the cells of levels 2..depth, if smaller); a
+ *                    plan's first call counts the pairs of its tree, and a
+ *                    call grows the pool by half again once the last step
+ *                    used more than 80 % of it (synchronising the device).  A
+ *                    step whose pairs exceed the pool returns PT_ERR_OOM (its
+ *                    far field is missing) and the next call grows the pool;
  *   PT_M2L_ROTATION  CUDA-core precisions, p <= 16: the pair work list, each
  *                    translation done by rotating the multipole so that the
  *                    offset points along +z, translating along z (orders m
