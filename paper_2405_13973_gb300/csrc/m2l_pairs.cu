@@ -141,26 +141,61 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         __syncthreads();
     }
     const int total = s_carry;
+    // offsets: pair bases (scan of the counts) and item bases (scan of the
+    // 128-pair runs), 343 entries by the first 11 warps
+    __shared__ int s_pb[344], s_nof;
+    if (wid < 11) {
+        const int o = tid;  // 0 .. 351
+        const int c = o < 343 ? ocnt[o] : 0;
+        const int runs = (c + kPairRows - 1) / kPairRows;
+        int x = c, y = runs, f = c > 0 ? 1 : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int xa = __shfl_up_sync(0xffffffffu, x, d);
+            const int ya = __shfl_up_sync(0xffffffffu, y, d);
+            const int fa = __shfl_up_sync(0xffffffffu, f, d);
+            if (lane >= d) {
+                x += xa;
+                y += ya;
+                f += fa;
+            }
+        }
+        if (o < 343) {
+            s_pb[o + 1] = x;         // inclusive, per warp for now
+            s_ibase[o + 1] = y;
+        }
+        if (lane == 31) wsum[wid] = f;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // carry the per-warp inclusive scans across the 11 warps
+        int cx = 0, cy = 0, nof = 0;
+        for (int w = 0; w < 11; ++w) {
+            const int last = min(32 * w + 31, 342);
+            const int wx = s_pb[last + 1], wy = s_ibase[last + 1];
+            for (int o = 32 * w; o <= last; ++o) {
+                s_pb[o + 1] += cx;
+                s_ibase[o + 1] += cy;
+            }
+            cx += wx;
+            cy += wy;
+            nof += wsum[w];
+        }
+        s_pb[0] = 0;
+        s_ibase[0] = 0;
+        s_nof = nof;
+    }
+    __syncthreads();
+    for (int o = tid; o <= 343; o += kPpScanThreads) obase[o] = s_pb[o];
     if (tid == 0) {
         tbase[nt] = total;
-        // offsets: pair bases and item bases (343 entries, serial)
-        int pb = 0, ib = 0, nof = 0;
-        for (int o = 0; o < 343; ++o) {
-            obase[o] = pb;
-            s_ibase[o] = ib;
-            pb += ocnt[o];
-            ib += (ocnt[o] + kPairRows - 1) / kPairRows;
-            nof += ocnt[o] > 0;
-        }
-        obase[343] = pb;
-        s_ibase[343] = ib;
+        const int pb = s_pb[343], ib = s_ibase[343];
         const bool over = (int64_t)total > slot_cap || ib > item_cap || pb != total;
         hdr->overflow = over ? 1 : 0;
         if (over) atomicOr(err, ERR_CAPACITY);
         hdr->n_items = over ? 0 : ib;
         hdr->n_pairs = total;
         hdr->n_targets = nt;
-        hdr->n_offsets = nof;
+        hdr->n_offsets = s_nof;
     }
     __syncthreads();
     if ((int64_t)total > slot_cap || s_ibase[343] > item_cap) return;
@@ -169,7 +204,7 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         for (int k = 0; k * kPairRows < c; ++k) {
             M2lPairItem it;
             it.op = o;
-            it.begin = obase[o] + k * kPairRows;
+            it.begin = s_pb[o] + k * kPairRows;
             it.rows = min(kPairRows, c - k * kPairRows);
             it.pad = 0;
             items[s_ibase[o] + k] = it;
@@ -245,31 +280,32 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
                                                        const LevelInfo* linfo,
                                                        const M2lPairHdr* hdr, const int* tbase,
                                                        const float4* __restrict__ part, float* L) {
-    const int lane = threadIdx.x & 31;
+    // one thread per (target, 16-byte column group): consecutive threads read
+    // consecutive columns of a slot row; eight rows in flight per thread
     const int g0 = linfo->gbase[2], nt = linfo->gbase[D + 1] - g0;
     const int s4 = stride / 4, w4 = width / 4;
     const bool over = hdr->overflow != 0;
-    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
-         t += gridDim.x * (blockDim.x >> 5)) {
+    const int64_t total = (int64_t)nt * w4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / w4), u = (int)(e - (int64_t)t * w4);
         const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
-        for (int u = lane; u < w4; u += 32) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            int s = s0;
-            for (; s + 4 <= s1; s += 4) {
-                float4 q[4];
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int s = s0;
+        for (; s + 8 <= s1; s += 8) {
+            float4 q[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) q[k] = part[(int64_t)(s + k) * s4 + u];
+            for (int k = 0; k < 8; ++k) q[k] = __ldcs(part + (int64_t)(s + k) * s4 + u);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
-                }
+            for (int k = 0; k < 8; ++k) {
+                v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
             }
-            for (; s < s1; ++s) {
-                const float4 q = part[(int64_t)s * s4 + u];
-                v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
-            }
-            *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
         }
+        for (; s < s1; ++s) {
+            const float4 q = __ldcs(part + (int64_t)s * s4 + u);
+            v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+        }
+        *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
     }
 }
 
@@ -585,7 +621,9 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
         k_pp_reduce<double><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
                                                L.tbase, (const double*)ws.pp_part, (double*)ws.L);
     } else if (width % 4 == 0 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
-        k_pp_reduce_f4<<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr, L.tbase,
+        const int64_t th = tb * (width / 4);
+        const unsigned g4 = (unsigned)std::min<int64_t>((th + 255) / 256, 152 * 16);
+        k_pp_reduce_f4<<<g4, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr, L.tbase,
                                           (const float4*)ws.pp_part, (float*)ws.L);
     } else {
         k_pp_reduce<float><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,

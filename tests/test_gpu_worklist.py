@@ -43,9 +43,9 @@ def decode(codes, l):
 def expected_counts(pos, D):
     keys, _, _ = oracle.leaf_keys(pos, D)
     out = {"cells": 0, "m2l_pairs": 0, "shifts": 0, "tiles": 0, "products": 0, "rows": 0}
-    per_offset = np.zeros(len(offs), np.int64)
     offs = [(ox, oy, oz) for ox in range(-3, 4) for oy in range(-3, 4) for oz in range(-3, 4)
             if max(abs(ox), abs(oy), abs(oz)) > 1]
+    per_offset = np.zeros(len(offs), np.int64)
     for l in range(2, D + 1):
         codes = np.unique(keys >> np.uint64(3 * (D - l)))
         oct_ = (codes & np.uint64(7)).astype(np.int64)
