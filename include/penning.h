@@ -157,6 +157,12 @@ int fmm_plan_set_expansion(fmm_plan plan, int mode);
 #define PT_M2L_PAIRS 1
 #define PT_M2L_ROTATION 2
 int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule);
+/* CTAs of the plan's persistent tensor-core M2L kernel: 0 (default) one per
+ * SM, else at most `ctas`, so that the M2L kernels of several plans stepped
+ * together (an ensemble) can run side by side.  Results do not depend on it:
+ * every work item is computed by one CTA whatever the grid.  Errors:
+ * PT_ERR_ARG. */
+int fmm_plan_set_m2l_ctas(fmm_plan plan, int ctas);
 /* The plan's M2L schedule (PT_M2L_*), or -1 for a NULL plan. */
 int fmm_plan_m2l_schedule(fmm_plan plan);
 
@@ -463,11 +469,8 @@ int fmm_plan_footprint(int64_t n_max, int p, int leaf_max, int depth, int precis
  *           them and must not destroy or use them elsewhere while the
  *           ensemble is stepping them.
  *   out   : receives the ensemble.
- * While grouped, each member's persistent tensor-core M2L kernel takes one
- * CTA per 256 ions (at least 2) instead of one per SM, so that the members'
- * M2L kernels share the SMs; results do not depend on it (every work item
- * is computed by one CTA whatever the grid).  pt_ensemble_destroy restores
- * the plans.
+ * Members' kernels share the GPU; fmm_plan_set_m2l_ctas lets each member's
+ * persistent M2L kernel take fewer CTAs than one per SM.
  * Errors: PT_ERR_ARG (NULL, duplicate plans, mixed devices), PT_ERR_OOM,
  * PT_ERR_CUDA. */
 typedef struct pt_ensemble_s* pt_ensemble;

@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_set_expansion.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_set_m2l_schedule.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_m2l_schedule.argtypes = [_VP]
+        L.fmm_plan_set_m2l_ctas.argtypes = [_VP, ctypes.c_int]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -272,6 +273,11 @@ class Plan:
             schedule = {"tiles": M2L_TILES, "pairs": M2L_PAIRS, "rotation": M2L_ROTATION}[schedule]
         _check(load(False).fmm_plan_set_m2l_schedule(self._h, int(schedule)),
                "fmm_plan_set_m2l_schedule")
+
+    def set_m2l_ctas(self, ctas: int):
+        """At most `ctas` CTAs for the persistent tensor-core M2L kernel (0:
+        one per SM)."""
+        _check(load(False).fmm_plan_set_m2l_ctas(self._h, int(ctas)), "fmm_plan_set_m2l_ctas")
 
     @property
     def m2l_schedule(self) -> str:
@@ -478,8 +484,14 @@ class Ensemble:
     one launch of one CUDA graph (members as parallel branches).  The plans
     stay the caller's; a member's result equals its plan stepped alone."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, share_sms: bool = True):
+        """share_sms: each member's persistent M2L kernel takes one CTA per
+        256 ions (at least 2) instead of one per SM, so that the members' M2L
+        kernels run side by side (results do not depend on it)."""
         self.plans = list(plans)
+        if share_sms:
+            for pl in self.plans:
+                pl.set_m2l_ctas(max(2, min(1024, (pl.n_max + 255) // 256)))
         arr = (_VP * len(self.plans))(*[pl._h.value for pl in self.plans])
         h = ctypes.c_void_p()
         _check(load(False).pt_ensemble_create(len(self.plans), arr, ctypes.byref(h)),

@@ -732,6 +732,12 @@ int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule) {
     return PT_OK;
 }
 
+int fmm_plan_set_m2l_ctas(fmm_plan plan, int ctas) {
+    if (!plan || ctas < 0) return PT_ERR_ARG;
+    plan->ws.m2l_ctas = ctas;
+    return PT_OK;
+}
+
 int fmm_plan_m2l_schedule(fmm_plan plan) {
     if (!plan) return -1;
     if (plan->ws.m2l_rot) return PT_M2L_ROTATION;
@@ -1125,13 +1131,6 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
         return PT_ERR_CUDA;
     }
     e->plans.assign(plans, plans + n_members);
-    // each member's persistent M2L kernel takes CTAs in proportion to its
-    // ions (one per 256, at least 2): the members' M2L kernels run side by
-    // side on the SMs instead of each waiting for all of them
-    for (int b = 0; b < n_members; ++b) {
-        const int64_t c = (plans[b]->n_max + 255) / 256;
-        plans[b]->ws.m2l_ctas = (int)(c < 2 ? 2 : (c > 1024 ? 1024 : c));
-    }
     e->br.assign(n_members, nullptr);
     e->join.assign(n_members, nullptr);
     bool ok = cudaStreamCreateWithPriority(&e->cap, cudaStreamNonBlocking, prio_high()) == cudaSuccess &&
@@ -1148,8 +1147,6 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
 }
 
 int pt_ensemble_destroy(pt_ensemble ens) {
-    if (ens)
-        for (fmm_plan_s* pl : ens->plans) pl->ws.m2l_ctas = 0;  // plans alone again
     free_ensemble(ens);
     return PT_OK;
 }

@@ -104,9 +104,8 @@ struct Workspace {
     // pair work list): per offset index [R^M | R^L | Z_re | Z_im], rot_op_vals
     // values of the path's type
     int m2l_rot = 0;
-    // CTAs of the persistent tensor-core M2L kernel (0: one per SM); an
-    // ensemble caps each member's by its share of the ions so that the
-    // members' M2L kernels share the SMs instead of queueing for all of them
+    // CTAs of the persistent tensor-core M2L kernel (0: one per SM); members
+    // of an ensemble may take fewer so that their M2L kernels share the SMs
     int m2l_ctas = 0;
     void* T_rot = nullptr;
     int rot_op_vals = 0;

@@ -10,8 +10,8 @@
 //   k_pp_scan   one block: target slot bases, offset pair bases, the items
 //               (each offset's pairs in runs of kPairRows, offsets in
 //               increasing order) and the pool check;
-//   k_pp_fill   one block per offset: its pairs in target order with their
-//               sources and slots.
+//   k_pp_fill   one warp per target: its pairs, each at the next position of
+//               its offset's list, with their sources and slots.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -166,23 +166,28 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         if (lane == 31) wsum[wid] = f;
     }
     __syncthreads();
+    __shared__ int s_cx[11], s_cy[11];
     if (tid == 0) {
-        // carry the per-warp inclusive scans across the 11 warps
+        // carries of the 11 per-warp inclusive scans
         int cx = 0, cy = 0, nof = 0;
         for (int w = 0; w < 11; ++w) {
             const int last = min(32 * w + 31, 342);
-            const int wx = s_pb[last + 1], wy = s_ibase[last + 1];
-            for (int o = 32 * w; o <= last; ++o) {
-                s_pb[o + 1] += cx;
-                s_ibase[o + 1] += cy;
-            }
-            cx += wx;
-            cy += wy;
+            s_cx[w] = cx;
+            s_cy[w] = cy;
+            cx += s_pb[last + 1];
+            cy += s_ibase[last + 1];
             nof += wsum[w];
         }
+        s_nof = nof;
+    }
+    __syncthreads();
+    if (tid < 343) {
+        s_pb[tid + 1] += s_cx[tid >> 5];
+        s_ibase[tid + 1] += s_cy[tid >> 5];
+    }
+    if (tid == 0) {
         s_pb[0] = 0;
         s_ibase[0] = 0;
-        s_nof = nof;
     }
     __syncthreads();
     for (int o = tid; o <= 343; o += kPpScanThreads) obase[o] = s_pb[o];
@@ -212,63 +217,41 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
     }
 }
 
-// One block per offset: its pairs in target order (a block-wide scan of the
-// targets' presence bits), each with its source and its slot (the target's
-// slot base plus the rank of the offset among the target's present ones).
+// One warp per target: each present offset takes the next position of that
+// offset's list (an atomic counter: the order of the pairs inside an
+// offset's list does not change any result, every product row being
+// computed alone), with its source and its slot (the target's slot base plus
+// the rank of the offset among the target's present ones).
 __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t* tmask,
                                                          const int* tbase, const int* obase,
-                                                         const M2lPairHdr* hdr, M2lPair* pairs) {
-    __shared__ int wsum[kPpThreads / 32];
-    __shared__ int s_carry;
+                                                         int* ofill, const M2lPairHdr* hdr,
+                                                         M2lPair* pairs) {
     __shared__ LevelInfo li;
-    const int op = blockIdx.x;
-    const int ox = op / 49 - 3, oy = (op / 7) % 7 - 3, oz = op % 7 - 3;
-    if (hdr->overflow) return;
-    if (ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return;
-    if (obase[op + 1] == obase[op]) return;  // uniform: no pairs at this offset
     stage_linfo(a.linfo, &li);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) s_carry = 0;
     __syncthreads();
-    const int g0 = li.gbase[2], nt = li.gbase[a.D + 1] - g0;
-    for (int c0 = 0; c0 < nt; c0 += kPpThreads) {
-        const int t = c0 + tid;
-        bool pres = false;
-        int c = 0, x = 0, y = 0, z = 0, l = 2;
-        uint32_t wbits[kPpWords];
-        if (t < nt) {
-            demorton3(a.code[g0 + t], x, y, z);
-            const int bx = x & 1, by = y & 1, bz = z & 1;
-            const int cx = ox - bx + 3, cy = oy - by + 3, cz = oz - bz + 3;
-            if (cx >= 0 && cx < 6 && cy >= 0 && cy < 6 && cz >= 0 && cz < 6) {
-                c = 36 * cx + 6 * cy + cz;
+    if (hdr->overflow) return;
+    const int lane = threadIdx.x & 31;
+    const int g0 = li.gbase[2], g1 = li.gbase[a.D + 1];
+    const int wpb = blockDim.x >> 5;
+    for (int g = g0 + blockIdx.x * wpb + (threadIdx.x >> 5); g < g1; g += gridDim.x * wpb) {
+        const int t = g - g0;
+        const int l = pp_level(li, a.D, g);
+        int x, y, z;
+        demorton3(a.code[g], x, y, z);
+        int rank = tbase[t];
 #pragma unroll
-                for (int w = 0; w < kPpWords; ++w) wbits[w] = tmask[(int64_t)t * kPpWords + w];
-                pres = (wbits[c >> 5] >> (c & 31)) & 1u;
+        for (int w = 0; w < kPpWords; ++w) {
+            const uint32_t bits = tmask[(int64_t)t * kPpWords + w];
+            if ((bits >> lane) & 1u) {
+                const int c = 32 * w + lane;
+                int op;
+                M2lPair pr;
+                pr.src = pp_source(a, l, x, y, z, c, &op);
+                pr.slot = rank + __popc(bits & ((1u << lane) - 1u));
+                pairs[obase[op] + atomicAdd(&ofill[op], 1)] = pr;
             }
+            rank += __popc(bits);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, pres);
-        if (lane == 0) wsum[wid] = __popc(bal);
-        __syncthreads();
-        if (pres) {
-            int pos = s_carry + __popc(bal & ((1u << lane) - 1u));
-            for (int v = 0; v < wid; ++v) pos += wsum[v];
-            int rank = __popc(wbits[c >> 5] & ((1u << (c & 31)) - 1u));
-            for (int w = 0; w < (c >> 5); ++w) rank += __popc(wbits[w]);
-            l = pp_level(li, a.D, g0 + t);
-            int opc;
-            M2lPair pr;
-            pr.src = pp_source(a, l, x, y, z, c, &opc);
-            pr.slot = tbase[t] + rank;
-            pairs[obase[op] + pos] = pr;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int tot = 0;
-            for (int v = 0; v < kPpThreads / 32; ++v) tot += wsum[v];
-            s_carry += tot;
-        }
-        __syncthreads();
     }
 }
 
@@ -550,7 +533,8 @@ PairList pair_list(const Workspace& ws, size_t* bytes) {
         return r;
     };
     L.hdr = (M2lPairHdr*)take(sizeof(M2lPairHdr));
-    L.ocnt = (int*)take(sizeof(int) * 343);
+    L.ocnt = (int*)take(sizeof(int) * 2 * 344);
+    L.ofill = L.ocnt + 344;
     L.obase = (int*)take(sizeof(int) * 344);
     L.tbase = (int*)take(sizeof(int) * (ws.cells_max + 1));
     L.tcount = (int*)take(sizeof(int) * ws.cells_max);
@@ -592,7 +576,7 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     const DenseLayout dl = dense_layout(D);
     for (int l = 0; l < kMaxDepth + 2; ++l) a.off[l] = dl.off[l];
     PairList L = pair_list(ws);
-    cudaError_t e = cudaMemsetAsync(L.ocnt, 0, sizeof(int) * 343, s);
+    cudaError_t e = cudaMemsetAsync(L.ocnt, 0, sizeof(int) * 2 * 344, s);  // counts, fills
     if (e != cudaSuccess) return e;
     const int64_t tb = target_cells_bound(n, D);
     const int64_t warps = kPpThreads / 32;
@@ -603,7 +587,7 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
                                             L.tcount, L.tbase, L.ocnt, L.obase, L.hdr, L.items,
                                             ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pp_fill<<<343, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.hdr, L.pairs);
+    k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the header (pair count, overflow flag) to pinned host memory, for the
     // host's pool check at the next call

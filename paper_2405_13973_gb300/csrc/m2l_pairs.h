@@ -30,12 +30,12 @@ struct M2lPairHdr {
     int n_offsets, pad[3];
 };
 
-// The work list in ws.pp_work: header, per-offset counts and pair bases,
-// per-target slot bases, counts and candidate-presence words, the items and
-// the pairs.
+// The work list in ws.pp_work: header, per-offset counts, fill counters and
+// pair bases, per-target slot bases, counts and candidate-presence words, the
+// items and the pairs.
 struct PairList {
     M2lPairHdr* hdr;
-    int *ocnt, *obase, *tbase, *tcount;
+    int *ocnt, *ofill, *obase, *tbase, *tcount;
     uint32_t* tmask;
     M2lPairItem* items;
     M2lPair* pairs;

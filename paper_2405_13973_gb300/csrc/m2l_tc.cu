@@ -313,6 +313,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// tcgen05.ld of 16 columns without the wait (several loads, one wait)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2, MODE_PAIR = 3 };
 
 constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator indices
@@ -906,6 +920,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             float* orow_p = out + orow * (MODE == MODE_PAIR ? a.Npad : a.ld);
             const float* own_p = a.L + orow * a.ld;
             const bool live = row < w.rows;
+            if (MODE == MODE_PAIR) {
+                // two column groups of both accumulators per wait; the row
+                // (one pair's partial expansion) goes straight to its slot
+                for (int cb = 0; cb * 16 < a.Npad; cb += 2) {
+                    const bool two = (cb + 1) * 16 < a.Npad;  // uniform
+                    const uint32_t t0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 16);
+                    uint32_t h0[16], c0[16], h1[16], c1[16];
+                    tmem_ld16_nw(t0, h0);
+                    tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                    if (two) {
+                        tmem_ld16_nw(t0 + 16u, h1);
+                        tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
+                    }
+                    tmem_wait_ld();
+                    if (live) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float4 v;
+                            v.x = __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]);
+                            v.y = __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]);
+                            v.z = __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]);
+                            v.w = __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]);
+                            *reinterpret_cast<float4*>(orow_p + cb * 16 + 4 * q) = v;
+                        }
+                        if (two) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                float4 v;
+                                v.x = __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]);
+                                v.y = __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]);
+                                v.z = __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]);
+                                v.w = __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]);
+                                *reinterpret_cast<float4*>(orow_p + (cb + 1) * 16 + 4 * q) = v;
+                            }
+                        }
+                    }
+                }
+            } else
             for (int cb0 = 0; cb0 * 16 < a.Npad; cb0 += 4) {
                 float4 own[16];
 #pragma unroll
