@@ -199,20 +199,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-// the same with an L2 eviction-priority hint (a createpolicy value)
-__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes,
-                                              uint64_t* bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
-        : "memory");
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 // 16-byte global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
@@ -608,8 +594,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
     if (warp == 0) {
         // ---- operator producer
         if (lane == 0) {
-            const uint64_t evict_first = policy_evict_first();
-            (void)evict_first;
             int g = 0;
             for (int idx = first; idx < count && !*abort_v; idx += stride) {
                 TcWork w;
@@ -626,13 +610,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                     mbar_arrive_expect_tx(&fullB_bar[st], pieces * b_bytes);
                     const unsigned char* src =
                         a.ops + ((size_t)tc_op<MODE>(a, w, j) * a.kchunks + kc) * pieces * b_bytes;
-                    if (MODE == MODE_PAIR)
-                        // the offset's items run side by side in one wave and
-                        // the operators were prefetched into L2: once read,
-                        // they may go first, ahead of the partial rows
-                        bulk_g2s_hint(sB, src, pieces * b_bytes, &fullB_bar[st], evict_first);
-                    else
-                        bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
+                    bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
                     issued_par[st] = use & 1;
                 }
             }
@@ -1316,29 +1294,6 @@ void host_m2l_offsets(int16_t out[8][189]);
 
 int m2l_tc_npad(int p) { return tc_geom(p, true).Npad; }
 
-// L2 prefetch of the tensor-core operator images of the offsets that have
-// pairs this step (the M2L kernel then finds them in L2 instead of HBM): one
-// bulk prefetch per (offset, K chunk).
-__global__ void k_tc_prefetch_ops(const int* ocnt, const unsigned char* ops, int kchunks,
-                                  uint32_t chunk_bytes) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 343 * kchunks) return;
-    const int op = e / kchunks;
-    if (ocnt[op] <= 0) return;
-    const unsigned char* src = ops + (size_t)e * chunk_bytes;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(chunk_bytes)
-                 : "memory");
-}
-
-cudaError_t launch_m2l_tc_prefetch(const Workspace& ws, const int* ocnt, cudaStream_t s) {
-    const TcGeom g = tc_geom(ws.p, ws.tc_bf16 != 0);
-    const int total = 343 * g.kchunks;
-    k_tc_prefetch_ops<<<(total + 255) / 256, 256, 0, s>>>(
-        ocnt, static_cast<const unsigned char*>(ws.T_m2l_tc), g.kchunks,
-        (uint32_t)(g.pieces * g.b_bytes));
-    return cudaGetLastError();
-}
-
 size_t m2l_tc_operand_bytes(int p, bool bf16) {
     if (!tc_supported(p, bf16)) return 0;
     TcGeom g = tc_geom(p, bf16);
@@ -1554,11 +1509,7 @@ static TcArgs pair_args(int64_t n, int D, Workspace& ws) {
 
 cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
-    if (ws.m2l_pairs) {
-        cudaError_t e = launch_m2l_pairs_worklist(n, D, ws, s);
-        if (e != cudaSuccess) return e;
-        return launch_m2l_tc_prefetch(ws, pair_list(ws).ocnt, s);
-    }
+    if (ws.m2l_pairs) return launch_m2l_pairs_worklist(n, D, ws, s);
     int64_t tiles;
     TcPlanHdr* hdr;
     TcTile* tl;
