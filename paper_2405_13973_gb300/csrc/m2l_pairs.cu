@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
 __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t* tmask,
                                                          const int* tbase, const int* obase,
                                                          int* ofill, const M2lPairHdr* hdr,
-                                                         M2lPair* pairs) {
+                                                         M2lPair* pairs, int* tpair) {
     __shared__ LevelInfo li;
     stage_linfo(a.linfo, &li);
     __syncthreads();
@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t
                 M2lPair pr;
                 pr.src = pp_source(a, l, x, y, z, c, &op);
                 pr.slot = rank + __popc(bits & ((1u << lane) - 1u));
-                pairs[obase[op] + atomicAdd(&ofill[op], 1)] = pr;
+                const int pidx = obase[op] + atomicAdd(&ofill[op], 1);
+                pairs[pidx] = pr;
+                tpair[pr.slot] = pidx;
             }
             rank += __popc(bits);
         }
@@ -262,6 +264,7 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t
 __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride, int width,
                                                        const LevelInfo* linfo,
                                                        const M2lPairHdr* hdr, const int* tbase,
+                                                       const int* __restrict__ tpair,
                                                        const float4* __restrict__ part, float* L) {
     // one thread per (target, 16-byte column group): consecutive threads read
     // consecutive columns of a slot row; eight rows in flight per thread
@@ -276,16 +279,19 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         int s = s0;
         for (; s + 8 <= s1; s += 8) {
+            int rw[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) rw[k] = tpair[s + k];
             float4 q[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) q[k] = __ldcs(part + (int64_t)(s + k) * s4 + u);
+            for (int k = 0; k < 8; ++k) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
             }
         }
         for (; s < s1; ++s) {
-            const float4 q = __ldcs(part + (int64_t)s * s4 + u);
+            const float4 q = __ldcs(part + (int64_t)tpair[s] * s4 + u);
             v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
         }
         *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
@@ -295,8 +301,8 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
 template <typename T>
 __global__ void __launch_bounds__(256) k_pp_reduce(int D, int ld, int stride, int width,
                                                     const LevelInfo* linfo, const M2lPairHdr* hdr,
-                                                    const int* tbase, const T* __restrict__ part,
-                                                    T* L) {
+                                                    const int* tbase, const int* __restrict__ tpair,
+                                                    const T* __restrict__ part, T* L) {
     const int lane = threadIdx.x & 31;
     const int g0 = linfo->gbase[2], nt = linfo->gbase[D + 1] - g0;
     const bool over = hdr->overflow != 0;
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(256) k_pp_reduce(int D, int ld, int stride, in
         const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
         for (int u = lane; u < width; u += 32) {
             T v = T(0);
-            for (int s = s0; s < s1; ++s) v += part[(int64_t)s * stride + u];
+            for (int s = s0; s < s1; ++s) v += part[(int64_t)tpair[s] * stride + u];
             L[(int64_t)(g0 + t) * ld + u] = v;
         }
     }
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(256) k_m2l_pairs_simt(int P, int ld, int strid
         if (tid < kSimtRows) {
             const bool live = tid < rows;
             s_src[tid] = live ? pairs[it.begin + r0 + tid].src : -1;
-            s_slot[tid] = live ? pairs[it.begin + r0 + tid].slot : -1;
+            s_slot[tid] = live ? it.begin + r0 + tid : -1;  // partial rows in pair order
         }
         __syncthreads();
         const T* To = Tm2l + (int64_t)it.op * P * P;
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(256) k_m2l_rot(int p, int P, int ld, int strid
             if (tid < np) {
                 const bool live = tid < rows;
                 s_src[tid] = live ? pairs[it.begin + r0 + tid].src : -1;
-                s_slot[tid] = live ? pairs[it.begin + r0 + tid].slot : -1;
+                s_slot[tid] = live ? it.begin + r0 + tid : -1;  // partial rows in pair order
             }
             __syncthreads();
             for (int e = tid; e < np * P; e += blockDim.x) {
@@ -541,6 +547,7 @@ PairList pair_list(const Workspace& ws, size_t* bytes) {
     L.tmask = (uint32_t*)take(sizeof(uint32_t) * kPpWords * ws.cells_max);
     L.items = (M2lPairItem*)take(sizeof(M2lPairItem) * ws.pp_item_cap);
     L.pairs = (M2lPair*)take(sizeof(M2lPair) * ws.pp_slot_cap);
+    L.tpair = (int*)take(sizeof(int) * ws.pp_slot_cap);
     if (bytes) *bytes = o;
     return L;
 }
@@ -587,7 +594,8 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
                                             L.tcount, L.tbase, L.ocnt, L.obase, L.hdr, L.items,
                                             ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs);
+    k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs,
+                                         L.tpair);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the header (pair count, overflow flag) to pinned host memory, for the
     // host's pool check at the next call
@@ -603,15 +611,17 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
     const unsigned gr = (unsigned)std::min<int64_t>((tb + 7) / 8, 152 * 16);
     if (ws.fp64) {
         k_pp_reduce<double><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
-                                               L.tbase, (const double*)ws.pp_part, (double*)ws.L);
+                                               L.tbase, L.tpair, (const double*)ws.pp_part,
+                                               (double*)ws.L);
     } else if (width % 4 == 0 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
         const int64_t th = tb * (width / 4);
         const unsigned g4 = (unsigned)std::min<int64_t>((th + 255) / 256, 152 * 16);
         k_pp_reduce_f4<<<g4, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr, L.tbase,
-                                          (const float4*)ws.pp_part, (float*)ws.L);
+                                          L.tpair, (const float4*)ws.pp_part, (float*)ws.L);
     } else {
         k_pp_reduce<float><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
-                                              L.tbase, (const float*)ws.pp_part, (float*)ws.L);
+                                              L.tbase, L.tpair, (const float*)ws.pp_part,
+                                              (float*)ws.L);
     }
     return cudaGetLastError();
 }

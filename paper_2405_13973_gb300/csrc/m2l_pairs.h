@@ -8,9 +8,10 @@
 // stored scaled by the cell size, so T_o depends on o only, not on the level:
 // the (target, source) pairs of one offset, gathered over every level, form
 // one dense product [pairs x P] x [P x P].  Each pair's result row is a
-// partial local expansion, stored in the target's slot row (a target's pairs
-// take consecutive slots in increasing offset order), and the target's L is
-// the sum of its slot rows in that order (deterministic).
+// partial local expansion, stored at the pair's index (the rows of a work
+// item are consecutive); a target's pairs take consecutive slots in
+// increasing offset order, each naming its pair, and the target's L is the
+// sum of its pairs' rows in slot order (deterministic).
 #pragma once
 #include "internal.h"
 
@@ -20,7 +21,7 @@ constexpr int kPairRows = 128;   // pairs per work item (one tensor-core product
 
 struct M2lPair {
     int32_t src;   // global compact id of the source cell
-    int32_t slot;  // row of the partial-result array
+    int32_t slot;  // the target's slot (its pairs in increasing offset order)
 };
 struct M2lPairItem {
     int32_t op, begin, rows, pad;  // offset index, first pair, pairs (<= kPairRows)
@@ -39,6 +40,7 @@ struct PairList {
     uint32_t* tmask;
     M2lPairItem* items;
     M2lPair* pairs;
+    int* tpair;  // [slot] -> pair index (partial rows are stored in pair order)
 };
 PairList pair_list(const Workspace& ws, size_t* bytes = nullptr);
 

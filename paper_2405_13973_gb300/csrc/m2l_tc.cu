@@ -78,6 +78,10 @@ struct TcGeom {
     int P = 0, Kpad = 0, Npad = 0, kchunks = 0, tmem_cols = 0, acc_cols = 0, pieces = 2,
         row_bytes = 128;
     int a_bytes = 0, b_bytes = 0, stage_bytes = 0, smem_bytes = 0, stages = 2, raw = 2;
+    // BF16 pair-packed epilogue: the accumulators pass through shared memory
+    // (the producers' raw ring, unused in that mode) in two column halves of
+    // epi_half columns, rows epi_stride floats apart
+    int epi_half = 0, epi_stride = 0, region = 0;
 };
 
 // raw FP32 A chunks in flight per producer thread (cp.async ring): 16 KB a slot
@@ -98,15 +102,23 @@ TcGeom tc_geom(int p, bool bf16) {
     g.a_bytes = kTcRows * g.row_bytes;   // one piece of A for a 32-wide chunk
     g.b_bytes = g.Npad * g.row_bytes;    // one piece of B
     g.stage_bytes = g.pieces * (g.a_bytes + g.b_bytes);
-    // three raw A slots when three operand stages still fit, else two
+    if (bf16) {
+        g.epi_half = ((g.Npad / 16 + 1) / 2) * 16;
+        g.epi_stride = g.epi_half + 4;  // 16-byte rows, 4-bank shift per row
+    }
+    const int epi_bytes = kTcRows * g.epi_stride * 4;
+    // three raw A slots when three operand stages still fit, else two; the
+    // region after the stages also holds the pair epilogue's staging
     g.raw = 3;
-    g.stages = (227 * 1024 - 1024 - g.raw * kRawSlotBytes) / g.stage_bytes;
+    g.region = g.raw * kRawSlotBytes > epi_bytes ? g.raw * kRawSlotBytes : epi_bytes;
+    g.stages = (227 * 1024 - 1024 - g.region) / g.stage_bytes;
     if (g.stages < 3) {
         g.raw = 2;
-        g.stages = (227 * 1024 - 1024 - g.raw * kRawSlotBytes) / g.stage_bytes;
+        g.region = g.raw * kRawSlotBytes > epi_bytes ? g.raw * kRawSlotBytes : epi_bytes;
+        g.stages = (227 * 1024 - 1024 - g.region) / g.stage_bytes;
     }
     if (g.stages > kMaxStages) g.stages = kMaxStages;
-    g.smem_bytes = g.stages * g.stage_bytes + g.raw * kRawSlotBytes + 1024;
+    g.smem_bytes = g.stages * g.stage_bytes + g.region + 1024;
     return g;
 }
 
@@ -313,6 +325,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// barrier 1 over the 128 epilogue threads; the variant returns whether any
+// of them passed true
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool epi_bar_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
 // tcgen05.ld of 16 columns without the wait (several loads, one wait)
 __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
@@ -335,6 +360,7 @@ struct TcArgs {
     int mode, level;      // level: the target level of M2M / L2L launches
     int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages, raw;
     int bf16, pieces, a_bytes, b_bytes;  // operand format and per-piece tile bytes
+    int epi_half, epi_stride;            // BF16 pair epilogue staging (TcGeom)
     uint32_t idesc;
     const LevelInfo* linfo;
     const uint32_t* code;
@@ -879,6 +905,79 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         }
+    } else if (MODE == MODE_PAIR && BF16) {
+        // ---- epilogue of the BF16 pair-packed items: the accumulators (row =
+        // TMEM lane = pair) pass through shared memory in two column halves
+        // and are released before the second half is written out; the rows
+        // of an item are consecutive pair rows of the partial array, so the
+        // stores from shared memory are coalesced.  The four warps decide to
+        // stop together (barrier reduction), so their barriers stay matched.
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const int etid = (warp - kWarpEpi0) * 32 + lane;
+        float* stg = reinterpret_cast<float*>(base + NS * stage_bytes);
+        const int ngr = a.Npad / 16, gh = a.epi_half / 16, sstr = a.epi_stride;
+        const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+        int jacc = 0;
+        for (int idx = first; idx < count; idx += stride) {
+            TcWork w;
+            if (!tc_work<MODE>(a, li, idx, w)) continue;  // uniform: rows >= 1 for every item
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_or_abort(&accf_bar, jacc & 1, abort_v) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (epi_bar_any(ok == 0)) {
+                *abort_v = 1;
+                break;
+            }
+            tc_fence_after();
+            for (int pass = 0; pass < 2; ++pass) {
+                const int g0 = pass ? gh : 0, g1 = pass ? ngr : gh;
+                for (int gq = g0; gq < g1; gq += 2) {
+                    const bool two = gq + 1 < g1;  // uniform
+                    const uint32_t t0 = trow + (uint32_t)(gq * 16);
+                    uint32_t h0[16], c0[16], h1[16], c1[16];
+                    tmem_ld16_nw(t0, h0);
+                    tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                    if (two) {
+                        tmem_ld16_nw(t0 + 16u, h1);
+                        tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
+                    }
+                    tmem_wait_ld();
+                    float* dst = stg + row * sstr + (gq - g0) * 16;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
+                            __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
+                            __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
+                            __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
+                            __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
+                    if (two) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            *reinterpret_cast<float4*>(dst + 16 + 4 * q) = make_float4(
+                                __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
+                                __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
+                                __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
+                                __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
+                    }
+                }
+                if (pass == 1) {
+                    // accumulators read: the issuer may start the next item
+                    tc_fence_before();
+                    mbar_arrive(&acce_bar);
+                }
+                epi_bar();
+                const int units = (g1 - g0) * 4;  // 16-byte units per row of this half
+                float* outp = a.ppart + (int64_t)w.pbegin * a.Npad + g0 * 16;
+                for (int e = etid; e < w.rows * units; e += kEpiThreads) {
+                    const int r = e / units, u = e - r * units;
+                    *reinterpret_cast<float4*>(outp + (int64_t)r * a.Npad + 4 * u) =
+                        *reinterpret_cast<const float4*>(stg + r * sstr + 4 * u);
+                }
+                epi_bar();
+            }
+            ++jacc;
+        }
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the tile
         const int quad = warp & 3;
@@ -891,8 +990,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             float* out;
             int64_t orow;
             if (MODE == MODE_PAIR) {
-                out = a.ppart;
-                orow = row < w.rows ? (int64_t)a.pairs[w.pbegin + row].slot : 0;
+                out = a.ppart;  // rows in pair order
+                orow = (int64_t)w.pbegin + row;
             } else if (MODE == MODE_M2L && w.rank > 0) {
                 out = a.part + (int64_t)w.slot * kTcRows * a.ld;  // this item's partial slab
                 orow = row;
@@ -1422,6 +1521,8 @@ static TcArgs base_args(int64_t n, int D, Workspace& ws, int splits) {
     a.splits = splits;
     a.stages = g.stages;
     a.raw = g.raw;
+    a.epi_half = g.epi_half;
+    a.epi_stride = g.epi_stride;
     a.bf16 = bf16 ? 1 : 0;
     a.pieces = g.pieces;
     a.a_bytes = g.a_bytes;
