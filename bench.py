@@ -480,13 +480,13 @@ def forces_arm(args):
         flush_buf.fill_(1.0)
     w = W.sphere_sweep(args.forces)
     ref = sweep_reference(pt, torch, w) if not args.no_ref else None
-    r = force_eval_point(pt, torch, w, p, precision, args.steps, flush, ref,
+    r = force_eval_point(pt, torch, w, args.p, args.precision, args.steps, flush, ref,
                          warmup=args.warmup, schedule=args.schedule)
     line = {"metric": "single force evaluations/s (sweep sphere, 2e14 m^-3)",
             "value": r.get("evals_per_s"), "unit": "evaluations/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "dtype": precision, "data": "synthetic",
-            "config": {"workload": f"sphere N={args.forces}, 2e14 m^-3 + 1% jitter, p={p}",
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"sphere N={args.forces}, 2e14 m^-3 + 1% jitter, p={args.p}",
                        "l2": "flushed between timed evaluations (512 MiB write)"},
             "result": r, "reference": ref[2] if ref else None}
     print(json.dumps(line), flush=True)
