@@ -463,6 +463,7 @@ constexpr int kProdWarps = 8;
 constexpr int kWarpA0 = 2;
 constexpr int kWarpEpi0 = kWarpA0 + kProdWarps;
 constexpr int kEpiThreads = 128;
+constexpr int kEpiRegGroups = 5;  // pair epilogue: column groups of 16 kept in registers
 
 // One unit of work for a CTA: a run [begin, end) of the term list of one tile
 // of 128 target cells.  rank > 0 runs of M2L (and split > 0 of M2M) write
@@ -930,41 +931,95 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 break;
             }
             tc_fence_after();
-            for (int pass = 0; pass < 2; ++pass) {
-                const int g0 = pass ? gh : 0, g1 = pass ? ngr : gh;
-                for (int gq = g0; gq < g1; gq += 2) {
-                    const bool two = gq + 1 < g1;  // uniform
-                    const uint32_t t0 = trow + (uint32_t)(gq * 16);
-                    uint32_t h0[16], c0[16], h1[16], c1[16];
-                    tmem_ld16_nw(t0, h0);
-                    tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
-                    if (two) {
-                        tmem_ld16_nw(t0 + 16u, h1);
-                        tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
-                    }
-                    tmem_wait_ld();
-                    float* dst = stg + row * sstr + (gq - g0) * 16;
+            // first half (columns < epi_half) into shared memory; the second
+            // half (at most kEpiRegGroups column groups) into registers; then
+            // the accumulators are free and both halves go out from here
+            uint32_t keep[kEpiRegGroups][16];
+            const bool regs = ngr - gh <= kEpiRegGroups;  // uniform
+            for (int gq = 0; gq < gh; gq += 2) {
+                const bool two = gq + 1 < gh;  // uniform
+                const uint32_t t0 = trow + (uint32_t)(gq * 16);
+                uint32_t h0[16], c0[16], h1[16], c1[16];
+                tmem_ld16_nw(t0, h0);
+                tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                if (two) {
+                    tmem_ld16_nw(t0 + 16u, h1);
+                    tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
+                }
+                tmem_wait_ld();
+                float* dst = stg + row * sstr + gq * 16;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
+                        __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
+                        __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
+                        __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
+                        __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
+                if (two) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
-                            __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
-                            __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
-                            __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
-                            __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
-                    if (two) {
+                        *reinterpret_cast<float4*>(dst + 16 + 4 * q) = make_float4(
+                            __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
+                            __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
+                            __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
+                            __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
+                }
+            }
+            if (regs) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            *reinterpret_cast<float4*>(dst + 16 + 4 * q) = make_float4(
-                                __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
-                                __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
-                                __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
-                                __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
+                for (int k = 0; k < kEpiRegGroups; ++k) {
+                    if (gh + k < ngr) {  // uniform
+                        const uint32_t t0 = trow + (uint32_t)((gh + k) * 16);
+                        uint32_t c0[16];
+                        tmem_ld16_nw(t0, keep[k]);
+                        tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            keep[k][j] = __float_as_uint(__uint_as_float(keep[k][j]) +
+                                                         __uint_as_float(c0[j]));
                     }
                 }
+                // accumulators read: the issuer may start the next item
+                tc_fence_before();
+                mbar_arrive(&acce_bar);
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                const int g0 = pass ? gh : 0, g1 = pass ? ngr : gh;
                 if (pass == 1) {
-                    // accumulators read: the issuer may start the next item
-                    tc_fence_before();
-                    mbar_arrive(&acce_bar);
+                    if (regs) {
+#pragma unroll
+                        for (int k = 0; k < kEpiRegGroups; ++k) {
+                            if (gh + k < ngr) {
+                                float* dst = stg + row * sstr + k * 16;
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
+                                        __uint_as_float(keep[k][4 * q + 0]),
+                                        __uint_as_float(keep[k][4 * q + 1]),
+                                        __uint_as_float(keep[k][4 * q + 2]),
+                                        __uint_as_float(keep[k][4 * q + 3]));
+                            }
+                        }
+                    } else {
+                        for (int gq = gh; gq < ngr; ++gq) {
+                            const uint32_t t0 = trow + (uint32_t)(gq * 16);
+                            uint32_t h0[16], c0[16];
+                            tmem_ld16_nw(t0, h0);
+                            tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                            tmem_wait_ld();
+                            float* dst = stg + row * sstr + (gq - gh) * 16;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
+                                    __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
+                                    __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
+                                    __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
+                                    __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
+                        }
+                        tc_fence_before();
+                        mbar_arrive(&acce_bar);
+                    }
                 }
                 epi_bar();
                 const int units = (g1 - g0) * 4;  // 16-byte units per row of this half
