@@ -367,6 +367,7 @@ static int alloc_pairs(fmm_plan_s* pl) {
     // every later call checks the count of the last step (ensure_pairs)
     int64_t cap = std::min<int64_t>(exact, 12 * pl->n_max + 4096);
     ws.pp_slot_cap = cap > 0 ? cap : 1;
+    ws.pp_rows_cap = ws.pp_slot_cap + 343 * 128;
     ws.pp_item_cap = ws.pp_slot_cap / 128 + 344;
     ws.pp_stride = is_tc(pl->precision) ? m2l_tc_npad(pl->p) : ws.ld;
     bool ok = dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) &&
@@ -378,6 +379,7 @@ static int alloc_pairs(fmm_plan_s* pl) {
     }
     if (!pl->dry && cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess)
         return PT_ERR_CUDA;
+    if (!pl->dry && ws.tc_bf16 && m2l_tc_make_part_map(ws) != cudaSuccess) return PT_ERR_CUDA;
     if (!pl->dry && !ws.h_pp_hdr) {
         if (cudaMallocHost(&ws.h_pp_hdr, sizeof(M2lPairHdr)) != cudaSuccess) return PT_ERR_CUDA;
         memset(ws.h_pp_hdr, 0, sizeof(M2lPairHdr));
@@ -401,11 +403,13 @@ static int regrow_pairs(fmm_plan_s* pl, int64_t cap) {
     ws.pp_work = nullptr;
     ws.pp_part = nullptr;
     ws.pp_slot_cap = cap;
+    ws.pp_rows_cap = cap + 343 * 128;
     ws.pp_item_cap = cap / 128 + 344;
     if (!dalloc(pl, ws.pp_work, m2l_pp_work_bytes(ws)) ||
         !dalloc(pl, ws.pp_part, m2l_pp_part_bytes(ws)))
         return PT_ERR_OOM;
     if (cudaMemset(ws.pp_work, 0, m2l_pp_work_bytes(ws)) != cudaSuccess) return PT_ERR_CUDA;
+    if (ws.tc_bf16 && m2l_tc_make_part_map(ws) != cudaSuccess) return PT_ERR_CUDA;
     memset(ws.h_pp_hdr, 0, sizeof(M2lPairHdr));
     ++ws.pp_gen;
     return PT_OK;

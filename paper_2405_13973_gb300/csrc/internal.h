@@ -118,7 +118,12 @@ struct Workspace {
     int pp_gen = 0;                 // bumped whenever the pool is reallocated
     int pp_stride = 0;
     int64_t pp_slot_cap = 0;    // pairs the pool holds
+    int64_t pp_rows_cap = 0;    // partial rows: pairs, each offset's run padded to 128 rows
     int64_t pp_item_cap = 0;    // work items (runs of up to 128 pairs of one offset)
+    // TMA descriptor of the partial rows for the tensor-core epilogue
+    // (a CUtensorMap: rows x (P rounded up to 16) FP32, boxes of 128 rows x 16)
+    alignas(64) unsigned char pp_map[128] = {0};
+    int pp_map_ok = 0;
 };
 
 enum ErrBits { ERR_NONFINITE = 1, ERR_TIMEOUT = 2, ERR_CAPACITY = 4 };
@@ -188,6 +193,9 @@ int m2l_rot_tile(const Workspace& ws);
 cudaError_t m2l_rot_init();
 // the tensor-core partial-row width (P rounded up to 16)
 int m2l_tc_npad(int p);
+// (re)builds ws.pp_map for the current pp_part / pp_rows_cap (BF16 tensor-core
+// plans; others leave it unused)
+cudaError_t m2l_tc_make_part_map(Workspace& ws);
 cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
 // partial slabs of the M2L work items (a pool of 16 KB per ion, 16 MB to 8 GB)
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max);

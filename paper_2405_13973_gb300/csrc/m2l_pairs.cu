@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_count(PpArgs a, uint32_t* tma
 // (each offset's pairs in runs of 128, offsets in increasing order).
 constexpr int kPpScanThreads = 1024;
 __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelInfo* linfo,
-                                                             int64_t slot_cap, int item_cap,
+                                                             int64_t slot_cap, int64_t rows_cap,
+                                                             int item_cap,
                                                              const int* tcount, int* tbase,
                                                              const int* ocnt, int* obase,
                                                              M2lPairHdr* hdr, M2lPairItem* items,
@@ -148,7 +149,9 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         const int o = tid;  // 0 .. 351
         const int c = o < 343 ? ocnt[o] : 0;
         const int runs = (c + kPairRows - 1) / kPairRows;
-        int x = c, y = runs, f = c > 0 ? 1 : 0;
+        // each offset's pairs start on a multiple of 128 rows, so that every
+        // work item covers whole 128-row blocks of the partial array
+        int x = runs * kPairRows, y = runs, f = c > 0 ? 1 : 0;
         for (int d = 1; d < 32; d <<= 1) {
             const int xa = __shfl_up_sync(0xffffffffu, x, d);
             const int ya = __shfl_up_sync(0xffffffffu, y, d);
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
     if (tid == 0) {
         tbase[nt] = total;
         const int pb = s_pb[343], ib = s_ibase[343];
-        const bool over = (int64_t)total > slot_cap || ib > item_cap || pb != total;
+        const bool over = (int64_t)total > slot_cap || (int64_t)pb > rows_cap || ib > item_cap;
         hdr->overflow = over ? 1 : 0;
         if (over) atomicOr(err, ERR_CAPACITY);
         hdr->n_items = over ? 0 : ib;
@@ -203,7 +206,8 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         hdr->n_offsets = s_nof;
     }
     __syncthreads();
-    if ((int64_t)total > slot_cap || s_ibase[343] > item_cap) return;
+    if ((int64_t)total > slot_cap || (int64_t)s_pb[343] > rows_cap || s_ibase[343] > item_cap)
+        return;
     for (int o = tid; o < 343; o += kPpScanThreads) {
         const int c = ocnt[o];
         for (int k = 0; k * kPairRows < c; ++k) {
@@ -546,7 +550,7 @@ PairList pair_list(const Workspace& ws, size_t* bytes) {
     L.tcount = (int*)take(sizeof(int) * ws.cells_max);
     L.tmask = (uint32_t*)take(sizeof(uint32_t) * kPpWords * ws.cells_max);
     L.items = (M2lPairItem*)take(sizeof(M2lPairItem) * ws.pp_item_cap);
-    L.pairs = (M2lPair*)take(sizeof(M2lPair) * ws.pp_slot_cap);
+    L.pairs = (M2lPair*)take(sizeof(M2lPair) * ws.pp_rows_cap);
     L.tpair = (int*)take(sizeof(int) * ws.pp_slot_cap);
     if (bytes) *bytes = o;
     return L;
@@ -561,7 +565,7 @@ size_t m2l_pp_work_bytes(const Workspace& ws) {
 }
 
 size_t m2l_pp_part_bytes(const Workspace& ws) {
-    return (size_t)ws.pp_slot_cap * ws.pp_stride * (ws.fp64 ? sizeof(double) : sizeof(float));
+    return (size_t)ws.pp_rows_cap * ws.pp_stride * (ws.fp64 ? sizeof(double) : sizeof(float));
 }
 
 static int64_t target_cells_bound(int64_t n, int D) {
@@ -590,7 +594,8 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     const unsigned gc = (unsigned)std::min<int64_t>((tb + warps - 1) / warps, 152 * 8);
     k_pp_count<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tcount, L.ocnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pp_scan<<<1, kPpScanThreads, 0, s>>>(D, ws.linfo, ws.pp_slot_cap, (int)ws.pp_item_cap,
+    k_pp_scan<<<1, kPpScanThreads, 0, s>>>(D, ws.linfo, ws.pp_slot_cap, ws.pp_rows_cap,
+                                            (int)ws.pp_item_cap,
                                             L.tcount, L.tbase, L.ocnt, L.obase, L.hdr, L.items,
                                             ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

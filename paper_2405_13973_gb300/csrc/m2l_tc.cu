@@ -50,6 +50,8 @@
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // ERR_TIMEOUT, stops issuing, waits (bounded) for its own work in flight,
 // frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -104,9 +106,9 @@ TcGeom tc_geom(int p, bool bf16) {
     g.stage_bytes = g.pieces * (g.a_bytes + g.b_bytes);
     if (bf16) {
         g.epi_half = ((g.Npad / 16 + 1) / 2) * 16;
-        g.epi_stride = g.epi_half + 4;  // 16-byte rows, 4-bank shift per row
+        g.epi_stride = 16;  // boxes of 16 columns
     }
-    const int epi_bytes = kTcRows * g.epi_stride * 4;
+    const int epi_bytes = (g.epi_half / 16) * kTcRows * 16 * 4;
     // three raw A slots when three operand stages still fit, else two; the
     // region after the stages also holds the pair epilogue's staging
     g.raw = 3;
@@ -325,6 +327,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// TMA tensor store of one box (2D: x = column, y = row) from shared memory,
+// bulk-group completion
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y,
+                                             const void* src) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(smem_addr(src))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the source shared memory of this thread's committed bulk stores may be reused
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// this thread's committed bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 // barrier 1 over the 128 epilogue threads; the variant returns whether any
 // of them passed true
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
@@ -357,6 +380,7 @@ enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2, MODE_PAIR = 3 };
 constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator indices
 
 struct TcArgs {
+    CUtensorMap part_map;  // pair epilogue: TMA descriptor of the partial rows (BF16)
     int mode, level;      // level: the target level of M2M / L2L launches
     int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages, raw;
     int bf16, pieces, a_bytes, b_bytes;  // operand format and per-piece tile bytes
@@ -464,6 +488,7 @@ constexpr int kWarpA0 = 2;
 constexpr int kWarpEpi0 = kWarpA0 + kProdWarps;
 constexpr int kEpiThreads = 128;
 constexpr int kEpiRegGroups = 5;  // pair epilogue: column groups of 16 kept in registers
+constexpr int kEpiBoxBytes = kTcRows * 16 * 4;  // one TMA box: 128 rows x 16 FP32
 
 // One unit of work for a CTA: a run [begin, end) of the term list of one tile
 // of 128 target cells.  rank > 0 runs of M2L (and split > 0 of M2M) write
@@ -563,7 +588,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
 // One instantiation per mode and operand format (MODE == MODE, BF16 == BF16):
 // each kernel carries only its own paths.
 template <int MODE, int BF16>
-__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
         empty_bar[kMaxStages], accf_bar, acce_bar, drain_bar;
@@ -908,17 +933,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
         }
     } else if (MODE == MODE_PAIR && BF16) {
         // ---- epilogue of the BF16 pair-packed items: the accumulators (row =
-        // TMEM lane = pair) pass through shared memory in two column halves
-        // and are released before the second half is written out; the rows
-        // of an item are consecutive pair rows of the partial array, so the
-        // stores from shared memory are coalesced.  The four warps decide to
-        // stop together (barrier reduction), so their barriers stay matched.
+        // TMEM lane = pair) go to shared memory in boxes of 128 rows x 16
+        // columns (the TMA 64-byte swizzle: 16-byte unit u of row r at
+        // u ^ ((r & 7) >> 1), bank-conflict free), the first half of the
+        // column groups directly, the rest through registers, so that the
+        // accumulators are released after the two drains; one thread then
+        // stores the boxes with TMA (the item's rows are one 128-row block of
+        // the partial array) while the MMAs of the next item run.  The four
+        // warps decide to stop together (barrier reduction), so their
+        // barriers stay matched.
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         const int etid = (warp - kWarpEpi0) * 32 + lane;
-        float* stg = reinterpret_cast<float*>(base + NS * stage_bytes);
-        const int ngr = a.Npad / 16, gh = a.epi_half / 16, sstr = a.epi_stride;
+        unsigned char* boxes = base + NS * stage_bytes;  // kEpiBoxBytes apart
+        const int ngr = a.Npad / 16, gh = a.epi_half / 16;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+        const int rsw = (row & 7) >> 1;
+        auto put4 = [&](int box, int q, float x, float y, float z, float wv) {
+            *reinterpret_cast<float4*>(boxes + box * kEpiBoxBytes + row * 64 + ((q ^ rsw) << 4)) =
+                make_float4(x, y, z, wv);
+        };
         int jacc = 0;
         for (int idx = first; idx < count; idx += stride) {
             TcWork w;
@@ -926,14 +960,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
             int ok = 1;
             if (lane == 0) ok = mbar_wait_or_abort(&accf_bar, jacc & 1, abort_v) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
+            // the boxes of the previous item have been read by its stores
+            if (etid == 0) bulk_wait_read();
             if (epi_bar_any(ok == 0)) {
                 *abort_v = 1;
                 break;
             }
             tc_fence_after();
-            // first half (columns < epi_half) into shared memory; the second
-            // half (at most kEpiRegGroups column groups) into registers; then
-            // the accumulators are free and both halves go out from here
             uint32_t keep[kEpiRegGroups][16];
             const bool regs = ngr - gh <= kEpiRegGroups;  // uniform
             for (int gq = 0; gq < gh; gq += 2) {
@@ -947,22 +980,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                     tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
                 }
                 tmem_wait_ld();
-                float* dst = stg + row * sstr + gq * 16;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
-                        __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
-                        __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
-                        __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
-                        __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
+                    put4(gq, q, __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
+                         __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
+                         __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
+                         __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
                 if (two) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        *reinterpret_cast<float4*>(dst + 16 + 4 * q) = make_float4(
-                            __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
-                            __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
-                            __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
-                            __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
+                        put4(gq + 1, q,
+                             __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
+                             __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
+                             __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
+                             __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
                 }
             }
             if (regs) {
@@ -984,55 +1015,61 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(TcArgs a) {
                 tc_fence_before();
                 mbar_arrive(&acce_bar);
             }
-            for (int pass = 0; pass < 2; ++pass) {
-                const int g0 = pass ? gh : 0, g1 = pass ? ngr : gh;
-                if (pass == 1) {
-                    if (regs) {
+            // first half out by TMA
+            fence_proxy_async();
+            epi_bar();
+            if (etid == 0) {
+                for (int gq = 0; gq < gh; ++gq)
+                    tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes);
+                bulk_commit();
+                bulk_wait_read();
+            }
+            epi_bar();
+            // second half: from the registers, or (wide rows) straight from TMEM
+            for (int k = 0; k < ngr - gh; ++k) {
+                if (regs) {
+                    if (k < kEpiRegGroups) {
 #pragma unroll
-                        for (int k = 0; k < kEpiRegGroups; ++k) {
-                            if (gh + k < ngr) {
-                                float* dst = stg + row * sstr + k * 16;
+                        for (int kk = 0; kk < kEpiRegGroups; ++kk) {
+                            if (kk == k) {
 #pragma unroll
                                 for (int q = 0; q < 4; ++q)
-                                    *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
-                                        __uint_as_float(keep[k][4 * q + 0]),
-                                        __uint_as_float(keep[k][4 * q + 1]),
-                                        __uint_as_float(keep[k][4 * q + 2]),
-                                        __uint_as_float(keep[k][4 * q + 3]));
+                                    put4(k, q, __uint_as_float(keep[kk][4 * q + 0]),
+                                         __uint_as_float(keep[kk][4 * q + 1]),
+                                         __uint_as_float(keep[kk][4 * q + 2]),
+                                         __uint_as_float(keep[kk][4 * q + 3]));
                             }
                         }
-                    } else {
-                        for (int gq = gh; gq < ngr; ++gq) {
-                            const uint32_t t0 = trow + (uint32_t)(gq * 16);
-                            uint32_t h0[16], c0[16];
-                            tmem_ld16_nw(t0, h0);
-                            tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
-                            tmem_wait_ld();
-                            float* dst = stg + row * sstr + (gq - gh) * 16;
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                *reinterpret_cast<float4*>(dst + 4 * q) = make_float4(
-                                    __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
-                                    __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
-                                    __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
-                                    __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
-                        }
-                        tc_fence_before();
-                        mbar_arrive(&acce_bar);
                     }
+                } else {
+                    const uint32_t t0 = trow + (uint32_t)((gh + k) * 16);
+                    uint32_t h0[16], c0[16];
+                    tmem_ld16_nw(t0, h0);
+                    tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        put4(k, q, __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
+                             __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
+                             __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
+                             __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
                 }
-                epi_bar();
-                const int units = (g1 - g0) * 4;  // 16-byte units per row of this half
-                float* outp = a.ppart + (int64_t)w.pbegin * a.Npad + g0 * 16;
-                for (int e = etid; e < w.rows * units; e += kEpiThreads) {
-                    const int r = e / units, u = e - r * units;
-                    *reinterpret_cast<float4*>(outp + (int64_t)r * a.Npad + 4 * u) =
-                        *reinterpret_cast<const float4*>(stg + r * sstr + 4 * u);
-                }
-                epi_bar();
+            }
+            if (!regs) {
+                tc_fence_before();
+                mbar_arrive(&acce_bar);
+            }
+            fence_proxy_async();
+            epi_bar();
+            if (etid == 0) {
+                for (int k = 0; k < ngr - gh; ++k)
+                    tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin, boxes + k * kEpiBoxBytes);
+                bulk_commit();
             }
             ++jacc;
         }
+        // every store done before the CTA's shared memory goes away
+        if (etid == 0) bulk_wait_all();
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the tile
         const int quad = warp & 3;
@@ -1448,6 +1485,35 @@ void host_m2l_offsets(int16_t out[8][189]);
 
 int m2l_tc_npad(int p) { return tc_geom(p, true).Npad; }
 
+// TMA descriptor of the pair-packed partial rows: rows_cap rows of Npad FP32
+// values, stored by boxes of 128 rows x 16 columns with the 64-byte swizzle.
+cudaError_t m2l_tc_make_part_map(Workspace& ws) {
+    ws.pp_map_ok = 0;
+    if (!ws.pp_part || !ws.tc_bf16) return cudaSuccess;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const int npad = m2l_tc_npad(ws.p);
+    const cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)ws.pp_rows_cap};
+    const cuuint64_t strides[1] = {(cuuint64_t)npad * sizeof(float)};
+    const cuuint32_t box[2] = {16, (cuuint32_t)kTcRows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(ws.pp_map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        2, ws.pp_part, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    ws.pp_map_ok = 1;
+    return cudaSuccess;
+}
+
 size_t m2l_tc_operand_bytes(int p, bool bf16) {
     if (!tc_supported(p, bf16)) return 0;
     TcGeom g = tc_geom(p, bf16);
@@ -1655,6 +1721,7 @@ static bool tc_worklist_layout(int64_t n, int D, Workspace& ws, int64_t& tiles, 
 static TcArgs pair_args(int64_t n, int D, Workspace& ws) {
     TcArgs a = base_args(n, D, ws, 1);
     a.mode = MODE_PAIR;
+    memcpy(&a.part_map, ws.pp_map, sizeof(CUtensorMap));
     PairList L = pair_list(ws);
     a.pairs = L.pairs;
     a.pitems = L.items;
