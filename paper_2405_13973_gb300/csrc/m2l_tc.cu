@@ -328,13 +328,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 
 // TMA tensor store of one box (2D: x = column, y = row) from shared memory,
-// bulk-group completion
+// bulk-group completion, with an L2 eviction-priority hint (a createpolicy
+// value)
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y,
-                                             const void* src) {
+                                             const void* src, uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-            reinterpret_cast<uint64_t>(map)),
-        "r"(x), "r"(y), "r"(smem_addr(src))
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], "
+        "[%3], %4;" ::"l"(reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(smem_addr(src)), "l"(policy)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// bulk global -> shared copy with an L2 eviction-priority hint
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
 __device__ __forceinline__ void bulk_commit() {
@@ -646,6 +666,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
     if (warp == 0) {
         // ---- operator producer
         if (lane == 0) {
+            const uint64_t op_l2 = policy_evict_first();
+            (void)op_l2;
             int g = 0;
             for (int idx = first; idx < count && !*abort_v; idx += stride) {
                 TcWork w;
@@ -662,7 +684,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                     mbar_arrive_expect_tx(&fullB_bar[st], pieces * b_bytes);
                     const unsigned char* src =
                         a.ops + ((size_t)tc_op<MODE>(a, w, j) * a.kchunks + kc) * pieces * b_bytes;
-                    bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
+                    if (MODE == MODE_PAIR && BF16)
+                        // an offset's items run side by side in one wave: once
+                        // read, its operator may leave L2 before the partial rows
+                        bulk_g2s_hint(sB, src, pieces * b_bytes, &fullB_bar[st], op_l2);
+                    else
+                        bulk_g2s(sB, src, pieces * b_bytes, &fullB_bar[st]);
                     issued_par[st] = use & 1;
                 }
             }
@@ -949,6 +976,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
         const int ngr = a.Npad / 16, gh = a.epi_half / 16;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
         const int rsw = (row & 7) >> 1;
+        // the partial rows are read back by the reduction right after this
+        // kernel: keep them in L2 ahead of the operators
+        const uint64_t keep_l2 = policy_evict_last();
         auto put4 = [&](int box, int q, float x, float y, float z, float wv) {
             *reinterpret_cast<float4*>(boxes + box * kEpiBoxBytes + row * 64 + ((q ^ rsw) << 4)) =
                 make_float4(x, y, z, wv);
@@ -1020,7 +1050,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
             epi_bar();
             if (etid == 0) {
                 for (int gq = 0; gq < gh; ++gq)
-                    tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes);
+                    tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes, keep_l2);
                 bulk_commit();
                 bulk_wait_read();
             }
@@ -1063,7 +1093,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
             epi_bar();
             if (etid == 0) {
                 for (int k = 0; k < ngr - gh; ++k)
-                    tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin, boxes + k * kEpiBoxBytes);
+                    tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin, boxes + k * kEpiBoxBytes,
+                                 keep_l2);
                 bulk_commit();
             }
             ++jacc;
