@@ -158,6 +158,31 @@ def test_pair_schedule_equals_tile_schedule(sphere4k, depth, prec):
         assert rel(out[sched], out["tiles"]) < (1e-12 if prec == "fp64" else 2e-6), sched
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-7), ("fp32", 1e-6)])
+def test_rotation_m2l_at_p16_against_the_oracle(sphere4k, precision, tol):
+    # Order 16 (beyond the tensor-core paths): the rotation-based M2L, and
+    # the dense per-pair M2L beside it, against the oracle's direct sum; the
+    # two factorisations of the same operator agree to rounding.
+    pos, q, Eo, _ = sphere4k
+    out = {}
+    for sched in ("rotation", "pairs"):
+        plan = pt.Plan(len(q), p=16, depth=3, precision=precision)
+        plan.set_m2l_schedule(sched)
+        E, _ = plan.forces(dev_pos(pos), dev_vec(q))
+        out[sched] = E.cpu().numpy().T
+        plan.close()
+    assert rel(out["rotation"], Eo) < tol
+    assert rel(out["rotation"], out["pairs"]) < (1e-13 if precision == "fp64" else 1e-6)
+
+
+def test_rotation_schedule_is_refused_on_the_tensor_cores():
+    plan = pt.Plan(100, p=8, precision="bf16x3")
+    with pytest.raises(pt.PenningError) as ei:
+        plan.set_m2l_schedule("rotation")
+    assert ei.value.status == pt.PT_ERR_UNSUPPORTED
+    plan.close()
+
+
 def test_field_of_one_and_two_ions():
     for precision in ("fp64", "fp32", "tf32x3", "bf16x3"):
         plan = pt.Plan(2, p=6, precision=precision)
