@@ -69,7 +69,6 @@ namespace pt {
 
 namespace {
 
-constexpr int kTcThreads = 448;
 constexpr int kMaxStages = 4;
 constexpr int kTcRows = 128;
 constexpr int kMaxSplits = 8;    // M2M: CTAs per tile (one per child octant at most)
@@ -364,20 +363,20 @@ __device__ __forceinline__ void bulk_commit() {
 __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
-// this thread's committed bulk stores are complete
-__device__ __forceinline__ void bulk_wait_all() {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-// barrier 1 over the 128 epilogue threads; the variant returns whether any
+// barrier 1 over the N epilogue threads; the variant returns whether any
 // of them passed true
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void epi_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+template <int N>
 __device__ __forceinline__ bool epi_bar_any(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
         " selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(N)
         : "memory");
     return r != 0;
 }
@@ -394,6 +393,19 @@ __device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) 
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+// tcgen05.st of 16 columns; tmem_wait_st before the columns are read back
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 
 enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2, MODE_PAIR = 3 };
 
@@ -405,6 +417,7 @@ struct TcArgs {
     int D, P, ld, kchunks, Npad, tmem_cols, acc_cols, splits, stages, raw;
     int bf16, pieces, a_bytes, b_bytes;  // operand format and per-piece tile bytes
     int epi_half, epi_stride;            // BF16 pair epilogue staging (TcGeom)
+    int epi_scratch;                     // the second half fits the free TMEM columns
     uint32_t idesc;
     const LevelInfo* linfo;
     const uint32_t* code;
@@ -499,15 +512,27 @@ __device__ __forceinline__ void stage_linfo(const LevelInfo* g, LevelInfo* s) {
     for (int i = threadIdx.x; i < (int)(sizeof(LevelInfo) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
 }
 
-// Warp roles: warp 0 = operator producer (bulk copies), warp 1 = MMA issuer,
-// warps 2..9 = A producers (gather + split), warps 10..13 = epilogue (one
-// TMEM lane quarter each).  The epilogue has warps of its own so that the
-// producers run on into the next work item while the accumulators drain.
-constexpr int kProdWarps = 8;
-constexpr int kWarpA0 = 2;
-constexpr int kWarpEpi0 = kWarpA0 + kProdWarps;
-constexpr int kEpiThreads = 128;
-constexpr int kEpiRegGroups = 5;  // pair epilogue: column groups of 16 kept in registers
+// Warp roles: an operator producer (bulk copies), an MMA issuer, A producers
+// (gather + split) and epilogue warps, which have warps of their own so that
+// the producers run on into the next work item while the accumulators drain.
+// Default: warp 0 = operator producer, warp 1 = MMA issuer, warps 2..9 = A
+// producers, warps 10..13 = epilogue (one TMEM lane quarter each).  The BF16
+// pair-packed kernel, whose items are short, drains its accumulators with
+// two warps per lane quarter: warps 0..7 = epilogue, warp 8 = operator
+// producer, warp 9 = MMA issuer, warps 10..11 = A producers (it copies
+// pre-split rows only); 384 threads leave 168 registers a thread, room for
+// three column groups of both accumulators per TMEM wait.  Warp 0
+// allocates and frees TMEM in either layout.
+template <int MODE, int BF16>
+struct TcLayout {
+    static constexpr bool kWide = MODE == 3 && BF16;  // MODE_PAIR
+    static constexpr int kThreads = kWide ? 384 : 448;
+    static constexpr int kWarpOp = kWide ? 8 : 0;
+    static constexpr int kWarpMma = kWide ? 9 : 1;
+    static constexpr int kWarpA0 = kWide ? 10 : 2;
+    static constexpr int kAWarps = kWide ? 2 : 8;
+    static constexpr int kEpiWarps = kWide ? 8 : 4;
+};
 constexpr int kEpiBoxBytes = kTcRows * 16 * 4;  // one TMA box: 128 rows x 16 FP32
 
 // One unit of work for a CTA: a run [begin, end) of the term list of one tile
@@ -605,10 +630,85 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
     }
 }
 
+// Pair epilogue helpers.  A row's 16 FP32 values of one column group go to
+// its 64-byte line of a TMA box, 16-byte unit q at q ^ rsw (the 64-byte
+// swizzle, rsw = (row & 7) >> 1).
+__device__ __forceinline__ void epi_put16(unsigned char* b, int rsw, const uint32_t (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(b + ((q ^ rsw) << 4)) =
+            make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+// TMEM column of the k-th parked group of 16 (pair_epi_scratch_fits): the
+// free columns after the hh accumulator, then after the cross one, then
+// after both
+__device__ __forceinline__ uint32_t epi_scratch_col(int k, int Npad, int acc_cols) {
+    const int W = acc_cols - Npad;
+    int c = k * 16;
+    if (c < W) return (uint32_t)(Npad + c);
+    c -= W;
+    if (c < W) return (uint32_t)(acc_cols + Npad + c);
+    return (uint32_t)(2 * acc_cols + c - W);
+}
+template <bool PARK>
+__device__ __forceinline__ void epi_sink(int k, const uint32_t (&v)[16], unsigned char* brow,
+                                         int rsw, uint32_t trow, int Npad, int acc_cols) {
+    if (PARK)
+        tmem_st16(trow + epi_scratch_col(k, Npad, acc_cols), v);
+    else
+        epi_put16(brow + k * kEpiBoxBytes, rsw, v);
+}
+// column groups [g0, g1) of the two accumulators (hh at trow, cross at trow +
+// cross), summed, into boxes 0.. (kEpiBoxBytes apart from brow) or, PARK,
+// into the free TMEM columns (k-th group at epi_scratch_col(k)); two groups
+// per TMEM wait
+template <bool PARK>
+__device__ __forceinline__ void epi_drain(uint32_t trow, uint32_t cross, int g0, int g1,
+                                          unsigned char* brow, int rsw, int Npad, int acc_cols) {
+#pragma unroll 1
+    for (int gq = g0; gq < g1; gq += 2) {
+        uint32_t h0[16], c0[16], h1[16], c1[16];
+        const bool two = gq + 1 < g1;  // uniform
+        tmem_ld16_nw(trow + (uint32_t)(gq * 16), h0);
+        tmem_ld16_nw(trow + (uint32_t)(gq * 16) + cross, c0);
+        if (two) {
+            tmem_ld16_nw(trow + (uint32_t)(gq * 16 + 16), h1);
+            tmem_ld16_nw(trow + (uint32_t)(gq * 16 + 16) + cross, c1);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            h0[j] = __float_as_uint(__uint_as_float(h0[j]) + __uint_as_float(c0[j]));
+        epi_sink<PARK>(gq - g0, h0, brow, rsw, trow, Npad, acc_cols);
+        if (two) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                h1[j] = __float_as_uint(__uint_as_float(h1[j]) + __uint_as_float(c1[j]));
+            epi_sink<PARK>(gq - g0 + 1, h1, brow, rsw, trow, Npad, acc_cols);
+        }
+    }
+}
+// n parked groups from the free TMEM columns into boxes 0.., two per wait
+__device__ __forceinline__ void epi_unpark(uint32_t trow, int n, unsigned char* brow, int rsw,
+                                           int Npad, int acc_cols) {
+#pragma unroll 1
+    for (int k = 0; k < n; k += 2) {
+        uint32_t v0[16], v1[16];
+        const bool two = k + 1 < n;  // uniform
+        tmem_ld16_nw(trow + epi_scratch_col(k, Npad, acc_cols), v0);
+        if (two) tmem_ld16_nw(trow + epi_scratch_col(k + 1, Npad, acc_cols), v1);
+        tmem_wait_ld();
+        epi_put16(brow + k * kEpiBoxBytes, rsw, v0);
+        if (two) epi_put16(brow + (k + 1) * kEpiBoxBytes, rsw, v1);
+    }
+}
+
 // One instantiation per mode and operand format (MODE == MODE, BF16 == BF16):
 // each kernel carries only its own paths.
 template <int MODE, int BF16>
-__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
+    k_m2l_tc(const __grid_constant__ TcArgs a) {
+    using L = TcLayout<MODE, BF16>;
     extern __shared__ unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
         empty_bar[kMaxStages], accf_bar, acce_bar, drain_bar;
@@ -638,10 +738,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
     if (tid == 0) {
         abort_sh = 0;
         mbar_init(&accf_bar, 1);
-        mbar_init(&acce_bar, kEpiThreads);
+        mbar_init(&acce_bar, L::kEpiWarps * 32);
         mbar_init(&drain_bar, 1);
         for (int s = 0; s < NS; ++s) {
-            mbar_init(&fullA_bar[s], kProdWarps * 32);
+            mbar_init(&fullA_bar[s], L::kAWarps * 32);
             mbar_init(&fullB_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -663,7 +763,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
 #pragma unroll
     for (int s = 0; s < kMaxStages; ++s) issued_par[s] = -1;
 
-    if (warp == 0) {
+    if (warp == L::kWarpOp) {
         // ---- operator producer
         if (lane == 0) {
             const uint64_t op_l2 = policy_evict_first();
@@ -694,7 +794,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == L::kWarpMma) {
         // ---- MMA issuer
         if (lane == 0) {
             int g = 0, jacc = 0;
@@ -757,14 +857,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                 ++jacc;
             }
         }
-    } else if (warp < kWarpEpi0) {
+    } else if (warp >= L::kWarpA0 && warp < L::kWarpA0 + L::kAWarps) {
         if ((MODE == MODE_M2L || MODE == MODE_PAIR) && BF16) {
             // ---- A producers, BF16x3 M2L: the sources' M rows are already
             // split into bf16 pieces (k_split_m), so each thread copies its
             // 16-byte unit (8 values) of each piece for two rows by cp.async
             // straight into the stage's swizzled layout, and the stage barrier
             // counts its arrival once those copies land; no conversion here.
-            const int ta = tid - kWarpA0 * 32;
+            // Thread ta owns unit c = ta % 4 of rows ta / 4 + RS j.
+            constexpr int RS = L::kAWarps * 8;             // rows per pass
+            constexpr int NJ = (kTcRows + RS - 1) / RS;    // passes
+            const int ta = tid - L::kWarpA0 * 32;
             const int r0 = ta >> 2, c = ta & 3;
             int g = 0;
             for (int idx = first; idx < count && !*abort_v; idx += stride) {
@@ -772,13 +875,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                 if (!tc_work<MODE>(a, li, idx, w)) continue;
                 const int n_it = (w.end - w.begin) * a.kchunks;
                 const int l = w.level, lim = 1 << l;
-                int tix[2], tiy[2], tiz[2], pg[2];
+                int tix[NJ], tiy[NJ], tiz[NJ], pg[NJ];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < NJ; ++j) {
                     tix[j] = tiy[j] = tiz[j] = 0;
                     pg[j] = -1;
-                    if (MODE == MODE_M2L && r0 + 64 * j < w.rows)
-                        demorton3(a.code[w.base + r0 + 64 * j], tix[j], tiy[j], tiz[j]);
+                    if (MODE == MODE_M2L && r0 + RS * j < w.rows)
+                        demorton3(a.code[w.base + r0 + RS * j], tix[j], tiy[j], tiz[j]);
                 }
                 for (int it = 0; it < n_it; ++it) {
                     const int gg = g + it;
@@ -786,16 +889,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                     const int kc = it % a.kchunks;
                     if (MODE == MODE_PAIR && it == 0) {
 #pragma unroll
-                        for (int j = 0; j < 2; ++j)
-                            pg[j] = r0 + 64 * j < w.rows ? a.pairs[w.pbegin + r0 + 64 * j].src : -1;
+                        for (int j = 0; j < NJ; ++j)
+                            pg[j] = r0 + RS * j < w.rows ? a.pairs[w.pbegin + r0 + RS * j].src : -1;
                     } else if (MODE == MODE_M2L && kc == 0) {
                         const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
                         const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
 #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
+                        for (int j = 0; j < NJ; ++j) {
                             int gs = -1;
                             const int sx = tix[j] - ox, sy = tiy[j] - oy, sz = tiz[j] - oz;
-                            if (r0 + 64 * j < w.rows &&
+                            if (r0 + RS * j < w.rows &&
                                 tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
                                 sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
                                 gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
@@ -811,8 +914,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
                     }
                     unsigned char* sA = base + st * stage_bytes;
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int r = r0 + 64 * j;
+                    for (int j = 0; j < NJ; ++j) {
+                        const int r = r0 + RS * j;
+                        if (r >= kTcRows) break;
                         const int off = (r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r & 7) >> 1)) << 4);
                         const int gs = pg[j];
 #pragma unroll
@@ -831,7 +935,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
         // ---- A producers: each thread owns rows r0 + 32 j (j < 4) and 16-byte unit c.
         // Its raw FP32 values travel by cp.async into its own slots of a ring
         // of a.raw chunks, a.raw - 1 iterations ahead of their split.
-        const int ta = tid - kWarpA0 * 32;
+        static_assert(L::kWide || L::kAWarps == 8, "the FP32 row ring assumes 256 A threads");
+        const int ta = tid - L::kWarpA0 * 32;
         const int r0 = ta >> 3, c = ta & 7;
         const float* src_base = MODE == MODE_L2L ? a.L : a.M;
         unsigned char* raw = base + NS * stage_bytes;  // [slot][j][256 threads][16 B]
@@ -959,30 +1064,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
         asm volatile("cp.async.wait_all;" ::: "memory");
         }
     } else if (MODE == MODE_PAIR && BF16) {
-        // ---- epilogue of the BF16 pair-packed items: the accumulators (row =
-        // TMEM lane = pair) go to shared memory in boxes of 128 rows x 16
-        // columns (the TMA 64-byte swizzle: 16-byte unit u of row r at
-        // u ^ ((r & 7) >> 1), bank-conflict free), the first half of the
-        // column groups directly, the rest through registers, so that the
-        // accumulators are released after the two drains; one thread then
-        // stores the boxes with TMA (the item's rows are one 128-row block of
-        // the partial array) while the MMAs of the next item run.  The four
-        // warps decide to stop together (barrier reduction), so their
-        // barriers stay matched.
-        const int quad = warp & 3;
+        // ---- epilogue of the BF16 pair-packed items, warps 0..7: warp w
+        // reads TMEM lanes 32 (w % 4) .. + 31 (row = lane = pair), warps 0..3
+        // the first half of the column groups, warps 4..7 the rest.  The
+        // first half goes to shared memory in boxes of 128 rows x 16 columns
+        // (the TMA 64-byte swizzle: 16-byte unit u of row r at
+        // u ^ ((r & 7) >> 1), bank-conflict free), the second half to
+        // registers, two or three TMEM waits per warp, and the accumulators are
+        // released; one thread then stores the boxes with TMA (the item's
+        // rows are one 128-row block of the partial array), the second half
+        // follows through the same boxes, while the MMAs of the next item
+        // run.  The warps decide to stop together (barrier reduction), so
+        // their barriers stay matched.
+        constexpr int NE = L::kEpiWarps * 32;
+        const int quad = warp & 3, second = warp >> 2;
         const int row = quad * 32 + lane;
-        const int etid = (warp - kWarpEpi0) * 32 + lane;
+        const int etid = warp * 32 + lane;
         unsigned char* boxes = base + NS * stage_bytes;  // kEpiBoxBytes apart
         const int ngr = a.Npad / 16, gh = a.epi_half / 16;
         const uint32_t trow = tmem + ((uint32_t)(quad * 32) << 16);
+        const uint32_t cross = (uint32_t)a.acc_cols;
         const int rsw = (row & 7) >> 1;
         // the partial rows are read back by the reduction right after this
         // kernel: keep them in L2 ahead of the operators
         const uint64_t keep_l2 = policy_evict_last();
-        auto put4 = [&](int box, int q, float x, float y, float z, float wv) {
-            *reinterpret_cast<float4*>(boxes + box * kEpiBoxBytes + row * 64 + ((q ^ rsw) << 4)) =
-                make_float4(x, y, z, wv);
-        };
+        unsigned char* brow = boxes + row * 64;
         int jacc = 0;
         for (int idx = first; idx < count; idx += stride) {
             TcWork w;
@@ -992,115 +1098,66 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
             ok = __shfl_sync(0xffffffffu, ok, 0);
             // the boxes of the previous item have been read by its stores
             if (etid == 0) bulk_wait_read();
-            if (epi_bar_any(ok == 0)) {
+            if (epi_bar_any<NE>(ok == 0)) {
                 *abort_v = 1;
                 break;
             }
             tc_fence_after();
-            uint32_t keep[kEpiRegGroups][16];
-            const bool regs = ngr - gh <= kEpiRegGroups;  // uniform
-            for (int gq = 0; gq < gh; gq += 2) {
-                const bool two = gq + 1 < gh;  // uniform
-                const uint32_t t0 = trow + (uint32_t)(gq * 16);
-                uint32_t h0[16], c0[16], h1[16], c1[16];
-                tmem_ld16_nw(t0, h0);
-                tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
-                if (two) {
-                    tmem_ld16_nw(t0 + 16u, h1);
-                    tmem_ld16_nw(t0 + 16u + (uint32_t)a.acc_cols, c1);
+            // the two warp sets take separate branches for the whole item;
+            // their barriers match
+            if (!second) {
+                epi_drain<false>(trow, cross, 0, gh, brow, rsw, a.Npad, a.acc_cols);
+                tc_fence_before();
+                mbar_arrive(&acce_bar);  // this half of the accumulators read
+                // first half out by TMA
+                fence_proxy_async();
+                epi_bar<NE>();
+                if (etid == 0) {
+                    for (int gq = 0; gq < gh; ++gq)
+                        tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes,
+                                     keep_l2);
+                    bulk_commit();
+                    bulk_wait_read();
                 }
-                tmem_wait_ld();
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    put4(gq, q, __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
-                         __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
-                         __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
-                         __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
-                if (two) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        put4(gq + 1, q,
-                             __uint_as_float(h1[4 * q + 0]) + __uint_as_float(c1[4 * q + 0]),
-                             __uint_as_float(h1[4 * q + 1]) + __uint_as_float(c1[4 * q + 1]),
-                             __uint_as_float(h1[4 * q + 2]) + __uint_as_float(c1[4 * q + 2]),
-                             __uint_as_float(h1[4 * q + 3]) + __uint_as_float(c1[4 * q + 3]));
+                epi_bar<NE>();
+                // (the other warps refill the boxes)
+                epi_bar<NE>();
+                if (etid == 0) {
+                    for (int k = 0; k < ngr - gh; ++k)
+                        tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin,
+                                     boxes + k * kEpiBoxBytes, keep_l2);
+                    bulk_commit();
                 }
-            }
-            if (regs) {
-#pragma unroll
-                for (int k = 0; k < kEpiRegGroups; ++k) {
-                    if (gh + k < ngr) {  // uniform
-                        const uint32_t t0 = trow + (uint32_t)((gh + k) * 16);
-                        uint32_t c0[16];
-                        tmem_ld16_nw(t0, keep[k]);
-                        tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            keep[k][j] = __float_as_uint(__uint_as_float(keep[k][j]) +
-                                                         __uint_as_float(c0[j]));
-                    }
-                }
-                // accumulators read: the issuer may start the next item
+            } else if (a.epi_scratch) {  // uniform
+                // second half summed into the free TMEM columns, so that the
+                // accumulators are released after two waits
+                epi_drain<true>(trow, cross, gh, ngr, brow, rsw, a.Npad, a.acc_cols);
+                tmem_wait_st();
+                tc_fence_before();
+                mbar_arrive(&acce_bar);  // the other half read: the issuer may go on
+                epi_bar<NE>();
+                // (the first half is stored from the boxes)
+                epi_bar<NE>();
+                tc_fence_after();
+                epi_unpark(trow, ngr - gh, brow, rsw, a.Npad, a.acc_cols);
+                fence_proxy_async();
+                epi_bar<NE>();
+            } else {
+                // wide rows: the second half straight from TMEM once the
+                // first half's boxes are free (the accumulators held longer)
+                epi_bar<NE>();
+                epi_bar<NE>();
+                epi_drain<false>(trow, cross, gh, ngr, brow, rsw, a.Npad, a.acc_cols);
                 tc_fence_before();
                 mbar_arrive(&acce_bar);
-            }
-            // first half out by TMA
-            fence_proxy_async();
-            epi_bar();
-            if (etid == 0) {
-                for (int gq = 0; gq < gh; ++gq)
-                    tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes, keep_l2);
-                bulk_commit();
-                bulk_wait_read();
-            }
-            epi_bar();
-            // second half: from the registers, or (wide rows) straight from TMEM
-            for (int k = 0; k < ngr - gh; ++k) {
-                if (regs) {
-                    if (k < kEpiRegGroups) {
-#pragma unroll
-                        for (int kk = 0; kk < kEpiRegGroups; ++kk) {
-                            if (kk == k) {
-#pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    put4(k, q, __uint_as_float(keep[kk][4 * q + 0]),
-                                         __uint_as_float(keep[kk][4 * q + 1]),
-                                         __uint_as_float(keep[kk][4 * q + 2]),
-                                         __uint_as_float(keep[kk][4 * q + 3]));
-                            }
-                        }
-                    }
-                } else {
-                    const uint32_t t0 = trow + (uint32_t)((gh + k) * 16);
-                    uint32_t h0[16], c0[16];
-                    tmem_ld16_nw(t0, h0);
-                    tmem_ld16_nw(t0 + (uint32_t)a.acc_cols, c0);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        put4(k, q, __uint_as_float(h0[4 * q + 0]) + __uint_as_float(c0[4 * q + 0]),
-                             __uint_as_float(h0[4 * q + 1]) + __uint_as_float(c0[4 * q + 1]),
-                             __uint_as_float(h0[4 * q + 2]) + __uint_as_float(c0[4 * q + 2]),
-                             __uint_as_float(h0[4 * q + 3]) + __uint_as_float(c0[4 * q + 3]));
-                }
-            }
-            if (!regs) {
-                tc_fence_before();
-                mbar_arrive(&acce_bar);
-            }
-            fence_proxy_async();
-            epi_bar();
-            if (etid == 0) {
-                for (int k = 0; k < ngr - gh; ++k)
-                    tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin, boxes + k * kEpiBoxBytes,
-                                 keep_l2);
-                bulk_commit();
+                fence_proxy_async();
+                epi_bar<NE>();
             }
             ++jacc;
         }
-        // every store done before the CTA's shared memory goes away
-        if (etid == 0) bulk_wait_all();
+        // the boxes read before the CTA's shared memory goes away (the
+        // stores themselves complete with the grid)
+        if (etid == 0) bulk_wait_read();
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the tile
         const int quad = warp & 3;
@@ -1232,11 +1289,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const __grid_constant_
     if (*abort_v) {
         // drain (bounded): the issuer's MMAs in flight and every bulk copy
         // still owed to a stage
-        if (tid == 32) {
+        if (tid == L::kWarpMma * 32) {
             mma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0);
         }
-        if (tid == 0) {
+        if (tid == L::kWarpOp * 32) {
             for (int s = 0; s < NS; ++s)
                 if (issued_par[s] >= 0) mbar_wait(&fullB_bar[s], (uint32_t)issued_par[s]);
             atomicOr(a.err, ERR_TIMEOUT);
@@ -1622,8 +1679,8 @@ void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T
 
 template <int MODE>
 static cudaError_t tc_launch_mode(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
-    if (a.bf16) k_m2l_tc<MODE, 1><<<grid, kTcThreads, smem, s>>>(a);
-    else k_m2l_tc<MODE, 0><<<grid, kTcThreads, smem, s>>>(a);
+    if (a.bf16) k_m2l_tc<MODE, 1><<<grid, TcLayout<MODE, 1>::kThreads, smem, s>>>(a);
+    else k_m2l_tc<MODE, 0><<<grid, TcLayout<MODE, 0>::kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
@@ -1749,9 +1806,22 @@ static bool tc_worklist_layout(int64_t n, int D, Workspace& ws, int64_t& tiles, 
 }
 
 
+// Free TMEM columns of the pair kernel (all 512 allocated): after each
+// accumulator's Npad columns up to acc_cols, then after both accumulators.
+// The BF16 epilogue parks the summed second half of the columns there.
+static bool pair_epi_scratch_fits(const TcArgs& a) {
+    const int need = a.Npad - a.epi_half;
+    const int free = 2 * (a.acc_cols - a.Npad) + (512 - 2 * a.acc_cols);
+    return need <= free;
+}
+
 static TcArgs pair_args(int64_t n, int D, Workspace& ws) {
     TcArgs a = base_args(n, D, ws, 1);
     a.mode = MODE_PAIR;
+    if (a.bf16) {
+        a.tmem_cols = 512;
+        a.epi_scratch = pair_epi_scratch_fits(a) ? 1 : 0;
+    }
     memcpy(&a.part_map, ws.pp_map, sizeof(CUtensorMap));
     PairList L = pair_list(ws);
     a.pairs = L.pairs;
