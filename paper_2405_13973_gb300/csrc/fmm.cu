@@ -643,7 +643,8 @@ __device__ __forceinline__ void l2p_derive(int p, const T* Lr, const HarmTables<
 
 // column m of the potential and gradient at (x, y, z) from derived
 // expansions D4; every lane of the half-warp calls it (the prefix product
-// shuffles), lanes m > p return zeros
+// shuffles), lanes m > p return zeros.  At p = 16 the last column (m = 16,
+// degree 16 only) goes to lane 15 beside its own.
 template <typename T>
 __device__ __forceinline__ void l2p_columns(int p, int m, unsigned hw_mask, T x, T y, T z,
                                             const HarmTables<T>& t, const T (*D4)[kPmax], T& ph,
@@ -690,6 +691,15 @@ __device__ __forceinline__ void l2p_columns(int p, int m, unsigned hw_mask, T x,
             ay += D4[2][k + 1] * yi;
             az += D4[3][k + 1] * yi;
         }
+    }
+    if (p == 16 && m == 15) {
+        // Y_16^16 = c_16 (x + i y) Y_15^15, the one term of column 16
+        const T gr = (dre * x - dim * y) * t.c[16], gi = (dre * y + dim * x) * t.c[16];
+        const int k = re_idx(16, 16);
+        ph += D4[0][k] * gr + D4[0][k + 1] * gi;
+        ax += D4[1][k] * gr + D4[1][k + 1] * gi;
+        ay += D4[2][k] * gr + D4[2][k + 1] * gi;
+        az += D4[3][k] * gr + D4[3][k + 1] * gi;
     }
 }
 

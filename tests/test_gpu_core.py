@@ -175,6 +175,24 @@ def test_rotation_m2l_at_p16_against_the_oracle(sphere4k, precision, tol):
     assert rel(out["rotation"], out["pairs"]) < (1e-13 if precision == "fp64" else 1e-6)
 
 
+def test_fp64_error_keeps_falling_through_order_16_on_a_planar_crystal():
+    # In a planar crystal the ions sit where the sectoral harmonics Y_n^n are
+    # largest, so the last column of an order-16 expansion (m = 16, degree 16
+    # only) carries a large share of its degree-16 terms: were it dropped
+    # anywhere on the path, the error would stall between p = 15 and 16.
+    n = 4000
+    pos = W.spheroid(n, 100e-6, 0.1e-6, seed=31)
+    q = W.charges(n)
+    Eo, _ = oracle.coulomb_direct(pos, q, want_phi=False)
+    errs = []
+    for p in (14, 15, 16):
+        plan = pt.Plan(n, p=p, depth=3, precision="fp64")
+        E, _ = plan.forces(dev_pos(pos), dev_vec(q), want_phi=False)
+        errs.append(rel(E.cpu().numpy().T, Eo))
+        plan.close()
+    assert errs[1] < 0.9 * errs[0] and errs[2] < 0.9 * errs[1], errs
+
+
 def test_rotation_schedule_is_refused_on_the_tensor_cores():
     plan = pt.Plan(100, p=8, precision="bf16x3")
     with pytest.raises(pt.PenningError) as ei:
