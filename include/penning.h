@@ -485,7 +485,11 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out);
  *   stream : CUDA stream (cudaStream_t) or NULL.
  * Every step of the whole ensemble is one launch of one CUDA graph holding
  * each member's step as a parallel branch (captured once, again when a
- * member's depth, buffers or parameters change).  A member's result equals
+ * member's depth, buffers or parameters change).  The M2L launches of the
+ * members that use the BF16x3 pair-packed schedule (Eq. FMM_local) are
+ * replaced in that graph by one launch over all of their work items, which
+ * waits for every such member's multipoles and precedes every member's
+ * reduction (see pt_ensemble_set_joined_m2l).  A member's result equals
  * the same plan stepped alone by pt_step, bit for bit.  Asynchronous like
  * pt_step_async: automatic-depth plans keep the depth chosen at their first
  * step; device errors are latched and returned by pt_ensemble_sync.
@@ -494,8 +498,20 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
                      const pt_laser* lasers, const double* dt, int64_t n_steps, void* stream);
 
 /* pt_ensemble_sync -- waits for the stream and returns the first member's
- * latched device error (PT_ERR_NONFINITE, PT_ERR_TIMEOUT, ...) or PT_OK. */
+ * latched device error (PT_ERR_NONFINITE, PT_ERR_TIMEOUT, ...) or PT_OK.
+ * A timeout of the joined M2L launch is latched by the first joined member. */
 int pt_ensemble_sync(pt_ensemble ens, void* stream);
+
+/* pt_ensemble_set_joined_m2l -- on != 0 (default): the members' BF16x3
+ * pair-packed M2L launches run as one launch (pt_ensemble_step); 0: each
+ * member launches its own.  Takes effect at the next step (re-capture).
+ * Errors: PT_ERR_ARG (NULL). */
+int pt_ensemble_set_joined_m2l(pt_ensemble ens, int on);
+
+/* pt_ensemble_joined_m2l -- *members receives how many members the last
+ * captured graph's joined M2L launch covers (0: none joined; fewer than two
+ * eligible members are never joined).  Errors: PT_ERR_ARG (NULL). */
+int pt_ensemble_joined_m2l(pt_ensemble ens, int* members);
 
 /* pt_ensemble_destroy -- frees the ensemble (not its plans). */
 int pt_ensemble_destroy(pt_ensemble ens);

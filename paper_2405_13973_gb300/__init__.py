@@ -142,6 +142,8 @@ def load(build_if_missing: bool = True):
         L.pt_ensemble_step.argtypes = [_VP, ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                        ctypes.POINTER(pt_laser), ctypes.POINTER(_D), _I64, _VP]
         L.pt_ensemble_sync.argtypes = [_VP, _VP]
+        L.pt_ensemble_set_joined_m2l.argtypes = [_VP, ctypes.c_int]
+        L.pt_ensemble_joined_m2l.argtypes = [_VP, ctypes.POINTER(ctypes.c_int)]
         L.pt_ensemble_destroy.argtypes = [_VP]
         _lib = L
         return L
@@ -481,10 +483,11 @@ def plan_footprint(n_max: int, p: int, leaf_max: int = 32, depth: int = -1,
 
 class Ensemble:
     """Independent crystals advanced together: every step of all members is
-    one launch of one CUDA graph (members as parallel branches).  The plans
-    stay the caller's; a member's result equals its plan stepped alone."""
+    one launch of one CUDA graph (members as parallel branches; the BF16x3
+    pair-packed members' M2L as one joined launch).  The plans stay the
+    caller's; a member's result equals its plan stepped alone."""
 
-    def __init__(self, plans, share_sms: bool = False):
+    def __init__(self, plans, share_sms: bool = False, joined_m2l: bool = True):
         """share_sms: each member's persistent M2L kernel takes one CTA per
         256 ions (at least 2) instead of one per SM, so that the members' M2L
         kernels run side by side (results do not depend on it).  Measured on
@@ -500,6 +503,20 @@ class Ensemble:
         _check(load(False).pt_ensemble_create(len(self.plans), arr, ctypes.byref(h)),
                "pt_ensemble_create")
         self._h = h
+        if not joined_m2l:
+            self.set_joined_m2l(False)
+
+    def set_joined_m2l(self, on: bool):
+        """One M2L launch for all BF16x3 pair-packed members (default) or one
+        per member; takes effect at the next step."""
+        _check(load(False).pt_ensemble_set_joined_m2l(self._h, 1 if on else 0),
+               "pt_ensemble_set_joined_m2l")
+
+    def joined_m2l(self) -> int:
+        """Members covered by the joined M2L launch of the current graph."""
+        k = ctypes.c_int()
+        _check(load(False).pt_ensemble_joined_m2l(self._h, ctypes.byref(k)), "pt_ensemble_joined_m2l")
+        return k.value
 
     def step(self, states, traps, lasers, dts, n_steps: int, stream=None):
         """Enqueue n_steps steps of every member (asynchronous; see sync)."""

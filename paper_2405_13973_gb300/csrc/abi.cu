@@ -428,6 +428,7 @@ static int ensure_pairs(fmm_plan_s* pl, int64_t n, const double* x, const double
         cudaError_t e = launch_bbox(x, y, z, n, ws, s);
         if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, ws, s);
         if (e == cudaSuccess) e = launch_m2l_pairs_worklist(n, D, ws, s);
+        if (e == cudaSuccess) e = launch_m2l_pairs_hdr_copy(D, ws, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return status_from(e);
         int r = check_err(pl, s);  // an overflow of this count is not an error
@@ -670,7 +671,9 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
 
 // Independent crystals stepped together: one CUDA graph holds every member's
 // time step as a parallel branch, so one graph launch advances the whole
-// ensemble by one step and the members' kernels share the GPU.
+// ensemble by one step and the members' kernels share the GPU.  The members'
+// BF16 pair-packed M2L launches are joined into one launch over all their
+// work items (m2l_join_pair_launches), unless switched off.
 struct pt_ensemble_s {
     int device = 0;
     std::vector<fmm_plan_s*> plans;      // not owned
@@ -680,6 +683,10 @@ struct pt_ensemble_s {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<GraphKey> keys;
+    bool join_m2l = true;
+    int joined = 0;                      // members in the joined M2L launch
+    void* d_members = nullptr;           // joined launch: member records
+    int* d_prefix = nullptr;             // and their first items
 };
 
 namespace {
@@ -693,6 +700,8 @@ void free_ensemble(pt_ensemble_s* e) {
         if (j) cudaEventDestroy(j);
     if (e->fork) cudaEventDestroy(e->fork);
     if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->d_members) cudaFree(e->d_members);
+    if (e->d_prefix) cudaFree(e->d_prefix);
     delete e;
 }
 }  // namespace
@@ -1142,6 +1151,8 @@ int pt_ensemble_create(int n_members, const fmm_plan* plans, pt_ensemble* out) {
     for (int b = 0; ok && b < n_members; ++b)
         ok = cudaStreamCreateWithPriority(&e->br[b], cudaStreamNonBlocking, prio_high()) == cudaSuccess &&
              cudaEventCreateWithFlags(&e->join[b], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&e->d_members, m2l_join_member_bytes() * (size_t)n_members) == cudaSuccess &&
+         cudaMalloc(&e->d_prefix, sizeof(int) * ((size_t)n_members + 1)) == cudaSuccess;
     if (!ok) {
         free_ensemble(e);
         return PT_ERR_CUDA;
@@ -1214,6 +1225,13 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
                 if (g) cudaGraphDestroy(g);
                 return status_from(e2 != cudaSuccess ? e2 : e);
             }
+            ens->joined = 0;
+            if (ens->join_m2l &&
+                (e = m2l_join_pair_launches(g, ens->d_members, ens->d_prefix, nm, &ens->joined)) !=
+                    cudaSuccess) {
+                cudaGraphDestroy(g);
+                return status_from(e);
+            }
             e = cudaGraphInstantiate(&ens->graph, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) {
@@ -1235,6 +1253,21 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
         states[b].t = anchored_end(ens->plans[b], step0[b] + n_steps);
         states[b].step = step0[b] + n_steps;
     }
+    return PT_OK;
+}
+
+int pt_ensemble_set_joined_m2l(pt_ensemble ens, int on) {
+    if (!ens) return PT_ERR_ARG;
+    if (ens->join_m2l != (on != 0)) {
+        ens->join_m2l = on != 0;
+        ens->keys.clear();  // re-capture at the next step
+    }
+    return PT_OK;
+}
+
+int pt_ensemble_joined_m2l(pt_ensemble ens, int* members) {
+    if (!ens || !members) return PT_ERR_ARG;
+    *members = ens->joined;
     return PT_OK;
 }
 

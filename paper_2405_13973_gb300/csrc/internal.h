@@ -179,6 +179,10 @@ size_t m2l_pp_work_bytes(const Workspace& ws);
 size_t m2l_pp_part_bytes(const Workspace& ws);
 // the work list of the current tree (reads the tree only)
 cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
+// the work list's header (pair count, overflow flag) to pinned host memory,
+// for the host's pool check at the next call; queued after the consumers of
+// the work list are released
+cudaError_t launch_m2l_pairs_hdr_copy(int D, Workspace& ws, cudaStream_t s);
 // L of every cell of levels 2..D = the sum of its pairs' partial rows
 // (`width` columns)
 cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s);
@@ -196,6 +200,13 @@ int m2l_tc_npad(int p);
 // (re)builds ws.pp_map for the current pp_part / pp_rows_cap (BF16 tensor-core
 // plans; others leave it unused)
 cudaError_t m2l_tc_make_part_map(Workspace& ws);
+// ensembles: replaces the BF16 pair-packed M2L launches of a captured graph
+// by one launch over all of them (d_members: room for cap member records of
+// m2l_join_member_bytes() each; d_prefix: cap + 1 ints); *joined = members
+// joined (0 when fewer than two were found)
+size_t m2l_join_member_bytes();
+cudaError_t m2l_join_pair_launches(cudaGraph_t g, void* d_members, int* d_prefix, int cap,
+                                   int* joined);
 cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s);
 // partial slabs of the M2L work items (a pool of 16 KB per ion, 16 MB to 8 GB)
 int64_t m2l_tc_slab_cap(int ld, int64_t tiles_cap, int64_t n_max);

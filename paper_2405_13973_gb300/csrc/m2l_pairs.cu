@@ -281,22 +281,23 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
         const int t = (int)(e / w4), u = (int)(e - (int64_t)t * w4);
         const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        int s = s0;
-        for (; s + 8 <= s1; s += 8) {
-            int rw[8];
+        // batches of 8 slots; the next batch's row indices load while this
+        // batch's rows are in flight (the sum stays in slot order)
+        int rw[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) rw[k] = tpair[s + k];
+        for (int k = 0; k < 8; ++k) rw[k] = s0 + k < s1 ? tpair[s0 + k] : 0;
+        for (int s = s0; s < s1; s += 8) {
             float4 q[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
+            for (int k = 0; k < 8; ++k)
+                if (s + k < s1) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
-            }
-        }
-        for (; s < s1; ++s) {
-            const float4 q = __ldcs(part + (int64_t)tpair[s] * s4 + u);
-            v.x += q.x; v.y += q.y; v.z += q.z; v.w += q.w;
+            for (int k = 0; k < 8; ++k) rw[k] = s + 8 + k < s1 ? tpair[s + 8 + k] : 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (s + k < s1) {
+                    v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
+                }
         }
         *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
     }
@@ -601,12 +602,13 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs,
                                          L.tpair);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // the header (pair count, overflow flag) to pinned host memory, for the
-    // host's pool check at the next call
-    if (ws.h_pp_hdr)
-        e = cudaMemcpyAsync(ws.h_pp_hdr, L.hdr, sizeof(M2lPairHdr), cudaMemcpyDeviceToHost, s);
-    return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_pairs_hdr_copy(int D, Workspace& ws, cudaStream_t s) {
+    if (D < 2 || !ws.h_pp_hdr) return cudaSuccess;
+    PairList L = pair_list(ws);
+    return cudaMemcpyAsync(ws.h_pp_hdr, L.hdr, sizeof(M2lPairHdr), cudaMemcpyDeviceToHost, s);
 }
 
 cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s) {

@@ -411,6 +411,16 @@ enum TcMode { MODE_M2L = 0, MODE_M2M = 1, MODE_L2L = 2, MODE_PAIR = 3 };
 
 constexpr int kOpM2M = 343, kOpL2L = 351, kNumOps = 359;  // packed operator indices
 
+// One member of a joined ensemble M2L launch (BF16 pair-packed): its work
+// list, its split multipoles and the TMA map of its partial rows.
+struct alignas(64) PairMember {
+    CUtensorMap map;
+    const M2lPairItem* items;
+    const M2lPair* pairs;
+    const uint16_t* Mp;
+    const M2lPairHdr* hdr;
+};
+
 struct TcArgs {
     CUtensorMap part_map;  // pair epilogue: TMA descriptor of the partial rows (BF16)
     int mode, level;      // level: the target level of M2M / L2L launches
@@ -440,6 +450,12 @@ struct TcArgs {
     const M2lPairItem* pitems;
     const M2lPairHdr* phdr;
     float* ppart;
+    // joined ensemble launch (n_pm > 0): the members, and the first item of
+    // each (pm_prefix[n_pm] = all items); work item idx belongs to the last
+    // member k with pm_prefix[k] <= idx
+    const PairMember* pm;
+    const int* pm_prefix;
+    int n_pm;
 };
 
 // One M2L tile (up to 128 targets of one level) and its non-empty offsets,
@@ -548,14 +564,27 @@ template <int MODE>
 __device__ __forceinline__ bool tc_work(const TcArgs& a, const LevelInfo& li, int idx, TcWork& w) {
     w.rows = 0;
     if (MODE == MODE_PAIR) {
-        const M2lPairItem it = a.pitems[idx];
+        M2lPairItem it;
+        int k = 0;
+        if (a.n_pm > 0) {
+            int lo = 0, hi = a.n_pm - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.pm_prefix[mid] <= idx) lo = mid;
+                else hi = mid - 1;
+            }
+            k = lo;
+            it = a.pm[k].items[idx - a.pm_prefix[k]];
+        } else {
+            it = a.pitems[idx];
+        }
         w.op = it.op;
         w.pbegin = it.begin;
         w.rows = it.rows;
         w.begin = 0;
         w.end = 1;
         w.rank = 0;
-        w.tile = -1;
+        w.tile = k;  // the member of a joined launch
         w.slot = idx;
         w.level = 0;
         w.oct = 0;
@@ -725,7 +754,8 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
     // work items of this CTA: idx = first, first + stride, ... < count
     int count, first, stride;
     if (MODE == MODE_M2L || MODE == MODE_PAIR) {
-        count = MODE == MODE_PAIR ? a.phdr->n_items : a.hdr->n_items;
+        count = MODE == MODE_PAIR ? (a.n_pm > 0 ? a.pm_prefix[a.n_pm] : a.phdr->n_items)
+                                  : a.hdr->n_items;
         first = blockIdx.x;
         stride = gridDim.x;
     } else {
@@ -888,9 +918,10 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                     const int st = gg % NS, use = gg / NS;
                     const int kc = it % a.kchunks;
                     if (MODE == MODE_PAIR && it == 0) {
+                        const M2lPair* pr = a.n_pm > 0 ? a.pm[w.tile].pairs : a.pairs;
 #pragma unroll
                         for (int j = 0; j < NJ; ++j)
-                            pg[j] = r0 + RS * j < w.rows ? a.pairs[w.pbegin + r0 + RS * j].src : -1;
+                            pg[j] = r0 + RS * j < w.rows ? pr[w.pbegin + r0 + RS * j].src : -1;
                     } else if (MODE == MODE_M2L && kc == 0) {
                         const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
                         const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
@@ -913,6 +944,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                         break;
                     }
                     unsigned char* sA = base + st * stage_bytes;
+                    const uint16_t* Mp = MODE == MODE_PAIR && a.n_pm > 0 ? a.pm[w.tile].Mp : a.Mp;
 #pragma unroll
                     for (int j = 0; j < NJ; ++j) {
                         const int r = r0 + RS * j;
@@ -922,7 +954,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             const uint16_t* src =
-                                gs >= 0 ? a.Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 8 : a.Mp;
+                                gs >= 0 ? Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 8 : Mp;
                             cp_async16ca(sA + q * a_bytes + off, src, gs >= 0 ? 16u : 0u);
                         }
                     }
@@ -1103,6 +1135,12 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                 break;
             }
             tc_fence_after();
+            // the member's partial rows (joined launch: its map in global
+            // memory, written by the host before the launch)
+            const CUtensorMap* map = a.n_pm > 0 ? &a.pm[w.tile].map : &a.part_map;
+            if (a.n_pm > 0 && etid == 0)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map)
+                             : "memory");
             // the two warp sets take separate branches for the whole item;
             // their barriers match
             if (!second) {
@@ -1114,8 +1152,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                 epi_bar<NE>();
                 if (etid == 0) {
                     for (int gq = 0; gq < gh; ++gq)
-                        tma_store_2d(&a.part_map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes,
-                                     keep_l2);
+                        tma_store_2d(map, gq * 16, w.pbegin, boxes + gq * kEpiBoxBytes, keep_l2);
                     bulk_commit();
                     bulk_wait_read();
                 }
@@ -1124,8 +1161,8 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                 epi_bar<NE>();
                 if (etid == 0) {
                     for (int k = 0; k < ngr - gh; ++k)
-                        tma_store_2d(&a.part_map, (gh + k) * 16, w.pbegin,
-                                     boxes + k * kEpiBoxBytes, keep_l2);
+                        tma_store_2d(map, (gh + k) * 16, w.pbegin, boxes + k * kEpiBoxBytes,
+                                     keep_l2);
                     bulk_commit();
                 }
             } else if (a.epi_scratch) {  // uniform
@@ -1961,6 +1998,129 @@ cudaError_t m2l_tc_work_stats(const Workspace& ws, int64_t* out, cudaStream_t s)
 size_t m2l_tc_work_bytes(int64_t tiles_cap, int64_t slab_cap) {
     return sizeof(TcPlanHdr) + (size_t)tiles_cap * sizeof(TcTile) +
            (size_t)(tiles_cap + slab_cap) * sizeof(TcItem);
+}
+
+// ---------------------------------------------------------------------------
+// Joined M2L of an ensemble.  Every BF16 pair-packed member's M2L launch in
+// a captured ensemble graph is replaced by one launch over all members'
+// items: a member's partial rows are the same products as in its own launch
+// (a row depends on its own source row and the offset's operator only), so
+// results are unchanged bit for bit, while the members' M2L phases share the
+// SMs instead of each taking all of them in turn.
+// ---------------------------------------------------------------------------
+
+// pm_prefix[k] = items of members 0 .. k-1 (a member whose pool overflowed
+// has none); one block
+constexpr int kJoinThreads = 1024;
+__global__ void __launch_bounds__(kJoinThreads) k_pm_prefix(const PairMember* pm, int n,
+                                                            int* prefix) {
+    __shared__ int s_c[kJoinThreads];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    for (int b = 0; b < n; b += kJoinThreads) {
+        const int k = b + (int)threadIdx.x;
+        __syncthreads();
+        s_c[threadIdx.x] = k < n ? pm[k].hdr->n_items : 0;
+        __syncthreads();
+        // inclusive scan (Hillis-Steele) over the chunk
+        for (int off = 1; off < kJoinThreads; off <<= 1) {
+            const int v = threadIdx.x >= (unsigned)off ? s_c[threadIdx.x - off] : 0;
+            __syncthreads();
+            s_c[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (k < n) prefix[k + 1] = s_carry + s_c[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == kJoinThreads - 1) s_carry += s_c[kJoinThreads - 1];
+    }
+    if (threadIdx.x == 0) prefix[0] = 0;
+}
+
+size_t m2l_join_member_bytes() { return sizeof(PairMember); }
+
+cudaError_t m2l_join_pair_launches(cudaGraph_t g, void* d_members, int* d_prefix, int cap,
+                                   int* joined) {
+    *joined = 0;
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nn);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && (e = cudaGraphGetNodes(g, nodes.data(), &nn)) != cudaSuccess) return e;
+    const void* fn = (const void*)k_m2l_tc<MODE_PAIR, 1>;
+    std::vector<cudaGraphNode_t> found;
+    std::vector<TcArgs> args;
+    cudaKernelNodeParams first{};
+    for (cudaGraphNode_t x : nodes) {
+        cudaGraphNodeType t;
+        if ((e = cudaGraphNodeGetType(x, &t)) != cudaSuccess) return e;
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if ((e = cudaGraphKernelNodeGetParams(x, &kp)) != cudaSuccess) return e;
+        if (kp.func != fn) continue;
+        if (found.empty()) first = kp;
+        found.push_back(x);
+        args.push_back(*static_cast<const TcArgs*>(kp.kernelParams[0]));
+    }
+    const int n = (int)found.size();
+    if (n < 2) return cudaSuccess;  // nothing to share
+    if (n > cap) return cudaErrorInvalidValue;
+    std::vector<PairMember> hm((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        memset(&hm[k], 0, sizeof(PairMember));
+        hm[k].map = args[k].part_map;
+        hm[k].items = args[k].pitems;
+        hm[k].pairs = args[k].pairs;
+        hm[k].Mp = args[k].Mp;
+        hm[k].hdr = args[k].phdr;
+    }
+    if ((e = cudaMemcpy(d_members, hm.data(), sizeof(PairMember) * n, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    // the joined launch waits for every member's inputs and precedes every
+    // member's consumers of its partial rows
+    std::vector<cudaGraphNode_t> preds, succs;
+    for (cudaGraphNode_t x : found) {
+        size_t np = 0, ns = 0;
+        if ((e = cudaGraphNodeGetDependencies(x, nullptr, nullptr, &np)) != cudaSuccess ||
+            (e = cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &ns)) != cudaSuccess)
+            return e;
+        std::vector<cudaGraphNode_t> a(np), b(ns);
+        if (np && (e = cudaGraphNodeGetDependencies(x, a.data(), nullptr, &np)) != cudaSuccess)
+            return e;
+        if (ns && (e = cudaGraphNodeGetDependentNodes(x, b.data(), nullptr, &ns)) != cudaSuccess)
+            return e;
+        for (cudaGraphNode_t y : a)
+            if (std::find(preds.begin(), preds.end(), y) == preds.end()) preds.push_back(y);
+        for (cudaGraphNode_t y : b)
+            if (std::find(succs.begin(), succs.end(), y) == succs.end()) succs.push_back(y);
+    }
+    const PairMember* dm = static_cast<const PairMember*>(d_members);
+    int nm = n;
+    void* pargs[] = {(void*)&dm, (void*)&nm, (void*)&d_prefix};
+    cudaKernelNodeParams pp{};
+    pp.func = (void*)k_pm_prefix;
+    pp.gridDim = dim3(1);
+    pp.blockDim = dim3(kJoinThreads);
+    pp.sharedMemBytes = 0;
+    pp.kernelParams = pargs;
+    cudaGraphNode_t pnode, jnode;
+    if ((e = cudaGraphAddKernelNode(&pnode, g, preds.data(), preds.size(), &pp)) != cudaSuccess)
+        return e;
+    TcArgs ja = args[0];
+    ja.pm = dm;
+    ja.pm_prefix = d_prefix;
+    ja.n_pm = n;
+    void* jargs[] = {(void*)&ja};
+    cudaKernelNodeParams jp = first;
+    jp.kernelParams = jargs;
+    jp.extra = nullptr;
+    if ((e = cudaGraphAddKernelNode(&jnode, g, &pnode, 1, &jp)) != cudaSuccess) return e;
+    for (cudaGraphNode_t y : succs)
+        if ((e = cudaGraphAddDependencies(g, &jnode, &y, nullptr, 1)) != cudaSuccess) return e;
+    for (cudaGraphNode_t x : found)
+        if ((e = cudaGraphDestroyNode(x)) != cudaSuccess) return e;
+    *joined = n;
+    return cudaSuccess;
 }
 
 }  // namespace pt

@@ -1,7 +1,9 @@
 """Batched ensembles through the C ABI: each member of an ensemble of uneven
 ion counts and shapes, stepped in one graph with the others, ends in the
 state that the same plan reaches when stepped alone, bit for bit (the kernels
-are deterministic and the members share nothing but the device)."""
+are deterministic and the members share nothing but the device; the joined
+M2L launch computes each member's partial rows from that member's data
+only)."""
 import numpy as np
 import pytest
 import torch
@@ -18,18 +20,20 @@ def members():
     return [W.ensemble_member(n, a, seed=11 + k) for k, (n, a) in enumerate(spec)]
 
 
-def run(precision, p, steps_a, steps_b, together):
+def run(precision, p, steps_a, steps_b, together, joined=True):
     crs = members()
     plans = [pt.Plan(len(c["q"]), p=p, leaf_max=32, depth=-1, precision=precision) for c in crs]
     states = [pt.State.from_numpy(c["pos"], c["vel"], c["q"]) for c in crs]
     traps = [pt.make_trap(c["trap"]) for c in crs]
     lasers = [pt.make_laser(c["beams"], seed=5 + k, gamma0=W.GAMMA0) for k, c in enumerate(crs)]
     dts = [c["dt"] for c in crs]
+    n_joined = 0
     if together:
-        ens = pt.Ensemble(plans)
+        ens = pt.Ensemble(plans, joined_m2l=joined)
         ens.step(states, traps, lasers, dts, steps_a)
         ens.step(states, traps, lasers, dts, steps_b)
         ens.sync()
+        n_joined = ens.joined_m2l()
         ens.close()
     else:
         for pl, st, tr, lz, dt in zip(plans, states, traps, lasers, dts):
@@ -40,13 +44,18 @@ def run(precision, p, steps_a, steps_b, together):
            for s, pl in zip(states, plans)]
     for pl in plans:
         pl.close()
-    return out
+    return out, n_joined
 
 
-@pytest.mark.parametrize("precision,p", [("fp64", 6), ("bf16x3", 8)])
-def test_member_alone_equals_member_in_the_mix(precision, p):
-    mixed = run(precision, p, 5, 3, together=True)
-    alone = run(precision, p, 5, 3, together=False)
+@pytest.mark.parametrize("precision,p,joined", [("fp64", 6, True), ("bf16x3", 8, True),
+                                                ("bf16x3", 12, True), ("bf16x3", 12, False)])
+def test_member_alone_equals_member_in_the_mix(precision, p, joined):
+    mixed, n_joined = run(precision, p, 5, 3, together=True, joined=joined)
+    alone, _ = run(precision, p, 5, 3, together=False)
+    far = sum(1 for (_, _, _, _, d) in alone if d >= 2)
+    # the BF16x3 members with a far field share one M2L launch; FP64 members
+    # use the CUDA-core M2L and are never joined
+    assert n_joined == (far if precision == "bf16x3" and joined and far >= 2 else 0)
     for (xm, vm, tm, sm, dm), (xa, va, ta, sa, da) in zip(mixed, alone):
         assert dm == da
         assert sm == sa == 8 and tm == ta
