@@ -428,7 +428,6 @@ static int ensure_pairs(fmm_plan_s* pl, int64_t n, const double* x, const double
         cudaError_t e = launch_bbox(x, y, z, n, ws, s);
         if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, ws, s);
         if (e == cudaSuccess) e = launch_m2l_pairs_worklist(n, D, ws, s);
-        if (e == cudaSuccess) e = launch_m2l_pairs_hdr_copy(D, ws, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return status_from(e);
         int r = check_err(pl, s);  // an overflow of this count is not an error

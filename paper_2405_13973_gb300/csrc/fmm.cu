@@ -921,7 +921,6 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                         : launch_m2l_pairs_worklist(n, D, ws, sn)) != cudaSuccess)
             return e;
         if (fork && (e = cudaEventRecord(ws.ev_items, sn)) != cudaSuccess) return e;
-        if (ws.m2l_pairs && (e = launch_m2l_pairs_hdr_copy(D, ws, sn)) != cudaSuccess) return e;
     }
     // Multipoles from the ions: at the leaves, and on the tensor-core path also
     // at their parents (a parent holds about eight leaves' ions, cheaper to

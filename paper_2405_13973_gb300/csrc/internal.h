@@ -114,7 +114,8 @@ struct Workspace {
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
     void* pp_work = nullptr;
     void* pp_part = nullptr;
-    void* h_pp_hdr = nullptr;       // pinned copy of the last work list's header (pairs, overflow)
+    void* h_pp_hdr = nullptr;       // pinned copy of the last work list's header (pairs, overflow),
+                                    // written by k_pp_scan through the unified address space
     int pp_gen = 0;                 // bumped whenever the pool is reallocated
     int pp_stride = 0;
     int64_t pp_slot_cap = 0;    // pairs the pool holds
@@ -179,10 +180,6 @@ size_t m2l_pp_work_bytes(const Workspace& ws);
 size_t m2l_pp_part_bytes(const Workspace& ws);
 // the work list of the current tree (reads the tree only)
 cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
-// the work list's header (pair count, overflow flag) to pinned host memory,
-// for the host's pool check at the next call; queued after the consumers of
-// the work list are released
-cudaError_t launch_m2l_pairs_hdr_copy(int D, Workspace& ws, cudaStream_t s);
 // L of every cell of levels 2..D = the sum of its pairs' partial rows
 // (`width` columns)
 cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s);

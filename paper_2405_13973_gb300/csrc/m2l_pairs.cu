@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
                                                              int64_t slot_cap, int64_t rows_cap,
                                                              int item_cap,
                                                              const int* tcount, int* tbase,
-                                                             const int* ocnt, int* obase,
-                                                             M2lPairHdr* hdr, M2lPairItem* items,
-                                                             int* err) {
+                                                             int* ocnt, int* ofill, int* obase,
+                                                             M2lPairHdr* hdr, M2lPairHdr* host_hdr,
+                                                             M2lPairItem* items, int* err) {
     __shared__ int wsum[32];
     __shared__ int s_carry;
     __shared__ int s_ibase[344];
@@ -204,13 +204,23 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
         hdr->n_pairs = total;
         hdr->n_targets = nt;
         hdr->n_offsets = s_nof;
+        // the header also to pinned host memory, for the host's pool check
+        // at the next call (no copy node)
+        if (host_hdr) {
+            volatile int* h = reinterpret_cast<volatile int*>(host_hdr);
+            h[0] = hdr->n_items;
+            h[1] = hdr->n_pairs;
+            h[2] = hdr->n_targets;
+            h[3] = hdr->overflow;
+            h[4] = hdr->n_offsets;
+        }
     }
     __syncthreads();
-    if ((int64_t)total > slot_cap || (int64_t)s_pb[343] > rows_cap || s_ibase[343] > item_cap)
-        return;
-    for (int o = tid; o < 343; o += kPpScanThreads) {
-        const int c = ocnt[o];
-        for (int k = 0; k * kPairRows < c; ++k) {
+    const bool over =
+        (int64_t)total > slot_cap || (int64_t)s_pb[343] > rows_cap || s_ibase[343] > item_cap;
+    for (int o = tid; o < 344; o += kPpScanThreads) {
+        const int c = o < 343 ? ocnt[o] : 0;
+        for (int k = 0; !over && k * kPairRows < c; ++k) {
             M2lPairItem it;
             it.op = o;
             it.begin = s_pb[o] + k * kPairRows;
@@ -218,6 +228,10 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
             it.pad = 0;
             items[s_ibase[o] + k] = it;
         }
+        // counts read: zero them and the fill counters for the next work
+        // list (zeroed once at allocation)
+        ocnt[o] = 0;
+        ofill[o] = 0;
     }
 }
 
@@ -261,45 +275,62 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t
     }
 }
 
-// L of every target = the sum of its partial rows in slot order (increasing
-// offset), one warp per target, lanes over 16-byte column groups (FP32) or
-// single columns (FP64); `width` columns are written.  Targets without pairs
-// get zeros.  On a pool overflow nothing is summed (the call reports it).
+// L of every target = the sum of its partial rows over its slots (increasing
+// offset); `width` columns are written.  Targets without pairs get zeros.  On
+// a pool overflow nothing is summed (the call reports it).  FP32 rows with
+// width a multiple of 4 (k_pp_reduce_f4): a block per target, the slots in
+// four ordered parts; otherwise (k_pp_reduce) a warp per target in slot
+// order, lanes over columns.
+constexpr int kRedParts = 4;  // slot-range parts per (target, column group)
 __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride, int width,
                                                        const LevelInfo* linfo,
                                                        const M2lPairHdr* hdr, const int* tbase,
                                                        const int* __restrict__ tpair,
                                                        const float4* __restrict__ part, float* L) {
-    // one thread per (target, 16-byte column group): consecutive threads read
-    // consecutive columns of a slot row; eight rows in flight per thread
+    // one block per target, kRedParts x (width / 4) threads: thread (j, u)
+    // sums column group u of the j-th quarter of the target's slots in slot
+    // order (consecutive threads read consecutive columns of a row, the next
+    // 8 slot indices loading while 8 rows are in flight); the quarters are
+    // then added in order j = 0, 1, 2, 3 (a fixed association: deterministic)
+    __shared__ float4 s_part[kRedParts][64];
     const int g0 = linfo->gbase[2], nt = linfo->gbase[D + 1] - g0;
     const int s4 = stride / 4, w4 = width / 4;
     const bool over = hdr->overflow != 0;
-    const int64_t total = (int64_t)nt * w4;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(e / w4), u = (int)(e - (int64_t)t * w4);
-        const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
+    const int j = threadIdx.x / w4, u = threadIdx.x - j * w4;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        const int b0 = tbase[t], b1 = over ? b0 : tbase[t + 1];
+        const int cs = (b1 - b0 + kRedParts - 1) / kRedParts;
+        const int s0 = min(b0 + j * cs, b1), s1 = min(s0 + cs, b1);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        // batches of 8 slots; the next batch's row indices load while this
-        // batch's rows are in flight (the sum stays in slot order)
-        int rw[8];
+        if (j < kRedParts) {
+            int rw[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) rw[k] = s0 + k < s1 ? tpair[s0 + k] : 0;
-        for (int s = s0; s < s1; s += 8) {
-            float4 q[8];
+            for (int k = 0; k < 8; ++k) rw[k] = s0 + k < s1 ? tpair[s0 + k] : 0;
+            for (int s = s0; s < s1; s += 8) {
+                float4 q[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (s + k < s1) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
+                for (int k = 0; k < 8; ++k)
+                    if (s + k < s1) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) rw[k] = s + 8 + k < s1 ? tpair[s + 8 + k] : 0;
+                for (int k = 0; k < 8; ++k) rw[k] = s + 8 + k < s1 ? tpair[s + 8 + k] : 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (s + k < s1) {
-                    v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
-                }
+                for (int k = 0; k < 8; ++k)
+                    if (s + k < s1) {
+                        v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
+                    }
+            }
+            s_part[j][u] = v;
         }
-        *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
+        __syncthreads();
+        if (j == 0) {
+#pragma unroll
+            for (int k = 1; k < kRedParts; ++k) {
+                const float4 w = s_part[k][u];
+                v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+            }
+            *reinterpret_cast<float4*>(L + (int64_t)(g0 + t) * ld + 4 * u) = v;
+        }
+        __syncthreads();
     }
 }
 
@@ -588,8 +619,9 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     const DenseLayout dl = dense_layout(D);
     for (int l = 0; l < kMaxDepth + 2; ++l) a.off[l] = dl.off[l];
     PairList L = pair_list(ws);
-    cudaError_t e = cudaMemsetAsync(L.ocnt, 0, sizeof(int) * 2 * 344, s);  // counts, fills
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    // the offset counts and fill counters are zero here: zeroed at allocation
+    // and by k_pp_scan after use
     const int64_t tb = target_cells_bound(n, D);
     const int64_t warps = kPpThreads / 32;
     const unsigned gc = (unsigned)std::min<int64_t>((tb + warps - 1) / warps, 152 * 8);
@@ -597,19 +629,15 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_pp_scan<<<1, kPpScanThreads, 0, s>>>(D, ws.linfo, ws.pp_slot_cap, ws.pp_rows_cap,
                                             (int)ws.pp_item_cap,
-                                            L.tcount, L.tbase, L.ocnt, L.obase, L.hdr, L.items,
-                                            ws.err);
+                                            L.tcount, L.tbase, L.ocnt, L.ofill, L.obase, L.hdr,
+                                            (M2lPairHdr*)ws.h_pp_hdr, L.items, ws.err);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs,
                                          L.tpair);
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2l_pairs_hdr_copy(int D, Workspace& ws, cudaStream_t s) {
-    if (D < 2 || !ws.h_pp_hdr) return cudaSuccess;
-    PairList L = pair_list(ws);
-    return cudaMemcpyAsync(ws.h_pp_hdr, L.hdr, sizeof(M2lPairHdr), cudaMemcpyDeviceToHost, s);
-}
+
 
 cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, cudaStream_t s) {
     if (D < 2) return cudaSuccess;
@@ -620,11 +648,12 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
         k_pp_reduce<double><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
                                                L.tbase, L.tpair, (const double*)ws.pp_part,
                                                (double*)ws.L);
-    } else if (width % 4 == 0 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
-        const int64_t th = tb * (width / 4);
-        const unsigned g4 = (unsigned)std::min<int64_t>((th + 255) / 256, 152 * 16);
-        k_pp_reduce_f4<<<g4, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr, L.tbase,
-                                          L.tpair, (const float4*)ws.pp_part, (float*)ws.L);
+    } else if (width % 4 == 0 && width <= 256 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
+        const unsigned g4 = (unsigned)std::min<int64_t>(tb, 152 * 32);
+        k_pp_reduce_f4<<<g4, kRedParts * (width / 4), 0, s>>>(D, ws.ld, ws.pp_stride, width,
+                                                              ws.linfo, L.hdr, L.tbase, L.tpair,
+                                                              (const float4*)ws.pp_part,
+                                                              (float*)ws.L);
     } else {
         k_pp_reduce<float><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
                                               L.tbase, L.tpair, (const float*)ws.pp_part,
