@@ -148,9 +148,9 @@ int fmm_plan_set_expansion(fmm_plan plan, int mode);
  *                    factorisation of the dense operator, exact up to
  *                    rounding): O(p^3) instead of (p+1)^4 multiply-adds per
  *                    translation (7.3k instead of 28.6k at p = 12).
- * Default: PT_M2L_ROTATION for FP64 and PT_M2L_PAIRS for the other
- * precisions up to n_max = 65536, PT_M2L_TILES above.  Selecting another
- * schedule allocates what it needs.
+ * Default: PT_M2L_PAIRS for the tensor-core precisions up to n_max = 65536;
+ * PT_M2L_ROTATION for FP64 and PT_M2L_PAIRS for FP32 up to n_max = 262144;
+ * PT_M2L_TILES above.  Selecting another schedule allocates what it needs.
  * Errors: PT_ERR_ARG, PT_ERR_UNSUPPORTED (rotation on the tensor-core
  * precisions or beyond p = 16), PT_ERR_OOM, PT_ERR_CUDA. */
 #define PT_M2L_TILES 0

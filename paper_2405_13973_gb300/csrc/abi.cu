@@ -23,7 +23,13 @@ namespace {
 
 constexpr int kWallChunk = 4096;  // steps per wall-phase table upload
 // tensor-core plans up to this many ions use the pair-packed M2L schedule
+// (above it the tile schedule is faster: its rows are already mostly
+// pairs, and it has no partial rows to round-trip)
 constexpr int64_t kPairsDefaultIons = 65536;
+// CUDA-core plans up to this many ions use the pair work list (rotation M2L
+// in FP64), which beats the per-level tile kernel at every size measured;
+// the bound keeps the FP64 partial-row pool within a few GB
+constexpr int64_t kPairsDefaultIonsCudaCore = 262144;
 
 struct GraphKey {
     int D = -1;
@@ -878,7 +884,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
             ok = alloc_pairs(pl) == PT_OK;
             ws.m2l_pairs = ok ? 1 : 0;
         }
-    } else if (ok && n_max <= kPairsDefaultIons) {
+    } else if (ok && n_max <= kPairsDefaultIonsCudaCore) {
         // CUDA-core precisions: the pair work list by default as well, with
         // the rotation-based M2L for FP64 (a quarter of the dense
         // translation's FP64 operations at p = 12)

@@ -73,6 +73,10 @@ def test_autotuned_depth_is_a_neighbour_of_the_automatic_one():
     plan.step(pt.State.from_numpy(pos, vel, q), pt.make_trap(tr), None, dt, 1)
     assert abs(d - plan.last_depth) <= 1
     assert autotune.tune_depth(2500, 8, "bf16x3", crystal) == d   # same band: cached
+    # ensemble throughput: four copies stepped together, cached apart
+    db = autotune.tune_depth(3000, 8, "bf16x3", crystal, steps=4, batch=4)
+    assert abs(db - plan.last_depth) <= 1
+    assert (autotune.band(3000), 8, "bf16x3", 4) in autotune._cache
     plan.close()
 
 
