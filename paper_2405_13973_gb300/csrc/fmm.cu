@@ -43,6 +43,12 @@ template <>
 __device__ __forceinline__ const HarmTables<double>& tab<double>() { return c_tab_d; }
 template <>
 __device__ __forceinline__ const HarmTables<float>& tab<float>() { return c_tab_f; }
+template <typename T>
+__device__ __forceinline__ const HarmTables<T>& gtab();
+template <>
+__device__ __forceinline__ const HarmTables<double>& gtab<double>() { return g_tab_d; }
+template <>
+__device__ __forceinline__ const HarmTables<float>& gtab<float>() { return g_tab_f; }
 
 void host_m2l_offsets(int16_t out[8][189]) {
     for (int oct = 0; oct < 8; ++oct) {
@@ -590,12 +596,6 @@ __global__ void __launch_bounds__(kNfThreads) k_p2p(
 constexpr int kL2pThreads = 256;
 constexpr int kPmax = (kMaxOrder + 1) * (kMaxOrder + 1);
 
-template <typename T>
-__device__ __forceinline__ const HarmTables<T>& gtab();
-template <>
-__device__ __forceinline__ const HarmTables<double>& gtab<double>() { return g_tab_d; }
-template <>
-__device__ __forceinline__ const HarmTables<float>& gtab<float>() { return g_tab_f; }
 
 // the derived expansions of one local expansion Lr (see k_l2p) into D4[4][P]
 template <typename T>
