@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(kP2mThreads) k_p2m_anc(
     const typename Ion<T>::rec* __restrict__ sorted, T* __restrict__ M) {
     extern __shared__ unsigned char p2m_smem[];
     const int P = (p + 1) * (p + 1);
+    pdl_wait();
     T* terms = reinterpret_cast<T*>(p2m_smem);  // [kP2mAncIons][P]
     const HarmTables<T>& t = tab<T>();
     const int g0 = linfo->gbase[lmin], g1 = linfo->gbase[D + 1];
@@ -714,6 +715,7 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     const typename Ion<T>::rec* __restrict__ sorted, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ cstart, const int32_t* __restrict__ ccount,
     const T* __restrict__ L, const T* __restrict__ near, double* E, double* phi) {
+    pdl_wait();
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
     if (g0 + (int)blockIdx.x >= g1) return;  // no leaf for this block
     __shared__ T sL[2][kPmax];
@@ -932,10 +934,12 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         for (int l = lmin_p2m; l <= D; ++l)
             cells += n < ((int64_t)1 << (3 * l)) ? n : ((int64_t)1 << (3 * l));
         const int grid = (int)(cells < 152 * 16 ? cells : 152 * 16);
-        k_p2m_anc<T><<<grid, kP2mThreads, kP2mAncIons * P * sizeof(T), s>>>(
-            D, lmin_p2m, p, ws.ld, ws.linfo, ws.code, ws.leaf_start, ws.leaf_of,
-            (const typename Ion<T>::rec*)ws.sorted, M);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_p2m_anc<T>, dim3(grid), dim3(kP2mThreads), kP2mAncIons * P * sizeof(T),
+                            s, D, lmin_p2m, p, ws.ld, (const LevelInfo*)ws.linfo,
+                            (const uint32_t*)ws.code, (const int32_t*)ws.leaf_start,
+                            (const int32_t*)ws.leaf_of, (const typename Ion<T>::rec*)ws.sorted,
+                            M)) != cudaSuccess)
+            return e;
     } else if (far) {
         int grid = leaf_grid;
         k_p2m<T><<<grid, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
@@ -1021,10 +1025,14 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
             (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
             nf ? near : nullptr, E, phi);
     else
-        k_l2p<T><<<leaf_grid, kL2pThreads, 0, s>>>(
-            n, D, p, ws.ld, far, use_tc && D >= 3 ? 2 : 1, ws.root, ws.linfo, ws.code, ws.cid,
-            (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
-            nf ? near : nullptr, E, phi);
+        e = launch_pdl(k_l2p<T>, dim3(leaf_grid), dim3(kL2pThreads), 0, s, n, D, p, ws.ld, far,
+                       use_tc && D >= 3 ? 2 : 1, (const RootCube*)ws.root,
+                       (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code,
+                       (const int32_t*)ws.cid, (const typename Ion<T>::rec*)ws.sorted,
+                       (const int32_t*)ws.perm, (const int32_t*)ws.cstart,
+                       (const int32_t*)ws.ccount, (const T*)L, (const T*)(nf ? near : nullptr),
+                       E, phi);
+    if (e != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
         return e;

@@ -8,6 +8,31 @@
 
 namespace pt {
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// scheduled while its predecessor in the stream finishes (its blocks become
+// resident, its set-up runs); it calls pdl_wait() before it touches memory
+// that earlier work writes or reads, which returns once the predecessor has
+// completed and its writes are visible.  In a kernel launched normally,
+// pdl_wait() returns at once.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 constexpr int kMaxDepth = 8;      // uniform octree depth limit (8^8 leaf cells)
 constexpr int kMaxOrder = 16;     // expansion order limit
 constexpr int kScanTile = 2048;   // elements per block in the device scans

@@ -744,6 +744,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
     k_m2l_tc(const __grid_constant__ TcArgs a) {
     using L = TcLayout<MODE, BF16>;
     extern __shared__ unsigned char smem_dyn[];
+    pdl_wait();  // launched after its inputs' producer (programmatic launches)
     __shared__ __align__(8) uint64_t fullA_bar[kMaxStages], fullB_bar[kMaxStages],
         empty_bar[kMaxStages], accf_bar, acce_bar, drain_bar;
     __shared__ uint32_t tmem_base_sh;
@@ -1593,6 +1594,7 @@ __global__ void __launch_bounds__(256) k_tc_reduce_tiles(int ld, const TcPlanHdr
 // whole padded rows: the partials' padding stays zero from allocation).
 __global__ void k_tc_reduce(int lfirst, int llast, int ld, int nparts, const LevelInfo* linfo,
                             const float4* __restrict__ part, int64_t part_stride4, float4* L) {
+    pdl_wait();
     const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[llast + 1];
     const int64_t w = ld / 4;
     for (int64_t e = g0 * w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g1 * w;
@@ -1719,17 +1721,28 @@ void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T
     }
 }
 
+// pdl: a programmatic dependent launch (launch_pdl); the M2L launches stay
+// plain (the ensemble's graph rewrite takes their edges as they are)
 template <int MODE>
-static cudaError_t tc_launch_mode(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
+static cudaError_t tc_launch_mode(const TcArgs& a, unsigned grid, int smem, cudaStream_t s,
+                                  bool pdl) {
+    if (pdl) {
+        if (a.bf16)
+            return launch_pdl(k_m2l_tc<MODE, 1>, dim3(grid), dim3(TcLayout<MODE, 1>::kThreads),
+                              (size_t)smem, s, a);
+        return launch_pdl(k_m2l_tc<MODE, 0>, dim3(grid), dim3(TcLayout<MODE, 0>::kThreads),
+                          (size_t)smem, s, a);
+    }
     if (a.bf16) k_m2l_tc<MODE, 1><<<grid, TcLayout<MODE, 1>::kThreads, smem, s>>>(a);
     else k_m2l_tc<MODE, 0><<<grid, TcLayout<MODE, 0>::kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
-static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStream_t s) {
-    if (a.mode == MODE_PAIR) return tc_launch_mode<MODE_PAIR>(a, grid, smem, s);
-    if (a.mode == MODE_M2L) return tc_launch_mode<MODE_M2L>(a, grid, smem, s);
-    if (a.mode == MODE_M2M) return tc_launch_mode<MODE_M2M>(a, grid, smem, s);
-    return tc_launch_mode<MODE_L2L>(a, grid, smem, s);
+static cudaError_t tc_launch(const TcArgs& a, unsigned grid, int smem, cudaStream_t s,
+                             bool pdl = false) {
+    if (a.mode == MODE_PAIR) return tc_launch_mode<MODE_PAIR>(a, grid, smem, s, false);
+    if (a.mode == MODE_M2L) return tc_launch_mode<MODE_M2L>(a, grid, smem, s, false);
+    if (a.mode == MODE_M2M) return tc_launch_mode<MODE_M2M>(a, grid, smem, s, pdl);
+    return tc_launch_mode<MODE_L2L>(a, grid, smem, s, pdl);
 }
 
 cudaError_t m2l_tc_init() {
@@ -1810,11 +1823,12 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
     TcArgs a = base_args(n, D, ws, splits);
     a.mode = MODE_M2M;
     a.level = l;
-    cudaError_t e = tc_launch(a, (unsigned)(tiles * splits), tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes, s);
+    cudaError_t e = tc_launch(a, (unsigned)(tiles * splits), tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes, s,
+                              true);
     if (e != cudaSuccess || splits == 1) return e;
-    k_tc_reduce<<<152 * 2, 256, 0, s>>>(l, l, ws.ld, splits - 1, ws.linfo, (const float4*)ws.tc_part,
-                                        ws.cells_max * ws.ld / 4, (float4*)ws.M);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_reduce, dim3(152 * 2), dim3(256), 0, s, l, l, ws.ld, splits - 1,
+                      (const LevelInfo*)ws.linfo, (const float4*)ws.tc_part,
+                      (int64_t)(ws.cells_max * ws.ld / 4), (float4*)ws.M);
 }
 
 // M of every cell of levels 2..D as bf16 hi/mid/lo pieces (split_bf16x3, the
@@ -1822,6 +1836,7 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
 // gathers the cell): Mp[(cell * 3 + q) * ld + k].
 __global__ void k_split_m(int lfirst, int D, int ld, const LevelInfo* linfo, const float* M,
                           uint16_t* Mp) {
+    pdl_wait();
     const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[D + 1];
     for (int64_t e = g0 * ld + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g1 * ld;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -1904,7 +1919,7 @@ static cudaError_t launch_l2l_levels(int64_t n, int D, Workspace& ws, int l2l_la
         b.mode = MODE_L2L;
         b.level = l;
         const int64_t t2 = (level_cells(n, l) + kTcRows - 1) / kTcRows + 8;
-        cudaError_t e = tc_launch(b, (unsigned)t2, smem, s);
+        cudaError_t e = tc_launch(b, (unsigned)t2, smem, s, true);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -1931,8 +1946,10 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cud
         TcArgs a = pair_args(n, D, ws);
         cudaError_t e;
         if (ws.tc_bf16) {
-            k_split_m<<<152 * 8, 256, 0, s>>>(2, D, ws.ld, ws.linfo, (const float*)ws.M, ws.M_pieces);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = launch_pdl(k_split_m, dim3(152 * 8), dim3(256), 0, s, 2, D, ws.ld,
+                                (const LevelInfo*)ws.linfo, (const float*)ws.M, ws.M_pieces)) !=
+                cudaSuccess)
+                return e;
         }
         if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
                              cudaSuccess)

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(32 * PT_MAX_BEAMS) k_kick_drift(
     int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
     const double* __restrict__ q, const double* __restrict__ E, PushParams pp, pt_laser laser,
     const StepCounter* steps, const double* __restrict__ wall_cs) {
+    pdl_wait();
     __shared__ int s_cnt[PT_MAX_BEAMS][kKickIons];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const bool lasers = laser.enabled && laser.n_beams > 0;
@@ -239,9 +240,9 @@ cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double
     const int nb = laser.enabled && laser.n_beams > 0 ? laser.n_beams : 1;
     int64_t g = (n + kKickIons - 1) / kKickIons;
     if (g > 152 * 16) g = 152 * 16;
-    k_kick_drift<<<g > 0 ? (int)g : 1, 32 * nb, 0, s>>>(n, x, y, z, vx, vy, vz, q, E, pp, laser,
-                                                         ws.steps, ws.wall_cs);
-    return cudaGetLastError();
+    return launch_pdl(k_kick_drift, dim3(g > 0 ? (int)g : 1), dim3(32 * nb), 0, s, n, x, y, z, vx,
+                      vy, vz, q, E, pp, laser, (const StepCounter*)ws.steps,
+                      (const double*)ws.wall_cs);
 }
 
 cudaError_t launch_laser_kicks(const pt_laser& laser, double rk, int64_t n, const double* x,

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t 
 template <class SrcA, class SrcB>
 __global__ void __launch_bounds__(kScan1Threads) k_scan_single2(SrcA a, int64_t total_a, SrcB b,
                                                                  int64_t total_b) {
+    pdl_wait();
     scan_single_body(a, total_a);
     __syncthreads();
     scan_single_body(b, total_b);
@@ -321,6 +322,7 @@ struct CellCompaction {
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                           const int32_t* __restrict__ leaf_start, int64_t n, int32_t* perm_tmp) {
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         perm_tmp[leaf_start[key[i]] + rank[i]] = (int32_t)i;
@@ -359,6 +361,7 @@ __global__ void k_leaf_gather(const double* __restrict__ x, const double* __rest
                               const int32_t* __restrict__ cid_leaf,
                               const int32_t* __restrict__ perm_tmp, int32_t* perm,
                               int32_t* slot_of, int32_t* leaf_of, T4* sorted) {
+    pdl_wait();
     const double lo0 = root->lo[0], lo1 = root->lo[1], lo2 = root->lo[2], side = root->side;
     const double scale = (double)(1 << D);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -404,25 +407,28 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
     // the cell compaction reads only the leaf starts: both scans in one
     // single-block launch when they fit, then the scatter
     if (ncells <= kScan1Max && dl.total <= kScan1Max) {
-        k_scan_single2<<<1, kScan1Threads, 0, s>>>(ls, ncells, cc, dl.total);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_pdl(k_scan_single2<LeafCountScan, CellCompaction>, dim3(1),
+                            dim3(kScan1Threads), 0, s, ls, ncells, cc, dl.total)) != cudaSuccess)
+            return e;
     } else {
         if ((e = run_scan(ls, ncells, ws, s)) != cudaSuccess) return e;
         if ((e = run_scan(cc, dl.total, ws, s)) != cudaSuccess) return e;
     }
-    k_scatter<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(ws.key, ws.rank, ws.leaf_start, n,
-                                                            ws.perm_tmp);
     const int g = grid_ions > 0 ? grid_ions : 1;
+    if ((e = launch_pdl(k_scatter, dim3(g), dim3(256), 0, s, (const uint32_t*)ws.key,
+                        (const uint32_t*)ws.rank, (const int32_t*)ws.leaf_start, n,
+                        ws.perm_tmp)) != cudaSuccess)
+        return e;
     const int32_t* cid_leaf = ws.cid + dl.off[D];
     if (ws.fp64)
-        k_leaf_gather<double4_32a><<<g, 256, 0, s>>>(
-            x, y, z, q, n, D, ws.root, ws.key, ws.leaf_start, cid_leaf, ws.perm_tmp, ws.perm,
-            ws.slot_of, ws.leaf_of, (double4_32a*)ws.sorted);
-    else
-        k_leaf_gather<int4><<<g, 256, 0, s>>>(
-            x, y, z, q, n, D, ws.root, ws.key, ws.leaf_start, cid_leaf, ws.perm_tmp, ws.perm,
-            ws.slot_of, ws.leaf_of, (int4*)ws.sorted);
-    return cudaGetLastError();
+        return launch_pdl(k_leaf_gather<double4_32a>, dim3(g), dim3(256), 0, s, x, y, z, q, n, D,
+                          (const RootCube*)ws.root, (const uint32_t*)ws.key,
+                          (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
+                          ws.perm, ws.slot_of, ws.leaf_of, (double4_32a*)ws.sorted);
+    return launch_pdl(k_leaf_gather<int4>, dim3(g), dim3(256), 0, s, x, y, z, q, n, D,
+                      (const RootCube*)ws.root, (const uint32_t*)ws.key,
+                      (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
+                      ws.perm, ws.slot_of, ws.leaf_of, (int4*)ws.sorted);
 }
 
 // ---------------------------------------------------------------------------
