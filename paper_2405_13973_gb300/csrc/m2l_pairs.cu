@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kPpScanThreads) k_pp_scan(int D, const LevelIn
                                                              int* ocnt, int* ofill, int* obase,
                                                              M2lPairHdr* hdr, M2lPairHdr* host_hdr,
                                                              M2lPairItem* items, int* err) {
+    pdl_wait();
     __shared__ int wsum[32];
     __shared__ int s_carry;
     __shared__ int s_ibase[344];
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t
                                                          const int* tbase, const int* obase,
                                                          int* ofill, const M2lPairHdr* hdr,
                                                          M2lPair* pairs, int* tpair) {
+    pdl_wait();
     __shared__ LevelInfo li;
     stage_linfo(a.linfo, &li);
     __syncthreads();
@@ -287,6 +289,7 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
                                                        const M2lPairHdr* hdr, const int* tbase,
                                                        const int* __restrict__ tpair,
                                                        const float4* __restrict__ part, float* L) {
+    pdl_wait();
     // one block per target, kRedParts x (width / 4) threads: thread (j, u)
     // sums column group u of the j-th quarter of the target's slots in slot
     // order (consecutive threads read consecutive columns of a row, the next
@@ -627,14 +630,15 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     const unsigned gc = (unsigned)std::min<int64_t>((tb + warps - 1) / warps, 152 * 8);
     k_pp_count<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tcount, L.ocnt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pp_scan<<<1, kPpScanThreads, 0, s>>>(D, ws.linfo, ws.pp_slot_cap, ws.pp_rows_cap,
-                                            (int)ws.pp_item_cap,
-                                            L.tcount, L.tbase, L.ocnt, L.ofill, L.obase, L.hdr,
-                                            (M2lPairHdr*)ws.h_pp_hdr, L.items, ws.err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pp_fill<<<gc, kPpThreads, 0, s>>>(a, L.tmask, L.tbase, L.obase, L.ofill, L.hdr, L.pairs,
-                                         L.tpair);
-    return cudaGetLastError();
+    if ((e = launch_pdl(k_pp_scan, dim3(1), dim3(kPpScanThreads), 0, s, D,
+                        (const LevelInfo*)ws.linfo, (int64_t)ws.pp_slot_cap,
+                        (int64_t)ws.pp_rows_cap, (int)ws.pp_item_cap, (const int*)L.tcount,
+                        L.tbase, L.ocnt, L.ofill, L.obase, L.hdr, (M2lPairHdr*)ws.h_pp_hdr,
+                        L.items, ws.err)) != cudaSuccess)
+        return e;
+    return launch_pdl(k_pp_fill, dim3(gc), dim3(kPpThreads), 0, s, a, (const uint32_t*)L.tmask,
+                      (const int*)L.tbase, (const int*)L.obase, L.ofill, (const M2lPairHdr*)L.hdr,
+                      L.pairs, L.tpair);
 }
 
 
@@ -650,10 +654,10 @@ cudaError_t launch_m2l_pairs_reduce(int64_t n, int D, Workspace& ws, int width, 
                                                (double*)ws.L);
     } else if (width % 4 == 0 && width <= 256 && ws.pp_stride % 4 == 0 && ws.ld % 4 == 0) {
         const unsigned g4 = (unsigned)std::min<int64_t>(tb, 152 * 32);
-        k_pp_reduce_f4<<<g4, kRedParts * (width / 4), 0, s>>>(D, ws.ld, ws.pp_stride, width,
-                                                              ws.linfo, L.hdr, L.tbase, L.tpair,
-                                                              (const float4*)ws.pp_part,
-                                                              (float*)ws.L);
+        return launch_pdl(k_pp_reduce_f4, dim3(g4), dim3(kRedParts * (width / 4)), 0, s, D,
+                          ws.ld, ws.pp_stride, width, (const LevelInfo*)ws.linfo,
+                          (const M2lPairHdr*)L.hdr, (const int*)L.tbase, (const int*)L.tpair,
+                          (const float4*)ws.pp_part, (float*)ws.L);
     } else {
         k_pp_reduce<float><<<gr, 256, 0, s>>>(D, ws.ld, ws.pp_stride, width, ws.linfo, L.hdr,
                                               L.tbase, L.tpair, (const float*)ws.pp_part,

@@ -2101,21 +2101,27 @@ cudaError_t m2l_join_pair_launches(cudaGraph_t g, void* d_members, int* d_prefix
         return e;
     // the joined launch waits for every member's inputs and precedes every
     // member's consumers of its partial rows
+    // (an edge to a successor may be programmatic: its edge data is kept)
     std::vector<cudaGraphNode_t> preds, succs;
+    std::vector<cudaGraphEdgeData> succ_ed;
     for (cudaGraphNode_t x : found) {
         size_t np = 0, ns = 0;
         if ((e = cudaGraphNodeGetDependencies(x, nullptr, nullptr, &np)) != cudaSuccess ||
             (e = cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &ns)) != cudaSuccess)
             return e;
         std::vector<cudaGraphNode_t> a(np), b(ns);
-        if (np && (e = cudaGraphNodeGetDependencies(x, a.data(), nullptr, &np)) != cudaSuccess)
+        std::vector<cudaGraphEdgeData> ea(np), eb(ns);
+        if (np && (e = cudaGraphNodeGetDependencies(x, a.data(), ea.data(), &np)) != cudaSuccess)
             return e;
-        if (ns && (e = cudaGraphNodeGetDependentNodes(x, b.data(), nullptr, &ns)) != cudaSuccess)
+        if (ns && (e = cudaGraphNodeGetDependentNodes(x, b.data(), eb.data(), &ns)) != cudaSuccess)
             return e;
-        for (cudaGraphNode_t y : a)
-            if (std::find(preds.begin(), preds.end(), y) == preds.end()) preds.push_back(y);
-        for (cudaGraphNode_t y : b)
-            if (std::find(succs.begin(), succs.end(), y) == succs.end()) succs.push_back(y);
+        for (size_t i = 0; i < np; ++i)
+            if (std::find(preds.begin(), preds.end(), a[i]) == preds.end()) preds.push_back(a[i]);
+        for (size_t i = 0; i < ns; ++i)
+            if (std::find(succs.begin(), succs.end(), b[i]) == succs.end()) {
+                succs.push_back(b[i]);
+                succ_ed.push_back(eb[i]);
+            }
     }
     const PairMember* dm = static_cast<const PairMember*>(d_members);
     int nm = n;
@@ -2138,8 +2144,9 @@ cudaError_t m2l_join_pair_launches(cudaGraph_t g, void* d_members, int* d_prefix
     jp.kernelParams = jargs;
     jp.extra = nullptr;
     if ((e = cudaGraphAddKernelNode(&jnode, g, &pnode, 1, &jp)) != cudaSuccess) return e;
-    for (cudaGraphNode_t y : succs)
-        if ((e = cudaGraphAddDependencies(g, &jnode, &y, nullptr, 1)) != cudaSuccess) return e;
+    for (size_t i = 0; i < succs.size(); ++i)
+        if ((e = cudaGraphAddDependencies(g, &jnode, &succs[i], &succ_ed[i], 1)) != cudaSuccess)
+            return e;
     for (cudaGraphNode_t x : found)
         if ((e = cudaGraphDestroyNode(x)) != cudaSuccess) return e;
     *joined = n;
