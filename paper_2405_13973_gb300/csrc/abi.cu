@@ -865,6 +865,9 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
          dalloc(pl, ws.ticket, sizeof(unsigned)) && dalloc(pl, ws.err, sizeof(int)) &&
          dalloc(pl, ws.steps, sizeof(StepCounter)) && dalloc(pl, ws.stats, sizeof(unsigned long long) * 8) &&
          dalloc(pl, ws.wall_cs, sizeof(double) * 2 * ws.wall_cap);
+    // the leaf histogram starts at zero; every scan of it zeroes what it read
+    if (ok && !dry)
+        ok = cudaMemset(ws.leaf_count, 0, sizeof(int32_t) * pow8(ws.depth_max)) == cudaSuccess;
     if (ok && is_tc(precision)) {
         ws.tc_splits_max = (int)m2l_tc_partial_splits(p, cells, ws.ld);
         int64_t tcap = 0;

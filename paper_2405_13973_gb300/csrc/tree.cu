@@ -69,6 +69,7 @@ __device__ __forceinline__ int leaf_coord(double v, double lo, double side, doub
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ z, int64_t n, int D, const RootCube* root,
                        uint32_t* key, uint32_t* rank, int32_t* leaf_count) {
+    pdl_wait();
     const double lo0 = root->lo[0], lo1 = root->lo[1], lo2 = root->lo[2], side = root->side;
     const double scale = (double)(1 << D);
     const int m = (1 << D) - 1;
@@ -243,13 +244,18 @@ static cudaError_t run_scan(Src src, int64_t total, Workspace& ws, cudaStream_t 
     return cudaGetLastError();
 }
 
-// Leaf histogram -> first slot of every leaf (leaf_start[8^D] = n).
+// Leaf histogram -> first slot of every leaf (leaf_start[8^D] = n).  The
+// histogram is zeroed as it is read (every element is stored by the thread
+// that loaded it, after the load): it is zero again for the next k_keys.
 struct LeafCountScan {
-    const int32_t* count;
+    int32_t* count;
     int32_t* start;
     int64_t ncells;
     __device__ int load(int64_t i) const { return count[i]; }
-    __device__ void store(int64_t i, int ex, int) const { start[i] = ex; }
+    __device__ void store(int64_t i, int ex, int) const {
+        start[i] = ex;
+        count[i] = 0;
+    }
     __device__ void finish(int tot) const { start[ncells] = tot; }
 };
 
@@ -387,11 +393,15 @@ __global__ void k_leaf_gather(const double* __restrict__ x, const double* __rest
 cudaError_t launch_tree(int64_t n, const double* x, const double* y, const double* z,
                         const double* q, int D, Workspace& ws, cudaStream_t s) {
     const int64_t ncells = (int64_t)1 << (3 * D);
-    cudaError_t e = cudaMemsetAsync(ws.leaf_count, 0, sizeof(int32_t) * ncells, s);
-    if (e != cudaSuccess) return e;
+    // the leaf histogram is zero here (zeroed at allocation and by its scans)
+    // the per-ion passes (keys, gather) do FP64 divisions: blocks of 64
+    // threads spread them over every SM (256-thread blocks left 3/4 idle at
+    // 10k ions); the scatter is integer work
     const int grid_ions = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-    k_keys<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(x, y, z, n, D, ws.root, ws.key, ws.rank,
-                                                         ws.leaf_count);
+    const int grid_fp64 = (int)((n + 63) / 64 < 152 * 32 ? (n + 63) / 64 : 152 * 32);
+    cudaError_t e = launch_pdl(k_keys, dim3(grid_fp64 > 0 ? grid_fp64 : 1), dim3(64), 0, s, x, y,
+                               z, n, D, (const RootCube*)ws.root, ws.key, ws.rank, ws.leaf_count);
+    if (e != cudaSuccess) return e;
     LeafCountScan ls{ws.leaf_count, ws.leaf_start, ncells};
     DenseLayout dl = dense_layout(D);
     CellCompaction cc;
@@ -420,12 +430,13 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
                         ws.perm_tmp)) != cudaSuccess)
         return e;
     const int32_t* cid_leaf = ws.cid + dl.off[D];
+    const int gf = grid_fp64 > 0 ? grid_fp64 : 1;
     if (ws.fp64)
-        return launch_pdl(k_leaf_gather<double4_32a>, dim3(g), dim3(256), 0, s, x, y, z, q, n, D,
+        return launch_pdl(k_leaf_gather<double4_32a>, dim3(gf), dim3(64), 0, s, x, y, z, q, n, D,
                           (const RootCube*)ws.root, (const uint32_t*)ws.key,
                           (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
                           ws.perm, ws.slot_of, ws.leaf_of, (double4_32a*)ws.sorted);
-    return launch_pdl(k_leaf_gather<int4>, dim3(g), dim3(256), 0, s, x, y, z, q, n, D,
+    return launch_pdl(k_leaf_gather<int4>, dim3(gf), dim3(64), 0, s, x, y, z, q, n, D,
                       (const RootCube*)ws.root, (const uint32_t*)ws.key,
                       (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
                       ws.perm, ws.slot_of, ws.leaf_of, (int4*)ws.sorted);
@@ -466,7 +477,6 @@ cudaError_t launch_level_counts(int64_t n, const double* x, const double* y, con
     cudaError_t e = launch_bbox(x, y, z, n, ws, s);
     if (e != cudaSuccess) return e;
     const int64_t ncells = (int64_t)1 << (3 * Dm);
-    if ((e = cudaMemsetAsync(ws.leaf_count, 0, sizeof(int32_t) * ncells, s)) != cudaSuccess) return e;
     const int grid_ions = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
     k_keys<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(x, y, z, n, Dm, ws.root, ws.key, ws.rank,
                                                          ws.leaf_count);
