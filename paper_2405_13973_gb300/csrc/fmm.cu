@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(kNfThreads) k_p2p(
 //     tree sums the columns (deterministic).
 // The near field (if any) is added and the field written in the original ion
 // order scaled to SI (k_e / s^2 for E, k_e / s for phi, s = leaf side).
-constexpr int kL2pThreads = 256;
+constexpr int kL2pThreads = 128;
 constexpr int kPmax = (kMaxOrder + 1) * (kMaxOrder + 1);
 
 
