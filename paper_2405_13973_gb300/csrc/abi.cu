@@ -174,6 +174,7 @@ void free_plan(fmm_plan_s* pl) {
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
     Workspace& ws = pl->ws;
     if (ws.side) cudaStreamDestroy(ws.side);
+    if (ws.side2) cudaStreamDestroy(ws.side2);
     for (cudaEvent_t ev : {ws.ev_fork, ws.ev_p2m, ws.ev_items, ws.ev_near})
         if (ev) cudaEventDestroy(ev);
     for (int k = 0; k < fmm_plan_s::kSlots; ++k) {
@@ -919,6 +920,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
         cudaMallocHost(&pl->h_err, sizeof(int)) != cudaSuccess ||
         cudaStreamCreateWithPriority(&pl->cap_stream, cudaStreamNonBlocking, prio_high()) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ws.side, cudaStreamNonBlocking, prio_low()) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ws.side2, cudaStreamNonBlocking, prio_low()) != cudaSuccess ||
         cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ws.ev_p2m, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ws.ev_items, cudaEventDisableTiming) != cudaSuccess ||

@@ -321,6 +321,152 @@ __global__ void __launch_bounds__(128) k_m2m(int l, int P, int ld, const LevelIn
 }
 
 // ---------------------------------------------------------------------------
+// M2M and L2L of the small upper levels on the tensor-core paths, on the CUDA
+// cores: out[g][r] (+)= sum_t Op[r][t] x_g[t], with
+//   M2M (MODE 0): x_g = the M of parent g's eight children side by side
+//                 (t = o P + c; absent children zero), Op = [T_0 ... T_7];
+//   L2L (MODE 1): x_g = the L of child g's parent, Op = T_octant(g), added
+//                 to the child's own M2L sum already in L.
+// A level of a few dozen or hundred cells is latency work: a launch of the
+// persistent tensor-core kernel (TMEM and barrier set-up, operator copies
+// from DRAM, one partial per octant and a reduction for M2M) costs more than
+// the products.  A block holds rows r0 .. r0 + 15 of the operator in shared
+// memory (staged before the programmatic wait: operators are constants) and
+// applies them to runs of kShCells cells; warp w owns rows w and w + 8, its
+// lanes split the dot products and a butterfly sums them (every lane gets the
+// same value: the order is fixed, results are deterministic).
+// ---------------------------------------------------------------------------
+constexpr int kShRows = 16;
+constexpr int kShThreads = 256;
+template <int MODE>
+struct ShCells { static constexpr int v = MODE == 0 ? 8 : 16; };
+
+// 4-byte asynchronous copy global -> shared (zero-filled when !valid): the
+// staging loops issue every copy before waiting once
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// row stride of the staged operator: K rounded up to 2 mod 32 (the M2M
+// staging writes two values of t for 16 rows per warp without conflicts)
+__host__ __device__ inline int sh_stride(int K) { return K + ((2 - K % 32) % 32 + 32) % 32; }
+
+template <typename T, int MODE>
+size_t shift_rows_smem(int P) {
+    const int K = MODE == 0 ? 8 * P : P;
+    return (size_t)(kShRows * sh_stride(K) + ShCells<MODE>::v * K) * sizeof(T);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kShThreads) k_shift_rows(int l, int P, int ld,
+                                                           const LevelInfo* linfo,
+                                                           const uint32_t* __restrict__ code,
+                                                           const int32_t* __restrict__ cid,
+                                                           int64_t off_nb,
+                                                           const T* __restrict__ Op, T* Y) {
+    static_assert(sizeof(T) == 4, "FP32 plans only (4-byte asynchronous copies)");
+    constexpr int CG = ShCells<MODE>::v;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_src[CG * (MODE == 0 ? 8 : 1)];
+    const int K = MODE == 0 ? 8 * P : P, S = sh_stride(K);
+    T* sOp = reinterpret_cast<T*>(smem_raw);  // [kShRows][S]
+    T* sX = sOp + kShRows * S;                // [CG][K]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * kShRows;
+    const int oct = MODE == 1 ? (int)blockIdx.y : 0;
+    if (MODE == 0) {
+        // Op = T_m2m transposed, [o][c][r]: element (r, t = o P + c) at t P + r
+        for (int e = tid; e < K * kShRows; e += kShThreads) {
+            const int t = e >> 4, rr = e & 15, r = r0 + rr;
+            cp_async4(&sOp[rr * S + t], Op + (int64_t)t * P + (r < P ? r : 0), r < P);
+        }
+    } else {
+        const T* To = Op + (int64_t)oct * P * P;  // T_l2l row-major [o][r][c]
+        for (int rr = w; rr < kShRows; rr += kShThreads / 32) {
+            const int r = r0 + rr;
+            for (int c = lane; c < K; c += 32)
+                cp_async4(&sOp[rr * S + c], To + (int64_t)(r < P ? r : 0) * P + c, r < P);
+        }
+    }
+    pdl_wait();
+    int g0, g1;
+    if (MODE == 0) {
+        g0 = linfo->gbase[l];
+        g1 = linfo->gbase[l + 1];
+    } else {
+        g0 = linfo->oct_start[l][oct];
+        g1 = linfo->oct_start[l][oct + 1];
+    }
+    const int nch = (g1 - g0 + CG - 1) / CG;
+    const int ch0 = MODE == 0 ? (int)blockIdx.y : (int)blockIdx.z;
+    const int chs = MODE == 0 ? (int)gridDim.y : (int)gridDim.z;
+    const T* op0 = sOp + w * S;
+    const T* op1 = sOp + (w + 8) * S;
+    for (int ch = ch0; ch < nch; ch += chs) {
+        const int gb = g0 + ch * CG, nc = min(CG, g1 - gb);
+        __syncthreads();  // the previous run is done with sX and s_src
+        if (MODE == 0) {
+            if (tid < CG * 8) {
+                const int ci = tid >> 3, o = tid & 7;
+                s_src[tid] = ci < nc ? cid[off_nb + (((int64_t)code[gb + ci] << 3) | o)] : -1;
+            }
+        } else if (tid < CG) {
+            s_src[tid] = tid < nc ? cid[off_nb + (code[gb + tid] >> 3)] : -1;
+        }
+        __syncthreads();
+        // x rows: (cell, octant) of M2M, one per cell for L2L
+        for (int q = w; q < CG * (MODE == 0 ? 8 : 1); q += kShThreads / 32) {
+            const int src = s_src[q];
+            T* dst = sX + (MODE == 0 ? (q >> 3) * K + (q & 7) * P : q * K);
+            const T* from = Y + (int64_t)(src >= 0 ? src : 0) * ld;
+            for (int c = lane; c < P; c += 32) cp_async4(&dst[c], from + c, src >= 0);
+        }
+        cp_async_wait_all();  // this thread's copies (and, first time round, the operator's)
+        __syncthreads();
+        T a0[CG], a1[CG];
+#pragma unroll
+        for (int ci = 0; ci < CG; ++ci) a0[ci] = a1[ci] = T(0);
+        for (int t = lane; t < K; t += 32) {
+            const T u0 = op0[t], u1 = op1[t];
+#pragma unroll
+            for (int ci = 0; ci < CG; ++ci) {
+                const T x = sX[ci * K + t];
+                a0[ci] += u0 * x;
+                a1[ci] += u1 * x;
+            }
+        }
+        T v0 = T(0), v1 = T(0);
+#pragma unroll
+        for (int ci = 0; ci < CG; ++ci) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                a0[ci] += __shfl_xor_sync(0xffffffffu, a0[ci], o);
+                a1[ci] += __shfl_xor_sync(0xffffffffu, a1[ci], o);
+            }
+            if (lane == ci) {
+                v0 = a0[ci];
+                v1 = a1[ci];
+            }
+        }
+        if (lane < nc) {  // lane ci stores cell ci's rows w and w + 8
+            T* y = Y + (int64_t)(gb + lane) * ld;
+            const int ra = r0 + w, rb = r0 + w + 8;
+            if (MODE == 0) {
+                if (ra < P) y[ra] = v0;
+                if (rb < P) y[rb] = v1;
+            } else {
+                if (ra < P) y[ra] += v0;
+                if (rb < P) y[rb] += v1;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // M2L (+ folded L2L) on the CUDA cores: block = 64 output rows x 32 targets of
 // one octant; loops over the 189 offsets (and the parent shift), each a
 // 64 x P x 32 product staged through shared memory.
@@ -949,32 +1095,42 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     // P2P on the side stream: after P2M on the CUDA-core paths (beside their
     // M2L); on the tensor-core path after the M2L kernel, which needs every
     // SM, beside the slab reduction and the L2L launches, which use few
+    // On the tensor-core paths the near field takes a third stream from the
+    // fork, beside the upward pass and the work list (both latency-bound).
+    const bool near_early = fork && use_tc && ws.side2 != nullptr;
+    cudaStream_t snf = near_early ? ws.side2 : sn;
     auto launch_near = [&](bool after_event) -> cudaError_t {
         cudaError_t r;
-        if (fork && after_event && (r = cudaStreamWaitEvent(sn, ws.ev_p2m, 0)) != cudaSuccess)
+        if (fork && after_event && (r = cudaStreamWaitEvent(snf, ws.ev_p2m, 0)) != cudaSuccess)
             return r;
-        if (ws.kev[2] && (r = cudaEventRecordWithFlags(ws.kev[2], sn, cudaEventRecordExternal)) !=
+        if (ws.kev[2] && (r = cudaEventRecordWithFlags(ws.kev[2], snf, cudaEventRecordExternal)) !=
                              cudaSuccess)
             return r;
-        k_p2p<T><<<leaf_grid, kNfThreads, 0, sn>>>(D, ws.linfo,
-                                                  (const typename Ion<T>::rec*)ws.sorted, ws.code,
-                                                  ws.cid + dl.off[D], ws.cstart, ws.ccount, near);
+        k_p2p<T><<<leaf_grid, kNfThreads, 0, snf>>>(D, ws.linfo,
+                                                   (const typename Ion<T>::rec*)ws.sorted, ws.code,
+                                                   ws.cid + dl.off[D], ws.cstart, ws.ccount, near);
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
-        if (ws.kev[3] && (r = cudaEventRecordWithFlags(ws.kev[3], sn, cudaEventRecordExternal)) !=
+        if (ws.kev[3] && (r = cudaEventRecordWithFlags(ws.kev[3], snf, cudaEventRecordExternal)) !=
                              cudaSuccess)
             return r;
-        if (fork && (r = cudaEventRecord(ws.ev_near, sn)) != cudaSuccess) return r;
+        if (fork && (r = cudaEventRecord(ws.ev_near, snf)) != cudaSuccess) return r;
         return cudaSuccess;
     };
-    const bool near_late = fork && use_tc;
-    if (nf && !near_late) {
+    if (nf && near_early) {
+        if ((e = cudaStreamWaitEvent(snf, ws.ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = launch_near(false)) != cudaSuccess) return e;
+    }
+    const bool near_late = fork && use_tc && !near_early;
+    if (nf && !near_late && !near_early) {
         if (fork && (e = cudaEventRecord(ws.ev_p2m, s)) != cudaSuccess) return e;
         if ((e = launch_near(true)) != cudaSuccess) return e;
     }
     if (far) {
         for (int l = lmin_p2m - 1; l >= 2; --l) {
             if (use_tc) {
-                if ((e = launch_m2m_tc(n, D, l, ws, s)) != cudaSuccess) return e;
+                e = level_cap(n, l) <= kShiftSmallM2M ? launch_shift_small(0, n, D, l, ws, s)
+                                                      : launch_m2m_tc(n, D, l, ws, s);
+                if (e != cudaSuccess) return e;
                 continue;
             }
             int64_t cl = (int64_t)1 << (3 * l);
@@ -1048,6 +1204,30 @@ cudaError_t launch_fmm_phased(int64_t n, int D, int phases, Workspace& ws, bool 
 cudaError_t launch_fmm(int64_t n, int D, int phases, Workspace& ws, bool use_tc, double* E,
                        double* phi, cudaStream_t s) {
     return launch_fmm_phased(n, D, phases, ws, use_tc, E, phi, s, nullptr);
+}
+
+// M2M into level l (mode 0) or L2L into level l (mode 1) of a small level of
+// the tensor-core paths on the CUDA cores (k_shift_rows; FP32 plans).
+cudaError_t launch_shift_small(int mode, int64_t n, int D, int l, Workspace& ws, cudaStream_t s) {
+    const int P = ws.P;
+    const DenseLayout dl = dense_layout(D);
+    const unsigned rg = (unsigned)((P + kShRows - 1) / kShRows);
+    const int64_t cl = (int64_t)1 << (3 * l);
+    const int64_t cells = n < cl ? n : cl;
+    if (mode == 0) {
+        const int64_t ch = (cells + ShCells<0>::v - 1) / ShCells<0>::v;
+        return launch_pdl(k_shift_rows<float, 0>, dim3(rg, (unsigned)(ch < 16 ? ch : 16)),
+                          dim3(kShThreads), shift_rows_smem<float, 0>(P), s, l, P, ws.ld,
+                          (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code,
+                          (const int32_t*)ws.cid, dl.off[l + 1], (const float*)ws.T_m2m,
+                          (float*)ws.M);
+    }
+    // per octant: runs of 16 children, a few blocks per octant
+    const int64_t ch = (cells + ShCells<1>::v * 8 - 1) / (ShCells<1>::v * 8);
+    return launch_pdl(k_shift_rows<float, 1>, dim3(rg, 8, (unsigned)(ch < 4 ? (ch > 0 ? ch : 1) : 4)),
+                      dim3(kShThreads), shift_rows_smem<float, 1>(P), s, l, P, ws.ld,
+                      (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code, (const int32_t*)ws.cid,
+                      dl.off[l - 1], (const float*)ws.T_l2l, (float*)ws.L);
 }
 
 // ---------------------------------------------------------------------------
@@ -1203,6 +1383,14 @@ cudaError_t upload_harmonic_tables() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_p2m_anc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kP2mAncIons * pmax * (int)sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_shift_rows<float, 0>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shift_rows_smem<float, 0>(pmax));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_shift_rows<float, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)shift_rows_smem<float, 1>(pmax));
     return e;
 }
 

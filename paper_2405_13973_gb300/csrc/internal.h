@@ -94,6 +94,7 @@ struct Workspace {
     // which overlap the main chain; events of the fork and the joins
     // (ev_p2m: when the near field may start)
     cudaStream_t side = nullptr;
+    cudaStream_t side2 = nullptr;  // the near field of the tensor-core paths
     cudaEvent_t ev_fork = nullptr, ev_p2m = nullptr, ev_items = nullptr, ev_near = nullptr;
     int32_t* block_sums = nullptr; // scan scratch
     int64_t block_sums_cap = 0;
@@ -238,6 +239,16 @@ void m2l_tc_pack_operands(int p, bool bf16, const double* T_m2l, const double* T
                           const double* T_l2l, void* out);
 // M2M of one level (targets = parents at level l) on the tensor cores.
 cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s);
+// M2M (mode 0, targets at level l) or L2L (mode 1, into level l) of a small
+// level on the CUDA cores, for the FP32 plans of the tensor-core paths: up to
+// kShiftSmallM2M parents / kShiftSmallL2L children (capacity bounds).
+constexpr int64_t kShiftSmallM2M = 64;
+constexpr int64_t kShiftSmallL2L = 512;
+inline int64_t level_cap(int64_t n, int l) {
+    const int64_t c = (int64_t)1 << (3 * l);
+    return n < c ? n : c;
+}
+cudaError_t launch_shift_small(int mode, int64_t n, int D, int l, Workspace& ws, cudaStream_t s);
 void host_m2l_offsets(int16_t out[8][189]);
 
 // ---- push (push.cu) ----------------------------------------------------------

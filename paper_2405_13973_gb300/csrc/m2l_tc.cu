@@ -1915,6 +1915,11 @@ cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t
 static cudaError_t launch_l2l_levels(int64_t n, int D, Workspace& ws, int l2l_last, int smem,
                                      cudaStream_t s) {
     for (int l = 3; l <= l2l_last && l <= D; ++l) {
+        if (level_cap(n, l) <= kShiftSmallL2L) {
+            cudaError_t e = launch_shift_small(1, n, D, l, ws, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         TcArgs b = base_args(n, D, ws, 1);
         b.mode = MODE_L2L;
         b.level = l;

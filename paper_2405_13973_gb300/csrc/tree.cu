@@ -12,6 +12,7 @@
 //      leaf-relative scaled coordinates and charges into sorted slots.
 // All grids are sized by the plan's capacities, not by device-side counts, so
 // the whole sequence can be captured in a CUDA graph.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "harmonics.cuh"
@@ -218,15 +219,100 @@ __global__ void __launch_bounds__(kScan1Threads) k_scan_single(Src src, int64_t 
     scan_single_body(src, total);
 }
 
-// Two dependent single-block scans in one launch: b's loads read what a's
-// stores wrote (made visible to the block by the barrier between them).
-template <class SrcA, class SrcB>
-__global__ void __launch_bounds__(kScan1Threads) k_scan_single2(SrcA a, int64_t total_a, SrcB b,
-                                                                 int64_t total_b) {
-    pdl_wait();
-    scan_single_body(a, total_a);
+// Two dependent scans in one launch on a cluster of kScanCtas CTAs (the work
+// of one block spread over eight SMs): each CTA scans its contiguous
+// share in registers, the CTAs' totals are exchanged through distributed
+// shared memory after a cluster barrier (each CTA adds those of the lower
+// ranks), and a second barrier makes every CTA's stores visible to the whole
+// cluster before the next scan loads them (through L2: __ldcg).
+constexpr int kScanCtas = 8;
+constexpr int kScanCtaThreads = 1024;
+constexpr int kScanCtaItems = kScan1Max / (kScanCtas * kScanCtaThreads);
+
+template <class Src>
+__device__ __forceinline__ void scan_cluster_body(const Src& src, int64_t total, int* warp_tot,
+                                                  int* cta_tot, int* s_tot) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), nr = (int)cl.num_blocks();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t share = (total + nr - 1) / nr;
+    const int64_t b0 = min(total, (int64_t)rank * share), b1 = min(total, b0 + share);
+    const int ipt = (int)((b1 - b0 + kScanCtaThreads - 1) / kScanCtaThreads);
+    const int64_t base = b0 + (int64_t)threadIdx.x * ipt;
+    int vals[kScanCtaItems];
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanCtaItems; ++k) {  // all loads in flight at once
+        const int64_t i = base + k;
+        vals[k] = (k < ipt && i < b1) ? src.load(i) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanCtaItems; ++k) acc += vals[k];
+    int x = acc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
-    scan_single_body(b, total_b);
+    if (wid == 0) {
+        int w = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int ex = (wid > 0 ? warp_tot[wid - 1] : 0) + x - acc;
+    if (threadIdx.x == 0) *cta_tot = warp_tot[kScanCtaThreads / 32 - 1];
+    cl.sync();  // every CTA's total is in its shared memory
+    if (threadIdx.x < nr) s_tot[threadIdx.x] = *cl.map_shared_rank(cta_tot, (unsigned)threadIdx.x);
+    __syncthreads();
+    int all = 0;
+    for (int r = 0; r < nr; ++r) {
+        if (r == rank) ex += all;
+        all += s_tot[r];
+    }
+#pragma unroll
+    for (int k = 0; k < kScanCtaItems; ++k) {
+        const int64_t i = base + k;
+        if (k < ipt && i < b1) src.store(i, ex, vals[k]);
+        ex += vals[k];
+    }
+    if (rank == nr - 1 && threadIdx.x == 0) src.finish(all);
+    cl.sync();  // the stores are visible cluster-wide; cta_tot and s_tot are free again
+}
+
+template <class SrcA, class SrcB>
+__global__ void __launch_bounds__(kScanCtaThreads) k_scan_cluster2(SrcA a, int64_t total_a, SrcB b,
+                                                                  int64_t total_b) {
+    __shared__ int warp_tot[kScanCtaThreads / 32];
+    __shared__ int cta_tot, s_tot[kScanCtas];
+    pdl_wait();
+    scan_cluster_body(a, total_a, warp_tot, &cta_tot, s_tot);
+    scan_cluster_body(b, total_b, warp_tot, &cta_tot, s_tot);
+}
+
+// a cluster launch of kScanCtas CTAs, programmatic (see launch_pdl)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_scan_cluster(void (*k)(KArgs...), cudaStream_t s, Args... args) {
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kScanCtas;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kScanCtas);
+    cfg.blockDim = dim3(kScanCtaThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
 template <class Src>
@@ -283,8 +369,10 @@ struct CellCompaction {
     __device__ int range(int l, uint32_t c, int& first) const {
         int sh = 3 * (D - l);
         int64_t a = (int64_t)c << sh, b = ((int64_t)c + 1) << sh;
-        first = leaf_start[a];
-        return leaf_start[b] - first;
+        // written by the leaf scan of the same launch, possibly by another
+        // CTA of the cluster: read through L2
+        first = __ldcg(&leaf_start[a]);
+        return __ldcg(&leaf_start[b]) - first;
     }
     __device__ int load(int64_t v) const {
         int l;
@@ -415,10 +503,10 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
     cc.lmin = dl.lmin;
     for (int l = 0; l < kMaxDepth + 2; ++l) cc.off[l] = dl.off[l];
     // the cell compaction reads only the leaf starts: both scans in one
-    // single-block launch when they fit, then the scatter
+    // cluster launch when they fit, then the scatter
     if (ncells <= kScan1Max && dl.total <= kScan1Max) {
-        if ((e = launch_pdl(k_scan_single2<LeafCountScan, CellCompaction>, dim3(1),
-                            dim3(kScan1Threads), 0, s, ls, ncells, cc, dl.total)) != cudaSuccess)
+        if ((e = launch_scan_cluster(k_scan_cluster2<LeafCountScan, CellCompaction>, s, ls,
+                                     ncells, cc, dl.total)) != cudaSuccess)
             return e;
     } else {
         if ((e = run_scan(ls, ncells, ws, s)) != cudaSuccess) return e;
