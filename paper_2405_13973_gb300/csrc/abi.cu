@@ -831,7 +831,14 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
     ws.cells_max = cells;
     ws.dense_max = dense;
     ws.block_sums_cap = (dense + kScanTile - 1) / kScanTile + 16;
-    ws.bbox_blocks = 152 * 4;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            sms > 0)
+            ws.sms = sms;
+    }
+    ws.bbox_blocks = ws.sms * 4;
     ws.wall_cap = kWallChunk;
     const size_t tsz = ws.fp64 ? sizeof(double) : sizeof(float);
     const size_t PP = (size_t)pl->P * pl->P;

@@ -17,13 +17,13 @@
 namespace pt {
 
 constexpr int kBboxWords = 8;  // [0..2] ~key of the minimum, [3..5] key of the maximum, [6] bad
-constexpr int kBboxThreads = 64;  // small blocks: the FP64 work of a pass spreads over every SM
+constexpr int kBboxThreads = 128;
 
-// blocks of a bounding-box pass over n points
-inline int bbox_grid(int64_t n, const Workspace& ws) {
-    int64_t g = (n + kBboxThreads - 1) / kBboxThreads;
-    if (g > ws.bbox_blocks) g = ws.bbox_blocks;
-    return g > 0 ? (int)g : 1;
+// blocks of a bounding-box pass over n points: equal shares over the SMs
+// (ion_split), at most bbox_blocks (each block folds into the accumulator
+// with a few atomics)
+inline IonSplit bbox_split(int64_t n, const Workspace& ws) {
+    return ion_split(n, kBboxThreads, ws.sms, ws.bbox_blocks);
 }
 
 __device__ __forceinline__ unsigned long long ord_key(double v) {

@@ -850,11 +850,91 @@ __device__ __forceinline__ void l2p_columns(int p, int m, unsigned hw_mask, T x,
     }
 }
 
+// The same sums on an 8-lane group (p <= 15): lane j takes column j and, if
+// p - j > j, column p - j, about p + 2 recurrence steps on every lane instead
+// of p + 1 - m on a lane per column (on 16 lanes half the lane steps idle).
+// Diagonals: lanes hold w_j = (x + i y) c_j and w_{8+j}; two inclusive prefix
+// products over the group give Y_j^j and prod_{k=8..8+j} w_k, and Y_m^m for
+// m >= 8 is Y_7^7 times the latter (one more rounding than the sequential
+// product; every lane fetches its second diagonal by one shuffle).
+template <typename T>
+__device__ __forceinline__ void l2p_col_run(int p, int m, T yr, T yi, T z, T r2,
+                                            const HarmTables<T>& t, const T (*D4)[kPmax], T& ph,
+                                            T& ax, T& ay, T& az) {
+    T y1r = 0, y1i = 0;  // Y_{n-1}^m
+    for (int nn = m; nn <= p; ++nn) {
+        if (nn == m + 1) {
+            y1r = yr;
+            y1i = yi;
+            yr = z * t.d[m] * y1r;
+            yi = z * t.d[m] * y1i;
+        } else if (nn > m + 1) {
+            const T a = t.a[nn][m] * z, b = t.b[nn][m] * r2;
+            const T cr = a * yr - b * y1r, ci = a * yi - b * y1i;
+            y1r = yr;
+            y1i = yi;
+            yr = cr;
+            yi = ci;
+        }
+        const int k = re_idx(nn, m);
+        ph += D4[0][k] * yr;
+        ax += D4[1][k] * yr;
+        ay += D4[2][k] * yr;
+        az += D4[3][k] * yr;
+        if (m > 0) {
+            ph += D4[0][k + 1] * yi;
+            ax += D4[1][k + 1] * yi;
+            ay += D4[2][k + 1] * yi;
+            az += D4[3][k + 1] * yi;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void l2p_columns8(int p, int j, unsigned gmask, T x, T y, T z,
+                                             const HarmTables<T>& t, const T (*D4)[kPmax], T& ph,
+                                             T& ax, T& ay, T& az) {
+    T ar = T(1), ai = T(0), br = T(1), bi = T(0);
+    if (j >= 1 && j <= p) {
+        ar = x * t.c[j];
+        ai = y * t.c[j];
+    }
+    if (8 + j <= p) {
+        br = x * t.c[8 + j];
+        bi = y * t.c[8 + j];
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+        const T oar = __shfl_up_sync(gmask, ar, off, 8), oai = __shfl_up_sync(gmask, ai, off, 8);
+        const T obr = __shfl_up_sync(gmask, br, off, 8), obi = __shfl_up_sync(gmask, bi, off, 8);
+        if (j >= off) {
+            const T r = oar * ar - oai * ai;
+            ai = oar * ai + oai * ar;
+            ar = r;
+            const T s2 = obr * br - obi * bi;
+            bi = obr * bi + obi * br;
+            br = s2;
+        }
+    }
+    const T d7r = __shfl_sync(gmask, ar, 7, 8), d7i = __shfl_sync(gmask, ai, 7, 8);
+    const T er = d7r * br - d7i * bi, ei = d7r * bi + d7i * br;  // Y_{8+j}^{8+j}
+    const int m2 = p - j;
+    const int src = m2 >= 8 ? m2 - 8 : (m2 >= 0 ? m2 : 0);
+    const T gar = __shfl_sync(gmask, ar, src, 8), gai = __shfl_sync(gmask, ai, src, 8);
+    const T ger = __shfl_sync(gmask, er, src, 8), gei = __shfl_sync(gmask, ei, src, 8);
+    ph = ax = ay = az = T(0);
+    const T r2 = x * x + y * y + z * z;
+    if (j <= m2) l2p_col_run<T>(p, j, ar, ai, z, r2, t, D4, ph, ax, ay, az);
+    if (m2 > j)
+        l2p_col_run<T>(p, m2, m2 >= 8 ? ger : gar, m2 >= 8 ? gei : gai, z, r2, t, D4, ph, ax, ay,
+                       az);
+}
+
 // nlev = 2: the leaf's expansion holds its own M2L sum only, and the
 // parent's complete expansion is evaluated at the ion in the parent's frame
 // (equal to the L2L shift into the leaf, which shifts a truncated expansion
 // exactly), saving the last L2L launch.
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     int64_t n, int D, int p, int ld, bool far, int nlev, const RootCube* root,
     const LevelInfo* linfo, const uint32_t* __restrict__ code, const int32_t* __restrict__ cid,
@@ -883,10 +963,11 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     }
     __syncthreads();
     const T tE = (T)s_f[0], tP = (T)s_f[1];
-    const int lane = threadIdx.x & 31, m = lane & 15;
-    const int slot_in_pass = threadIdx.x >> 4;        // target of this half-warp
-    constexpr int kPerPass = kL2pThreads / 16;
-    const unsigned hw_mask = 0xffffu << (lane & 16);  // this half-warp's lanes
+    // a group of G lanes per target: G = 8 (p <= 15, l2p_columns8) or 16
+    const int lane = threadIdx.x & 31, m = lane & (G - 1);
+    const int slot_in_pass = threadIdx.x / G;         // target of this group
+    constexpr int kPerPass = kL2pThreads / G;
+    const unsigned hw_mask = (G == 8 ? 0xffu : 0xffffu) << (lane & (32 - G));
     const int P = (p + 1) * (p + 1);
     const int levs = far ? nlev : 0;
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
@@ -905,14 +986,15 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
         __syncthreads();
         for (int t0 = 0; t0 < nt; t0 += kPerPass) {
             const int ti = t0 + slot_in_pass;
-            if (ti >= nt) continue;  // whole half-warps only: the shuffles stay within one
+            if (ti >= nt) continue;  // whole groups only: the shuffles stay within one
             T ex = 0, ey = 0, ez = 0, ph = 0;
             const typename Ion<T>::rec me = sorted[ts + ti];
             for (int lv = 0; lv < levs; ++lv) {
                 T x, y, z, q;
                 ion_in_ancestor(me, lv, ix & lv, iy & lv, iz & lv, x, y, z, q);
                 T cph, cax, cay, caz;
-                l2p_columns<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
+                if (G == 8) l2p_columns8<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
+                else l2p_columns<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
                 // level units -> leaf units: phi / 2^lv, E / 4^lv (exact)
                 const T fp1 = lv == 0 ? T(1) : T(0.5), fe1 = fp1 * fp1;
                 ph += fp1 * cph;
@@ -920,13 +1002,13 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
                 ey -= fe1 * cay;
                 ez -= fe1 * caz;
             }
-            // column sums: a fixed shuffle tree over the half-warp
+            // column sums: a fixed shuffle tree over the group
 #pragma unroll
-            for (int off = 8; off > 0; off >>= 1) {
-                ex += __shfl_xor_sync(hw_mask, ex, off, 16);
-                ey += __shfl_xor_sync(hw_mask, ey, off, 16);
-                ez += __shfl_xor_sync(hw_mask, ez, off, 16);
-                ph += __shfl_xor_sync(hw_mask, ph, off, 16);
+            for (int off = G / 2; off > 0; off >>= 1) {
+                ex += __shfl_xor_sync(hw_mask, ex, off, G);
+                ey += __shfl_xor_sync(hw_mask, ey, off, G);
+                ez += __shfl_xor_sync(hw_mask, ez, off, G);
+                ph += __shfl_xor_sync(hw_mask, ph, off, G);
             }
             if (m == 0) {
                 // near + far and the SI scale in T: in FP32 one conversion per
@@ -1181,7 +1263,8 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
             (const typename Ion<T>::rec*)ws.sorted, ws.perm, ws.cstart, ws.ccount, L,
             nf ? near : nullptr, E, phi);
     else
-        e = launch_pdl(k_l2p<T>, dim3(leaf_grid), dim3(kL2pThreads), 0, s, n, D, p, ws.ld, far,
+        e = launch_pdl(p <= 15 ? k_l2p<T, 8> : k_l2p<T, 16>, dim3(leaf_grid), dim3(kL2pThreads),
+                       0, s, n, D, p, ws.ld, far,
                        use_tc && D >= 3 ? 2 : 1, (const RootCube*)ws.root,
                        (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code,
                        (const int32_t*)ws.cid, (const typename Ion<T>::rec*)ws.sorted,

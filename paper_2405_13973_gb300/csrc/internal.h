@@ -33,6 +33,29 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
     return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
 }
 
+// Blocks of a per-ion FP64 pass (FP64 is scarce on this GPU: a few results
+// per SM per cycle): a multiple of the SM count where the ions allow, each
+// block an equal contiguous share [blockIdx.x * per, min(n, (blockIdx.x + 1) *
+// per)) of about `cap` ions at most (at least about 16), so that every SM's
+// FP64 pipes get the same work; max_blocks bounds the grid (then per > cap).
+struct IonSplit {
+    int grid;
+    int64_t per;
+};
+inline IonSplit ion_split(int64_t n, int cap, int sms, int64_t max_blocks) {
+    const int64_t w = (int64_t)sms * cap;
+    int64_t g = (int64_t)sms * ((n + w - 1) / w);
+    const int64_t gmin = (n + 15) / 16;
+    if (g > gmin) g = gmin;
+    if (g > max_blocks) g = max_blocks;
+    if (g < 1) g = 1;
+    IonSplit r;
+    r.grid = (int)g;
+    r.per = (n + g - 1) / g;
+    if (r.per < 1) r.per = 1;
+    return r;
+}
+
 constexpr int kMaxDepth = 8;      // uniform octree depth limit (8^8 leaf cells)
 constexpr int kMaxOrder = 16;     // expansion order limit
 constexpr int kScanTile = 2048;   // elements per block in the device scans
@@ -70,6 +93,7 @@ struct Workspace {
     int ld = 0;                 // row stride of M and L (P for FP64, P rounded up to 32 for FP32)
     bool fp64 = true;
     int64_t cells_max = 0;      // capacity of the compact cell arrays
+    int sms = 152;              // multiprocessors of the plan's device
     int64_t dense_max = 0;      // capacity of the concatenated dense maps
 
     uint32_t* key = nullptr;       // [n] leaf key of every ion (original order)

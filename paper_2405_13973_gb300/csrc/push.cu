@@ -121,15 +121,16 @@ __device__ __forceinline__ void gyrate(const PushParams& pp, double& x, double& 
 
 // First half-drift of a step, fused with the bounding cube of the midpoint
 // positions; the finalising thread also advances the step counter.
-__global__ void __launch_bounds__(kBboxThreads) k_drift_bbox(int64_t n, double* x, double* y,
-                                                             double* z, double* vx, double* vy,
-                                                             const double* vz, PushParams pp,
+__global__ void __launch_bounds__(kBboxThreads) k_drift_bbox(int64_t n, int64_t per, double* x,
+                                                             double* y, double* z, double* vx,
+                                                             double* vy, const double* vz,
+                                                             PushParams pp,
                                                              unsigned long long* acc,
                                                              unsigned* ticket, RootCube* root,
                                                              int* err, StepCounter* steps) {
     BboxAcc t;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i];
         gyrate(pp, px, py, pz, ux, uy, vz[i]);
         x[i] = px;
@@ -146,42 +147,49 @@ __global__ void __launch_bounds__(kBboxThreads) k_drift_bbox(int64_t n, double* 
 }
 
 // Kick (Eq. velocity_kick with the laser kicks of Eq. laser_kick) and the
-// second half-drift.  A block takes 32 ions at a time with one warp per beam:
-// warp l draws beam l's photon counts (the rate and Poisson draw, the bulk
-// of the FP64 work), then warp 0 adds the recoils of the beams in order,
-// kicks and drifts, exactly the sequence of laser_ion per ion.
-constexpr int kKickIons = 32;
-__global__ void __launch_bounds__(32 * PT_MAX_BEAMS) k_kick_drift(
-    int64_t n, double* x, double* y, double* z, double* vx, double* vy, double* vz,
+// second half-drift.  A block takes an equal contiguous share of the ions
+// (ion_split: FP64 is the bound, so every SM gets the same amount) in runs of
+// kKickIons: the block's threads first draw the photon counts of every
+// (beam, ion) pair of the run in parallel (the rate and Poisson draw, the
+// bulk of the FP64 work), then one thread per ion adds the recoils of the
+// beams in order, kicks and drifts, exactly the sequence of laser_ion.
+constexpr int kKickIons = 128;
+constexpr int kKickThreads = 256;
+__global__ void __launch_bounds__(kKickThreads) k_kick_drift(
+    int64_t n, int64_t per, double* x, double* y, double* z, double* vx, double* vy, double* vz,
     const double* __restrict__ q, const double* __restrict__ E, PushParams pp, pt_laser laser,
     const StepCounter* steps, const double* __restrict__ wall_cs) {
     pdl_wait();
     __shared__ int s_cnt[PT_MAX_BEAMS][kKickIons];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const bool lasers = laser.enabled && laser.n_beams > 0;
+    const int nb = lasers ? laser.n_beams : 0;
     const int64_t step = steps->cur;
     const int64_t widx = step - steps->base;
     const double c = wall_cs[2 * widx], s = wall_cs[2 * widx + 1];
     const double kw = 0.5 * pp.kz * pp.delta;
-    for (int64_t g0 = (int64_t)blockIdx.x * kKickIons; g0 < n; g0 += (int64_t)gridDim.x * kKickIons) {
-        const int64_t i = g0 + lane;
+    const int64_t b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+    for (int64_t r0 = b0; r0 < b1; r0 += kKickIons) {
+        const int nr = (int)min((int64_t)kKickIons, b1 - r0);
         if (lasers) {
-            if (w < laser.n_beams && i < n)
-                s_cnt[w][lane] = beam_count(laser, i, step, pp.dt, w, y[i], z[i], vx[i], vy[i], vz[i]);
+            for (int j = threadIdx.x; j < nb * nr; j += kKickThreads) {
+                const int l = j / nr, k = j - l * nr;
+                const int64_t i = r0 + k;
+                s_cnt[l][k] = beam_count(laser, i, step, pp.dt, l, y[i], z[i], vx[i], vy[i], vz[i]);
+            }
             __syncthreads();
         }
-        if (w == 0 && i < n) {
+        for (int k = threadIdx.x; k < nr; k += kKickThreads) {
+            const int64_t i = r0 + k;
             double px = x[i], py = y[i], pz = z[i], ux = vx[i], uy = vy[i], uz = vz[i];
             double etx = 0.5 * pp.kz * px, ety = 0.5 * pp.kz * py, etz = -pp.kz * pz;
             double ewx = -kw * (px * c - py * s);
             double ewy = -kw * (-py * c - px * s);
             double Fx = etx + ewx, Fy = ety + ewy, Fz = etz;
             double dx = 0.0, dy = 0.0, dz = 0.0;
-            if (lasers)
-                for (int l = 0; l < laser.n_beams; ++l) {
-                    const int cnt = s_cnt[l][lane];
-                    if (cnt != 0) beam_recoil(laser, pp.rk, i, step, l, cnt, dx, dy, dz);
-                }
+            for (int l = 0; l < nb; ++l) {
+                const int cnt = s_cnt[l][k];
+                if (cnt != 0) beam_recoil(laser, pp.rk, i, step, l, cnt, dx, dy, dz);
+            }
             double qm = q[i] / pp.mass;
             ux = ux + qm * (E[i] + Fx) * pp.dt + dx;
             uy = uy + qm * (E[n + i] + Fy) * pp.dt + dy;
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(32 * PT_MAX_BEAMS) k_kick_drift(
             vy[i] = uy;
             vz[i] = uz;
         }
-        if (lasers) __syncthreads();  // s_cnt is rewritten for the next 32 ions
+        if (lasers) __syncthreads();  // s_cnt is rewritten for the next run
     }
 }
 
@@ -229,18 +237,17 @@ static int grid_for(int64_t n, int threads) {
 
 cudaError_t launch_drift_bbox(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const PushParams& pp, Workspace& ws, cudaStream_t s) {
-    k_drift_bbox<<<bbox_grid(n, ws), kBboxThreads, 0, s>>>(n, x, y, z, vx, vy, vz, pp, ws.bbox_acc,
-                                                          ws.ticket, ws.root, ws.err, ws.steps);
+    const IonSplit sp = bbox_split(n, ws);
+    k_drift_bbox<<<sp.grid, kBboxThreads, 0, s>>>(n, sp.per, x, y, z, vx, vy, vz, pp, ws.bbox_acc,
+                                                  ws.ticket, ws.root, ws.err, ws.steps);
     return cudaGetLastError();
 }
 
 cudaError_t launch_kick_drift(int64_t n, double* x, double* y, double* z, double* vx, double* vy,
                               double* vz, const double* q, const double* E, const PushParams& pp,
                               const pt_laser& laser, Workspace& ws, cudaStream_t s) {
-    const int nb = laser.enabled && laser.n_beams > 0 ? laser.n_beams : 1;
-    int64_t g = (n + kKickIons - 1) / kKickIons;
-    if (g > 152 * 16) g = 152 * 16;
-    return launch_pdl(k_kick_drift, dim3(g > 0 ? (int)g : 1), dim3(32 * nb), 0, s, n, x, y, z, vx,
+    const IonSplit sp = ion_split(n, kKickIons, ws.sms, (int64_t)1 << 30);
+    return launch_pdl(k_kick_drift, dim3(sp.grid), dim3(kKickThreads), 0, s, n, sp.per, x, y, z, vx,
                       vy, vz, q, E, pp, laser, (const StepCounter*)ws.steps,
                       (const double*)ws.wall_cs);
 }

@@ -40,19 +40,19 @@ DenseLayout dense_layout(int D) {
 __global__ void __launch_bounds__(kBboxThreads) k_bbox(const double* __restrict__ x,
                                                       const double* __restrict__ y,
                                                       const double* __restrict__ z, int64_t n,
-                                                      unsigned long long* acc, unsigned* ticket,
-                                                      RootCube* root, int* err) {
+                                                      int64_t per, unsigned long long* acc,
+                                                      unsigned* ticket, RootCube* root, int* err) {
     BboxAcc t;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        t.add(x[i], y[i], z[i]);
+    const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) t.add(x[i], y[i], z[i]);
     bbox_commit(t, acc, ticket, root, err);
 }
 
 cudaError_t launch_bbox(const double* x, const double* y, const double* z, int64_t n,
                         Workspace& ws, cudaStream_t s) {
-    k_bbox<<<bbox_grid(n, ws), kBboxThreads, 0, s>>>(x, y, z, n, ws.bbox_acc, ws.ticket, ws.root,
-                                                     ws.err);
+    const IonSplit sp = bbox_split(n, ws);
+    k_bbox<<<sp.grid, kBboxThreads, 0, s>>>(x, y, z, n, sp.per, ws.bbox_acc, ws.ticket, ws.root,
+                                            ws.err);
     return cudaGetLastError();
 }
 
@@ -68,14 +68,14 @@ __device__ __forceinline__ int leaf_coord(double v, double lo, double side, doub
 }
 
 __global__ void k_keys(const double* __restrict__ x, const double* __restrict__ y,
-                       const double* __restrict__ z, int64_t n, int D, const RootCube* root,
-                       uint32_t* key, uint32_t* rank, int32_t* leaf_count) {
+                       const double* __restrict__ z, int64_t n, int64_t per, int D,
+                       const RootCube* root, uint32_t* key, uint32_t* rank, int32_t* leaf_count) {
     pdl_wait();
     const double lo0 = root->lo[0], lo1 = root->lo[1], lo2 = root->lo[2], side = root->side;
     const double scale = (double)(1 << D);
     const int m = (1 << D) - 1;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         uint32_t k = morton3(leaf_coord(x[i], lo0, side, scale, m),
                              leaf_coord(y[i], lo1, side, scale, m),
                              leaf_coord(z[i], lo2, side, scale, m));
@@ -450,7 +450,8 @@ __device__ __forceinline__ double4_32a make4<double4_32a>(double a, double b, do
 template <typename T4>
 __global__ void k_leaf_gather(const double* __restrict__ x, const double* __restrict__ y,
                               const double* __restrict__ z, const double* __restrict__ q, int64_t n,
-                              int D, const RootCube* root, const uint32_t* __restrict__ key,
+                              int64_t per, int D, const RootCube* root,
+                              const uint32_t* __restrict__ key,
                               const int32_t* __restrict__ leaf_start,
                               const int32_t* __restrict__ cid_leaf,
                               const int32_t* __restrict__ perm_tmp, int32_t* perm,
@@ -458,8 +459,8 @@ __global__ void k_leaf_gather(const double* __restrict__ x, const double* __rest
     pdl_wait();
     const double lo0 = root->lo[0], lo1 = root->lo[1], lo2 = root->lo[2], side = root->side;
     const double scale = (double)(1 << D);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = blockIdx.x * per, i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const int idx = perm_tmp[i];
         const uint32_t c = key[idx];
         const int s = leaf_start[c], k = leaf_start[c + 1] - s;
@@ -482,13 +483,12 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
                         const double* q, int D, Workspace& ws, cudaStream_t s) {
     const int64_t ncells = (int64_t)1 << (3 * D);
     // the leaf histogram is zero here (zeroed at allocation and by its scans)
-    // the per-ion passes (keys, gather) do FP64 divisions: blocks of 64
-    // threads spread them over every SM (256-thread blocks left 3/4 idle at
-    // 10k ions); the scatter is integer work
+    // the per-ion passes (keys, gather) do FP64 divisions: equal shares of
+    // the ions per SM (ion_split); the scatter is integer work
     const int grid_ions = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-    const int grid_fp64 = (int)((n + 63) / 64 < 152 * 32 ? (n + 63) / 64 : 152 * 32);
-    cudaError_t e = launch_pdl(k_keys, dim3(grid_fp64 > 0 ? grid_fp64 : 1), dim3(64), 0, s, x, y,
-                               z, n, D, (const RootCube*)ws.root, ws.key, ws.rank, ws.leaf_count);
+    const IonSplit sp = ion_split(n, 128, ws.sms, (int64_t)1 << 30);
+    cudaError_t e = launch_pdl(k_keys, dim3(sp.grid), dim3(128), 0, s, x, y, z, n, sp.per, D,
+                               (const RootCube*)ws.root, ws.key, ws.rank, ws.leaf_count);
     if (e != cudaSuccess) return e;
     LeafCountScan ls{ws.leaf_count, ws.leaf_start, ncells};
     DenseLayout dl = dense_layout(D);
@@ -518,13 +518,14 @@ cudaError_t launch_tree(int64_t n, const double* x, const double* y, const doubl
                         ws.perm_tmp)) != cudaSuccess)
         return e;
     const int32_t* cid_leaf = ws.cid + dl.off[D];
-    const int gf = grid_fp64 > 0 ? grid_fp64 : 1;
     if (ws.fp64)
-        return launch_pdl(k_leaf_gather<double4_32a>, dim3(gf), dim3(64), 0, s, x, y, z, q, n, D,
+        return launch_pdl(k_leaf_gather<double4_32a>, dim3(sp.grid), dim3(128), 0, s, x, y, z, q,
+                          n, sp.per, D,
                           (const RootCube*)ws.root, (const uint32_t*)ws.key,
                           (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
                           ws.perm, ws.slot_of, ws.leaf_of, (double4_32a*)ws.sorted);
-    return launch_pdl(k_leaf_gather<int4>, dim3(gf), dim3(64), 0, s, x, y, z, q, n, D,
+    return launch_pdl(k_leaf_gather<int4>, dim3(sp.grid), dim3(128), 0, s, x, y, z, q, n, sp.per,
+                      D,
                       (const RootCube*)ws.root, (const uint32_t*)ws.key,
                       (const int32_t*)ws.leaf_start, cid_leaf, (const int32_t*)ws.perm_tmp,
                       ws.perm, ws.slot_of, ws.leaf_of, (int4*)ws.sorted);
@@ -565,9 +566,9 @@ cudaError_t launch_level_counts(int64_t n, const double* x, const double* y, con
     cudaError_t e = launch_bbox(x, y, z, n, ws, s);
     if (e != cudaSuccess) return e;
     const int64_t ncells = (int64_t)1 << (3 * Dm);
-    const int grid_ions = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-    k_keys<<<grid_ions > 0 ? grid_ions : 1, 256, 0, s>>>(x, y, z, n, Dm, ws.root, ws.key, ws.rank,
-                                                         ws.leaf_count);
+    const IonSplit sk = ion_split(n, 128, ws.sms, (int64_t)1 << 30);
+    k_keys<<<sk.grid, 128, 0, s>>>(x, y, z, n, sk.per, Dm, ws.root, ws.key, ws.rank,
+                                   ws.leaf_count);
     LeafCountScan ls{ws.leaf_count, ws.leaf_start, ncells};
     if ((e = run_scan(ls, ncells, ws, s)) != cudaSuccess) return e;
     int32_t* d_counts = (int32_t*)ws.block_sums;  // reuse scratch after the scan
