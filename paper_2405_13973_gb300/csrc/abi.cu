@@ -77,6 +77,14 @@ struct fmm_plan_s {
     StepCounter* h_steps[kSlots] = {nullptr};
     cudaEvent_t slot_ev[kSlots] = {nullptr};
     int next_slot = 0;
+    // The wall-phase table on the device covers steps [win_base, win_base +
+    // win_count) of the anchor (win_t, win_step, win_dt) at rotation win_wr;
+    // dev_next is the step the device counter will start next once the work
+    // enqueued so far has run (-1: unknown).  Chunks inside the window that
+    // continue the device counter upload nothing.
+    double win_t = 0.0, win_dt = 0.0, win_wr = 0.0;
+    int64_t win_step = 0, win_base = 0, win_count = 0;
+    int64_t dev_next = -1;
     // per-phase device timing (events captured into the step graph)
     bool profile = false;
     static constexpr int kPhases = 6;
@@ -561,20 +569,37 @@ int prepare_chunk(fmm_plan_s* plan, const pt_state* st, const pt_trap* trap, dou
     }
     int rp = ensure_pairs(plan, st->n, st->x, st->y, st->z, st->q, *D, s);
     if (rp != PT_OK) return rp;
+    const int64_t first = step0 + s0;  // global index of the chunk's first step
+    const bool in_window = plan->win_count > 0 && plan->win_t == t0 && plan->win_step == step0 &&
+                           plan->win_dt == dt && plan->win_wr == trap->omega_r &&
+                           first >= plan->win_base && first + k <= plan->win_base + plan->win_count;
+    if (in_window && plan->dev_next == first) return PT_OK;  // table and counter in place
     const int slot = plan->next_slot;
     plan->next_slot = (slot + 1) % fmm_plan_s::kSlots;
     cudaError_t e = cudaEventSynchronize(plan->slot_ev[slot]);  // slot free again
     if (e != cudaSuccess) return status_from(e);
-    double* hw = plan->h_wall[slot];
-    for (int64_t j = 0; j < k; ++j) {
-        double tm = (t0 + (double)(s0 + j) * dt) + 0.5 * dt;
-        hw[2 * j] = cos(2.0 * trap->omega_r * tm);
-        hw[2 * j + 1] = sin(2.0 * trap->omega_r * tm);
+    plan->dev_next = -1;
+    if (!in_window) {
+        // a new window of wall_cap steps from this chunk's first (the table
+        // depends on the anchor and the step index only)
+        double* hw = plan->h_wall[slot];
+        for (int64_t j = 0; j < ws.wall_cap; ++j) {
+            double tm = (t0 + (double)(s0 + j) * dt) + 0.5 * dt;
+            hw[2 * j] = cos(2.0 * trap->omega_r * tm);
+            hw[2 * j + 1] = sin(2.0 * trap->omega_r * tm);
+        }
+        e = cudaMemcpyAsync(ws.wall_cs, hw, sizeof(double) * 2 * ws.wall_cap,
+                            cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return status_from(e);
+        plan->win_t = t0;
+        plan->win_step = step0;
+        plan->win_dt = dt;
+        plan->win_wr = trap->omega_r;
+        plan->win_base = first;
+        plan->win_count = ws.wall_cap;
     }
-    *plan->h_steps[slot] = StepCounter{0, step0 + s0, step0 + s0};
-    e = cudaMemcpyAsync(ws.wall_cs, hw, sizeof(double) * 2 * k, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ws.steps, plan->h_steps[slot], sizeof(StepCounter), cudaMemcpyHostToDevice, s);
+    *plan->h_steps[slot] = StepCounter{0, first, plan->win_base};
+    e = cudaMemcpyAsync(ws.steps, plan->h_steps[slot], sizeof(StepCounter), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(plan->slot_ev[slot], s);
     return status_from(e);
 }
@@ -659,8 +684,13 @@ int step_impl(fmm_plan_s* plan, pt_state* st, const pt_trap* trap, const pt_lase
         }
         for (int64_t j = 0; j < k; ++j) {
             e = cudaGraphLaunch(plan->graph, s);
-            if (e != cudaSuccess) return status_from(e);
+            if (e != cudaSuccess) {
+                plan->dev_next = -1;
+                return status_from(e);
+            }
         }
+        // each launch advances the device's step counter by one
+        plan->dev_next = plan->anc_step + off + s0 + k;
         plan->last_depth = D;
         plan->last_n = st->n;
         if (sync) {
@@ -1259,9 +1289,14 @@ int pt_ensemble_step(pt_ensemble ens, pt_state* states, const pt_trap* traps,
         }
         for (int64_t j = 0; j < k; ++j) {
             e = cudaGraphLaunch(ens->graph, s);
-            if (e != cudaSuccess) return status_from(e);
+            if (e != cudaSuccess) {
+                for (int b = 0; b < nm; ++b) ens->plans[b]->dev_next = -1;
+                return status_from(e);
+            }
         }
         for (int b = 0; b < nm; ++b) {
+            fmm_plan_s* pl = ens->plans[b];
+            pl->dev_next = step0[b] + s0 + k;
             ens->plans[b]->last_depth = D[b];
             ens->plans[b]->last_n = states[b].n;
         }
