@@ -944,8 +944,9 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     pdl_wait();
     const int g0 = linfo->gbase[D], g1 = linfo->gbase[D + 1];
     if (g0 + (int)blockIdx.x >= g1) return;  // no leaf for this block
-    __shared__ T sL[2][kPmax];
-    __shared__ T sD[2][4][kPmax];  // derived expansions: phi, grad x, grad y, grad z
+    constexpr int NL = sizeof(T) == 4 ? 3 : 2;  // levels evaluated at most (shared memory)
+    __shared__ T sL[NL][kPmax];
+    __shared__ T sD[NL][4][kPmax];  // derived expansions: phi, grad x, grad y, grad z
     __shared__ HarmTables<T> t;
     __shared__ double s_f[2];
     {
@@ -969,7 +970,7 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
     constexpr int kPerPass = kL2pThreads / G;
     const unsigned hw_mask = (G == 8 ? 0xffu : 0xffffu) << (lane & (32 - G));
     const int P = (p + 1) * (p + 1);
-    const int levs = far ? nlev : 0;
+    const int levs = far ? (nlev < NL ? nlev : NL) : 0;
     for (int g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
         const int ts = cstart[g], nt = ccount[g];
         const uint32_t cl = code[g];
@@ -978,7 +979,8 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
         __syncthreads();  // sL, sD free from the previous leaf
         for (int lv = 0; lv < levs; ++lv) {
             // dense maps of levels 2.. concatenated: level l starts at (8^l - 64) / 7
-            const int ga = lv == 0 ? g : cid[(((1ll << (3 * (D - 1))) - 64) / 7) + (cl >> 3)];
+            const int ga =
+                lv == 0 ? g : cid[(((1ll << (3 * (D - lv))) - 64) / 7) + (cl >> (3 * lv))];
             for (int c = threadIdx.x; c < P; c += kL2pThreads) sL[lv][c] = L[(int64_t)ga * ld + c];
         }
         __syncthreads();
@@ -991,12 +993,13 @@ __global__ void __launch_bounds__(kL2pThreads) k_l2p(
             const typename Ion<T>::rec me = sorted[ts + ti];
             for (int lv = 0; lv < levs; ++lv) {
                 T x, y, z, q;
-                ion_in_ancestor(me, lv, ix & lv, iy & lv, iz & lv, x, y, z, q);
+                const int am = (1 << lv) - 1;  // the leaf's position inside the ancestor
+                ion_in_ancestor(me, lv, ix & am, iy & am, iz & am, x, y, z, q);
                 T cph, cax, cay, caz;
                 if (G == 8) l2p_columns8<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
                 else l2p_columns<T>(p, m, hw_mask, x, y, z, t, sD[lv], cph, cax, cay, caz);
                 // level units -> leaf units: phi / 2^lv, E / 4^lv (exact)
-                const T fp1 = lv == 0 ? T(1) : T(0.5), fe1 = fp1 * fp1;
+                const T fp1 = lv == 0 ? T(1) : (lv == 1 ? T(0.5) : T(0.25)), fe1 = fp1 * fp1;
                 ph += fp1 * cph;
                 ex -= fe1 * cax;
                 ey -= fe1 * cay;
@@ -1138,6 +1141,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     // ancestor expansions of the tensor-core path directly from the ions
     // instead of the M2M / L2L shifts (an option: a cross-check of the shifts)
     const bool direct = far && use_tc && ws.expand == PT_EXPAND_DIRECT;
+    // ancestor levels the leaves' L2P evaluates on the tensor-core paths: the
+    // leaf, its parent and grandparent (each shift that L2P replaces is one
+    // launch fewer; M2L levels start at 2)
+    const int l2p_levels = use_tc ? (D - 1 < 3 ? (D - 1 > 1 ? D - 1 : 1) : 3) : 1;
     cudaError_t e;
     if (fork) {
         if ((e = cudaEventRecord(ws.ev_fork, s)) != cudaSuccess) return e;
@@ -1227,9 +1234,10 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         return e;
     if (far && use_tc) {
         if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
-        // L2L down to the leaves' parents; the leaves' L2P evaluates the
-        // parent's expansion itself (direct mode: no L2L at all)
-        if ((e = launch_m2l_tc_run(n, D, ws, direct ? 2 : D - 1, s,
+        // L2L down to level D - l2p_levels + 1; the leaves' L2P evaluates the
+        // own M2L sums of the leaf and its parent and the complete expansion
+        // of the ancestor above them itself (direct mode: no L2L at all)
+        if ((e = launch_m2l_tc_run(n, D, ws, direct ? 2 : D + 1 - l2p_levels, s,
                                    near_late ? ws.ev_p2m : nullptr)) != cudaSuccess)
             return e;
         if (nf && near_late && (e = launch_near(true)) != cudaSuccess) return e;
@@ -1265,7 +1273,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     else
         e = launch_pdl(p <= 15 ? k_l2p<T, 8> : k_l2p<T, 16>, dim3(leaf_grid), dim3(kL2pThreads),
                        0, s, n, D, p, ws.ld, far,
-                       use_tc && D >= 3 ? 2 : 1, (const RootCube*)ws.root,
+                       l2p_levels, (const RootCube*)ws.root,
                        (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code,
                        (const int32_t*)ws.cid, (const typename Ion<T>::rec*)ws.sorted,
                        (const int32_t*)ws.perm, (const int32_t*)ws.cstart,
