@@ -949,6 +949,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
          cudaMemset(ws.tc_work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap)) != cudaSuccess) ||
         (ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * ws.tc_part_floats) != cudaSuccess) ||
         cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
+        (ws.M_pieces && cudaMemset(ws.M_pieces, 0, sizeof(uint16_t) * 3 * ws.ld * cells) != cudaSuccess) ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ws.bbox_acc, 0, sizeof(unsigned long long) * 8) != cudaSuccess ||

@@ -20,6 +20,7 @@
 // the normalised real storage of harmonics.cuh, scaled by the cell size.
 #include <cuda_runtime.h>
 
+#include "bf16split.cuh"
 #include "fmm_math.cuh"
 #include "harmonics.cuh"
 #include "internal.h"
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kP2mThreads) k_p2m(int D, int p, int ld, const
                                                      const int32_t* __restrict__ cstart,
                                                      const int32_t* __restrict__ ccount,
                                                      const typename Ion<T>::rec* __restrict__ sorted,
-                                                     T* __restrict__ M) {
+                                                     T* __restrict__ M, uint16_t* Mp) {
     extern __shared__ unsigned char p2m_smem[];
     const int P = (p + 1) * (p + 1);
     T* terms = reinterpret_cast<T*>(p2m_smem);  // [kP2mIons][P]
@@ -207,7 +208,10 @@ __global__ void __launch_bounds__(kP2mThreads) k_p2m(int D, int p, int ld, const
 #pragma unroll
         for (int r = 0; r < NA; ++r) {
             const int c = threadIdx.x + r * kP2mThreads;
-            if (c < P) M[(int64_t)g * ld + c] = acc[r];
+            if (c < P) {
+                M[(int64_t)g * ld + c] = acc[r];
+                if (Mp) store_pieces(Mp, g, ld, c, (float)acc[r]);  // BF16x3 operand
+            }
         }
     }
 }
@@ -226,7 +230,7 @@ template <typename T>
 __global__ void __launch_bounds__(kP2mThreads) k_p2m_anc(
     int D, int lmin, int p, int ld, const LevelInfo* linfo, const uint32_t* __restrict__ code,
     const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_of,
-    const typename Ion<T>::rec* __restrict__ sorted, T* __restrict__ M) {
+    const typename Ion<T>::rec* __restrict__ sorted, T* __restrict__ M, uint16_t* Mp) {
     extern __shared__ unsigned char p2m_smem[];
     const int P = (p + 1) * (p + 1);
     pdl_wait();
@@ -271,7 +275,11 @@ __global__ void __launch_bounds__(kP2mThreads) k_p2m_anc(
 #pragma unroll
         for (int r = 0; r < NA; ++r) {
             const int cc = threadIdx.x + r * kP2mThreads;
-            if (cc < P) M[(int64_t)g * ld + cc] = acc[r] + cmp[r];
+            if (cc < P) {
+                const T v = acc[r] + cmp[r];
+                M[(int64_t)g * ld + cc] = v;
+                if (Mp) store_pieces(Mp, g, ld, cc, (float)v);  // BF16x3 operand
+            }
         }
     }
 }
@@ -367,7 +375,8 @@ __global__ void __launch_bounds__(kShThreads) k_shift_rows(int l, int P, int ld,
                                                            const uint32_t* __restrict__ code,
                                                            const int32_t* __restrict__ cid,
                                                            int64_t off_nb,
-                                                           const T* __restrict__ Op, T* Y) {
+                                                           const T* __restrict__ Op, T* Y,
+                                                           uint16_t* Mp) {
     static_assert(sizeof(T) == 4, "FP32 plans only (4-byte asynchronous copies)");
     constexpr int CG = ShCells<MODE>::v;
     extern __shared__ unsigned char smem_raw[];
@@ -458,6 +467,10 @@ __global__ void __launch_bounds__(kShThreads) k_shift_rows(int l, int P, int ld,
             if (MODE == 0) {
                 if (ra < P) y[ra] = v0;
                 if (rb < P) y[rb] = v1;
+                if (Mp) {  // BF16x3 operand of the M2L
+                    if (ra < P) store_pieces(Mp, gb + lane, ld, ra, (float)v0);
+                    if (rb < P) store_pieces(Mp, gb + lane, ld, rb, (float)v1);
+                }
             } else {
                 if (ra < P) y[ra] += v0;
                 if (rb < P) y[rb] += v1;
@@ -1164,6 +1177,11 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
     // expand directly than one more M2M launch and its reduction), or at every
     // level >= 2 in the direct mode; M2M shifts the rest up.
     const int lmin_p2m = direct ? 2 : (far && use_tc && D >= 3 ? D - 1 : D);
+    // BF16x3: the multipoles' bf16 pieces, the M2L operand, are written by
+    // their producers (P2M and the small-level M2M); a split pass covers the
+    // levels of the tensor-core M2M (3 .. lmin_p2m - 1)
+    uint16_t* Mp = use_tc && ws.tc_bf16 ? ws.M_pieces : nullptr;
+    const int split_last = use_tc && ws.tc_bf16 && !direct ? lmin_p2m - 1 : 0;
     if (far && lmin_p2m < D) {
         int64_t cells = 0;
         for (int l = lmin_p2m; l <= D; ++l)
@@ -1173,12 +1191,13 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                             s, D, lmin_p2m, p, ws.ld, (const LevelInfo*)ws.linfo,
                             (const uint32_t*)ws.code, (const int32_t*)ws.leaf_start,
                             (const int32_t*)ws.leaf_of, (const typename Ion<T>::rec*)ws.sorted,
-                            M)) != cudaSuccess)
+                            M, Mp)) != cudaSuccess)
             return e;
     } else if (far) {
         int grid = leaf_grid;
         k_p2m<T><<<grid, kP2mThreads, kP2mIons * P * sizeof(T), s>>>(
-            D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M);
+            D, p, ws.ld, ws.linfo, ws.cstart, ws.ccount, (const typename Ion<T>::rec*)ws.sorted, M,
+            Mp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // P2P on the side stream: after P2M on the CUDA-core paths (beside their
@@ -1237,7 +1256,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         // L2L down to level D - l2p_levels + 1; the leaves' L2P evaluates the
         // own M2L sums of the leaf and its parent and the complete expansion
         // of the ancestor above them itself (direct mode: no L2L at all)
-        if ((e = launch_m2l_tc_run(n, D, ws, direct ? 2 : D + 1 - l2p_levels, s,
+        if ((e = launch_m2l_tc_run(n, D, ws, direct ? 2 : D + 1 - l2p_levels, split_last, s,
                                    near_late ? ws.ev_p2m : nullptr)) != cudaSuccess)
             return e;
         if (nf && near_late && (e = launch_near(true)) != cudaSuccess) return e;
@@ -1311,14 +1330,14 @@ cudaError_t launch_shift_small(int mode, int64_t n, int D, int l, Workspace& ws,
                           dim3(kShThreads), shift_rows_smem<float, 0>(P), s, l, P, ws.ld,
                           (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code,
                           (const int32_t*)ws.cid, dl.off[l + 1], (const float*)ws.T_m2m,
-                          (float*)ws.M);
+                          (float*)ws.M, ws.tc_bf16 ? ws.M_pieces : (uint16_t*)nullptr);
     }
     // per octant: runs of 16 children, a few blocks per octant
     const int64_t ch = (cells + ShCells<1>::v * 8 - 1) / (ShCells<1>::v * 8);
     return launch_pdl(k_shift_rows<float, 1>, dim3(rg, 8, (unsigned)(ch < 4 ? (ch > 0 ? ch : 1) : 4)),
                       dim3(kShThreads), shift_rows_smem<float, 1>(P), s, l, P, ws.ld,
                       (const LevelInfo*)ws.linfo, (const uint32_t*)ws.code, (const int32_t*)ws.cid,
-                      dl.off[l - 1], (const float*)ws.T_l2l, (float*)ws.L);
+                      dl.off[l - 1], (const float*)ws.T_l2l, (float*)ws.L, (uint16_t*)nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -215,10 +215,11 @@ cudaError_t launch_direct(int64_t n, const double* pos, const double* q, double*
 // of every level on the tensor cores with the slab reduction and the L2L
 // shifts level by level (L is complete once the second has run).
 cudaError_t launch_m2l_tc_worklist(int64_t n, int D, Workspace& ws, cudaStream_t s);
-// L2L into levels 3 .. l2l_last; after_m2l (optional) is recorded on s right
-// after the M2L kernel.
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s,
-                              cudaEvent_t after_m2l = nullptr);
+// L2L into levels 3 .. l2l_last; BF16x3: M of levels 3 .. split_last split
+// into bf16 pieces first (the other levels' producers store theirs);
+// after_m2l (optional) is recorded on s right after the M2L kernel.
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, int split_last,
+                              cudaStream_t s, cudaEvent_t after_m2l = nullptr);
 cudaError_t m2l_tc_init();
 size_t m2l_tc_operand_bytes(int p, bool bf16);   // 0 if the order is not supported
 size_t m2l_tc_partial_splits(int p, int64_t cells_max, int ld);

@@ -61,6 +61,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bf16split.cuh"
 #include "harmonics.cuh"
 #include "internal.h"
 #include "m2l_pairs.h"
@@ -302,17 +303,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t b
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
         "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
         : "memory");
-}
-// x = hi + mid + lo, each round-to-nearest bf16 of the remainder so far
-__device__ __forceinline__ void split_bf16x3(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
-    const __nv_bfloat16 bh = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(bh);
-    const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(bm);
-    const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-    h = __bfloat16_as_ushort(bh);
-    m = __bfloat16_as_ushort(bm);
-    l = __bfloat16_as_ushort(bl);
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
@@ -1831,22 +1821,18 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
                       (int64_t)(ws.cells_max * ws.ld / 4), (float4*)ws.M);
 }
 
-// M of every cell of levels 2..D as bf16 hi/mid/lo pieces (split_bf16x3, the
-// split the M2L producers would otherwise repeat for every target that
-// gathers the cell): Mp[(cell * 3 + q) * ld + k].
-__global__ void k_split_m(int lfirst, int D, int ld, const LevelInfo* linfo, const float* M,
+// M of the cells of levels lfirst..llast as bf16 hi/mid/lo pieces
+// (split_bf16x3, the split the M2L producers would otherwise repeat for
+// every target that gathers the cell): Mp[(cell * 3 + q) * ld + k].  The
+// other levels' pieces are stored by the kernels that compute their M.
+__global__ void k_split_m(int lfirst, int llast, int ld, const LevelInfo* linfo, const float* M,
                           uint16_t* Mp) {
     pdl_wait();
-    const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[D + 1];
+    const int64_t g0 = linfo->gbase[lfirst], g1 = linfo->gbase[llast + 1];
     for (int64_t e = g0 * ld + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g1 * ld;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t cell = e / ld, k = e - cell * ld;
-        uint32_t h, m, l;
-        split_bf16x3(M[e], h, m, l);
-        uint16_t* row = Mp + cell * 3 * ld + k;
-        row[0] = (uint16_t)h;
-        row[ld] = (uint16_t)m;
-        row[2 * ld] = (uint16_t)l;
+        store_pieces(Mp, cell, ld, (int)k, M[e]);
     }
 }
 
@@ -1943,15 +1929,15 @@ static unsigned m2l_grid(const Workspace& ws) {
     return (unsigned)(ws.m2l_ctas > 0 && ws.m2l_ctas < sms ? ws.m2l_ctas : sms);
 }
 
-cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cudaStream_t s,
-                              cudaEvent_t after_m2l) {
+cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, int split_last,
+                              cudaStream_t s, cudaEvent_t after_m2l) {
     if (D < 2) return cudaSuccess;
     const int smem = tc_geom(ws.p, ws.tc_bf16 != 0).smem_bytes;
     if (ws.m2l_pairs) {
         TcArgs a = pair_args(n, D, ws);
         cudaError_t e;
-        if (ws.tc_bf16) {
-            if ((e = launch_pdl(k_split_m, dim3(152 * 8), dim3(256), 0, s, 2, D, ws.ld,
+        if (ws.tc_bf16 && split_last >= 3) {
+            if ((e = launch_pdl(k_split_m, dim3(152 * 8), dim3(256), 0, s, 3, split_last, ws.ld,
                                 (const LevelInfo*)ws.linfo, (const float*)ws.M, ws.M_pieces)) !=
                 cudaSuccess)
                 return e;
@@ -1979,7 +1965,9 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, cud
     a.hdr = hdr;
     cudaError_t e;
     if (ws.tc_bf16) {
-        k_split_m<<<152 * 8, 256, 0, s>>>(2, D, ws.ld, ws.linfo, (const float*)ws.M, ws.M_pieces);
+        if (split_last >= 3)
+            k_split_m<<<152 * 8, 256, 0, s>>>(3, split_last, ws.ld, ws.linfo, (const float*)ws.M,
+                                              ws.M_pieces);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // persistent: one CTA per SM walks the work list
