@@ -540,6 +540,9 @@ def main():
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched-ensemble measurement with this many crystals instead of the "
                          "single-crystal step (N log-uniform in [100, 20000], aspect 0.1-1)")
+    ap.add_argument("--no-mirror", action="store_true",
+                    help="BF16x3 pair schedule without offset mirroring (offsets o and -o in "
+                         "runs of their own)")
     ap.add_argument("--schedule", default="", choices=["", "tiles", "pairs", "rotation"],
                     help="M2L schedule (default: the library's for the plan)")
     ap.add_argument("--forces", type=int, default=0,
@@ -609,6 +612,8 @@ def main():
     plan = pt.Plan(n, p=args.p, leaf_max=32, depth=-1, precision=args.precision)
     if args.schedule and args.precision in ("tf32x3", "bf16x3"):
         plan.set_m2l_schedule(args.schedule)
+    if args.no_mirror and args.precision == "bf16x3":
+        plan.set_m2l_mirror(False)
     schedule = plan.m2l_schedule if args.precision in ("tf32x3", "bf16x3") else "cuda-core"
     ferr = force_err(plan)
     ferr_oracle = force_err_oracle(plan) if rank == 0 and not args.no_cpu else None
@@ -696,7 +701,9 @@ def main():
         achieved = byts / (ph[dom] * 1e-3) / 1e9
         roof.update(bound="hbm", achieved=achieved, peak=pk["hbm_gbs"], unit="GB/s",
                     frac=achieved / pk["hbm_gbs"], work="96 B per ion")
-    tr = recorded_traffic(f"k_m2l_tc:{args.precision}:p{args.p}:{schedule}") if dom == "m2l" else None
+    mirrored = schedule == "pairs" and args.precision == "bf16x3" and not args.no_mirror
+    tr = recorded_traffic(f"k_m2l_tc:{args.precision}:p{args.p}:{schedule}"
+                          f"{':mirrored' if mirrored else ''}") if dom == "m2l" else None
     roof["traffic"] = tr["dram_bytes_per_launch"] if tr else None
     if tr:
         roof["traffic_note"] = tr["note"]
@@ -709,6 +716,7 @@ def main():
            "data": "synthetic",
            "config": {"workload": workload_name(args.p), "precision": args.precision, "p": args.p,
                       "depth": depth, "n": n, "m2l_schedule": schedule,
+                      "m2l_mirrored_offsets": mirrored,
                       "l2": "flushed between timed steps (512 MiB write)",
                       "parallelism": "replicas" if world > 1 else "single"},
            "force_err": ferr, "force_err_note": "relative RMS vs the FP64 GPU direct sum, initial state",

@@ -163,6 +163,18 @@ int fmm_plan_set_m2l_schedule(fmm_plan plan, int schedule);
  * every work item is computed by one CTA whatever the grid.  Errors:
  * PT_ERR_ARG. */
 int fmm_plan_set_m2l_ctas(fmm_plan plan, int ctas);
+/* Offset mirroring of the BF16x3 pair schedule: 1 (default) or 0.  The M2L
+ * operator of Eq. FMM_local obeys T_{-o}[l][j] = (-1)^(j + l) T_o[l][j]
+ * (Sec. 2.3.1: the irregular solid harmonic of degree n is even or odd in
+ * its argument as n is), so with mirroring on the pairs of offset -o are
+ * products with the operator of o: their multipole enters with its
+ * odd-degree coefficients negated and their partial local expansion leaves
+ * with its odd-degree coefficients negated.  Both negations are exact, so
+ * the forces equal those with mirroring off; half the operators are read
+ * and fewer 128-row products are padded.  Takes effect at the next call.
+ * Errors: PT_ERR_ARG (on not 0 or 1), PT_ERR_UNSUPPORTED (on, on a plan of
+ * another precision). */
+int fmm_plan_set_m2l_mirror(fmm_plan plan, int on);
 /* The plan's M2L schedule (PT_M2L_*), or -1 for a NULL plan. */
 int fmm_plan_m2l_schedule(fmm_plan plan);
 

@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
         L.fmm_plan_set_m2l_schedule.argtypes = [_VP, ctypes.c_int]
         L.fmm_plan_m2l_schedule.argtypes = [_VP]
         L.fmm_plan_set_m2l_ctas.argtypes = [_VP, ctypes.c_int]
+        L.fmm_plan_set_m2l_mirror.argtypes = [_VP, ctypes.c_int]
         L.pt_energy_noalloc.argtypes = [ctypes.POINTER(pt_state), ctypes.POINTER(pt_trap),
                                         ctypes.POINTER(_D), _VP]
         L.fmm_plan_footprint.argtypes = [_I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -280,6 +281,12 @@ class Plan:
         """At most `ctas` CTAs for the persistent tensor-core M2L kernel (0:
         one per SM)."""
         _check(load(False).fmm_plan_set_m2l_ctas(self._h, int(ctas)), "fmm_plan_set_m2l_ctas")
+
+    def set_m2l_mirror(self, on: bool):
+        """Pairs of offsets o and -o in the same BF16x3 products, with the
+        operator of o (default on; fmm_plan_set_m2l_mirror)."""
+        _check(load(False).fmm_plan_set_m2l_mirror(self._h, 1 if on else 0),
+               "fmm_plan_set_m2l_mirror")
 
     @property
     def m2l_schedule(self) -> str:

@@ -13,6 +13,7 @@
 #include <set>
 #include <vector>
 
+#include "bf16split.cuh"
 #include "internal.h"
 #include "m2l_pairs.h"
 #include "operators.h"
@@ -615,7 +616,7 @@ GraphKey make_key(const fmm_plan_s* plan, const pt_state* st, const PushParams& 
     key.laser = lz;
     key.profile = plan->profile;
     key.expand = plan->ws.expand;
-    key.sched = plan->ws.m2l_pairs + 2 * plan->ws.m2l_rot;
+    key.sched = plan->ws.m2l_pairs + 2 * plan->ws.m2l_rot + 4 * plan->ws.pp_mirror;
     key.ctas = plan->ws.m2l_ctas;
     key.pool = plan->ws.pp_gen;
     return key;
@@ -787,6 +788,13 @@ int fmm_plan_set_m2l_ctas(fmm_plan plan, int ctas) {
     return PT_OK;
 }
 
+int fmm_plan_set_m2l_mirror(fmm_plan plan, int on) {
+    if (!plan || (on != 0 && on != 1)) return PT_ERR_ARG;
+    if (on && !plan->ws.tc_bf16) return PT_ERR_UNSUPPORTED;
+    plan->ws.pp_mirror = on;
+    return PT_OK;
+}
+
 int fmm_plan_m2l_schedule(fmm_plan plan) {
     if (!plan) return -1;
     if (plan->ws.m2l_rot) return PT_M2L_ROTATION;
@@ -844,6 +852,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
     ws.P = pl->P;
     ws.fp64 = (precision == PT_FP64);
     ws.tc_bf16 = (precision == PT_MIXED_BF16X3) ? 1 : 0;
+    ws.pp_mirror = ws.tc_bf16;  // offset mirroring: the BF16x3 pair products only
     ws.ld = ws.fp64 ? pl->P : ((pl->P + 31) / 32) * 32;
     ws.rot_op_vals = rot_operator_bytes(pl) > 0 ? ops::rot_op_vals(p) : 0;
     if (depth >= 0) {
@@ -920,7 +929,7 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
                                                ws.tc_slab_cap);
         ok = dalloc(pl, ws.tc_work, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap));
         ok = ok && dalloc(pl, ws.tc_part, sizeof(float) * ws.tc_part_floats);
-        if (ws.tc_bf16) ok = ok && dalloc(pl, ws.M_pieces, sizeof(uint16_t) * 3 * ws.ld * cells);
+        if (ws.tc_bf16) ok = ok && dalloc(pl, ws.M_pieces, sizeof(uint16_t) * kPieceRows * ws.ld * cells);
         if (ok && pairs) {
             ok = alloc_pairs(pl) == PT_OK;
             ws.m2l_pairs = ok ? 1 : 0;
@@ -949,7 +958,8 @@ static int plan_create_impl(int64_t n_max, int p, int leaf_max, int depth, int p
          cudaMemset(ws.tc_work, 0, m2l_tc_work_bytes(ws.tc_tiles_cap, ws.tc_slab_cap)) != cudaSuccess) ||
         (ws.tc_part && cudaMemset(ws.tc_part, 0, sizeof(float) * ws.tc_part_floats) != cudaSuccess) ||
         cudaMemset(ws.M, 0, tsz * ws.ld * cells) != cudaSuccess ||
-        (ws.M_pieces && cudaMemset(ws.M_pieces, 0, sizeof(uint16_t) * 3 * ws.ld * cells) != cudaSuccess) ||
+        (ws.M_pieces &&
+         cudaMemset(ws.M_pieces, 0, sizeof(uint16_t) * kPieceRows * ws.ld * cells) != cudaSuccess) ||
         cudaMemset(ws.L, 0, tsz * ws.ld * cells) != cudaSuccess ||
         cudaMemset(ws.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ws.bbox_acc, 0, sizeof(unsigned long long) * 8) != cudaSuccess ||

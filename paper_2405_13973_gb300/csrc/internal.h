@@ -136,7 +136,8 @@ struct Workspace {
     void* T_l2l = nullptr;   // [8][P][P]
     void* T_m2l = nullptr;   // [343][P][P], index (ox+3)*49+(oy+3)*7+(oz+3)
     void* T_m2l_tc = nullptr;   // tensor-core operand tiles (mixed modes)
-    uint16_t* M_pieces = nullptr;  // BF16x3: M split into bf16 hi/mid/lo, [cell][3][ld]
+    uint16_t* M_pieces = nullptr;  // BF16x3: M split into bf16 hi/mid/lo and the same of
+                                   // the mirrored M, [cell][kPieceRows = 6][ld]
     int tc_bf16 = 0;            // tensor-core operand format: 0 TF32 hi/lo, 1 BF16 hi/mid/lo
     float* tc_part = nullptr;   // M2M split partials, then M2L item slabs (tc_part_floats)
     size_t tc_part_floats = 0;
@@ -157,6 +158,11 @@ struct Workspace {
     // CTAs of the persistent tensor-core M2L kernel (0: one per SM); members
     // of an ensemble may take fewer so that their M2L kernels share the SMs
     int m2l_ctas = 0;
+    // BF16x3 pair schedule: the pairs of offsets o and -o share the runs of
+    // o (the pairs of -o read the mirrored multipole pieces and their partial
+    // rows carry negated odd-degree terms, undone by the per-target sums):
+    // half the operators, and fewer runs padded to 128 rows
+    int pp_mirror = 0;
     void* T_rot = nullptr;
     int rot_op_vals = 0;
     // kernel timing (profiled steps only, else null): recorded right before

@@ -12,11 +12,14 @@
 //               increasing order) and the pool check;
 //   k_pp_fill   one warp per target: its pairs, each at the next position of
 //               its offset's list, with their sources and slots.
+// With mirroring (BF16x3), offsets o and -o count, and fill, as one: the
+// pairs of -o (operator index above 171) go to the list of o, marked.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 
+#include "bf16split.cuh"
 #include "harmonics.cuh"
 #include "m2l_pairs.h"
 
@@ -26,6 +29,7 @@ namespace {
 
 struct PpArgs {
     int D;
+    int mirror;  // pairs of -o in the runs of o (kPairMirror)
     const LevelInfo* linfo;
     const uint32_t* code;
     const int32_t* cid;
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_count(PpArgs a, uint32_t* tma
             int op = 0, src = -1;
             if (c < kPpCand) src = pp_source(a, l, x, y, z, c, &op);
             const unsigned bal = __ballot_sync(0xffffffffu, src >= 0);
-            if (src >= 0) atomicAdd(&hist[op], 1);
+            if (src >= 0) atomicAdd(&hist[a.mirror && op > 171 ? 342 - op : op], 1);
             if (lane == 0) tmask[(int64_t)(g - g0) * kPpWords + w] = bal;
             cnt += __popc(bal);
         }
@@ -268,9 +272,14 @@ __global__ void __launch_bounds__(kPpThreads) k_pp_fill(PpArgs a, const uint32_t
                 M2lPair pr;
                 pr.src = pp_source(a, l, x, y, z, c, &op);
                 pr.slot = rank + __popc(bits & ((1u << lane) - 1u));
+                const bool mir = a.mirror && op > 171;
+                if (mir) {
+                    op = 342 - op;
+                    pr.src |= kPairMirror;
+                }
                 const int pidx = obase[op] + atomicAdd(&ofill[op], 1);
                 pairs[pidx] = pr;
-                tpair[pr.slot] = pidx;
+                tpair[pr.slot] = mir ? ~pidx : pidx;
             }
             rank += __popc(bits);
         }
@@ -300,6 +309,13 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
     const int s4 = stride / 4, w4 = width / 4;
     const bool over = hdr->overflow != 0;
     const int j = threadIdx.x / w4, u = threadIdx.x - j * w4;
+    // sign bits of this thread's four columns that a mirrored row carries
+    // negated (odd degree; tpair entry ~pair)
+    uint4 odd;
+    odd.x = (coef_degree(4 * u) & 1) ? 0x80000000u : 0u;
+    odd.y = (coef_degree(4 * u + 1) & 1) ? 0x80000000u : 0u;
+    odd.z = (coef_degree(4 * u + 2) & 1) ? 0x80000000u : 0u;
+    odd.w = (coef_degree(4 * u + 3) & 1) ? 0x80000000u : 0u;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         const int b0 = tbase[t], b1 = over ? b0 : tbase[t + 1];
         const int cs = (b1 - b0 + kRedParts - 1) / kRedParts;
@@ -311,15 +327,21 @@ __global__ void __launch_bounds__(256) k_pp_reduce_f4(int D, int ld, int stride,
             for (int k = 0; k < 8; ++k) rw[k] = s0 + k < s1 ? tpair[s0 + k] : 0;
             for (int s = s0; s < s1; s += 8) {
                 float4 q[8];
+                uint32_t fm[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (s + k < s1) q[k] = __ldcs(part + (int64_t)rw[k] * s4 + u);
+                for (int k = 0; k < 8; ++k) {
+                    fm[k] = rw[k] < 0 ? 0xffffffffu : 0u;
+                    if (s + k < s1) q[k] = __ldcs(part + (int64_t)(rw[k] ^ (int)fm[k]) * s4 + u);
+                }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) rw[k] = s + 8 + k < s1 ? tpair[s + 8 + k] : 0;
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
                     if (s + k < s1) {
-                        v.x += q[k].x; v.y += q[k].y; v.z += q[k].z; v.w += q[k].w;
+                        v.x += __uint_as_float(__float_as_uint(q[k].x) ^ (odd.x & fm[k]));
+                        v.y += __uint_as_float(__float_as_uint(q[k].y) ^ (odd.y & fm[k]));
+                        v.z += __uint_as_float(__float_as_uint(q[k].z) ^ (odd.z & fm[k]));
+                        v.w += __uint_as_float(__float_as_uint(q[k].w) ^ (odd.w & fm[k]));
                     }
             }
             s_part[j][u] = v;
@@ -350,7 +372,12 @@ __global__ void __launch_bounds__(256) k_pp_reduce(int D, int ld, int stride, in
         const int s0 = tbase[t], s1 = over ? s0 : tbase[t + 1];
         for (int u = lane; u < width; u += 32) {
             T v = T(0);
-            for (int s = s0; s < s1; ++s) v += part[(int64_t)tpair[s] * stride + u];
+            const bool odd = coef_degree(u) & 1;
+            for (int s = s0; s < s1; ++s) {
+                const int r = tpair[s];
+                const T x = part[(int64_t)(r < 0 ? ~r : r) * stride + u];
+                v += r < 0 && odd ? -x : x;  // mirrored row: odd degrees negated
+            }
             L[(int64_t)(g0 + t) * ld + u] = v;
         }
     }
@@ -616,6 +643,9 @@ cudaError_t launch_m2l_pairs_worklist(int64_t n, int D, Workspace& ws, cudaStrea
     if (D < 2) return cudaSuccess;
     PpArgs a;
     a.D = D;
+    // only the BF16x3 tensor-core product reads mirrored pairs (its A rows
+    // from the mirrored multipole pieces)
+    a.mirror = ws.tc_bf16 && ws.pp_mirror ? 1 : 0;
     a.linfo = ws.linfo;
     a.code = ws.code;
     a.cid = ws.cid;

@@ -20,9 +20,17 @@ namespace pt {
 constexpr int kPairRows = 128;   // pairs per work item (one tensor-core product)
 
 struct M2lPair {
-    int32_t src;   // global compact id of the source cell
+    int32_t src;   // global compact id of the source cell (| kPairMirror: a pair of -op)
     int32_t slot;  // the target's slot (its pairs in increasing offset order)
 };
+// Mirrored work lists (BF16x3 tensor-core schedule): the pairs of offset -o
+// (operator index 342 - op) join the runs of o (op < 171).  Such a pair has
+// kPairMirror set in its src, its A row is the mirrored multipole pieces,
+// and its slot's entry in tpair is ~(pair index) (negative); the per-target
+// sums negate the odd-degree columns of those rows, since T_{-o} =
+// (-1)^(j + l) T_o entry by entry (Eq. FMM_local with Th_n^m(-o) =
+// (-1)^n Th_n^m(o)).
+constexpr int32_t kPairMirror = 1 << 30;
 struct M2lPairItem {
     int32_t op, begin, rows, pad;  // offset index, first pair, pairs (<= kPairRows)
 };

@@ -432,7 +432,7 @@ struct TcArgs {
     float* L;
     float* Mout;           // M2M output (= M, other level)
     float* part;           // M2M: [splits-1][cells][ld]; M2L: [item][128][ld] slabs
-    const uint16_t* Mp;    // BF16x3 M2L: M already split, [cell][3 pieces][ld] bf16
+    const uint16_t* Mp;    // BF16x3 M2L: M already split, [cell][kPieceRows][ld] bf16 (store_pieces)
     int64_t part_stride;   // cells_max * ld
     const unsigned char* ops;  // [359][kchunks][pieces][Npad rows] swizzled
     int* err;
@@ -914,10 +914,18 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                     const int st = gg % NS, use = gg / NS;
                     const int kc = it % a.kchunks;
                     if (MODE == MODE_PAIR && it == 0) {
+                        // first piece row of each A row: the source's pieces,
+                        // or its mirrored pieces for a pair of -op
                         const M2lPair* pr = a.n_pm > 0 ? a.pm[w.tile].pairs : a.pairs;
 #pragma unroll
-                        for (int j = 0; j < NJ; ++j)
-                            pg[j] = r0 + RS * j < w.rows ? pr[w.pbegin + r0 + RS * j].src : -1;
+                        for (int j = 0; j < NJ; ++j) {
+                            pg[j] = -1;
+                            if (r0 + RS * j < w.rows) {
+                                const int sv = pr[w.pbegin + r0 + RS * j].src;
+                                pg[j] = (sv & (kPairMirror - 1)) * kPieceRows +
+                                        ((sv & kPairMirror) ? 3 : 0);
+                            }
+                        }
                     } else if (MODE == MODE_M2L && kc == 0) {
                         const int opi = a.tiles[w.tile].terms[w.begin + it / a.kchunks];
                         const int ox = opi / 49 - 3, oy = (opi / 7) % 7 - 3, oz = opi % 7 - 3;
@@ -929,7 +937,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
                                 tc_admits(ox, oy, oz, tix[j] & 1, tiy[j] & 1, tiz[j] & 1) &&
                                 sx >= 0 && sy >= 0 && sz >= 0 && sx < lim && sy < lim && sz < lim)
                                 gs = a.cid[a.off[l] + morton3(sx, sy, sz)];
-                            pg[j] = gs;
+                            pg[j] = gs >= 0 ? gs * kPieceRows : -1;
                         }
                     }
                     int okw = 1;
@@ -950,7 +958,7 @@ __global__ void __launch_bounds__((TcLayout<MODE, BF16>::kThreads), 1)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             const uint16_t* src =
-                                gs >= 0 ? Mp + ((int64_t)gs * 3 + q) * a.ld + kc * 32 + c * 8 : Mp;
+                                gs >= 0 ? Mp + ((int64_t)gs + q) * a.ld + kc * 32 + c * 8 : Mp;
                             cp_async16ca(sA + q * a_bytes + off, src, gs >= 0 ? 16u : 0u);
                         }
                     }
@@ -1823,8 +1831,9 @@ cudaError_t launch_m2m_tc(int64_t n, int D, int l, Workspace& ws, cudaStream_t s
 
 // M of the cells of levels lfirst..llast as bf16 hi/mid/lo pieces
 // (split_bf16x3, the split the M2L producers would otherwise repeat for
-// every target that gathers the cell): Mp[(cell * 3 + q) * ld + k].  The
-// other levels' pieces are stored by the kernels that compute their M.
+// every target that gathers the cell), with the mirrored copies that the
+// pairs of -o read: Mp[(cell * kPieceRows + q) * ld + k].  The other levels'
+// pieces are stored by the kernels that compute their M.
 __global__ void k_split_m(int lfirst, int llast, int ld, const LevelInfo* linfo, const float* M,
                           uint16_t* Mp) {
     pdl_wait();

@@ -15,7 +15,8 @@ Definitions counted:
     cells and across octants below; a tile's products are the offsets with at
     least one admitted target row whose source cell holds ions;
   * pair-packed products: per offset, its pairs over every level, cut into
-    runs of 128.
+    runs of 128; with mirroring (the BF16x3 default), per pair of offsets
+    {o, -o}, their pairs together.
 """
 import numpy as np
 import pytest
@@ -87,6 +88,13 @@ def expected_counts(pos, D):
     out["leaves"] = len(cnt)
     out["pair_offsets"] = int((per_offset > 0).sum())
     out["pair_products"] = int(((per_offset + ROWS - 1) // ROWS).sum())
+    # offsets o and -o as one (T_{-o} = (-1)^(j+l) T_o): each unordered pair once
+    index = {o: k for k, o in enumerate(offs)}
+    merged = np.array([per_offset[k] + per_offset[index[(-o[0], -o[1], -o[2])]]
+                       for k, o in enumerate(offs) if o < (0, 0, 0)])
+    assert len(merged) == len(offs) // 2
+    out["pair_offsets_mirrored"] = int((merged > 0).sum())
+    out["pair_products_mirrored"] = int(((merged + ROWS - 1) // ROWS).sum())
     return out
 
 
@@ -104,13 +112,25 @@ def test_interaction_and_work_list_counts(crystal, D):
     plan.forces(pd, torch.tensor(q, dtype=torch.float64, device=DEV), want_phi=False)
     st, tc = plan.stats(), plan.tc_stats()
     plan.set_m2l_schedule("pairs")
-    plan.forces(pd, torch.tensor(q, dtype=torch.float64, device=DEV), want_phi=False)
+    qd = torch.tensor(q, dtype=torch.float64, device=DEV)
+    e_mirrored = plan.forces(pd, qd, want_phi=False)[0].cpu().numpy()
+    tm = plan.tc_stats()
+    plan.set_m2l_mirror(False)
+    e_plain = plan.forces(pd, qd, want_phi=False)[0].cpu().numpy()
     tp = plan.tc_stats()
     plan.close()
     ex = expected_counts(pos, D)
     # pair-packed work list: offsets with pairs, 128-row runs per offset, every pair once
     assert tp == {"tiles": ex["pair_offsets"], "products": ex["pair_products"],
                   "items": ex["pair_products"], "rows": ex["m2l_pairs"]}
+    # mirrored: the runs of each offset pair {o, -o}, every pair once
+    assert tm == {"tiles": ex["pair_offsets_mirrored"], "products": ex["pair_products_mirrored"],
+                  "items": ex["pair_products_mirrored"], "rows": ex["m2l_pairs"]}
+    # both negations of a mirrored pair are exact, so the field is that of the
+    # plain work list (the same products, up to the sign of each term)
+    assert np.all(np.isfinite(e_mirrored))
+    diff = np.sqrt(((e_mirrored - e_plain) ** 2).sum() / (e_plain ** 2).sum())
+    assert diff <= 1e-7, diff
     assert (st["n"], st["depth"], st["leaves"], st["cells"]) == (n, D, ex["leaves"], ex["cells"])
     assert st["m2l_pairs"] == ex["m2l_pairs"]
     assert st["p2p_pairs"] == ex["p2p_pairs"]
