@@ -365,6 +365,21 @@ def sweep_reference(pt, torch, w, n_sample=512):
     return Eo, idx, f"FP64 oracle direct sum at {n_sample} sampled ions"
 
 
+def m2l_peak(precision, pk, pk_src):
+    """Roof of the M2L kernel for a precision: (peak TFLOP/s of FP32-accurate
+    (or FP64) products, bound, note)."""
+    if precision == "tf32x3":
+        return (pk["bf16_tflops"] * TF32_OVER_BF16 / 3.0, "tensor",
+                f"TF32 rate / 3 (3 products per FP32-accurate product), from {pk_src} bf16 x "
+                f"nominal ratio")
+    if precision == "bf16x3":
+        return (pk["bf16_tflops"] / 6.0, "tensor",
+                f"{pk_src} bf16 rate / 6 (6 products per FP32-accurate product)")
+    if precision == "fp32":
+        return FP32_ALU_TFLOPS, "alu", "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
+    return FP64_TFLOPS, "alu", "nominal dense FP64"
+
+
 def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=1, schedule=""):
     """Single force evaluations (config-3 sweep point): mean CUDA-event time
     of `steps` evaluations (L2 flushed before each) and the relative RMS force
@@ -396,6 +411,34 @@ def force_eval_point(pt, torch, w, p, precision, steps, flush, ref=None, warmup=
     out = {"ms": float(np.mean(ms)), "evals_per_s": 1e3 / float(np.mean(ms)),
            "ion_evals_per_s": n * 1e3 / float(np.mean(ms)), "depth": plan.last_depth}
     out["m2l_schedule"] = plan.m2l_schedule
+    # the M2L kernel alone in one more, profiled evaluation: its rate in
+    # 2 P^2 flop per (target, source) translation against its roof
+    try:
+        plan.profile(True)
+        flush()
+        plan.forces(pd, qd, E=E, want_phi=False)
+        torch.cuda.synchronize()
+        kms = plan.kernel_times()["m2l_kernel"]
+        pairs = plan.stats()["m2l_pairs"]
+        if kms > 0 and pairs > 0:
+            pk, pk_src = peaks()
+            peak, bound, _ = m2l_peak(precision, pk, pk_src)
+            if plan.m2l_schedule == "rotation":
+                # rotate to the z axis, translate along z, rotate back:
+                # 2 sum_n (2n+1)^2 + sum_m (p+1-m)^2 (twice for m > 0) multiply-adds
+                macs = (2 * sum((2 * k + 1) ** 2 for k in range(p + 1)) +
+                        sum((p + 1 - m) ** 2 * (1 if m == 0 else 2) for m in range(p + 1)))
+                work = "2 x rotation multiply-adds per translation"
+            else:
+                macs = (p + 1) ** 4
+                work = "2 P^2 per translation"
+            rate = 2.0 * macs * pairs / (kms * 1e-3) / 1e12
+            out["m2l_kernel"] = {"ms": kms, "tflops": rate, "peak": peak, "frac": rate / peak,
+                                 "bound": bound, "m2l_pairs": pairs, "work": work}
+    except pt.PenningError:
+        pass
+    finally:
+        plan.profile(False)
     if ref is not None:
         Er, idx, _ = ref
         e = E.cpu().numpy().T
@@ -668,20 +711,8 @@ def main():
             else "M2L kernels (k_m2l_simt, all levels)"
         roof["kernel_ms"] = kern["m2l_kernel"]
         roof["phase_achieved"] = m2l_flops / (ph["m2l"] * 1e-3) / 1e12
-        if args.precision == "tf32x3":
-            peak = pk["bf16_tflops"] * TF32_OVER_BF16 / 3.0
-            roof.update(bound="tensor", peak_note=f"TF32 rate / 3 (3 products per FP32-accurate "
-                                                  f"product), from {pk_src} bf16 x nominal ratio")
-        elif args.precision == "bf16x3":
-            peak = pk["bf16_tflops"] / 6.0
-            roof.update(bound="tensor", peak_note=f"{pk_src} bf16 rate / 6 (6 products per "
-                                                  f"FP32-accurate product)")
-        elif args.precision == "fp32":
-            peak = FP32_ALU_TFLOPS
-            roof.update(bound="alu", peak_note="152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz")
-        else:
-            peak = FP64_TFLOPS
-            roof.update(bound="alu", peak_note="nominal dense FP64")
+        peak, bound, note = m2l_peak(args.precision, pk, pk_src)
+        roof.update(bound=bound, peak_note=note)
         roof.update(achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                     work=f"2 P^2 x {stats['m2l_pairs']} M2L translations per launch",
                     phase_frac=roof["phase_achieved"] / peak,

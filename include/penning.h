@@ -296,7 +296,7 @@ int pt_sync(fmm_plan plan, void* stream);
 int fmm_plan_profile(fmm_plan plan, int enable);
 int fmm_plan_phase_times(fmm_plan plan, double* ms);
 /* fmm_plan_kernel_times: device milliseconds, in the last executed profiled
- *   step, of the M2L kernel alone (host ms[0]: the tensor-core M2L launch,
+ *   step or force evaluation (fmm_forces), of the M2L kernel alone (host ms[0]: the tensor-core M2L launch,
  *   or the CUDA-core M2L launches of all levels) and of the near-field (P2P)
  *   kernel (ms[1]), each between events recorded right before and after the
  *   launch on its own stream.  Errors: PT_ERR_ARG (profiling off). */

@@ -353,7 +353,7 @@ class Plan:
 
     def kernel_times(self) -> dict:
         """Device ms of the M2L kernel and the P2P kernel alone in the last
-        profiled step."""
+        profiled step or force evaluation."""
         out = (ctypes.c_double * 2)()
         _check(load(False).fmm_plan_kernel_times(self._h, out), "fmm_plan_kernel_times")
         return {"m2l_kernel": out[0], "p2p_kernel": out[1]}

@@ -503,10 +503,13 @@ int forces_impl(fmm_plan_s* pl, int64_t n, const double* x, const double* y, con
                 const double* q, double* E, double* phi, cudaStream_t s, int D) {
     int r = ensure_pairs(pl, n, x, y, z, q, D, s);
     if (r != PT_OK) return r;
+    // with profiling on, the M2L and near-field kernels are timed as in a step
+    for (int k = 0; k < 4; ++k) pl->ws.kev[k] = pl->profile ? pl->k_ev[k] : nullptr;
     cudaError_t e = launch_bbox(x, y, z, n, pl->ws, s);
     if (e == cudaSuccess) e = launch_tree(n, x, y, z, q, D, pl->ws, s);
     if (e == cudaSuccess)
         e = launch_fmm(n, D, pl->phases, pl->ws, is_tc(pl->precision), E, phi, s);
+    for (int k = 0; k < 4; ++k) pl->ws.kev[k] = nullptr;
     pl->last_depth = D;
     pl->last_n = n;
     return status_from(e);
@@ -520,7 +523,7 @@ cudaError_t enqueue_step(fmm_plan_s* pl, const pt_state& st, const PushParams& p
     const int64_t n = st.n;
     for (int k = 0; k < 4; ++k) ws.kev[k] = pl->profile ? pl->k_ev[k] : nullptr;
     auto mark = [&](int k) -> cudaError_t {
-        return pl->profile ? cudaEventRecordWithFlags(pl->ph_ev[k], s, cudaEventRecordExternal)
+        return pl->profile ? record_timing(pl->ph_ev[k], s)
                            : cudaSuccess;
     };
     cudaError_t e = mark(0);
@@ -1098,7 +1101,10 @@ int fmm_plan_kernel_times(fmm_plan plan, double* ms) {
     for (int k = 0; k < 2; ++k) {
         float v = 0.f;
         cudaError_t e = cudaEventElapsedTime(&v, plan->k_ev[2 * k], plan->k_ev[2 * k + 1]);
-        if (e != cudaSuccess) return status_from(e);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();  // an unrecorded event: not a fault of later launches
+            return status_from(e);
+        }
         ms[k] = v;
     }
     return PT_OK;
@@ -1109,7 +1115,10 @@ int fmm_plan_phase_times(fmm_plan plan, double* ms) {
     for (int k = 0; k < fmm_plan_s::kPhases; ++k) {
         float v = 0.f;
         cudaError_t e = cudaEventElapsedTime(&v, plan->ph_ev[k], plan->ph_ev[k + 1]);
-        if (e != cudaSuccess) return status_from(e);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();  // an unrecorded event: not a fault of later launches
+            return status_from(e);
+        }
         ms[k] = v;
     }
     return PT_OK;

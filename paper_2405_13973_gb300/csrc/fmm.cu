@@ -1211,14 +1211,14 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         cudaError_t r;
         if (fork && after_event && (r = cudaStreamWaitEvent(snf, ws.ev_p2m, 0)) != cudaSuccess)
             return r;
-        if (ws.kev[2] && (r = cudaEventRecordWithFlags(ws.kev[2], snf, cudaEventRecordExternal)) !=
+        if (ws.kev[2] && (r = record_timing(ws.kev[2], snf)) !=
                              cudaSuccess)
             return r;
         k_p2p<T><<<leaf_grid, kNfThreads, 0, snf>>>(D, ws.linfo,
                                                    (const typename Ion<T>::rec*)ws.sorted, ws.code,
                                                    ws.cid + dl.off[D], ws.cstart, ws.ccount, near);
         if ((r = cudaGetLastError()) != cudaSuccess) return r;
-        if (ws.kev[3] && (r = cudaEventRecordWithFlags(ws.kev[3], snf, cudaEventRecordExternal)) !=
+        if (ws.kev[3] && (r = record_timing(ws.kev[3], snf)) !=
                              cudaSuccess)
             return r;
         if (fork && (r = cudaEventRecord(ws.ev_near, snf)) != cudaSuccess) return r;
@@ -1249,7 +1249,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                                                        dl.off[l + 1], (const T*)ws.T_m2m, M);
         }
     }
-    if (ev && (e = cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal)) != cudaSuccess)
+    if (ev && (e = record_timing(ev[0], s)) != cudaSuccess)
         return e;
     if (far && use_tc) {
         if (fork && (e = cudaStreamWaitEvent(s, ws.ev_items, 0)) != cudaSuccess) return e;
@@ -1266,7 +1266,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
         // the leaves (their L2P evaluates their own expansion)
         if ((e = launch_m2l_pairs_simt(n, D, ws, direct ? 2 : D, s)) != cudaSuccess) return e;
     } else if (far) {
-        if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+        if (ws.kev[0] && (e = record_timing(ws.kev[0], s)) !=
                              cudaSuccess)
             return e;
         for (int l = 2; l <= D; ++l) {
@@ -1277,11 +1277,11 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                                                l >= 3 ? dl.off[l - 1] : 0, M, L,
                                                (const T*)ws.T_m2l, (const T*)ws.T_l2l);
         }
-        if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+        if (ws.kev[1] && (e = record_timing(ws.kev[1], s)) !=
                              cudaSuccess)
             return e;
     }
-    if (ev && (e = cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal)) != cudaSuccess)
+    if (ev && (e = record_timing(ev[1], s)) != cudaSuccess)
         return e;
     if (fork && (e = cudaStreamWaitEvent(s, ws.ev_near, 0)) != cudaSuccess) return e;
     if (direct)
@@ -1300,7 +1300,7 @@ static cudaError_t run_fmm(int64_t n, int D, int phases, Workspace& ws, bool use
                        E, phi);
     if (e != cudaSuccess) return e;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ev && (e = cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal)) != cudaSuccess)
+    if (ev && (e = record_timing(ev[2], s)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }

@@ -8,6 +8,17 @@
 
 namespace pt {
 
+// A timing event on s: an external event node while s is being captured
+// into a graph (so that the event is recorded when the graph runs), a plain
+// record otherwise (the external flag is refused outside a capture).
+inline cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
 // Programmatic dependent launch: a kernel launched by launch_pdl may be
 // scheduled while its predecessor in the stream finishes (its blocks become
 // resident, its set-up runs); it calls pdl_wait() before it touches memory

@@ -737,7 +737,7 @@ static cudaError_t simt_pairs(int64_t n, int D, Workspace& ws, int l2l_last, cud
     const int P = ws.P;
     PairList L = pair_list(ws);
     cudaError_t e;
-    if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+    if (ws.kev[0] && (e = record_timing(ws.kev[0], s)) !=
                          cudaSuccess)
         return e;
     if (ws.m2l_rot) {
@@ -750,7 +750,7 @@ static cudaError_t simt_pairs(int64_t n, int D, Workspace& ws, int l2l_last, cud
                                                  (T*)ws.pp_part);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+    if (ws.kev[1] && (e = record_timing(ws.kev[1], s)) !=
                          cudaSuccess)
         return e;
     if ((e = launch_m2l_pairs_reduce(n, D, ws, P, s)) != cudaSuccess) return e;

@@ -1951,11 +1951,11 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, int
                 cudaSuccess)
                 return e;
         }
-        if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+        if (ws.kev[0] && (e = record_timing(ws.kev[0], s)) !=
                              cudaSuccess)
             return e;
         if ((e = tc_launch(a, m2l_grid(ws), smem, s)) != cudaSuccess) return e;
-        if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+        if (ws.kev[1] && (e = record_timing(ws.kev[1], s)) !=
                              cudaSuccess)
             return e;
         if (after_m2l && (e = cudaEventRecord(after_m2l, s)) != cudaSuccess) return e;
@@ -1980,11 +1980,11 @@ cudaError_t launch_m2l_tc_run(int64_t n, int D, Workspace& ws, int l2l_last, int
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // persistent: one CTA per SM walks the work list
-    if (ws.kev[0] && (e = cudaEventRecordWithFlags(ws.kev[0], s, cudaEventRecordExternal)) !=
+    if (ws.kev[0] && (e = record_timing(ws.kev[0], s)) !=
                          cudaSuccess)
         return e;
     if ((e = tc_launch(a, m2l_grid(ws), smem, s)) != cudaSuccess) return e;
-    if (ws.kev[1] && (e = cudaEventRecordWithFlags(ws.kev[1], s, cudaEventRecordExternal)) !=
+    if (ws.kev[1] && (e = record_timing(ws.kev[1], s)) !=
                          cudaSuccess)
         return e;
     if (after_m2l && (e = cudaEventRecord(after_m2l, s)) != cudaSuccess) return e;

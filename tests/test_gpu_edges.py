@@ -88,3 +88,23 @@ def test_dense_core_in_a_dilute_halo(precision):
     err = rel(E.cpu().numpy().T, Eo)
     assert err <= TOL, err
     plan.close()
+
+
+def test_profiled_force_evaluation_times_its_kernels():
+    # fmm_plan_kernel_times after a profiled fmm_forces (not only after a
+    # step); the plan's next calls are unaffected
+    w = W.sphere_sweep(20000, seed=13)
+    pd, qd = dev_pos(w["pos"]), dev_vec(w["q"])
+    plan = pt.Plan(len(w["q"]), p=12, precision="bf16x3")
+    E0, _ = plan.forces(pd, qd, want_phi=False)
+    E0 = E0.clone()
+    plan.profile(True)
+    E1, _ = plan.forces(pd, qd, want_phi=False)
+    torch.cuda.synchronize()
+    kt = plan.kernel_times()
+    plan.profile(False)
+    assert kt["m2l_kernel"] > 0 and kt["p2p_kernel"] > 0
+    assert torch.equal(E0, E1)
+    E2, _ = plan.forces(pd, qd, want_phi=False)
+    assert torch.equal(E0, E2)
+    plan.close()
